@@ -1,0 +1,119 @@
+/*
+ * drag_expm.h — C ABI of libdragexpm.so, the GB300 (sm_103a) FP64 exponential
+ * drag update for a gas plus N pressureless dust species.
+ *
+ * What is computed (Sec. 2.2-2.3 of arXiv:2509.25347). Per cell, with
+ * eps_i = rho_d,i / rho_g (Eq. DragEqVar2) and alpha_i = 1 / t_s,i
+ * (Eq. DragEqVar3), the drag sub-system dU/dt = Omega U on the momenta
+ * U = [rho_g v_g, rho_d,i v_d,i] (Eqs. DragEq, DragEqBis, jacobian) is solved
+ * exactly over one step dt: U(t0 + dt) = exp(dt Omega) U(t0) (Eq. ExacSolEqu).
+ * The densities do not change during the drag step, so the library works on
+ * velocities: v_out = exp(dt Omega_v) v_in with Omega_v = Omega^T
+ * (= D^-1 Omega D, D = diag(rho)), applied to the x, y and z components.
+ * exp(dt Omega_v) is formed by Taylor scaling and squaring: Algorithm 2 picks
+ * the Taylor order m* = m_{k*} (Table B.1) and the squaring count s* from the
+ * 1-norm of A = dt Omega_v and the theta_m of Eq. B8 (u = 2^-53, K = 9); the
+ * order-m Taylor polynomial of 2^-s* A is evaluated and squared s* times
+ * (Eq. ExpEq1, Algorithm 6). Row sums of the propagator are kept equal to one
+ * after the Taylor step and after every squaring (momentum conservation).
+ *
+ * Array layout (all FP64, structure of arrays, cell index fastest):
+ *   rho_g [c]                      gas density, c = 0..ncells-1
+ *   rho_d [i*ncells + c]           dust density of species i+1, i = 0..N-1
+ *   t_s   [i*ncells + c]           stopping time of species i+1
+ *   v     [(d*(N+1) + f)*ncells + c]  velocity component d (0=x,1=y,2=z) of
+ *                                  fluid f (0 = gas, f = i >= 1 dust species i)
+ *
+ * Ownership: every pointer is caller-owned; the library never frees, keeps or
+ * reallocates caller memory. Pointers documented as DEVICE must be device
+ * (or managed) memory of the current CUDA device.
+ *
+ * Errors: functions return 0 on success or a negative DRAG_E* code for errors
+ * found on the host, before anything is launched. Kernels run asynchronously
+ * on `stream` (NULL = legacy default stream). Bad cell DATA is not a return
+ * code: such a cell gets NaN outputs and sets a sticky bit that
+ * drag_expm_get_status() reads. Valid data: rho_g > 0 finite, rho_d >= 0
+ * finite, t_s > 0 (t_s = +inf is a species with alpha = 0), dt >= 0 finite.
+ * A dust density below 1e-200 * rho_g is treated as 1e-200 * rho_g
+ * (its feedback on the other fluids is then below FP64 resolution).
+ */
+#ifndef DRAG_EXPM_H
+#define DRAG_EXPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DRAG_EXPM_VERSION 1
+
+/* Largest supported number of dust species (matrix size N+1 <= 32). */
+#define DRAG_EXPM_NMAX 31
+
+/* Host-detected error codes. */
+#define DRAG_OK 0
+#define DRAG_EINVAL_SIZE (-1)   /* ncells < 0, nspecies outside [1, DRAG_EXPM_NMAX], dt < 0 or not finite */
+#define DRAG_ENULL (-2)         /* a required pointer is NULL while ncells > 0 */
+#define DRAG_EALIGN (-3)        /* a pointer is not 8-byte aligned */
+#define DRAG_ECUDA (-4)         /* a CUDA runtime call or kernel launch failed */
+#define DRAG_EWORKSPACE (-5)    /* workspace missing or smaller than required */
+#define DRAG_EBLOCKS (-6)       /* bad block count in the batched entry point */
+
+/* Sticky device status bits (drag_expm_get_status). */
+#define DRAG_STATUS_BAD_CELL 0x1u      /* some cell had invalid data; its outputs are NaN */
+#define DRAG_STATUS_BAD_BLOCK 0x2u     /* a batched block descriptor was out of range; it was skipped */
+#define DRAG_STATUS_QUEUE_GUARD 0x4u   /* a persistent work loop hit its iteration guard */
+
+/*
+ * drag_expm_apply — forward drag update (Eq. ExacSolEqu) for ncells cells with
+ * the same nspecies N and time step dt.
+ *   ncells   : number of cells (0 is a no-op).
+ *   nspecies : N, 1 <= N <= DRAG_EXPM_NMAX.
+ *   rho_g, rho_d, t_s : DEVICE, layout above, read only.
+ *   dt       : time step, >= 0 (dt = 0 returns v_in unchanged).
+ *   v_in     : DEVICE, 3*(N+1)*ncells doubles, read only.
+ *   v_out    : DEVICE, 3*(N+1)*ncells doubles, written. v_out == v_in (in
+ *              place) is allowed; other overlaps are not.
+ *   stream   : CUDA stream for the launch.
+ * Returns DRAG_OK or a DRAG_E* code (nothing launched on error).
+ */
+int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d, const double *t_s,
+                    double dt, const double *v_in, double *v_out, cudaStream_t stream);
+
+/*
+ * drag_expm_select — the (k*, s*) that drag_expm_apply uses for each cell:
+ * Algorithm 2 with K = 9 on the 1-norm of A = dt Omega_v. The Taylor order is
+ * m* = m_{k*} of Table B.1 and the cell costs k* + s* matrix products
+ * (App. B, "Numerical cost").
+ *   k_out : DEVICE int8[ncells], s_out : DEVICE int16[ncells] (either may be NULL).
+ * Cells with invalid data get k = 0, s = -1 and set DRAG_STATUS_BAD_CELL.
+ */
+int drag_expm_select(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d, const double *t_s,
+                     double dt, int8_t *k_out, int16_t *s_out, cudaStream_t stream);
+
+/*
+ * drag_expm_get_status — copy the current device's sticky status bits
+ * (DRAG_STATUS_*) into *status_out and clear them. Synchronises `stream`.
+ */
+int drag_expm_get_status(cudaStream_t stream, uint32_t *status_out);
+
+/*
+ * drag_expm_theta — theta_{m_k} (Eq. B8, u = 2^-53) that the library uses
+ * for k = 1..9 (Table B.1 prints these to five digits). Host only.
+ */
+int drag_expm_theta(int32_t k, double *theta_out);
+
+/* drag_expm_strerror — static text for a DRAG_E* code. */
+const char *drag_expm_strerror(int code);
+
+/* drag_expm_version — DRAG_EXPM_VERSION of the loaded library. */
+int drag_expm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DRAG_EXPM_H */

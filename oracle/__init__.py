@@ -1,0 +1,145 @@
+"""CPU oracle for the exponential multi-fluid drag update (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package. The product
+path (``paper_2509_25347_gb300``) never imports it and shares no code with it.
+
+The arithmetic lives in ``drag_oracle.c`` (plain FP64 C, no FMA contraction),
+compiled by :func:`build` into ``liboracle_drag.so`` and called through ctypes.
+``truth.py`` holds a second, independent check in extended precision.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "drag_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle_drag.so")
+_lib = None
+
+K_MAX = 9
+NMAX = 64
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FMA contraction, portable flags)."""
+    out = _LIB_PATH if not openmp else os.path.join(_HERE, "liboracle_drag_omp.so")
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", "-o", out, _SRC, "-lm"]
+        if openmp:
+            cmd.insert(1, "-fopenmp")
+            cmd.insert(1, "-DORC_OPENMP")
+        subprocess.run(cmd, check=True)
+    return out
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = build()
+    lib = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.orc_theta_m.restype = ctypes.c_double
+    lib.orc_theta_m.argtypes = [ctypes.c_int, ctypes.c_double]
+    lib.orc_theta_table.restype = None
+    lib.orc_theta_table.argtypes = [dp]
+    lib.orc_select_alg2.restype = ctypes.c_int
+    lib.orc_select_alg2.argtypes = [ctypes.c_double, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
+    lib.orc_expm_dense.restype = ctypes.c_int
+    lib.orc_expm_dense.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
+    lib.orc_assemble.restype = None
+    lib.orc_assemble.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_double, ctypes.c_int, dp]
+    lib.orc_drag_apply.restype = ctypes.c_int
+    lib.orc_drag_apply.argtypes = [ctypes.c_int64, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp, dp, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int16),
+                                   ctypes.POINTER(ctypes.c_uint32)]
+    for name in ("orc_table_mk", "orc_table_qk", "orc_table_rk"):
+        getattr(lib, name).restype = ctypes.c_int
+        getattr(lib, name).argtypes = [ctypes.c_int]
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def theta_table() -> np.ndarray:
+    """theta_{m_k} for k = 0..9 (index 0 unused), Eq. B8 with u = 2^-53."""
+    out = np.zeros(K_MAX + 1)
+    _load().orc_theta_table(_dptr(out))
+    return out
+
+
+def theta_m(m: int, u: float = 2.0 ** -53) -> float:
+    """theta_m of Eq. B8 for any order m and unit round-off u."""
+    return _load().orc_theta_m(int(m), float(u))
+
+
+def table_b1(k: int) -> tuple[int, int, int]:
+    """(m_k, q_k, r_k) of Table B.1."""
+    lib = _load()
+    return lib.orc_table_mk(k), lib.orc_table_qk(k), lib.orc_table_rk(k)
+
+
+def select(norm: float) -> tuple[int, int, int]:
+    """Algorithm 2 (K = 9): returns (k*, m*, s*) for a given 1-norm."""
+    k, m, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _load().orc_select_alg2(float(norm), K_MAX, ctypes.byref(k), ctypes.byref(m), ctypes.byref(s))
+    return k.value, m.value, s.value
+
+
+def expm(A: np.ndarray, structured: bool = True) -> tuple[np.ndarray, int, int, int]:
+    """exp(A) by the oracle's Taylor scaling and squaring. Returns (P, k*, m*, s*)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    P = np.zeros_like(A)
+    k, m, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rc = _load().orc_expm_dense(n, _dptr(A), _dptr(P), int(structured), ctypes.byref(k), ctypes.byref(m),
+                                ctypes.byref(s))
+    if rc == -2:
+        raise ValueError("matrix too large for the oracle")
+    return P, k.value, m.value, s.value
+
+
+def assemble(rho_g: float, rho_d: np.ndarray, t_s: np.ndarray, dt: float, structured: bool = True) -> np.ndarray:
+    """A = dt * Omega_v for one cell (velocity form of Eq. jacobian)."""
+    rho_d = np.ascontiguousarray(rho_d, dtype=np.float64)
+    t_s = np.ascontiguousarray(t_s, dtype=np.float64)
+    N = rho_d.shape[0]
+    A = np.zeros((N + 1, N + 1))
+    _load().orc_assemble(N, float(rho_g), _dptr(rho_d), _dptr(t_s), float(dt), int(structured), _dptr(A))
+    return A
+
+
+def drag_apply(rho_g, rho_d, t_s, dt, v_in, structured: bool = True, return_ks: bool = False):
+    """Forward drag update over SoA arrays (layout of the CUDA library).
+
+    rho_g: (C,), rho_d: (N, C), t_s: (N, C), v_in: (3, N+1, C). Returns v_out of
+    the same shape as v_in (and, with return_ks, k*, s* per cell and the status word).
+    """
+    rho_g = np.ascontiguousarray(rho_g, dtype=np.float64)
+    rho_d = np.ascontiguousarray(rho_d, dtype=np.float64)
+    t_s = np.ascontiguousarray(t_s, dtype=np.float64)
+    v_in = np.ascontiguousarray(v_in, dtype=np.float64)
+    C = rho_g.shape[0]
+    N = rho_d.shape[0]
+    assert rho_d.shape == (N, C) and t_s.shape == (N, C) and v_in.shape == (3, N + 1, C)
+    v_out = np.empty_like(v_in)
+    k_out = np.zeros(C, dtype=np.int8)
+    s_out = np.zeros(C, dtype=np.int16)
+    st = ctypes.c_uint32(0)
+    rc = _load().orc_drag_apply(C, N, _dptr(rho_g), _dptr(rho_d), _dptr(t_s), float(dt), _dptr(v_in), _dptr(v_out),
+                                int(structured), k_out.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                s_out.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), ctypes.byref(st))
+    if rc != 0:
+        raise ValueError(f"oracle rejected sizes (rc={rc})")
+    if return_ks:
+        return v_out, k_out, s_out, st.value
+    return v_out

@@ -1,0 +1,371 @@
+/*
+ * CPU oracle for the exponential ("EXP") multi-fluid drag update.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library. The product path (the CUDA library
+ * and its Python binding) never calls it, links it or shares code with it.
+ *
+ * Plain, slow, FP64 C that follows the paper step by step:
+ *   Sec. 2.2, Eqs. DragEq..jacobian : the drag matrix Omega of gas + N dust species
+ *   Sec. 2.3, Eq. ExacSolEqu        : U(t) = exp(t Omega) U(t0)
+ *   App. B, Eqs. B1-B8              : backward-error bound, theta_m for u = 2^-53
+ *   App. B, Table B.1               : m_k, q_k, r_k for k = 1..9
+ *   App. B, Algorithm 2             : choice of (k*, m*, s*)
+ *   App. B, Eqs. Pat_Stk..Pat_Stk3, Algorithm 3 : Paterson-Stockmeyer evaluation
+ *   Sec. 2.3.2, Eq. ExpEq1/def_s, Algorithm 6   : scaling and squaring
+ *
+ * Velocity form. The drag step keeps densities fixed, so with U = D v and
+ * D = diag(rho_g, rho_d,1..N) the velocities obey dv/dt = Omega_v v with
+ * Omega_v = D^-1 Omega D = Omega^T (Eq. jacobian transposed):
+ *   (Omega_v)_00 = -sum_i eps_i alpha_i, (Omega_v)_0i = eps_i alpha_i,
+ *   (Omega_v)_i0 = alpha_i,              (Omega_v)_ii = -alpha_i.
+ * Every row of Omega_v sums to zero (momentum conservation, Eq. DragEq).
+ *
+ * "Structured" mode (the default) keeps that property exactly in floating
+ * point: the diagonal of A = dt Omega_v is assembled as minus the sum of its
+ * row's off-diagonals, and after the Taylor step and after every squaring the
+ * diagonal of P is reset to 1 - sum of the row's off-diagonals. "Raw" mode is
+ * the literal reading (diagonal accumulated as in Eq. jacobian, no reset); it
+ * is kept only to report how far the literal method drifts in stiff cells.
+ *
+ * Everything is plain IEEE double with no FMA contraction (built with
+ * -ffp-contract=off), so results are identical on x86-64 and aarch64.
+ * No long double is used anywhere.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_K 9          /* maximum number of products in the Taylor phase (all Table B.1 rows) */
+#define ORC_NMAX 64      /* largest matrix the oracle accepts (n = N + 1) */
+
+/* Table B.1: k, m_k, q_k, r_k (index 0 unused). m_k = q_k * r_k. */
+static const int orc_mk[ORC_K + 1] = {0, 2, 4, 6, 9, 12, 16, 20, 25, 30};
+static const int orc_qk[ORC_K + 1] = {0, 1, 2, 2, 3, 3, 4, 4, 5, 5};
+static const int orc_rk[ORC_K + 1] = {0, 2, 2, 3, 3, 4, 4, 5, 5, 6};
+
+/* ------------------------------------------------------------------------ */
+/* Eqs. B4-B8: theta_m                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Coefficients c_j of rho(x) = e^{-x} T_m(x) - 1 = sum_{j>=m+1} c_j x^j
+ * (Eq. B5): rho(x) = -(sum_i (-x)^i/i!) (sum_{l>=m+1} x^l/l!), so
+ * c_j = -sum_{l=m+1}^{j} (-1)^{j-l} / ((j-l)! l!).  Returns c_{m+1..m+L}. */
+static void orc_rho_coeffs(int m, int L, double *c)
+{
+    for (int t = 0; t < L; t++) {
+        int j = m + 1 + t;
+        double acc = 0.0;
+        for (int l = m + 1; l <= j; l++) {
+            double term = 1.0;
+            for (int a = 2; a <= j - l; a++) term /= a;   /* 1/(j-l)! */
+            for (int a = 2; a <= l; a++) term /= a;       /* 1/l! */
+            if ((j - l) & 1) term = -term;
+            acc += term;
+        }
+        c[t] = -acc;
+    }
+}
+
+/* f_m(theta) = sum_{j>=m+1} |c_j| theta^j (Eq. B6), truncated after L terms. */
+static double orc_fm(int m, int L, const double *c, double theta)
+{
+    double f = 0.0, p = pow(theta, (double)(m + 1));
+    for (int t = 0; t < L; t++) {
+        f += fabs(c[t]) * p;
+        p *= theta;
+    }
+    return f;
+}
+
+/* theta_m = max{theta : -log(1 - f_m(theta))/theta <= u} (Eq. B8), found by
+ * bisection; the bound is increasing in theta. */
+double orc_theta_m(int m, double u)
+{
+    enum { L = 80 };
+    double c[L];
+    orc_rho_coeffs(m, L, c);
+    double lo = 0.0, hi = 64.0;
+    for (int it = 0; it < 400; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double f = orc_fm(m, L, c, mid);
+        double bound = (f < 1.0) ? -log1p(-f) / mid : INFINITY;
+        if (bound <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+/* theta_{m_k}, k = 1..9, for u = 2^-53 (Table B.1, column theta_{m_k}). */
+void orc_theta_table(double *theta /* [ORC_K + 1], index 0 unused */)
+{
+    theta[0] = 0.0;
+    for (int k = 1; k <= ORC_K; k++) theta[k] = orc_theta_m(orc_mk[k], ldexp(1.0, -53));
+}
+
+static double g_theta[ORC_K + 1];
+static int g_theta_ready = 0;
+
+static const double *orc_thetas(void)
+{
+    if (!g_theta_ready) {
+        orc_theta_table(g_theta);
+        g_theta_ready = 1;
+    }
+    return g_theta;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 2: polynomial order and scale factor                           */
+/* ------------------------------------------------------------------------ */
+
+/* Readings (the listing is ambiguous in places):
+ *  - s^ = ceil(max(log2(|A|/theta_{m_K}), 0)) is taken as the smallest
+ *    integer s >= 0 with 2^-s |A| <= theta_{m_K} (no log/ceil rounding).
+ *  - s* starts at s^ (the listing writes s* = 0, which would leave large
+ *    norms unscaled; Algorithm 1 sets s* = s^ in that case).
+ *  - k^ is the k at which the search loop stopped (first k with
+ *    |A| <= theta_{m_k}), or K if there is none.
+ *  - The three reduction branches are taken only when v > 0; the listing's
+ *    max() gives v3 priority over v2 over v1.
+ *  - "m* = m_k*" means m* = m_{k*}.
+ * Returns 0, or -1 if |A| is not finite (the caller marks the cell invalid). */
+int orc_select_alg2(double normA, int K, int *kstar, int *mstar, int *sstar)
+{
+    const double *th = orc_thetas();
+    if (!isfinite(normA) || normA < 0.0) {
+        *kstar = K; *mstar = orc_mk[K]; *sstar = 0;
+        return -1;
+    }
+    int ms = orc_mk[K];
+    int ks = K;
+    int shat = 0;
+    while (ldexp(normA, -shat) > th[K]) shat++;
+    int ss = shat;
+    int cond = 0;
+    int khat = K;
+    for (int k = 1; k <= K && !cond; k++) {
+        double lim = th[k] < th[K] ? th[k] : th[K];
+        cond = normA <= lim;
+        if (cond) {
+            ms = orc_mk[k];
+            ks = k;
+            khat = k;
+        }
+    }
+    double cmp = ldexp(normA, -shat);
+    int v1 = (khat >= 7) && (cmp <= th[khat - 1]);
+    int v2 = ((khat >= 8) && (cmp <= 2.0 * th[khat - 2])) * 2;
+    int v3 = ((khat >= 9) && (cmp <= 4.0 * th[khat - 3])) * 3;
+    int v = v1;
+    if (v2 > v) v = v2;
+    if (v3 > v) v = v3;
+    if (v > 0) {
+        if (v == v1) {
+            ks = khat - 1; ms = orc_mk[ks];
+        } else if (v == v2) {
+            ks = khat - 2; ms = orc_mk[ks]; ss = (shat + 1 > 1) ? shat + 1 : 1;
+        } else {
+            ks = khat - 3; ms = orc_mk[ks]; ss = (shat + 2 > 2) ? shat + 2 : 2;
+        }
+    }
+    *kstar = ks; *mstar = ms; *sstar = ss;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense n x n helpers (row-major), plain loops, ascending index order       */
+/* ------------------------------------------------------------------------ */
+
+static void orc_matmul(int n, const double *A, const double *B, double *C)
+{
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            double acc = 0.0;
+            for (int k = 0; k < n; k++) acc += A[i * n + k] * B[k * n + j];
+            C[i * n + j] = acc;
+        }
+}
+
+/* 1-norm: maximum absolute column sum. */
+static double orc_norm1(int n, const double *A)
+{
+    double best = 0.0;
+    for (int j = 0; j < n; j++) {
+        double s = 0.0;
+        for (int i = 0; i < n; i++) s += fabs(A[i * n + j]);
+        if (s > best || isnan(s)) best = s;
+    }
+    return best;
+}
+
+/* Row-sum restoration: P_ii = 1 - sum_{j != i} P_ij. */
+static void orc_restore(int n, double *P)
+{
+    for (int i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int j = 0; j < n; j++)
+            if (j != i) s += P[i * n + j];
+        P[i * n + i] = 1.0 - s;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Taylor scaling and squaring (Algorithm 6 with Algorithm 2 and the         */
+/* Paterson-Stockmeyer evaluation of Eqs. Pat_Stk..Pat_Stk3 / Algorithm 3)   */
+/* ------------------------------------------------------------------------ */
+
+/* P = T_{m}(X) for X = 2^-s A, then s squarings.
+ * T_m(X) = I + sum_{k=0}^{r-1} Bbar_k (X^q)^k with
+ * Bbar_k = sum_{j=1}^{q} b_{qk+j} X^j, b_i = 1/i!  (Algorithm 3; m = q r),
+ * evaluated by Horner in X^q with the stored powers X, X^2, ..., X^q.
+ * With structured != 0 the diagonal is restored after the Taylor step and
+ * after every squaring. Returns 0, or -1 when |A| is not finite. */
+int orc_expm(int n, const double *A, double *P, int structured, int *k_out, int *m_out, int *s_out)
+{
+    int k, m, s;
+    int rc = orc_select_alg2(orc_norm1(n, A), ORC_K, &k, &m, &s);
+    if (k_out) *k_out = k;
+    if (m_out) *m_out = m;
+    if (s_out) *s_out = s;
+    if (rc != 0) {
+        for (int i = 0; i < n * n; i++) P[i] = NAN;
+        return -1;
+    }
+    const int q = orc_qk[k], r = orc_rk[k];
+    const size_t nn = (size_t)n * n;
+    double *pw = (double *)calloc((size_t)(q + 1) * nn, sizeof(double)); /* pw[j] = X^j */
+    double *F = (double *)calloc(nn, sizeof(double));
+    double *T = (double *)calloc(nn, sizeof(double));
+    double *Bb = (double *)calloc(nn, sizeof(double));
+    double b[64];
+    b[0] = 1.0;
+    for (int i = 1; i <= m; i++) b[i] = b[i - 1] / (double)i;
+
+    for (size_t e = 0; e < nn; e++) pw[nn + e] = ldexp(A[e], -s);       /* X = 2^-s A */
+    for (int j = 2; j <= q; j++) orc_matmul(n, pw + (size_t)(j - 1) * nn, pw + nn, pw + (size_t)j * nn);
+
+    /* Horner in X^q: F = Bbar_{r-1}; F = Bbar_k + F X^q for k = r-2..0 */
+    for (int kk = r - 1; kk >= 0; kk--) {
+        for (size_t e = 0; e < nn; e++) {
+            double acc = 0.0;
+            for (int j = 1; j <= q; j++) acc += b[q * kk + j] * pw[(size_t)j * nn + e];
+            Bb[e] = acc;
+        }
+        if (kk == r - 1) {
+            memcpy(F, Bb, nn * sizeof(double));
+        } else {
+            orc_matmul(n, F, pw + (size_t)q * nn, T);
+            for (size_t e = 0; e < nn; e++) F[e] = Bb[e] + T[e];
+        }
+    }
+    for (size_t e = 0; e < nn; e++) P[e] = F[e];
+    for (int i = 0; i < n; i++) P[i * n + i] += 1.0;                   /* + b_0 I */
+    if (structured) orc_restore(n, P);
+
+    for (int t = 0; t < s; t++) {                                       /* Eq. ExpEq1, n = 2^s */
+        orc_matmul(n, P, P, T);
+        memcpy(P, T, nn * sizeof(double));
+        if (structured) orc_restore(n, P);
+    }
+    free(pw); free(F); free(T); free(Bb);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Drag matrix (Eqs. DragEqVar2, DragEqVar3, jacobian) in velocity form      */
+/* ------------------------------------------------------------------------ */
+
+/* Cell input check: rho_g > 0, rho_d >= 0, t_s > 0 (t_s = +inf allowed:
+ * alpha = 0, a decoupled species), all finite except t_s = +inf. */
+static int orc_cell_valid(int N, double rho_g, const double *rho_d, const double *t_s, double dt)
+{
+    if (!(rho_g > 0.0) || !isfinite(rho_g) || !(dt >= 0.0) || !isfinite(dt)) return 0;
+    for (int i = 0; i < N; i++) {
+        if (!(rho_d[i] >= 0.0) || !isfinite(rho_d[i])) return 0;
+        if (!(t_s[i] > 0.0)) return 0;            /* also rejects NaN */
+    }
+    return 1;
+}
+
+/* A = dt * Omega_v, n = N + 1, row-major. */
+void orc_assemble(int N, double rho_g, const double *rho_d, const double *t_s, double dt, int structured, double *A)
+{
+    const int n = N + 1;
+    memset(A, 0, sizeof(double) * (size_t)n * n);
+    double sum_ea = 0.0;
+    for (int i = 1; i <= N; i++) {
+        double eps = rho_d[i - 1] / rho_g;        /* Eq. DragEqVar2 */
+        double alpha = 1.0 / t_s[i - 1];          /* Eq. DragEqVar3 */
+        A[0 * n + i] = (eps * alpha) * dt;
+        A[i * n + 0] = alpha * dt;
+        A[i * n + i] = -(alpha * dt);
+        sum_ea += eps * alpha;
+    }
+    if (structured) {
+        double s = 0.0;
+        for (int i = 1; i <= N; i++) s += A[0 * n + i];
+        A[0] = -s;
+    } else {
+        A[0] = -sum_ea * dt;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Public entry points                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Forward drag update for ncells cells, same SoA layout as the CUDA library:
+ *   rho_g[c], rho_d[i*C + c], t_s[i*C + c]  (i = 0..N-1),
+ *   v[(d*n + f)*C + c]  (d = x,y,z; f = 0 gas, f = i dust species i).
+ * Invalid cells get NaN outputs and set bit 0 of *status.
+ * k_out / s_out (optional) receive k* and s* per cell. */
+int orc_drag_apply(int64_t C, int N, const double *rho_g, const double *rho_d, const double *t_s, double dt,
+                   const double *v_in, double *v_out, int structured, int8_t *k_out, int16_t *s_out,
+                   uint32_t *status)
+{
+    if (C < 0 || N < 1 || N + 1 > ORC_NMAX) return -1;
+    const int n = N + 1;
+    double *A = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double *P = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double rd[ORC_NMAX], ts[ORC_NMAX], vin[ORC_NMAX];
+    uint32_t st = 0;
+    for (int64_t c = 0; c < C; c++) {
+        for (int i = 0; i < N; i++) {
+            rd[i] = rho_d[(int64_t)i * C + c];
+            ts[i] = t_s[(int64_t)i * C + c];
+        }
+        int k = 0, m = 0, s = 0;
+        int ok = orc_cell_valid(N, rho_g[c], rd, ts, dt);
+        if (ok) {
+            orc_assemble(N, rho_g[c], rd, ts, dt, structured, A);
+            ok = orc_expm(n, A, P, structured, &k, &m, &s) == 0;
+        }
+        if (k_out) k_out[c] = (int8_t)k;
+        if (s_out) s_out[c] = (int16_t)s;
+        for (int d = 0; d < 3; d++) {
+            for (int f = 0; f < n; f++) vin[f] = v_in[((int64_t)d * n + f) * C + c];
+            for (int i = 0; i < n; i++) {
+                double acc = 0.0;
+                for (int j = 0; j < n; j++) acc += P[i * n + j] * vin[j];
+                v_out[((int64_t)d * n + i) * C + c] = ok ? acc : NAN;
+            }
+        }
+        if (!ok) st |= 1u;
+    }
+    free(A); free(P);
+    if (status) *status |= st;
+    return 0;
+}
+
+/* exp(A) of one dense n x n matrix, for tests of the S&S machinery alone. */
+int orc_expm_dense(int n, const double *A, double *P, int structured, int *k, int *m, int *s)
+{
+    if (n < 1 || n > 2 * ORC_NMAX) return -2;
+    return orc_expm(n, A, P, structured, k, m, s);
+}
+
+int orc_table_mk(int k) { return (k >= 1 && k <= ORC_K) ? orc_mk[k] : -1; }
+int orc_table_qk(int k) { return (k >= 1 && k <= ORC_K) ? orc_qk[k] : -1; }
+int orc_table_rk(int k) { return (k >= 1 && k <= ORC_K) ? orc_rk[k] : -1; }

@@ -1,0 +1,120 @@
+"""Extended-precision truth for the drag update (test infrastructure only).
+
+An independent route to exp(dt Omega_v) v (Eq. ExacSolEqu in velocity form):
+the symmetric similarity S = D^(1/2) Omega_v D^(-1/2) (D = diag(rho)),
+S_00 = -sum eps_i alpha_i, S_0i = S_i0 = sqrt(eps_i) alpha_i, S_ii = -alpha_i,
+is built from the FP64 inputs in mpmath precision, diagonalised (mp.eigsy),
+exponentiated through its eigenvalues and mapped back,
+v_out = D^(-1/2) Q exp(dt Lambda) Q^T D^(1/2) v. The eigenvalues are those of
+the eigenvalue problem of Eq. eigen_problem (Sec. 3.1). It shares nothing with
+the FP64 Taylor scaling-and-squaring oracle in drag_oracle.c.
+
+Requires mpmath (present where sympy is installed; tests importorskip it).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _mp():
+    import mpmath
+    return mpmath
+
+
+def drag_truth_cell(rho_g, rho_d, t_s, dt, v, dps: int = 40) -> np.ndarray:
+    """exp(dt Omega_v) applied to v (shape (3, N+1)) for one cell, via eigsy."""
+    mp = _mp()
+    with mp.workdps(dps):
+        N = len(rho_d)
+        n = N + 1
+        rg = mp.mpf(float(rho_g))
+        eps = [mp.mpf(float(x)) / rg for x in rho_d]
+        al = [mp.mpf(0) if np.isinf(x) else 1 / mp.mpf(float(x)) for x in t_s]
+        dtm = mp.mpf(float(dt))
+        S = mp.zeros(n, n)
+        for i in range(1, n):
+            S[0, i] = S[i, 0] = mp.sqrt(eps[i - 1]) * al[i - 1] * dtm
+            S[i, i] = -al[i - 1] * dtm
+            S[0, 0] -= eps[i - 1] * al[i - 1] * dtm
+        lam, Q = mp.eigsy(S)
+        sig = [mp.mpf(1)] + [mp.sqrt(e) for e in eps]
+        out = np.zeros((3, n))
+        for d in range(3):
+            y = mp.matrix([sig[j] * mp.mpf(float(v[d][j])) for j in range(n)])
+            z = Q.T * y
+            z = mp.matrix([z[j] * mp.exp(lam[j]) for j in range(n)])
+            z = Q * z
+            for i in range(n):
+                out[d, i] = float(z[i] / sig[i])
+        return out
+
+
+def drag_truth(rho_g, rho_d, t_s, dt, v, dps: int = 40) -> np.ndarray:
+    """Truth over SoA arrays: rho_g (C,), rho_d (N, C), t_s (N, C), v (3, N+1, C)."""
+    C = len(rho_g)
+    out = np.zeros_like(np.asarray(v, dtype=np.float64))
+    for c in range(C):
+        out[:, :, c] = drag_truth_cell(rho_g[c], rho_d[:, c], t_s[:, c], dt, v[:, :, c], dps)
+    return out
+
+
+def propagator_truth(rho_g, rho_d, t_s, dt, dps: int = 40) -> np.ndarray:
+    """P = exp(dt Omega_v) for one cell (rows: output fluid, columns: input fluid)."""
+    N = len(rho_d)
+    n = N + 1
+    P = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros((3, n))
+        e[:, j] = 1.0
+        P[:, j] = drag_truth_cell(rho_g, rho_d, t_s, dt, e, dps)[0]
+    return P
+
+
+def expm_taylor_mp(A, terms: int = 80, dps: int = 60) -> np.ndarray:
+    """exp(A) of a small dense matrix by an un-scaled Taylor series in mpmath.
+
+    Only for tiny inputs with modest norm (brute force check of the S&S code).
+    """
+    mp = _mp()
+    with mp.workdps(dps):
+        n = len(A)
+        M = mp.matrix([[mp.mpf(float(A[i][j])) for j in range(n)] for i in range(n)])
+        term = mp.eye(n)
+        acc = mp.eye(n)
+        for k in range(1, terms + 1):
+            term = term * M / k
+            acc += term
+        return np.array([[float(acc[i, j]) for j in range(n)] for i in range(n)])
+
+
+def theta_closed_form(m: int, u=None, dps: int = 50) -> float:
+    """theta_m of Eq. B8 by an independent route, in mpmath.
+
+    The coefficients of rho(x) = e^-x T_m(x) - 1 have the closed form
+    |c_j| = C(j-1, m) / j!  (j >= m+1): from c_j = -sum_{l=m+1}^{j}
+    (-1)^{j-l} / ((j-l)! l!) = (-1)^(j+m) C(j-1, m) / j!, using
+    sum_{l=0}^{m} (-1)^l C(j, l) = (-1)^m C(j-1, m). The root of
+    -log(1 - f_m(theta))/theta = u is then found with mpmath's solver.
+    """
+    mp = _mp()
+    with mp.workdps(dps):
+        u = mp.mpf(2) ** -53 if u is None else mp.mpf(u)
+
+        def f(th):
+            s = mp.mpf(0)
+            for j in range(m + 1, m + 140):
+                s += mp.binomial(j - 1, m) / mp.factorial(j) * th ** j
+            return s
+
+        def g(th):
+            ft = f(th)
+            return mp.inf if ft >= 1 else -mp.log(1 - ft) / th - u
+
+        lo, hi = mp.mpf("1e-12"), mp.mpf(10)
+        for _ in range(130):
+            mid = (lo + hi) / 2
+            if g(mid) <= 0:
+                lo = mid
+            else:
+                hi = mid
+        return float(lo)
