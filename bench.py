@@ -1,0 +1,317 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the FP64 EXP drag update on GB300.
+
+One step = one forward drag update (drag_expm_apply) over the whole
+workload: the N=16 MRN-like workload of 128^3 = 2,097,152 cells by default
+(17x17 drag matrices, dt/t_s in [1e-4, 1e8]). Inputs are synthetic and seeded
+(paper_2509_25347_gb300.workloads) and larger than L2, so no flush is needed.
+
+Prints one JSON line (rank 0). Launch N>1 with torchrun; each rank then runs
+its own full copy of the workload (independent cells, weak scaling, no
+collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the CPU oracle, timed on host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2509_25347_gb300 import workloads as W  # noqa: E402
+
+METRIC = "FP64 cell drag updates/sec at N=16 (fwd, fwd+adjoint) and % of FP64/HBM roofline"
+UNIT = "cell-updates/s"
+# FP64 pipe of one GB300: 152 SMs x 4 sub-partitions x 0.5 DFMA/clk x 2 flop = 608 flop/clk
+# (measured: one warp-wide DFMA per 64 cycles per sub-partition), at the 2070 MHz maximum SM clock.
+FP64_FLOP_PER_CLK = 152 * 4 * 0.5 * 2
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="mrn_n16_128cube", choices=[k for k in W.WORKLOADS if "batched" not in k])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ helpers ---
+
+def algorithmic_counts(N, k, s):
+    """Per-cell algorithmic FLOPs (2 n^3 (k* + s*) + 6 n^2: k* + s* dense n x n
+    products, App. B "Numerical cost", plus three mat-vecs) and bytes
+    (8 (1 + 2N) inputs + 24 n in + 24 n out)."""
+    n = N + 1
+    flops = 2.0 * n ** 3 * (k.astype(np.float64) + s.astype(np.float64)) + 6.0 * n * n
+    bytes_per_cell = 8 * (1 + 2 * N) + 48 * n
+    return flops, bytes_per_cell
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ["uuid", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8 or (self.uuid and f[0] != self.uuid):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(pw) if pw else None}
+
+
+def _oracle_chunk(args):
+    import oracle
+    rg, rd, ts, dt, v = args
+    oracle.drag_apply(rg, rd, ts, dt, v)
+    return rg.shape[0]
+
+
+def cpu_oracle_rate(cells, seconds, steps=1):
+    """Oracle cell-updates/s on the host cores (spawned worker processes, one
+    chunk of contiguous cells each). Returns (rate, cores, sample_cells, wall_per_step)."""
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    probe = cells.subset(np.arange(min(64, cells.ncells)))
+    t0 = time.perf_counter()
+    oracle.drag_apply(probe.rho_g, probe.rho_d, probe.t_s, probe.dt, probe.v)
+    per_cell = (time.perf_counter() - t0) / probe.ncells
+    sample = int(min(cells.ncells, max(cores * 16, seconds * cores / max(per_cell, 1e-9))))
+    sub = cells.subset(np.arange(sample))
+    bounds = np.linspace(0, sample, cores + 1).astype(int)
+    chunks = [(sub.rho_g[a:b].copy(), sub.rho_d[:, a:b].copy(), sub.t_s[:, a:b].copy(), sub.dt,
+               sub.v[:, :, a:b].copy()) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+    ctx = mp.get_context("spawn")
+    walls = []
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_chunk, [(c[0][:1], c[1][:, :1], c[2][:, :1], c[3], c[4][:, :, :1]) for c in chunks])
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            done = sum(pool.map(_oracle_chunk, chunks))
+            walls.append(time.perf_counter() - t0)
+    wall = float(np.mean(walls))
+    return done / wall, cores, sample, wall
+
+
+# ---------------------------------------------------------------- reference ---
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    cells = W.workload(args.workload)
+    _, C, N, _ = W.WORKLOADS[args.workload]
+    rate, cores, sample, wall = cpu_oracle_rate(cells, seconds=max(2.0, 60.0 / max(1, args.steps + args.warmup)),
+                                                steps=args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "ncells": C, "nspecies": N, "step_sample_cells": sample},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"first {sample} cells of {args.workload} per step"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- ours ---
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2509_25347_gb300 as dx
+    from paper_2509_25347_gb300 import build as dxbuild
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        dxbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    dx.load_library()
+
+    _, C, N, _ = W.WORKLOADS[args.workload]
+    cells = W.workload(args.workload)
+    n = N + 1
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rg, rd, ts, v = dev(cells.rho_g), dev(cells.rho_d), dev(cells.t_s), dev(cells.v)
+    vout = torch.empty_like(v)
+    stream = torch.cuda.current_stream()
+
+    k, s = dx.select(rg, rd, ts, cells.dt)
+    k, s = k.cpu().numpy(), s.cpu().numpy()
+    flops_cell, bytes_cell = algorithmic_counts(N, k, s)
+    flops_launch = float(flops_cell.sum())
+
+    for _ in range(args.warmup):
+        dx.apply(rg, rd, ts, cells.dt, v, vout)
+    torch.cuda.synchronize()
+    dx.get_status()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for i in range(args.steps):
+        dx.apply(rg, rd, ts, cells.dt, v, vout)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    per_launch = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    status = dx.get_status()
+    if status:
+        raise RuntimeError(f"device status {status:#x} after timed region")
+
+    # e2e: pinned host buffers, H2D of the step's inputs, the apply, D2H of v_out
+    h = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hrg, hrd, hts, hv = h(cells.rho_g), h(cells.rho_d), h(cells.t_s), h(cells.v)
+    hout = torch.empty_like(hv).pin_memory()
+    h2d = sum(x.numel() * 8 for x in (hrg, hrd, hts, hv))
+    d2h = hout.numel() * 8
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        rg.copy_(hrg, non_blocking=True); rd.copy_(hrd, non_blocking=True)
+        ts.copy_(hts, non_blocking=True); v.copy_(hv, non_blocking=True)
+        dx.apply(rg, rd, ts, cells.dt, v, vout)
+        hout.copy_(vout, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+
+    t_ms = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t_ms, op=torch.distributed.ReduceOp.MAX)
+    total_ms, e2e_ms = float(t_ms[0]), float(t_ms[1])
+    ms_per_step = total_ms / args.steps
+    value = C * world / (ms_per_step * 1e-3)
+    e2e_value = C * world / (e2e_ms * 1e-3)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    mean_launch_s = float(np.mean(per_launch)) * 1e-3
+    achieved_tf = flops_launch / mean_launch_s / 1e12
+    peak_tf = FP64_FLOP_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    hbm_peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm_peak = json.load(f).get("hbm_gbs")
+    except Exception:
+        pass
+    gbs = bytes_cell * C / mean_launch_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "ncells": C, "nspecies": N, "matrix": f"{n}x{n}",
+                   "dt_over_ts": W.WORKLOADS[args.workload][0].split("dt/t_s in ")[-1],
+                   "l2": "inputs (%.2f GB) larger than L2, no flush" % (bytes_cell * C / 1e9),
+                   "mean_k_star": float(k.mean()), "mean_s_star": float(s.mean()), "max_s_star": int(s.max())},
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": achieved_tf / peak_tf, "traffic": None,
+                     "peak_source": "FP64 pipe: 152 SMs x 608/152 flop/clk x 2070 MHz (unit count x max clock)",
+                     "algorithmic_flop_per_launch": flops_launch, "kernel_mean_ms": mean_launch_s * 1e3,
+                     "hbm_gbs": gbs, "hbm_frac_of_measured": (gbs / hbm_peak) if hbm_peak else None},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample, _ = cpu_oracle_rate(cells, seconds=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"first {sample} cells of {args.workload}, one pass"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,1 +1,129 @@
-"""GB300-native exponential drag solver for gas + N dust species (FP64, sm_103a)."""
+"""GB300-native exponential drag solver for a gas plus N dust species (FP64, sm_103a).
+
+Thin binding over the C ABI of ``libdragexpm.so`` (declared in
+``include/drag_expm.h``): argument checks and marshalling only. Every step of
+the drag update runs in the library's CUDA kernels; there is no CPU path. If
+the library is missing or fails to load, every call raises.
+
+Tensors are torch float64 CUDA tensors in the library's SoA layout:
+``rho_g (C,)``, ``rho_d (N, C)``, ``t_s (N, C)``, ``v (3, N+1, C)``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = ["load_library", "apply", "select", "get_status", "theta", "DragExpmError",
+           "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdragexpm.so")
+NMAX = 31
+STATUS_BAD_CELL = 0x1
+STATUS_BAD_BLOCK = 0x2
+STATUS_QUEUE_GUARD = 0x4
+
+_lib = None
+
+
+class DragExpmError(RuntimeError):
+    pass
+
+
+def load_library(path: str | None = None):
+    """Load libdragexpm.so (built by ``paper_2509_25347_gb300.build``)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise DragExpmError(f"{p} not found: build it with `python -m paper_2509_25347_gb300.build` "
+                            "(the drag update has no CPU fallback)")
+    lib = ctypes.CDLL(p)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    lib.drag_expm_apply.restype = ctypes.c_int
+    lib.drag_expm_apply.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp]
+    lib.drag_expm_select.restype = ctypes.c_int
+    lib.drag_expm_select.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp]
+    lib.drag_expm_get_status.restype = ctypes.c_int
+    lib.drag_expm_get_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
+    lib.drag_expm_theta.restype = ctypes.c_int
+    lib.drag_expm_theta.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+    lib.drag_expm_strerror.restype = ctypes.c_char_p
+    lib.drag_expm_strerror.argtypes = [ctypes.c_int]
+    lib.drag_expm_version.restype = ctypes.c_int
+    lib.drag_expm_version.argtypes = []
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = load_library().drag_expm_strerror(rc).decode()
+        raise DragExpmError(f"libdragexpm error {rc}: {msg}")
+
+
+def _stream_handle(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _f64_cuda(name, t, shape):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+        raise DragExpmError(f"{name} must be a float64 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise DragExpmError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise DragExpmError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _shapes(rho_g, rho_d):
+    C = int(rho_g.shape[0])
+    N = int(rho_d.shape[0])
+    return C, N
+
+
+def apply(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, stream=None):
+    """v_out = exp(dt Omega_v) v_in per cell (forward drag update). Returns v_out.
+
+    ``v_out`` may be ``v_in`` (in place) or None (a new tensor is allocated).
+    """
+    import torch
+    C, N = _shapes(rho_g, rho_d)
+    if v_out is None:
+        v_out = torch.empty_like(v_in)
+    args = [_f64_cuda("rho_g", rho_g, (C,)), _f64_cuda("rho_d", rho_d, (N, C)), _f64_cuda("t_s", t_s, (N, C))]
+    vi = _f64_cuda("v_in", v_in, (3, N + 1, C))
+    vo = _f64_cuda("v_out", v_out, (3, N + 1, C))
+    _check(load_library().drag_expm_apply(C, N, *args, float(dt), vi, vo, _stream_handle(stream)))
+    return v_out
+
+
+def select(rho_g, rho_d, t_s, dt: float, stream=None):
+    """(k*, s*) per cell as chosen by Algorithm 2: int8 and int16 CUDA tensors."""
+    import torch
+    C, N = _shapes(rho_g, rho_d)
+    k = torch.empty(C, dtype=torch.int8, device=rho_g.device)
+    s = torch.empty(C, dtype=torch.int16, device=rho_g.device)
+    args = [_f64_cuda("rho_g", rho_g, (C,)), _f64_cuda("rho_d", rho_d, (N, C)), _f64_cuda("t_s", t_s, (N, C))]
+    _check(load_library().drag_expm_select(C, N, *args, float(dt), ctypes.c_void_p(k.data_ptr()),
+                                           ctypes.c_void_p(s.data_ptr()), _stream_handle(stream)))
+    return k, s
+
+
+def get_status(stream=None) -> int:
+    """Read and clear the device's sticky status bits (STATUS_*)."""
+    st = ctypes.c_uint32(0)
+    _check(load_library().drag_expm_get_status(_stream_handle(stream), ctypes.byref(st)))
+    return int(st.value)
+
+
+def theta(k: int) -> float:
+    """theta_{m_k} (Eq. B8, u = 2^-53) as used by the library, k = 1..9."""
+    out = ctypes.c_double(0.0)
+    _check(load_library().drag_expm_theta(int(k), ctypes.byref(out)))
+    return out.value

@@ -1,0 +1,150 @@
+// Host-side set-up of libdragexpm: the theta_m constants of Eq. B8, the
+// Taylor coefficients, the device status word and small query entry points.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "dx_common.cuh"
+
+// Sticky status bits, one word per device (DRAG_STATUS_*).
+__device__ uint32_t g_dx_status;
+
+namespace {
+
+// Table B.1: m_k for k = 1..9.
+const int kMk[DX_K + 1] = {0, 2, 4, 6, 9, 12, 16, 20, 25, 30};
+
+// f_m(theta)/theta with f_m of Eq. B6. The coefficients of
+// rho(x) = e^-x T_m(x) - 1 (Eq. B5) satisfy |c_j| = C(j-1, m)/j!, so
+// f_m(theta) = sum_{t>=0} theta^(m+1+t) / ((m+1+t) m! t!): all terms positive.
+double fm(int m, double th) {
+    double inv_mfact = 1.0;
+    for (int a = 2; a <= m; a++) inv_mfact /= a;
+    double term = std::pow(th, m + 1) * inv_mfact;   // theta^(m+1)/(m! 0!)
+    double f = 0.0;
+    for (int t = 0; t < 120; t++) {
+        f += term / (m + 1 + t);
+        term *= th / (t + 1);
+    }
+    return f;
+}
+
+// theta_m = max{theta : -log(1 - f_m(theta))/theta <= u} (Eq. B8), bisection.
+double theta_of(int m, double u) {
+    double lo = 0.0, hi = 64.0;
+    for (int it = 0; it < 300; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double f = fm(m, mid);
+        bool ok = f < 1.0 && -std::log1p(-f) / mid <= u;
+        (ok ? lo : hi) = mid;
+    }
+    return lo;
+}
+
+long long bits(double x) {
+    long long b;
+    std::memcpy(&b, &x, sizeof b);
+    return b;
+}
+
+DxConsts make_consts() {
+    DxConsts K;
+    std::memset(&K, 0, sizeof K);
+    const double u = std::ldexp(1.0, -53);
+    for (int k = 1; k <= DX_K; k++) {
+        double th = theta_of(kMk[k], u);
+        K.th[k] = bits(th);
+        K.th2[k] = bits(2.0 * th);
+        K.th4[k] = bits(4.0 * th);
+        K.mk[k] = kMk[k];
+    }
+    K.b[0] = 1.0;
+    for (int i = 1; i < 32; i++) K.b[i] = K.b[i - 1] / i;
+    return K;
+}
+
+std::mutex g_mu;
+uint32_t *g_status_ptr[64];
+int g_sm_count[64];
+bool g_once[64][16];
+
+}  // namespace
+
+const DxConsts &dx_consts() {
+    static const DxConsts K = make_consts();
+    return K;
+}
+
+uint32_t *dx_status_ptr() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_status_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_dx_status) != cudaSuccess) return nullptr;
+        g_status_ptr[dev] = static_cast<uint32_t *>(p);
+    }
+    return g_status_ptr[dev];
+}
+
+int dx_sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_sm_count[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        g_sm_count[dev] = v;
+    }
+    return g_sm_count[dev];
+}
+
+bool dx_once_per_device(int slot, bool (*fn)()) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || slot < 0 || slot >= 16) return false;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_once[dev][slot]) return true;
+    if (!fn()) return false;
+    g_once[dev][slot] = true;
+    return true;
+}
+
+extern "C" {
+
+int drag_expm_get_status(cudaStream_t stream, uint32_t *status_out) {
+    if (!status_out) return DRAG_ENULL;
+    uint32_t *p = dx_status_ptr();
+    if (!p) return DRAG_ECUDA;
+    uint32_t v = 0;
+    if (cudaMemcpyAsync(&v, p, sizeof v, cudaMemcpyDeviceToHost, stream) != cudaSuccess) return DRAG_ECUDA;
+    if (cudaMemsetAsync(p, 0, sizeof v, stream) != cudaSuccess) return DRAG_ECUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return DRAG_ECUDA;
+    *status_out = v;
+    return DRAG_OK;
+}
+
+int drag_expm_theta(int32_t k, double *theta_out) {
+    if (!theta_out) return DRAG_ENULL;
+    if (k < 1 || k > DX_K) return DRAG_EINVAL_SIZE;
+    long long b = dx_consts().th[k];
+    std::memcpy(theta_out, &b, sizeof b);
+    return DRAG_OK;
+}
+
+const char *drag_expm_strerror(int code) {
+    switch (code) {
+        case DRAG_OK: return "success";
+        case DRAG_EINVAL_SIZE: return "invalid size: ncells < 0, nspecies outside [1, DRAG_EXPM_NMAX] or bad dt";
+        case DRAG_ENULL: return "a required pointer is NULL";
+        case DRAG_EALIGN: return "a pointer is not 8-byte aligned";
+        case DRAG_ECUDA: return "a CUDA runtime call or kernel launch failed";
+        case DRAG_EWORKSPACE: return "workspace missing or too small";
+        case DRAG_EBLOCKS: return "invalid block count or block descriptor array";
+        default: return "unknown error code";
+    }
+}
+
+int drag_expm_version(void) { return DRAG_EXPM_VERSION; }
+
+}  // extern "C"

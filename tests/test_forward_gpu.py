@@ -1,0 +1,170 @@
+"""GPU forward parity: libdragexpm (through its C ABI) against the CPU oracle.
+
+Tolerance: per cell and velocity component d, for every fluid f,
+|v_gpu - v_oracle| <= 1e-13 * max_f |v_in[d, f]| (the update is a convex
+combination of the inputs, so this is the natural scale of the result).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_25347_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-13
+
+
+@pytest.fixture(scope="module")
+def dx():
+    import torch  # noqa: F401
+    from paper_2509_25347_gb300 import build
+    build.build()
+    import paper_2509_25347_gb300 as m
+    m.load_library()
+    m.get_status()
+    return m
+
+
+def dev(cells):
+    import torch
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return t(cells.rho_g), t(cells.rho_d), t(cells.t_s), t(cells.v)
+
+
+def gpu_apply(dx, cells, dt=None):
+    rg, rd, ts, v = dev(cells)
+    out = dx.apply(rg, rd, ts, cells.dt if dt is None else dt, v)
+    return out.cpu().numpy()
+
+
+def assert_parity(out, ref, vin, tol=TOL):
+    sc = np.abs(vin).max(axis=1, keepdims=True)
+    sc = np.where(sc > 0, sc, 1.0)
+    err = np.abs(out - ref) / sc
+    worst = np.unravel_index(np.argmax(err), err.shape)
+    assert np.all(np.isfinite(out))
+    assert err.max() <= tol, f"max scaled error {err.max():.3e} at {worst}"
+    return err.max()
+
+
+CASES = [("dustybox_n1_32k", 3001), ("mrn_n4_128cube", 1537), ("mrn_n8_128cube_adjoint", 777),
+         ("mrn_n16_128cube", 301)]
+
+
+@pytest.mark.parametrize("name,C", CASES)
+def test_forward_parity_small(dx, name, C):
+    cells = W.workload(name, ncells=C)
+    out = gpu_apply(dx, cells)
+    ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v)
+    assert_parity(out, ref, cells.v)
+    assert dx.get_status() == 0
+
+
+@pytest.mark.parametrize("name,C", CASES)
+def test_select_bit_exact(dx, name, C):
+    """(k*, s*) of Algorithm 2: integer decisions must match the oracle exactly."""
+    cells = W.workload(name, ncells=C)
+    rg, rd, ts, _ = dev(cells)
+    k, s = dx.select(rg, rd, ts, cells.dt)
+    _, ko, so, _ = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, return_ks=True)
+    assert np.array_equal(k.cpu().numpy(), ko)
+    assert np.array_equal(s.cpu().numpy(), so)
+
+
+@pytest.mark.parametrize("N", list(range(1, 32)))
+def test_forward_every_nspecies(dx, N):
+    """Every supported species count, stiff MRN-like cells, ragged cell count."""
+    cells = W.mrn(97 + N, N, seed=100 + N, stiff_lo=-4.0, stiff_hi=8.0)
+    out = gpu_apply(dx, cells)
+    ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v)
+    assert_parity(out, ref, cells.v)
+
+
+@pytest.mark.parametrize("dt", [0.0, 1e-12, 1e-3, 1.0, 1e3])
+def test_forward_dt_range(dx, dt):
+    cells = W.workload("mrn_n8_128cube_adjoint", ncells=129)
+    out = gpu_apply(dx, cells, dt=dt)
+    ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, dt, cells.v)
+    assert_parity(out, ref, cells.v)
+    if dt == 0.0:
+        assert np.array_equal(out, cells.v)
+
+
+def test_in_place(dx):
+    import torch
+    cells = W.workload("mrn_n4_128cube", ncells=1000)
+    rg, rd, ts, v = dev(cells)
+    ref = dx.apply(rg, rd, ts, cells.dt, v).clone()
+    dx.apply(rg, rd, ts, cells.dt, v, v_out=v)
+    assert torch.equal(ref, v)
+
+
+def test_decoupled_and_zero_density(dx):
+    rng = np.random.default_rng(1)
+    N, C = 5, 64
+    cells = W.mrn(C, N, seed=9, stiff_lo=-2.0, stiff_hi=6.0)
+    cells.t_s[1] = np.inf
+    cells.rho_d[2] = 0.0
+    cells.rho_d[3, ::2] = 1e-250 * cells.rho_g[::2]
+    out = gpu_apply(dx, cells)
+    ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v)
+    assert_parity(out, ref, cells.v)
+    assert np.array_equal(out[:, 2], cells.v[:, 2])
+
+
+def test_invalid_cells_flagged(dx):
+    cells = W.workload("mrn_n4_128cube", ncells=40)
+    cells.rho_g[3] = 0.0
+    cells.rho_d[1, 7] = -1.0
+    cells.t_s[2, 11] = 0.0
+    cells.t_s[0, 13] = np.nan
+    cells.rho_d[3, 17] = np.inf
+    out = gpu_apply(dx, cells)
+    bad = [3, 7, 11, 13, 17]
+    good = [c for c in range(40) if c not in bad]
+    assert np.all(np.isnan(out[:, :, bad]))
+    ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v)
+    assert_parity(out[:, :, good], ref[:, :, good], cells.v[:, :, good])
+    assert dx.get_status() & dx.STATUS_BAD_CELL
+    assert dx.get_status() == 0          # cleared by the read
+
+
+def test_empty_is_noop(dx):
+    import torch
+    z = torch.zeros(0, dtype=torch.float64, device="cuda")
+    out = dx.apply(z, z.reshape(4, 0), z.reshape(4, 0), 1.0, z.reshape(3, 5, 0))
+    assert out.shape == (3, 5, 0)
+
+
+def test_matches_eigen_truth(dx):
+    pytest.importorskip("mpmath")
+    from oracle.truth import drag_truth
+    cells = W.workload("mrn_n16_128cube", ncells=24)
+    out = gpu_apply(dx, cells)
+    ref = drag_truth(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v)
+    assert_parity(out, ref, cells.v, tol=4e-15)
+
+
+@pytest.mark.parametrize("name", ["mrn_n16_128cube", "mrn_n4_128cube", "dustybox_n1_32k"])
+def test_full_size_sampled(dx, name):
+    """Full-size workload in the benchmark's launch configuration: 256 sampled
+    cells against the oracle, conservation and convexity on every cell."""
+    import torch
+    cells = W.workload(name)
+    rg, rd, ts, v = dev(cells)
+    out = dx.apply(rg, rd, ts, cells.dt, v)
+    torch.cuda.synchronize()
+    assert dx.get_status() == 0
+    C = cells.ncells
+    idx = np.unique(np.concatenate([np.random.default_rng(0).integers(0, C, 254), [0, C - 1]]))
+    sub = cells.subset(idx)
+    ref = oracle.drag_apply(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v)
+    assert_parity(out[:, :, torch.from_numpy(idx).cuda()].cpu().numpy(), ref, sub.v)
+    rho = torch.cat([rg[None, :], rd], 0)
+    mom_in = torch.einsum("fc,dfc->dc", rho, v)
+    mom_out = torch.einsum("fc,dfc->dc", rho, out)
+    scale = torch.einsum("fc,dfc->dc", rho, v.abs())
+    assert bool(((mom_out - mom_in).abs() <= 8e-15 * scale).all())
+    vsc = v.abs().amax(dim=1)
+    assert bool((out.amin(dim=1) >= v.amin(dim=1) - 4e-15 * vsc).all())
+    assert bool((out.amax(dim=1) <= v.amax(dim=1) + 4e-15 * vsc).all())
