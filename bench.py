@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--workload", default="mrn_n16_128cube", choices=[k for k in W.WORKLOADS if "batched" not in k])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--ncells", type=int, default=None, help="truncate the workload (profiling runs only)")
     return p.parse_args()
 
 
@@ -192,7 +193,9 @@ def run_ours(args, rank, world):
     dx.load_library()
 
     _, C, N, _ = W.WORKLOADS[args.workload]
-    cells = W.workload(args.workload)
+    if args.ncells:
+        C = min(C, args.ncells)
+    cells = W.workload(args.workload, ncells=C)
     n = N + 1
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     rg, rd, ts, v = dev(cells.rho_g), dev(cells.rho_d), dev(cells.t_s), dev(cells.v)

@@ -58,6 +58,11 @@ def _load():
     lib.orc_drag_apply.argtypes = [ctypes.c_int64, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp, dp, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int16),
                                    ctypes.POINTER(ctypes.c_uint32)]
+    lib.orc_drag_backward.restype = ctypes.c_int
+    lib.orc_drag_backward.argtypes = [ctypes.c_int64, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp, dp, dp, dp, dp,
+                                      dp, ctypes.POINTER(ctypes.c_uint32)]
+    lib.orc_frechet_dense.restype = ctypes.c_int
+    lib.orc_frechet_dense.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int]
     for name in ("orc_table_mk", "orc_table_qk", "orc_table_rk"):
         getattr(lib, name).restype = ctypes.c_int
         getattr(lib, name).argtypes = [ctypes.c_int]
@@ -65,7 +70,9 @@ def _load():
     return lib
 
 
-def _dptr(a: np.ndarray):
+def _dptr(a):
+    if a is None:
+        return None
     assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
@@ -143,3 +150,41 @@ def drag_apply(rho_g, rho_d, t_s, dt, v_in, structured: bool = True, return_ks: 
     if return_ks:
         return v_out, k_out, s_out, st.value
     return v_out
+
+
+def frechet_T(A: np.ndarray, G: np.ndarray, structured: bool = False) -> np.ndarray:
+    """Z = L(A^T, G): Frechet derivative of exp at A^T in direction G (block S&S).
+
+    structured=True only for A with zero row sums (drag matrices)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    Z = np.zeros_like(A)
+    rc = _load().orc_frechet_dense(A.shape[0], _dptr(A), _dptr(G), _dptr(Z), int(structured))
+    if rc == -2:
+        raise ValueError("matrix too large for the oracle")
+    return Z
+
+
+def drag_backward(rho_g, rho_d, t_s, dt, v_in, grad_v_out):
+    """Gradients of <grad_v_out, v_out> through one drag step.
+
+    Returns (grad_v_in (3,N+1,C), grad_rho_g (C,), grad_rho_d (N,C), grad_t_s (N,C), status).
+    """
+    rho_g = np.ascontiguousarray(rho_g, dtype=np.float64)
+    rho_d = np.ascontiguousarray(rho_d, dtype=np.float64)
+    t_s = np.ascontiguousarray(t_s, dtype=np.float64)
+    v_in = np.ascontiguousarray(v_in, dtype=np.float64)
+    g = np.ascontiguousarray(grad_v_out, dtype=np.float64)
+    C = rho_g.shape[0]
+    N = rho_d.shape[0]
+    assert g.shape == v_in.shape == (3, N + 1, C)
+    gv = np.empty_like(v_in)
+    grg = np.empty(C)
+    grd = np.empty((N, C))
+    gts = np.empty((N, C))
+    st = ctypes.c_uint32(0)
+    rc = _load().orc_drag_backward(C, N, _dptr(rho_g), _dptr(rho_d), _dptr(t_s), float(dt), _dptr(v_in), _dptr(g),
+                                   _dptr(gv), _dptr(grg), _dptr(grd), _dptr(gts), ctypes.byref(st))
+    if rc != 0:
+        raise ValueError(f"oracle rejected sizes (rc={rc})")
+    return gv, grg, grd, gts, st.value

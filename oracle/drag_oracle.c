@@ -359,6 +359,180 @@ int orc_drag_apply(int64_t C, int N, const double *rho_g, const double *rho_d, c
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Adjoint: the Frechet derivative of the exponential                       */
+/* ------------------------------------------------------------------------ */
+
+/* Column-sum restoration of an n x n block stored inside a (ld x ld)
+ * row-major matrix at (r0, r0): B_jj = 1 - sum_{i != j} B_ij. Used for the
+ * diagonal blocks exp(A^T), whose columns sum to one. */
+static void orc_restore_cols_block(int ld, int r0, int n, double *M)
+{
+    for (int j = 0; j < n; j++) {
+        double s = 0.0;
+        for (int i = 0; i < n; i++)
+            if (i != j) s += M[(size_t)(r0 + i) * ld + r0 + j];
+        M[(size_t)(r0 + j) * ld + r0 + j] = 1.0 - s;
+    }
+}
+
+/* Z = L(A^T, G): the Frechet derivative of exp at A^T in direction G, read
+ * off the top-right block of exp([[A^T, tau G], [0, A^T]]) (block-triangular
+ * identity of the exponential), divided by tau. tau = 2^-e scales G so that
+ * |tau G|_1 <= |A|_1 (exact). exp of the 2n x 2n matrix uses the same Taylor
+ * scaling and squaring as the forward (Algorithm 2 on its 1-norm,
+ * Paterson-Stockmeyer, squarings). For drag matrices (structured != 0) the
+ * column sums of both diagonal blocks, exp(A^T), are restored to one after
+ * the Taylor step and after every squaring, as in the forward. */
+static int orc_frechet_T(int n, const double *A, const double *G, double *Z, int structured)
+{
+    const int n2 = 2 * n;
+    double *M = (double *)calloc((size_t)n2 * n2, sizeof(double));
+    double *E = (double *)calloc((size_t)n2 * n2, sizeof(double));
+    double nA = orc_norm1(n, A), nG = orc_norm1(n, G);
+    int e = 0;
+    if (nA > 0.0)
+        while (ldexp(nG, -e) > nA) e++;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            M[(size_t)i * n2 + j] = A[j * n + i];               /* A^T */
+            M[(size_t)(n + i) * n2 + n + j] = A[j * n + i];     /* A^T */
+            M[(size_t)i * n2 + n + j] = ldexp(G[i * n + j], -e);
+        }
+    int k, m, s;
+    int rc = orc_select_alg2(orc_norm1(n2, M), ORC_K, &k, &m, &s);
+    if (rc != 0) {
+        for (int i = 0; i < n * n; i++) Z[i] = NAN;
+        free(M); free(E);
+        return -1;
+    }
+    /* Taylor (same Paterson-Stockmeyer evaluation as orc_expm) */
+    const int q = orc_qk[k], r = orc_rk[k];
+    const size_t nn = (size_t)n2 * n2;
+    double *pw = (double *)calloc((size_t)(q + 1) * nn, sizeof(double));
+    double *F = (double *)calloc(nn, sizeof(double));
+    double *T = (double *)calloc(nn, sizeof(double));
+    double *Bb = (double *)calloc(nn, sizeof(double));
+    double b[64];
+    b[0] = 1.0;
+    for (int i = 1; i <= m; i++) b[i] = b[i - 1] / (double)i;
+    for (size_t x = 0; x < nn; x++) pw[nn + x] = ldexp(M[x], -s);
+    for (int j = 2; j <= q; j++) orc_matmul(n2, pw + (size_t)(j - 1) * nn, pw + nn, pw + (size_t)j * nn);
+    for (int kk = r - 1; kk >= 0; kk--) {
+        for (size_t x = 0; x < nn; x++) {
+            double acc = 0.0;
+            for (int j = 1; j <= q; j++) acc += b[q * kk + j] * pw[(size_t)j * nn + x];
+            Bb[x] = acc;
+        }
+        if (kk == r - 1) {
+            memcpy(F, Bb, nn * sizeof(double));
+        } else {
+            orc_matmul(n2, F, pw + (size_t)q * nn, T);
+            for (size_t x = 0; x < nn; x++) F[x] = Bb[x] + T[x];
+        }
+    }
+    memcpy(E, F, nn * sizeof(double));
+    for (int i = 0; i < n2; i++) E[(size_t)i * n2 + i] += 1.0;
+    if (structured) {
+        orc_restore_cols_block(n2, 0, n, E);
+        orc_restore_cols_block(n2, n, n, E);
+    }
+    for (int t = 0; t < s; t++) {
+        orc_matmul(n2, E, E, T);
+        memcpy(E, T, nn * sizeof(double));
+        if (structured) {
+            orc_restore_cols_block(n2, 0, n, E);
+            orc_restore_cols_block(n2, n, n, E);
+        }
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) Z[i * n + j] = ldexp(E[(size_t)i * n2 + n + j], e);
+    free(pw); free(F); free(T); free(Bb); free(M); free(E);
+    return 0;
+}
+
+/* Reverse-mode gradients of a loss L(v_out) through one drag step.
+ * With g_d = dL/dv_out,d (d = x, y, z), P = exp(A), A = dt Omega_v:
+ *   dL/dv_in,d = P^T g_d
+ *   dL/dA = Z = L(A^T, G), G = sum_d g_d v_in,d^T
+ * and, from A_0i = eps_i alpha_i dt, A_00 = -sum_i A_0i, A_i0 = -A_ii = alpha_i dt
+ * (Eqs. DragEqVar2, DragEqVar3, jacobian):
+ *   dL/deps_i   = alpha_i dt (Z_0i - Z_00)
+ *   dL/dalpha_i = dt [eps_i (Z_0i - Z_00) + (Z_i0 - Z_ii)]
+ *   dL/drho_d,i = dL/deps_i / rho_g,   dL/dt_s,i = -dL/dalpha_i / t_s,i^2
+ *   dL/drho_g   = -sum_i eps_i dL/deps_i / rho_g.
+ * Any output pointer may be NULL. Invalid cells get NaN gradients. */
+int orc_drag_backward(int64_t C, int N, const double *rho_g, const double *rho_d, const double *t_s, double dt,
+                      const double *v_in, const double *g_out, double *g_vin, double *g_rho_g, double *g_rho_d,
+                      double *g_ts, uint32_t *status)
+{
+    if (C < 0 || N < 1 || N + 1 > ORC_NMAX) return -1;
+    const int n = N + 1;
+    double *A = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double *P = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double *G = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double *Z = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double rd[ORC_NMAX], ts[ORC_NMAX], vin[3][ORC_NMAX], gg[3][ORC_NMAX];
+    uint32_t st = 0;
+    for (int64_t c = 0; c < C; c++) {
+        for (int i = 0; i < N; i++) {
+            rd[i] = rho_d[(int64_t)i * C + c];
+            ts[i] = t_s[(int64_t)i * C + c];
+        }
+        for (int d = 0; d < 3; d++)
+            for (int f = 0; f < n; f++) {
+                vin[d][f] = v_in[((int64_t)d * n + f) * C + c];
+                gg[d][f] = g_out[((int64_t)d * n + f) * C + c];
+            }
+        int ok = orc_cell_valid(N, rho_g[c], rd, ts, dt);
+        int k, m, s;
+        if (ok) {
+            orc_assemble(N, rho_g[c], rd, ts, dt, 1, A);
+            ok = orc_expm(n, A, P, 1, &k, &m, &s) == 0;
+        }
+        if (ok) {
+            for (int i = 0; i < n; i++)
+                for (int j = 0; j < n; j++) {
+                    double acc = 0.0;
+                    for (int d = 0; d < 3; d++) acc += gg[d][i] * vin[d][j];
+                    G[i * n + j] = acc;
+                }
+            ok = orc_frechet_T(n, A, G, Z, 1) == 0;
+        }
+        if (!ok) st |= 1u;
+        if (g_vin)
+            for (int d = 0; d < 3; d++)
+                for (int i = 0; i < n; i++) {
+                    double acc = 0.0;
+                    for (int j = 0; j < n; j++) acc += P[j * n + i] * gg[d][j];
+                    g_vin[((int64_t)d * n + i) * C + c] = ok ? acc : NAN;
+                }
+        double sum_eps_geps = 0.0;
+        for (int i = 1; i <= N; i++) {
+            double eps = ok ? rd[i - 1] / rho_g[c] : NAN;
+            double alpha = ok ? 1.0 / ts[i - 1] : NAN;
+            double d0 = ok ? Z[0 * n + i] - Z[0] : NAN;
+            double geps = alpha * dt * d0;
+            double galpha = dt * (eps * d0 + (Z[i * n + 0] - Z[i * n + i]));
+            sum_eps_geps += eps * geps;
+            if (g_rho_d) g_rho_d[(int64_t)(i - 1) * C + c] = ok ? geps / rho_g[c] : NAN;
+            if (g_ts) g_ts[(int64_t)(i - 1) * C + c] = ok ? -galpha * (alpha * alpha) : NAN;
+        }
+        if (g_rho_g) g_rho_g[c] = ok ? -sum_eps_geps / rho_g[c] : NAN;
+    }
+    free(A); free(P); free(G); free(Z);
+    if (status) *status |= st;
+    return 0;
+}
+
+/* Z = L(A^T, G) for one dense n x n pair (tests of the Frechet machinery).
+ * structured != 0 only for A with zero row sums (column sums of exp(A^T) = 1). */
+int orc_frechet_dense(int n, const double *A, const double *G, double *Z, int structured)
+{
+    if (n < 1 || n > ORC_NMAX) return -2;
+    return orc_frechet_T(n, A, G, Z, structured);
+}
+
 /* exp(A) of one dense n x n matrix, for tests of the S&S machinery alone. */
 int orc_expm_dense(int n, const double *A, double *P, int structured, int *k, int *m, int *s)
 {

@@ -118,3 +118,55 @@ def theta_closed_form(m: int, u=None, dps: int = 50) -> float:
             else:
                 hi = mid
         return float(lo)
+
+
+def drag_truth_grad_cell(rho_g, rho_d, t_s, dt, v, g, dps: int = 50, rel_h: float = 1e-14):
+    """Gradients of <g, v_out> for one cell by central differences of the
+    eigendecomposition truth carried out in ``dps``-digit arithmetic (the
+    O(h^2) truncation and the rounding are both far below FP64 resolution).
+
+    Returns (grad_v_in (3, n), grad_rho_g, grad_rho_d (N,), grad_t_s (N,)).
+    Independent of the Frechet-derivative machinery of the FP64 oracle.
+    """
+    mp = _mp()
+    N = len(rho_d)
+    n = N + 1
+    with mp.workdps(dps):
+        def loss(rg, rd, ts):
+            rg = mp.mpf(rg)
+            eps = [mp.mpf(x) / rg for x in rd]
+            al = [1 / mp.mpf(x) for x in ts]
+            dtm = mp.mpf(float(dt))
+            S = mp.zeros(n, n)
+            for i in range(1, n):
+                S[0, i] = S[i, 0] = mp.sqrt(eps[i - 1]) * al[i - 1] * dtm
+                S[i, i] = -al[i - 1] * dtm
+                S[0, 0] -= eps[i - 1] * al[i - 1] * dtm
+            lam, Q = mp.eigsy(S)
+            sig = [mp.mpf(1)] + [mp.sqrt(e) for e in eps]
+            tot = mp.mpf(0)
+            for d in range(3):
+                y = mp.matrix([sig[j] * mp.mpf(float(v[d][j])) for j in range(n)])
+                z = Q.T * y
+                z = mp.matrix([z[j] * mp.exp(lam[j]) for j in range(n)])
+                z = Q * z
+                for i in range(n):
+                    tot += mp.mpf(float(g[d][i])) * z[i] / sig[i]
+            return tot
+
+        rg0 = mp.mpf(float(rho_g))
+        rd0 = [mp.mpf(float(x)) for x in rho_d]
+        ts0 = [mp.mpf(float(x)) for x in t_s]
+
+        def cd(f, x0):
+            h = abs(x0) * mp.mpf(rel_h)
+            return (f(x0 + h) - f(x0 - h)) / (2 * h)
+
+        g_rg = cd(lambda x: loss(x, rd0, ts0), rg0)
+        g_rd, g_ts = [], []
+        for i in range(N):
+            g_rd.append(cd(lambda x: loss(rg0, rd0[:i] + [x] + rd0[i + 1:], ts0), rd0[i]))
+            g_ts.append(cd(lambda x: loss(rg0, rd0, ts0[:i] + [x] + ts0[i + 1:]), ts0[i]))
+    P = propagator_truth(rho_g, rho_d, t_s, dt, dps=dps)
+    gv = np.einsum("ji,dj->di", P, np.asarray(g, dtype=np.float64))
+    return gv, float(g_rg), np.array([float(x) for x in g_rd]), np.array([float(x) for x in g_ts])
