@@ -257,10 +257,34 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
 
-    t_ms = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device="cuda")
+    # forward + adjoint: loss 0.5 ||v_out - v_target||^2, v_target ~ N(0,1)
+    vt = dev(W.adjoint_target(C, N))
+    gvi = torch.empty_like(v)
+    grd, gts = torch.empty_like(rd), torch.empty_like(ts)
+    grg = torch.empty_like(rg)
+    fb_steps = max(1, min(args.steps, 3))
+
+    def fwd_bwd():
+        dx.apply(rg, rd, ts, cells.dt, v, vout)
+        torch.sub(vout, vt, out=gvi)                     # dL/dv_out
+        dx.backward(rg, rd, ts, cells.dt, v, gvi, out=(vout, grg, grd, gts))
+
+    fwd_bwd()
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    for _ in range(fb_steps):
+        fwd_bwd()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    fb_ms = b0.elapsed_time(b1) / fb_steps
+    if dx.get_status():
+        raise RuntimeError("device status set after forward + adjoint")
+
+    t_ms = torch.tensor([total_ms, e2e_ms, fb_ms], dtype=torch.float64, device="cuda")
     if world > 1:
         torch.distributed.all_reduce(t_ms, op=torch.distributed.ReduceOp.MAX)
-    total_ms, e2e_ms = float(t_ms[0]), float(t_ms[1])
+    total_ms, e2e_ms, fb_ms = float(t_ms[0]), float(t_ms[1]), float(t_ms[2])
     ms_per_step = total_ms / args.steps
     value = C * world / (ms_per_step * 1e-3)
     e2e_value = C * world / (e2e_ms * 1e-3)
@@ -294,6 +318,8 @@ def run_ours(args, rank, world):
                      "algorithmic_flop_per_launch": flops_launch, "kernel_mean_ms": mean_launch_s * 1e3,
                      "hbm_gbs": gbs, "hbm_frac_of_measured": (gbs / hbm_peak) if hbm_peak else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "fwd_adjoint": {"value": C * world / (fb_ms * 1e-3), "unit": UNIT, "ms_per_step": fb_ms, "steps": fb_steps,
+                        "note": "forward + dL/dv_out (torch sub) + drag_expm_backward, outside the headline timed region"},
         "gpu_launches": args.steps,
         "clocks": clocks,
     }

@@ -95,6 +95,30 @@ int drag_expm_select(int64_t ncells, int32_t nspecies, const double *rho_g, cons
                      double dt, int8_t *k_out, int16_t *s_out, cudaStream_t stream);
 
 /*
+ * drag_expm_backward — adjoint of drag_expm_apply (reverse mode). Given
+ * grad_v_out = dL/dv_out for a scalar loss L of v_out, returns
+ *   grad_v_in  = dL/dv_in  = P^T grad_v_out per component, P = exp(dt Omega_v);
+ *   grad_rho_d = dL/drho_d, grad_t_s = dL/dt_s, grad_rho_g = dL/drho_g,
+ * through the Frechet derivative of the exponential, Z = L(A^T, G) with
+ * A = dt Omega_v and G = sum_d grad_v_out,d v_in,d^T, and the dependence of
+ * Omega on eps_i = rho_d,i/rho_g and alpha_i = 1/t_s,i (Eqs. DragEqVar2,
+ * DragEqVar3, jacobian). The Frechet derivative is carried through the same
+ * Algorithm 2 / Taylor / squaring steps as the forward (block-triangular
+ * form [[A, E], [0, A]]), recomputing the forward on the fly (no storage).
+ *   rho_g, rho_d, t_s, v_in : DEVICE inputs of the forward call (read only).
+ *   grad_v_out : DEVICE, 3*(N+1)*ncells doubles, layout of v (read only).
+ *   grad_v_in  : DEVICE, layout of v, written (may be NULL).
+ *   grad_rho_g : DEVICE, ncells doubles, written (may be NULL).
+ *   grad_rho_d, grad_t_s : DEVICE, N*ncells doubles, layout of rho_d (may be NULL).
+ * Outputs must not overlap inputs. Invalid cells get NaN gradients and set
+ * DRAG_STATUS_BAD_CELL. Returns DRAG_OK or a DRAG_E* code.
+ */
+int drag_expm_backward(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                       const double *t_s, double dt, const double *v_in, const double *grad_v_out,
+                       double *grad_v_in, double *grad_rho_g, double *grad_rho_d, double *grad_t_s,
+                       cudaStream_t stream);
+
+/*
  * drag_expm_get_status — copy the current device's sticky status bits
  * (DRAG_STATUS_*) into *status_out and clear them. Synchronises `stream`.
  */

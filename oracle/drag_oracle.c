@@ -497,6 +497,25 @@ int orc_drag_backward(int64_t C, int N, const double *rho_g, const double *rho_d
                     for (int d = 0; d < 3; d++) acc += gg[d][i] * vin[d][j];
                     G[i * n + j] = acc;
                 }
+            /* Remove the stationary block of G before differentiating.
+             * rho^T A = 0 and A 1 = 0 (detailed balance and zero row sums of
+             * Eq. jacobian in velocity form), so Pi = rho 1^T / (1^T rho) is
+             * the spectral projector of A^T for eigenvalue 0 and
+             * L(A^T, Pi G Pi) = Pi G Pi = kappa rho 1^T, kappa = 1^T G rho / (1^T rho)^2.
+             * Its entries are constant along rows, so it adds nothing to
+             * Z_0i - Z_00 or Z_i0 - Z_ii, the only combinations the gradients
+             * use. Dropping it keeps the propagated derivative small in stiff
+             * cells, where this block doubles at every squaring and its rounding
+             * would otherwise be amplified by |A| in the chain rule. */
+            double rho[ORC_NMAX], srho = 0.0, gr = 0.0;
+            rho[0] = rho_g[c];
+            for (int i = 1; i < n; i++) rho[i] = rd[i - 1];
+            for (int i = 0; i < n; i++) srho += rho[i];
+            for (int i = 0; i < n; i++)
+                for (int j = 0; j < n; j++) gr += G[i * n + j] * rho[j];
+            const double kappa = gr / (srho * srho);
+            for (int i = 0; i < n; i++)
+                for (int j = 0; j < n; j++) G[i * n + j] -= kappa * rho[i];
             ok = orc_frechet_T(n, A, G, Z, 1) == 0;
         }
         if (!ok) st |= 1u;

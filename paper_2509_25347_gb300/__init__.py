@@ -13,7 +13,7 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["load_library", "apply", "select", "get_status", "theta", "DragExpmError",
+__all__ = ["load_library", "apply", "backward", "select", "get_status", "theta", "DragExpm", "DragExpmError",
            "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -43,6 +43,8 @@ def load_library(path: str | None = None):
     vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     lib.drag_expm_apply.restype = ctypes.c_int
     lib.drag_expm_apply.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp]
+    lib.drag_expm_backward.restype = ctypes.c_int
+    lib.drag_expm_backward.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp, vp, vp, vp, vp]
     lib.drag_expm_select.restype = ctypes.c_int
     lib.drag_expm_select.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp]
     lib.drag_expm_get_status.restype = ctypes.c_int
@@ -101,6 +103,76 @@ def apply(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, stream=None):
     vo = _f64_cuda("v_out", v_out, (3, N + 1, C))
     _check(load_library().drag_expm_apply(C, N, *args, float(dt), vi, vo, _stream_handle(stream)))
     return v_out
+
+
+def _opt_ptr(name, t, shape):
+    if t is None:
+        return ctypes.c_void_p(0)
+    return _f64_cuda(name, t, shape)
+
+
+def backward(rho_g, rho_d, t_s, dt: float, v_in, grad_v_out, need_v_in=True, need_rho_g=True, need_rho_d=True,
+             need_t_s=True, out=None, stream=None):
+    """Adjoint of :func:`apply`: returns (grad_v_in, grad_rho_g, grad_rho_d, grad_t_s),
+    None for the ones not requested. ``out`` may pass preallocated output tensors
+    (a 4-tuple, None entries are not computed)."""
+    import torch
+    C, N = _shapes(rho_g, rho_d)
+    dev = rho_g.device
+    if out is not None:
+        gvi, grg, grd, gts = out
+    else:
+        gvi = torch.empty((3, N + 1, C), dtype=torch.float64, device=dev) if need_v_in else None
+        grg = torch.empty((C,), dtype=torch.float64, device=dev) if need_rho_g else None
+        grd = torch.empty((N, C), dtype=torch.float64, device=dev) if need_rho_d else None
+        gts = torch.empty((N, C), dtype=torch.float64, device=dev) if need_t_s else None
+    args = [_f64_cuda("rho_g", rho_g, (C,)), _f64_cuda("rho_d", rho_d, (N, C)), _f64_cuda("t_s", t_s, (N, C))]
+    vi = _f64_cuda("v_in", v_in, (3, N + 1, C))
+    go = _f64_cuda("grad_v_out", grad_v_out, (3, N + 1, C))
+    _check(load_library().drag_expm_backward(C, N, *args, float(dt), vi, go, _opt_ptr("grad_v_in", gvi, (3, N + 1, C)),
+                                             _opt_ptr("grad_rho_g", grg, (C,)), _opt_ptr("grad_rho_d", grd, (N, C)),
+                                             _opt_ptr("grad_t_s", gts, (N, C)), _stream_handle(stream)))
+    return gvi, grg, grd, gts
+
+
+def _autograd_function():
+    import torch
+
+    class _DragExpm(torch.autograd.Function):
+        """v_out = exp(dt Omega_v) v_in with a hand-written adjoint kernel.
+
+        forward(rho_g, rho_d, t_s, dt, v_in) -> v_out; backward returns gradients
+        for rho_g, rho_d, t_s and v_in (None for dt)."""
+
+        @staticmethod
+        def forward(ctx, rho_g, rho_d, t_s, dt, v_in):
+            v_out = apply(rho_g.contiguous(), rho_d.contiguous(), t_s.contiguous(), float(dt), v_in.contiguous())
+            ctx.save_for_backward(rho_g, rho_d, t_s, v_in)
+            ctx.dt = float(dt)
+            return v_out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            rho_g, rho_d, t_s, v_in = ctx.saved_tensors
+            need = ctx.needs_input_grad
+            gvi, grg, grd, gts = backward(rho_g.contiguous(), rho_d.contiguous(), t_s.contiguous(), ctx.dt,
+                                          v_in.contiguous(), grad_out.contiguous(), need_v_in=need[4],
+                                          need_rho_g=need[0], need_rho_d=need[1], need_t_s=need[2])
+            return grg, grd, gts, None, gvi
+
+    return _DragExpm
+
+
+class _LazyFunction:
+    _fn = None
+
+    def apply(self, *args):
+        if _LazyFunction._fn is None:
+            _LazyFunction._fn = _autograd_function()
+        return _LazyFunction._fn.apply(*args)
+
+
+DragExpm = _LazyFunction()
 
 
 def select(rho_g, rho_d, t_s, dt: float, stream=None):

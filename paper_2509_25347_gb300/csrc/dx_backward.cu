@@ -1,0 +1,283 @@
+// Adjoint of the EXP drag update: gradients of a loss through
+// v_out = exp(dt Omega_v) v_in with respect to v_in, rho_d, t_s and rho_g.
+//
+// With g_d = dL/dv_out,d, P = exp(A), A = dt Omega_v:
+//   dL/dv_in,d = P^T g_d,   dL/dA = Z = L(A^T, G),   G = sum_d g_d v_in,d^T,
+// where L(., .) is the Frechet derivative of the exponential. In the symmetric
+// similarity form (A = D_sigma^-1 S D_sigma, S symmetric):
+//   Z = D_sigma L(S, G_S) D_sigma^-1,   G_S = D_sigma^-1 G D_sigma = sum_d a_d b_d^T,
+//   a_d = g_d / sigma, b_d = sigma o v_in,d   (rank 3).
+// The stationary block of the direction is removed first: sigma spans the null
+// space of S, so with P = sigma sigma^T / |sigma|^2, L(S, P G_S P) = P G_S P,
+// whose image under D_sigma . D_sigma^-1 has constant rows and therefore adds
+// nothing to Z_0i - Z_00 or Z_i0 - Z_ii. Carrying G_S - P G_S P instead keeps
+// the propagated derivative at the size of the answer in stiff cells (the
+// stationary block doubles at every squaring, and its rounding would otherwise
+// be amplified by |A| in the chain rule below). H is then rank 4:
+//   H = 2^-s (sum_d a_d b_d^T - kappa sigma sigma^T), kappa = sum_d (sigma.a_d)(sigma.b_d)/|sigma|^4.
+// L(S, G_S) is carried through the same scaling and squaring as the forward:
+//   Taylor: the Horner recurrence F <- F X + b_j I is differentiated,
+//           dF <- dF X + F H (F H = sum_d (F a_d) b_d^T over the 4 rank terms);
+//   squaring: (E, L) <- (E^2, E L + L E)  (block-triangular identity
+//           exp([[S, H], [0, S]]) = [[e^S, L(S, H)], [0, e^S]]).
+// The parameter gradients follow from A_0i = eps_i alpha_i dt,
+// A_00 = -sum_i A_0i, A_i0 = -A_ii = alpha_i dt (Eqs. DragEqVar2/3, jacobian):
+//   dL/deps_i = alpha_i dt (Z_0i - Z_00),
+//   dL/dalpha_i = dt [eps_i (Z_0i - Z_00) + (Z_i0 - Z_ii)],
+//   dL/drho_d,i = dL/deps_i / rho_g,  dL/dt_s,i = -alpha_i^2 dL/dalpha_i,
+//   dL/drho_g = -sum_i eps_i dL/deps_i / rho_g.
+#include <cmath>
+
+#include "dx_wpc.cuh"
+
+namespace {
+
+constexpr int kWarpsPerBlock = 4;
+
+struct BwdArgs {
+    long long C;
+    int N;
+    const double *rho_g, *rho_d, *t_s, *v_in, *g_out;
+    double *g_vin, *g_rho_g, *g_rho_d, *g_ts;
+    double dt;
+    uint32_t *status;
+};
+
+// Per-warp shared memory (doubles): E0, E1, L0, L1 and 19 vectors of 32.
+__host__ __device__ __forceinline__ int bwd_warp_smem_doubles(int n) { return 4 * n * dx_stride(n) + 19 * DX_NMAXF; }
+
+constexpr int kRank = 4;   // rank of the Frechet direction H
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+dx_backward_wpc(BwdArgs a, DxConsts K) {
+    extern __shared__ double smem[];
+    const int n = a.N + 1, N = a.N, ns = dx_stride(n);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int n_od = n * (n - 1) / 2;
+    const int n_hp = n * (n + 1) / 2 - 1;
+    const int nn = n * n;
+
+    unsigned short *od = reinterpret_cast<unsigned short *>(smem + kWarpsPerBlock * bwd_warp_smem_doubles(n));
+    unsigned short *hp = od + kPairSlots;
+    dx_build_pairs(n, od, hp);
+    __syncthreads();
+
+    double *E0 = smem + wib * bwd_warp_smem_doubles(n);
+    double *E1 = E0 + n * ns;
+    double *L0 = E1 + n * ns;
+    double *L1 = L0 + n * ns;
+    DxVecs V;
+    V.sig = L1 + n * ns;
+    V.tau = V.sig + DX_NMAXF;
+    V.xs = V.tau + DX_NMAXF;
+    V.ds = V.xs + DX_NMAXF;
+    double *av = V.ds + DX_NMAXF;      // a_d = g_d / sigma, a_3 = -kappa sigma     [4][32]
+    double *bv = av + 4 * DX_NMAXF;    // 2^-s sigma o v_d, b_3 = sigma             [4][32]
+    double *wv = bv + 4 * DX_NMAXF;    // F a_d                                     [4][32]
+    double *gg = wv + 4 * DX_NMAXF;    // g_d                                       [3][32]
+
+    const long long C = a.C;
+    const long long nwarps = (long long)gridDim.x * kWarpsPerBlock;
+    for (long long c = (long long)blockIdx.x * kWarpsPerBlock + wib; c < C; c += nwarps) {
+        const double rg = a.rho_g[c];
+        double rd = 0.0, ts = INFINITY;
+        if (lane >= 1 && lane <= N) {
+            rd = a.rho_d[(long long)(lane - 1) * C + c];
+            ts = a.t_s[(long long)(lane - 1) * C + c];
+        }
+        double vin[3] = {0.0, 0.0, 0.0}, gin[3] = {0.0, 0.0, 0.0};
+        if (lane < n) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                vin[d] = a.v_in[((long long)d * n + lane) * C + c];
+                gin[d] = a.g_out[((long long)d * n + lane) * C + c];
+            }
+        }
+        DxLane L;
+        if (!dx_wpc_setup(lane, N, rg, rd, ts, a.dt, K, V, L)) {
+            if (a.g_vin && lane < n)
+                for (int d = 0; d < 3; d++) a.g_vin[((long long)d * n + lane) * C + c] = NAN;
+            if (lane >= 1 && lane <= N) {
+                if (a.g_rho_d) a.g_rho_d[(long long)(lane - 1) * C + c] = NAN;
+                if (a.g_ts) a.g_ts[(long long)(lane - 1) * C + c] = NAN;
+            }
+            if (lane == 0) {
+                if (a.g_rho_g) a.g_rho_g[c] = NAN;
+                atomicOr(a.status, DRAG_STATUS_BAD_CELL);
+            }
+            continue;
+        }
+        const int m = K.mk[L.k];
+        const double p2 = dx_pow2(-L.s);
+        {
+            // rank-3 direction and its stationary block (kappa)
+            double a[3], b[3], sa[3], sb[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                a[d] = lane < n ? gin[d] * L.tu : 0.0;
+                b[d] = lane < n ? (L.sg * vin[d]) * p2 : 0.0;
+                sa[d] = L.sg * a[d];
+                sb[d] = L.sg * b[d];
+            }
+            double ss = lane < n ? L.sg * L.sg : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ss += __shfl_xor_sync(DX_FULL, ss, o);
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    sa[d] += __shfl_xor_sync(DX_FULL, sa[d], o);
+                    sb[d] += __shfl_xor_sync(DX_FULL, sb[d], o);
+                }
+            }
+            const double kappa = __ddiv_rn(fma(sa[2], sb[2], fma(sa[1], sb[1], sa[0] * sb[0])), ss * ss);
+            if (lane < n) {
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    av[d * DX_NMAXF + lane] = a[d];
+                    bv[d * DX_NMAXF + lane] = b[d];
+                    gg[d * DX_NMAXF + lane] = gin[d];
+                }
+                av[3 * DX_NMAXF + lane] = -kappa * L.sg;
+                bv[3 * DX_NMAXF + lane] = L.sg;
+            }
+        }
+
+        // ---- Taylor and its derivative: F = b_m X + b_{m-1} I, dF = b_m H
+        double *F = E0, *Fn = E1, *dF = L0, *dFn = L1;
+        dx_wpc_taylor_init(lane, n, ns, m, K, V, F);
+        for (int t = lane; t < nn; t += 32) {
+            const int i = t / n, j = t - i * n;
+            double acc = av[i] * bv[j];
+#pragma unroll
+            for (int d = 1; d < kRank; d++) acc = fma(av[d * DX_NMAXF + i], bv[d * DX_NMAXF + j], acc);
+            dF[i * ns + j] = K.b[m] * acc;
+        }
+        __syncwarp();
+        for (int jb = m - 2; jb >= 0; jb--) {
+            // w_d = F a_d (F before this step)
+            for (int t = lane; t < kRank * n; t += 32) {
+                const int d = t / n, i = t - d * n;
+                const double *ad = av + d * DX_NMAXF;
+                double acc = 0.0;
+                for (int k = 0; k < n; k++) acc = fma(F[i * ns + k], ad[k], acc);
+                wv[d * DX_NMAXF + i] = acc;
+            }
+            dx_wpc_horner_step(lane, n, ns, n_hp, hp, V, K.b[jb], F, Fn);
+            __syncwarp();
+            // dFn = dF X + F H. Columns j >= 1 (5 FMAs each: X has two
+            // nonzeros per column there) and column 0 (n + 3 FMAs) are dealt
+            // in separate rounds so short and long tasks do not share a round.
+            for (int t = lane; t < n * (n - 1); t += 32) {
+                const int i = t / (n - 1), j = t - i * (n - 1) + 1;
+                double acc = wv[i] * bv[j];
+#pragma unroll
+                for (int d = 1; d < kRank; d++) acc = fma(wv[d * DX_NMAXF + i], bv[d * DX_NMAXF + j], acc);
+                acc = fma(dF[i * ns], V.xs[j], acc);
+                acc = fma(dF[i * ns + j], V.ds[j], acc);
+                dFn[i * ns + j] = acc;
+            }
+            for (int i = lane; i < n; i += 32) {
+                double acc = wv[i] * bv[0];
+#pragma unroll
+                for (int d = 1; d < kRank; d++) acc = fma(wv[d * DX_NMAXF + i], bv[d * DX_NMAXF], acc);
+                const double *ri = dF + i * ns;
+                for (int k = 0; k < n; k++) acc = fma(ri[k], V.xs[k], acc);
+                dFn[i * ns] = acc;
+            }
+            __syncwarp();
+            double *t1 = F; F = Fn; Fn = t1;
+            double *t2 = dF; dF = dFn; dFn = t2;
+        }
+        dx_wpc_restore(lane, n, ns, V, F);
+        __syncwarp();
+
+        // ---- squarings: (E, L) <- (E^2, E L + L E)
+        for (int it = 0; it < L.s; it++) {
+            dx_wpc_square_offdiag(lane, n, ns, n_od, od, F, Fn);
+            for (int t = lane; t < nn; t += 32) {
+                const int i = t / n, j = t - i * n;
+                const double *ei = F + i * ns, *ej = F + j * ns, *li = dF + i * ns;
+                double acc = 0.0;
+                for (int k = 0; k < n; k++) {
+                    acc = fma(ei[k], dF[k * ns + j], acc);
+                    acc = fma(li[k], ej[k], acc);
+                }
+                dFn[i * ns + j] = acc;
+            }
+            __syncwarp();
+            dx_wpc_restore(lane, n, ns, V, Fn);
+            __syncwarp();
+            double *t1 = F; F = Fn; Fn = t1;
+            double *t2 = dF; dF = dFn; dFn = t2;
+        }
+
+        // ---- outputs
+        if (a.g_vin) {
+            // (P^T g)_i = E_ii g_i + sigma_i sum_{j != i} E_ij a_j
+            for (int t = lane; t < 3 * n; t += 32) {
+                const int d = t / n, i = t - d * n;
+                const double *ad = av + d * DX_NMAXF;
+                double acc = 0.0;
+                for (int q = 0; q < n - 1; q++) {
+                    const int k = q + (q >= i);
+                    acc = fma(F[i * ns + k], ad[k], acc);
+                }
+                a.g_vin[((long long)d * n + i) * C + c] =
+                    fma(V.sig[i], acc, F[i * ns + i] * gg[d * DX_NMAXF + i]);
+            }
+        }
+        double geps = 0.0;
+        if (lane >= 1 && lane <= N) {
+            const int i = lane;
+            const double z00 = dF[0], z0i = dF[i] * L.tu, zi0 = L.sg * dF[i * ns], zii = dF[i * ns + i];
+            const double d0 = z0i - z00;
+            geps = L.alpha * a.dt * d0;
+            const double galpha = a.dt * fma(L.eps, d0, zi0 - zii);
+            if (a.g_rho_d) a.g_rho_d[(long long)(i - 1) * C + c] = __ddiv_rn(geps, rg);
+            if (a.g_ts) a.g_ts[(long long)(i - 1) * C + c] = -galpha * (L.alpha * L.alpha);
+        }
+        if (a.g_rho_g) {
+            double part = L.eps * geps;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(DX_FULL, part, o);
+            if (lane == 0) a.g_rho_g[c] = -__ddiv_rn(part, rg);
+        }
+        __syncwarp();
+    }
+}
+
+bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
+
+size_t bwd_smem_bytes(int n) {
+    return sizeof(double) * (size_t)kWarpsPerBlock * bwd_warp_smem_doubles(n) + 2 * kPairSlots * sizeof(unsigned short);
+}
+
+}  // namespace
+
+extern "C" int drag_expm_backward(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                                  const double *t_s, double dt, const double *v_in, const double *grad_v_out,
+                                  double *grad_v_in, double *grad_rho_g, double *grad_rho_d, double *grad_t_s,
+                                  cudaStream_t stream) {
+    if (ncells < 0 || nspecies < 1 || nspecies > DRAG_EXPM_NMAX || !(dt >= 0.0) || !std::isfinite(dt))
+        return DRAG_EINVAL_SIZE;
+    if (ncells == 0) return DRAG_OK;
+    if (!rho_g || !rho_d || !t_s || !v_in || !grad_v_out) return DRAG_ENULL;
+    const void *ptrs[] = {rho_g, rho_d, t_s, v_in, grad_v_out, grad_v_in, grad_rho_g, grad_rho_d, grad_t_s};
+    for (const void *p : ptrs)
+        if (p && !aligned8(p)) return DRAG_EALIGN;
+    uint32_t *st = dx_status_ptr();
+    if (!st) return DRAG_ECUDA;
+    if (!dx_once_per_device(1, [] {
+            return cudaFuncSetAttribute(dx_backward_wpc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)bwd_smem_bytes(DX_NMAXF)) == cudaSuccess;
+        }))
+        return DRAG_ECUDA;
+    const int n = nspecies + 1;
+    BwdArgs a{ncells, nspecies, rho_g, rho_d, t_s, v_in, grad_v_out, grad_v_in, grad_rho_g, grad_rho_d, grad_t_s,
+              dt, st};
+    const long long want = (ncells + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const long long cap = (long long)dx_sm_count() * 8;
+    const int grid = (int)(want < cap ? want : cap);
+    dx_backward_wpc<<<grid, kWarpsPerBlock * 32, bwd_smem_bytes(n), stream>>>(a, dx_consts());
+    return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
+}

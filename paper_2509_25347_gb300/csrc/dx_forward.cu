@@ -21,12 +21,11 @@
 //      P_ii = E_ii, P_ij = E_ij sigma_j / sigma_i.
 #include <cmath>
 
-#include "dx_common.cuh"
+#include "dx_wpc.cuh"
 
 namespace {
 
 constexpr int kWarpsPerBlock = 4;
-constexpr int kPairSlots = 544;   // >= n(n+1)/2 for n <= 32
 
 struct FwdArgs {
     long long C;           // ncells
@@ -37,10 +36,8 @@ struct FwdArgs {
     uint32_t *status;
 };
 
-// Row stride of the n x n shared-memory matrices: odd, to spread banks.
-__host__ __device__ __forceinline__ int dx_stride(int n) { return n | 1; }
-
-// Per-warp shared-memory footprint (doubles).
+// Per-warp shared-memory footprint (doubles): E0, E1, sigma, tau, X_0f, X_ff,
+// sigma v (3 components) and v (3 components).
 __host__ __device__ __forceinline__ int warp_smem_doubles(int n) {
     return 2 * n * dx_stride(n) + 10 * DX_NMAXF;
 }
@@ -50,37 +47,27 @@ dx_forward_wpc(FwdArgs a, DxConsts K) {
     extern __shared__ double smem[];
     const int n = a.N + 1, N = a.N, ns = dx_stride(n);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int n_od = n * (n - 1) / 2;           // strict upper pairs (squaring)
-    const int n_hp = n * (n + 1) / 2 - 1;       // upper pairs except (0,0) (Horner)
+    const int n_od = n * (n - 1) / 2;
+    const int n_hp = n * (n + 1) / 2 - 1;
 
-    // Pair tables (shared by the block): od[t] = (i<<8)|j with i<j; hp[t] with i<=j, (i,j) != (0,0).
     unsigned short *od = reinterpret_cast<unsigned short *>(smem + kWarpsPerBlock * warp_smem_doubles(n));
     unsigned short *hp = od + kPairSlots;
-    for (int t = threadIdx.x; t < n_od; t += blockDim.x) {
-        int i = 0, r = t;
-        while (r >= n - 1 - i) { r -= n - 1 - i; i++; }
-        od[t] = (unsigned short)((i << 8) | (i + 1 + r));
-    }
-    for (int t = threadIdx.x; t < n_hp; t += blockDim.x) {
-        int i = 0, r = t + 1;                  // skip (0,0)
-        while (r >= n - i) { r -= n - i; i++; }
-        hp[t] = (unsigned short)((i << 8) | (i + r));
-    }
+    dx_build_pairs(n, od, hp);
     __syncthreads();
 
     double *E0 = smem + wib * warp_smem_doubles(n);
     double *E1 = E0 + n * ns;
-    double *sig = E1 + n * ns;         // sigma_f
-    double *tau = sig + DX_NMAXF;      // 1/sigma_f
-    double *xs = tau + DX_NMAXF;       // X_0f (f >= 1), xs[0] = X_00
-    double *ds = xs + DX_NMAXF;        // X_ff (f >= 1)
-    double *yv = ds + DX_NMAXF;        // sigma_f v_f, three components
+    DxVecs V;
+    V.sig = E1 + n * ns;
+    V.tau = V.sig + DX_NMAXF;
+    V.xs = V.tau + DX_NMAXF;
+    V.ds = V.xs + DX_NMAXF;
+    double *yv = V.ds + DX_NMAXF;      // sigma_f v_f, three components
     double *vv = yv + 3 * DX_NMAXF;    // v_f, three components
 
     const long long C = a.C;
     const long long nwarps = (long long)gridDim.x * kWarpsPerBlock;
     for (long long c = (long long)blockIdx.x * kWarpsPerBlock + wib; c < C; c += nwarps) {
-        // ---------------- load (lane f holds fluid f; species i on lane i)
         const double rg = a.rho_g[c];
         double rd = 0.0, ts = INFINITY;
         if (lane >= 1 && lane <= N) {
@@ -92,9 +79,8 @@ dx_forward_wpc(FwdArgs a, DxConsts K) {
 #pragma unroll
             for (int d = 0; d < 3; d++) vin[d] = a.v_in[((long long)d * n + lane) * C + c];
         }
-        const bool okl = (lane == 0 || lane > N) || (dx_nonneg_finite(rd) && dx_pos_or_inf(ts));
-        const bool ok = __all_sync(DX_FULL, okl) && dx_pos_finite(rg);
-        if (!ok) {
+        DxLane L;
+        if (!dx_wpc_setup(lane, N, rg, rd, ts, a.dt, K, V, L)) {
             if (lane < n) {
 #pragma unroll
                 for (int d = 0; d < 3; d++) a.v_out[((long long)d * n + lane) * C + c] = NAN;
@@ -102,115 +88,33 @@ dx_forward_wpc(FwdArgs a, DxConsts K) {
             if (lane == 0) atomicOr(a.status, DRAG_STATUS_BAD_CELL);
             continue;
         }
+        const int m = K.mk[L.k];
 
-        // ---------------- A = dt Omega_v entries (Eqs. DragEqVar2/3, jacobian)
-        const bool sp = lane >= 1 && lane <= N;
-        const double eps = sp ? __ddiv_rn(rd, rg) : 0.0;
-        const double alpha = sp ? __ddiv_rn(1.0, ts) : 0.0;
-        const double a0i = __dmul_rn(__dmul_rn(eps, alpha), a.dt);   // A_0i
-        const double ai0 = __dmul_rn(alpha, a.dt);                   // A_i0 = -A_ii
-
-        // 1-norm, summed in ascending species order: column 0 is
-        // |A_00| + sum_i A_i0 with A_00 = -sum_i A_0i; column i is A_0i + A_i0.
-        double s1 = 0.0;
-        for (int i = 1; i <= N; i++) s1 = __dadd_rn(s1, dx_shfl(a0i, i));
-        double col0 = s1;
-        for (int i = 1; i <= N; i++) col0 = __dadd_rn(col0, dx_shfl(ai0, i));
-        const double colj = sp ? __dadd_rn(a0i, ai0) : 0.0;
-        long long nb = dx_warp_max_ll(dx_bits(colj));
-        nb = nb > dx_bits(col0) ? nb : dx_bits(col0);
-        int kk, s;
-        dx_select(__longlong_as_double(nb), K, kk, s);
-        const int m = K.mk[kk];
-
-        // ---------------- symmetric arrowhead X = 2^-s D^(1/2) A D^(-1/2)
-        const double p2 = dx_pow2(-s);
-        double sg = 1.0, tu = 1.0;
-        if (sp) {
-            const double e = dx_bits(eps) < dx_bits(DX_EPS_FLOOR) ? DX_EPS_FLOOR : eps;
-            sg = __dsqrt_rn(e);
-            tu = __ddiv_rn(1.0, sg);
-        }
-        if (lane < n) {
-            sig[lane] = sg;
-            tau[lane] = tu;
-            xs[lane] = lane == 0 ? -s1 * p2 : __dmul_rn(__dmul_rn(sg, alpha), a.dt * p2);
-            ds[lane] = -(ai0 * p2);
-        }
-        __syncwarp();
-
-        // ---------------- Taylor: F = b_m X + b_{m-1} I, then F <- F X + b_j I
+        // Taylor polynomial T_m(X) by Horner's rule in X
         double *F = E0, *G = E1;
-        for (int t = lane; t < n * ns; t += 32) F[t] = 0.0;
-        __syncwarp();
-        if (lane < n) {
-            const double x = xs[lane];
-            if (lane == 0) {
-                F[0] = fma(K.b[m], x, K.b[m - 1]);
-            } else {
-                F[lane] = F[lane * ns] = K.b[m] * x;
-                F[lane * ns + lane] = fma(K.b[m], ds[lane], K.b[m - 1]);
-            }
-        }
-        __syncwarp();
+        dx_wpc_taylor_init(lane, n, ns, m, K, V, F);
         for (int j = m - 2; j >= 0; j--) {
-            const double bj = K.b[j];
-            // G_ij = F_i0 X_0j + F_ij X_jj (+ b_j on the diagonal), i <= j, (i,j) != (0,0)
-            for (int t = lane; t < n_hp; t += 32) {
-                const int p = hp[t], i = p >> 8, jj = p & 255;
-                double acc = fma(F[i * ns], xs[jj], i == jj ? bj : 0.0);
-                acc = fma(F[i * ns + jj], ds[jj], acc);
-                G[i * ns + jj] = acc;
-                G[jj * ns + i] = acc;
-            }
-            // G_00 = sum_k F_0k X_k0 + b_j
-            double part = lane < n ? F[lane] * xs[lane] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(DX_FULL, part, o);
-            if (lane == 0) G[0] = part + bj;
+            dx_wpc_horner_step(lane, n, ns, n_hp, hp, V, K.b[j], F, G);
             __syncwarp();
             double *tmp = F; F = G; G = tmp;
         }
-
-        // ---------------- restore: E_ii = 1 - tau_i sum_{k != i} E_ik sigma_k
-        if (lane < n) {
-            double acc = 0.0;
-            for (int q = 0; q < n - 1; q++) {
-                const int k = q + (q >= lane);
-                acc = fma(F[lane * ns + k], sig[k], acc);
-            }
-            F[lane * ns + lane] = fma(-tau[lane], acc, 1.0);
-        }
+        dx_wpc_restore(lane, n, ns, V, F);
         __syncwarp();
 
-        // ---------------- s squarings (Eq. ExpEq1 with n = 2^s)
-        for (int it = 0; it < s; it++) {
-            for (int t = lane; t < n_od; t += 32) {
-                const int p = od[t], i = p >> 8, jj = p & 255;
-                const double *ri = F + i * ns, *rj = F + jj * ns;
-                double acc = 0.0;
-                for (int k = 0; k < n; k++) acc = fma(ri[k], rj[k], acc);
-                G[i * ns + jj] = acc;
-                G[jj * ns + i] = acc;
-            }
+        // s squarings (Eq. ExpEq1 with n = 2^s), row sums restored each time
+        for (int it = 0; it < L.s; it++) {
+            dx_wpc_square_offdiag(lane, n, ns, n_od, od, F, G);
             __syncwarp();
-            if (lane < n) {
-                double acc = 0.0;
-                for (int q = 0; q < n - 1; q++) {
-                    const int k = q + (q >= lane);
-                    acc = fma(G[lane * ns + k], sig[k], acc);
-                }
-                G[lane * ns + lane] = fma(-tau[lane], acc, 1.0);
-            }
+            dx_wpc_restore(lane, n, ns, V, G);
             __syncwarp();
             double *tmp = F; F = G; G = tmp;
         }
 
-        // ---------------- apply: v_out_i = E_ii v_i + tau_i sum_{j != i} E_ij sigma_j v_j
+        // v_out_i = E_ii v_i + tau_i sum_{j != i} E_ij sigma_j v_j  (P = D_sigma^-1 E D_sigma)
         if (lane < n) {
 #pragma unroll
             for (int d = 0; d < 3; d++) {
-                yv[d * DX_NMAXF + lane] = sg * vin[d];
+                yv[d * DX_NMAXF + lane] = L.sg * vin[d];
                 vv[d * DX_NMAXF + lane] = vin[d];
             }
         }
@@ -223,7 +127,7 @@ dx_forward_wpc(FwdArgs a, DxConsts K) {
                 const int k = q + (q >= i);
                 acc = fma(F[i * ns + k], y[k], acc);
             }
-            a.v_out[((long long)d * n + i) * C + c] = fma(tau[i], acc, F[i * ns + i] * vv[d * DX_NMAXF + i]);
+            a.v_out[((long long)d * n + i) * C + c] = fma(V.tau[i], acc, F[i * ns + i] * vv[d * DX_NMAXF + i]);
         }
         __syncwarp();
     }

@@ -1,0 +1,157 @@
+// Warp-per-cell building blocks shared by the forward and adjoint kernels.
+//
+// One warp owns one cell. Matrices are n x n (n = N + 1 <= 32), stored row
+// major in shared memory with an odd row stride. Work inside a phase is split
+// into independent "tasks" (one output entry each) dealt round-robin to the
+// 32 lanes; __syncwarp() separates dependent phases.
+//
+// Symmetric similarity form. With D = diag(rho) and sigma_f = sqrt(rho_f/rho_g)
+// (sigma_0 = 1, sigma_i = sqrt(eps_i)), S = D_sigma A D_sigma^-1 is a symmetric
+// arrowhead for A = dt Omega_v (velocity form of Eq. jacobian):
+//   S_00 = A_00 = -sum_i eps_i alpha_i dt, S_0i = S_i0 = sigma_i alpha_i dt,
+//   S_ii = -alpha_i dt,
+// S sigma = 0, and E = exp(S) = D_sigma exp(A) D_sigma^-1 is symmetric with
+// E sigma = sigma.
+#pragma once
+
+#include "dx_common.cuh"
+
+constexpr int kPairSlots = 544;   // >= n(n+1)/2 for n <= 32
+
+// Row stride of the shared-memory matrices: odd, to spread banks.
+__host__ __device__ __forceinline__ int dx_stride(int n) { return n | 1; }
+
+// Block-wide pair tables: od[t] = (i<<8)|j, i<j (t < n(n-1)/2);
+// hp[t] = (i<<8)|j, i<=j, (i,j) != (0,0) (t < n(n+1)/2 - 1).
+__device__ __forceinline__ void dx_build_pairs(int n, unsigned short *od, unsigned short *hp) {
+    const int n_od = n * (n - 1) / 2, n_hp = n * (n + 1) / 2 - 1;
+    for (int t = threadIdx.x; t < n_od; t += blockDim.x) {
+        int i = 0, r = t;
+        while (r >= n - 1 - i) { r -= n - 1 - i; i++; }
+        od[t] = (unsigned short)((i << 8) | (i + 1 + r));
+    }
+    for (int t = threadIdx.x; t < n_hp; t += blockDim.x) {
+        int i = 0, r = t + 1;
+        while (r >= n - i) { r -= n - i; i++; }
+        hp[t] = (unsigned short)((i << 8) | (i + r));
+    }
+}
+
+// Per-cell vectors of the symmetric form, kept in shared memory.
+struct DxVecs {
+    double *sig;   // sigma_f
+    double *tau;   // 1 / sigma_f
+    double *xs;    // xs[0] = X_00, xs[f] = X_0f (f >= 1)
+    double *ds;    // ds[f] = X_ff (f >= 1)
+};
+
+// Lane-resident cell quantities after set-up (lane f = fluid f; species i on lane i).
+struct DxLane {
+    double eps, alpha;   // eps_i, alpha_i on species lanes, 0 elsewhere
+    double sg, tu;       // sigma_f, 1/sigma_f on lanes f < n
+    int k, s;            // k*, s* (warp uniform)
+};
+
+// Set-up of one cell: A = dt Omega_v entries, the 1-norm (summed in ascending
+// species order, as the oracle does, so (k*, s*) are reproducible), Algorithm 2,
+// and the scaled symmetric arrowhead X = 2^-s* S. Returns false (warp uniform)
+// when the cell's data are invalid.
+__device__ __forceinline__ bool dx_wpc_setup(int lane, int N, double rg, double rd, double ts, double dt,
+                                             const DxConsts &K, const DxVecs &V, DxLane &L) {
+    const int n = N + 1;
+    const bool okl = (lane == 0 || lane > N) || (dx_nonneg_finite(rd) && dx_pos_or_inf(ts));
+    const bool ok = __all_sync(DX_FULL, okl) && dx_pos_finite(rg);
+    if (!ok) return false;
+    const bool sp = lane >= 1 && lane <= N;
+    const double eps = sp ? __ddiv_rn(rd, rg) : 0.0;          // Eq. DragEqVar2
+    const double alpha = sp ? __ddiv_rn(1.0, ts) : 0.0;       // Eq. DragEqVar3
+    const double a0i = __dmul_rn(__dmul_rn(eps, alpha), dt);  // A_0i
+    const double ai0 = __dmul_rn(alpha, dt);                  // A_i0 = -A_ii
+    double s1 = 0.0;
+    for (int i = 1; i <= N; i++) s1 = __dadd_rn(s1, dx_shfl(a0i, i));
+    double col0 = s1;
+    for (int i = 1; i <= N; i++) col0 = __dadd_rn(col0, dx_shfl(ai0, i));
+    const double colj = sp ? __dadd_rn(a0i, ai0) : 0.0;
+    long long nb = dx_warp_max_ll(dx_bits(colj));
+    nb = nb > dx_bits(col0) ? nb : dx_bits(col0);
+    dx_select(__longlong_as_double(nb), K, L.k, L.s);
+    const double p2 = dx_pow2(-L.s);
+    double sg = 1.0, tu = 1.0;
+    if (sp) {
+        const double e = dx_bits(eps) < dx_bits(DX_EPS_FLOOR) ? DX_EPS_FLOOR : eps;
+        sg = __dsqrt_rn(e);
+        tu = __ddiv_rn(1.0, sg);
+    }
+    if (lane < n) {
+        V.sig[lane] = sg;
+        V.tau[lane] = tu;
+        V.xs[lane] = lane == 0 ? -s1 * p2 : __dmul_rn(__dmul_rn(sg, alpha), dt * p2);
+        V.ds[lane] = -(ai0 * p2);
+    }
+    L.eps = eps;
+    L.alpha = alpha;
+    L.sg = sg;
+    L.tu = tu;
+    __syncwarp();
+    return true;
+}
+
+// F = b_m X + b_{m-1} I (arrowhead), written into a zeroed n x n buffer.
+__device__ __forceinline__ void dx_wpc_taylor_init(int lane, int n, int ns, int m, const DxConsts &K,
+                                                   const DxVecs &V, double *F) {
+    for (int t = lane; t < n * ns; t += 32) F[t] = 0.0;
+    __syncwarp();
+    if (lane < n) {
+        const double x = V.xs[lane];
+        if (lane == 0) {
+            F[0] = fma(K.b[m], x, K.b[m - 1]);
+        } else {
+            F[lane] = F[lane * ns] = K.b[m] * x;
+            F[lane * ns + lane] = fma(K.b[m], V.ds[lane], K.b[m - 1]);
+        }
+    }
+    __syncwarp();
+}
+
+// One Horner step G = F X + bj I (F, G symmetric; X the arrowhead):
+//   G_ij = F_i0 X_0j + F_ij X_jj (+ bj if i == j) for i <= j, (i,j) != (0,0),
+//   G_00 = sum_k F_0k X_k0 + bj.
+__device__ __forceinline__ void dx_wpc_horner_step(int lane, int n, int ns, int n_hp, const unsigned short *hp,
+                                                   const DxVecs &V, double bj, const double *F, double *G) {
+    for (int t = lane; t < n_hp; t += 32) {
+        const int p = hp[t], i = p >> 8, jj = p & 255;
+        double acc = fma(F[i * ns], V.xs[jj], i == jj ? bj : 0.0);
+        acc = fma(F[i * ns + jj], V.ds[jj], acc);
+        G[i * ns + jj] = acc;
+        G[jj * ns + i] = acc;
+    }
+    double part = lane < n ? F[lane] * V.xs[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(DX_FULL, part, o);
+    if (lane == 0) G[0] = part + bj;
+}
+
+// Row-sum restoration in symmetric form: E_ii = 1 - tau_i sum_{k != i} E_ik sigma_k.
+__device__ __forceinline__ void dx_wpc_restore(int lane, int n, int ns, const DxVecs &V, double *E) {
+    if (lane < n) {
+        double acc = 0.0;
+        for (int q = 0; q < n - 1; q++) {
+            const int k = q + (q >= lane);
+            acc = fma(E[lane * ns + k], V.sig[k], acc);
+        }
+        E[lane * ns + lane] = fma(-V.tau[lane], acc, 1.0);
+    }
+}
+
+// Strict upper triangle of E^2 (symmetric), mirrored: G_ij = G_ji = sum_k E_ik E_jk.
+__device__ __forceinline__ void dx_wpc_square_offdiag(int lane, int n, int ns, int n_od, const unsigned short *od,
+                                                      const double *E, double *G) {
+    for (int t = lane; t < n_od; t += 32) {
+        const int p = od[t], i = p >> 8, jj = p & 255;
+        const double *ri = E + i * ns, *rj = E + jj * ns;
+        double acc = 0.0;
+        for (int k = 0; k < n; k++) acc = fma(ri[k], rj[k], acc);
+        G[i * ns + jj] = acc;
+        G[jj * ns + i] = acc;
+    }
+}

@@ -33,7 +33,7 @@ def declared_functions():
 
 def test_header_declares_entry_points():
     names = declared_functions()
-    for must in ("drag_expm_apply", "drag_expm_select", "drag_expm_get_status", "drag_expm_theta",
+    for must in ("drag_expm_apply", "drag_expm_backward", "drag_expm_select", "drag_expm_get_status", "drag_expm_theta",
                  "drag_expm_strerror", "drag_expm_version"):
         assert must in names
 
@@ -84,6 +84,12 @@ def test_host_argument_errors(lib):
     assert sel(-5, 4, good, good, good, 1.0, good, good, s) == -1
     assert sel(10, 4, good, null, good, 1.0, good, good, s) == -2
     assert lib.drag_expm_get_status(s, None) == -2
+    bwd = lib.drag_expm_backward
+    assert bwd(-1, 4, good, good, good, 1.0, good, good, null, null, null, null, s) == -1
+    assert bwd(10, 40, good, good, good, 1.0, good, good, null, null, null, null, s) == -1
+    assert bwd(10, 4, good, good, good, 1.0, good, null, null, null, null, null, s) == -2
+    assert bwd(10, 4, good, good, good, 1.0, good, good, bad_align, null, null, null, s) == -3
+    assert bwd(0, 4, null, null, null, 1.0, null, null, null, null, null, null, s) == 0
 
 
 def test_binding_fails_loudly_without_library(tmp_path):

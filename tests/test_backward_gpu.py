@@ -1,0 +1,183 @@
+"""GPU adjoint (drag_expm_backward through the C ABI) against the oracle's
+adjoint and against central finite differences of the GPU forward.
+
+Tolerances:
+* dL/dv_in = P^T g: per component, |gpu - oracle| <= 1e-13 * sum_f |g_{d,f}|
+  (the 1-norm bounds |P^T g| since P is row-stochastic);
+* parameter gradients, in log-derivative units x dL/dx, against the cell's
+  loss scale S = sum_{d,f} |g_{d,f}| max_f' |v_{d,f'}|:
+  |x (gpu - oracle)| <= 1e-13 S. Both implementations drop the stationary
+  block of the Frechet direction (it cancels in every parameter gradient) and
+  then sit within ~5e-15 S of a 50-digit truth even at dt/t_s = 1e8 (the
+  oracle's pins), so 1e-13 S bounds their difference with margin;
+* finite differences: the spec bar, 1e-6 relative (see
+  tests/test_oracle_adjoint_pins.py for the exact criterion and its noise floor).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_25347_gb300 import workloads as W
+from tests.test_oracle_adjoint_pins import assert_fd_agreement, finite_difference_gradients, loss_scale
+
+pytestmark = pytest.mark.gpu
+TOL_V = 1e-13
+TOL_P = 1e-13
+
+
+@pytest.fixture(scope="module")
+def dx():
+    import torch  # noqa: F401
+    from paper_2509_25347_gb300 import build
+    build.build()
+    import paper_2509_25347_gb300 as m
+    m.load_library()
+    m.get_status()
+    return m
+
+
+def t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_backward(dx, cells, g):
+    out = dx.backward(t(cells.rho_g), t(cells.rho_d), t(cells.t_s), cells.dt, t(cells.v), t(g))
+    return [o.cpu().numpy() for o in out]
+
+
+def assert_adjoint_parity(cells, g, got, ref):
+    gv, grg, grd, gts = got
+    rv, rrg, rrd, rts = ref
+    gsc = np.abs(g).sum(axis=1, keepdims=True)
+    assert np.all(np.isfinite(gv)) and np.all(np.isfinite(grd)) and np.all(np.isfinite(gts))
+    ev = np.max(np.abs(gv - rv) / gsc)
+    assert ev <= TOL_V, ev
+    S = np.array([loss_scale(g[:, :, c], cells.v[:, :, c]) for c in range(cells.ncells)])
+    erd = np.max(np.abs(cells.rho_d * (grd - rrd)) / S[None, :])
+    ets = np.max(np.abs(cells.t_s * (gts - rts)) / S[None, :])
+    erg = np.max(np.abs(cells.rho_g * (grg - rrg)) / S)
+    assert erd <= TOL_P and ets <= TOL_P and erg <= TOL_P, (erd, ets, erg)
+    return ev, erd, ets, erg
+
+
+CASES = [("dustybox_n1_32k", 1001), ("mrn_n4_128cube", 513), ("mrn_n8_128cube_adjoint", 385),
+         ("mrn_n16_128cube", 97)]
+
+
+@pytest.mark.parametrize("name,C", CASES)
+def test_backward_parity_small(dx, name, C):
+    cells = W.workload(name, ncells=C)
+    g = np.random.default_rng(17).standard_normal(cells.v.shape)
+    got = gpu_backward(dx, cells, g)
+    rv, rrg, rrd, rts, _ = oracle.drag_backward(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, g)
+    assert_adjoint_parity(cells, g, got, (rv, rrg, rrd, rts))
+    assert dx.get_status() == 0
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 7, 9, 12, 15, 20, 24, 31])
+def test_backward_every_size(dx, N):
+    cells = W.mrn(45 + N, N, seed=300 + N, stiff_lo=-4.0, stiff_hi=8.0)
+    g = np.random.default_rng(N).standard_normal(cells.v.shape)
+    got = gpu_backward(dx, cells, g)
+    rv, rrg, rrd, rts, _ = oracle.drag_backward(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, g)
+    assert_adjoint_parity(cells, g, got, (rv, rrg, rrd, rts))
+
+
+def test_backward_finite_differences_64_cells(dx):
+    """The N=8 adjoint workload: loss 0.5 ||v_out - v_target||^2 with
+    v_target ~ N(0,1); adjoint gradients with respect to v_in, rho_d, t_s on 64
+    random cells against central differences of the GPU forward (1e-6 relative)."""
+    cells = W.workload("mrn_n8_128cube_adjoint", ncells=8192)
+    target = W.adjoint_target(cells.ncells, cells.nspecies)
+    idx = np.sort(np.random.default_rng(1234).choice(cells.ncells, 64, replace=False))
+    sub = cells.subset(idx)
+    vt = target[:, :, idx]
+
+    def fwd(c):
+        return dx.apply(t(c.rho_g), t(c.rho_d), t(c.t_s), c.dt, t(c.v)).cpu().numpy()
+
+    g = fwd(sub) - vt
+    gv, _, grd, gts = gpu_backward(dx, sub, g)
+    gv_fd, grd_fd, gts_fd = finite_difference_gradients(fwd, sub, vt)
+    assert_fd_agreement(sub, g, gv, grd, gts, gv_fd, grd_fd, gts_fd)
+
+
+def test_autograd_function(dx):
+    """torch.autograd through DragExpm gives the same gradients as the raw entry point."""
+    import torch
+    cells = W.workload("mrn_n4_128cube", ncells=300)
+    target = t(W.adjoint_target(cells.ncells, cells.nspecies))
+    rg = t(cells.rho_g).requires_grad_(True)
+    rd = t(cells.rho_d).requires_grad_(True)
+    ts = t(cells.t_s).requires_grad_(True)
+    v = t(cells.v).requires_grad_(True)
+    out = dx.DragExpm.apply(rg, rd, ts, cells.dt, v)
+    loss = 0.5 * ((out - target) ** 2).sum()
+    loss.backward()
+    g = (out - target).detach()
+    gv, grg, grd, gts = dx.backward(rg.detach(), rd.detach(), ts.detach(), cells.dt, v.detach(), g)
+    assert torch.equal(v.grad, gv) and torch.equal(rd.grad, grd) and torch.equal(ts.grad, gts)
+    assert torch.equal(rg.grad, grg)
+
+
+def test_autograd_fit_stopping_times(dx):
+    """Gradient descent on log t_s through the adjoint recovers stopping times
+    from observed velocities (the fitting use of the adjoint)."""
+    import torch
+    rng = np.random.default_rng(5)
+    C, N = 256, 3
+    cells = W.mrn(C, N, seed=77, stiff_lo=-1.0, stiff_hi=4.0)
+    true_ts = t(cells.t_s)
+    obs = dx.apply(t(cells.rho_g), t(cells.rho_d), true_ts, cells.dt, t(cells.v))
+    log_ts = (torch.log(true_ts) + torch.from_numpy(rng.uniform(-0.3, 0.3, (N, C))).cuda()).requires_grad_(True)
+    opt = torch.optim.Adam([log_ts], lr=0.05)
+    first = None
+    for it in range(150):
+        opt.zero_grad()
+        out = dx.DragExpm.apply(t(cells.rho_g), t(cells.rho_d), torch.exp(log_ts), cells.dt, t(cells.v))
+        loss = ((out - obs) ** 2).sum()
+        loss.backward()
+        opt.step()
+        first = float(loss.detach()) if first is None else first
+    assert float(loss.detach()) < 1e-3 * first
+
+
+def test_backward_partial_outputs_and_invalid(dx):
+    import torch
+    cells = W.workload("mrn_n4_128cube", ncells=64)
+    cells.t_s[2, 5] = -1.0
+    g = np.random.default_rng(2).standard_normal(cells.v.shape)
+    gv, grg, grd, gts = dx.backward(t(cells.rho_g), t(cells.rho_d), t(cells.t_s), cells.dt, t(cells.v), t(g),
+                                    need_v_in=False, need_rho_g=False)
+    assert gv is None and grg is None
+    grd, gts = grd.cpu().numpy(), gts.cpu().numpy()
+    assert np.all(np.isnan(grd[:, 5])) and np.all(np.isnan(gts[:, 5]))
+    assert dx.get_status() & dx.STATUS_BAD_CELL
+    good = [c for c in range(64) if c != 5]
+    sub = cells.subset(good)
+    rv, rrg, rrd, rts, _ = oracle.drag_backward(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v, g[:, :, good])
+    S = np.array([loss_scale(g[:, :, c], cells.v[:, :, c]) for c in good])
+    assert np.max(np.abs(sub.rho_d * (grd[:, good] - rrd)) / S) <= TOL_P
+
+
+@pytest.mark.parametrize("name", ["mrn_n8_128cube_adjoint"])
+def test_backward_full_size_sampled(dx, name):
+    """Full-size adjoint workload in the benchmark's launch configuration;
+    128 sampled cells against the oracle's adjoint."""
+    import torch
+    cells = W.workload(name)
+    target = W.adjoint_target(cells.ncells, cells.nspecies)
+    rg, rd, ts, v = t(cells.rho_g), t(cells.rho_d), t(cells.t_s), t(cells.v)
+    out = dx.apply(rg, rd, ts, cells.dt, v)
+    g = out - t(target)
+    gv, grg, grd, gts = dx.backward(rg, rd, ts, cells.dt, v, g)
+    torch.cuda.synchronize()
+    assert dx.get_status() == 0
+    idx = np.unique(np.concatenate([np.random.default_rng(3).integers(0, cells.ncells, 126), [0, cells.ncells - 1]]))
+    sub = cells.subset(idx)
+    ti = torch.from_numpy(idx).cuda()
+    gs = g[:, :, ti].cpu().numpy()
+    ref = oracle.drag_backward(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v, gs)[:4]
+    got = (gv[:, :, ti].cpu().numpy(), grg[ti].cpu().numpy(), grd[:, ti].cpu().numpy(), gts[:, ti].cpu().numpy())
+    assert_adjoint_parity(sub, gs, got, ref)
