@@ -119,6 +119,59 @@ int drag_expm_backward(int64_t ncells, int32_t nspecies, const double *rho_g, co
                        cudaStream_t stream);
 
 /*
+ * Batched drag update over AMR-like blocks. Block b holds ncells cells that
+ * share nspecies N and time step dt. Its data live in slabs of the caller's
+ * arrays, each laid out like a plain call with C = ncells:
+ *   rho_g[cell_offset + c]
+ *   rho_d[dust_offset + i*ncells + c],  t_s[dust_offset + i*ncells + c]
+ *   v_in/v_out[vel_offset + (d*(N+1) + f)*ncells + c]
+ * Blocks must not overlap. 40 bytes, 8-byte aligned.
+ */
+typedef struct drag_block {
+    int64_t cell_offset;
+    int64_t dust_offset;
+    int64_t vel_offset;
+    int32_t ncells;
+    int32_t nspecies;
+    double dt;
+} drag_block_t;
+
+/*
+ * drag_expm_batched_workspace_bytes — scratch bytes drag_expm_apply_batched
+ * needs for nblocks blocks over arrays of total_cells gas cells (about
+ * 12 bytes per cell plus 300 KB). Host only, no CUDA call.
+ */
+size_t drag_expm_batched_workspace_bytes(int64_t nblocks, int64_t total_cells);
+
+/*
+ * drag_expm_apply_batched — forward drag update (Eq. ExacSolEqu, Algorithm 6
+ * with Algorithm 2) of every cell of every block in one pass. Cells are
+ * binned by (N, k*, s*) on the device and processed by one persistent kernel,
+ * so cells with different N and dt (hence different Taylor order and squaring
+ * count) share the GPU without idle lanes. Results per cell equal those of
+ * drag_expm_apply on the same cell (same arithmetic).
+ *   nblocks     : number of descriptors (0 is a no-op).
+ *   blocks      : DEVICE array of nblocks drag_block_t (read only).
+ *   total_cells, rho_d_len, v_len : lengths (in doubles) of rho_g, of rho_d
+ *                 and t_s, and of v_in/v_out; blocks outside them are skipped
+ *                 and set DRAG_STATUS_BAD_BLOCK, as are blocks with bad N or dt.
+ *   nspecies_max: upper bound on the blocks' N (sizes the shared memory).
+ *   rho_g, rho_d, t_s, v_in : DEVICE inputs; v_out : DEVICE output (may equal v_in).
+ *   workspace   : DEVICE scratch of at least drag_expm_batched_workspace_bytes()
+ *                 bytes, 256-byte aligned, caller-owned; contents are
+ *                 overwritten. Must not be shared by calls in flight at once.
+ * All work is queued on `stream` with no host synchronisation and no
+ * allocation, so the call can be captured in a CUDA graph. Blocks with N
+ * above nspecies_max are processed with too little shared memory: don't.
+ * Returns DRAG_OK or DRAG_EBLOCKS / DRAG_EINVAL_SIZE / DRAG_ENULL /
+ * DRAG_EALIGN / DRAG_EWORKSPACE / DRAG_ECUDA (nothing launched on error).
+ */
+int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *blocks, int64_t total_cells, int64_t rho_d_len,
+                            int64_t v_len, int32_t nspecies_max, const double *rho_g, const double *rho_d,
+                            const double *t_s, const double *v_in, double *v_out, void *workspace,
+                            size_t workspace_bytes, cudaStream_t stream);
+
+/*
  * drag_expm_get_status — copy the current device's sticky status bits
  * (DRAG_STATUS_*) into *status_out and clear them. Synchronises `stream`.
  */

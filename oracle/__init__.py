@@ -63,6 +63,11 @@ def _load():
                                       dp, ctypes.POINTER(ctypes.c_uint32)]
     lib.orc_frechet_dense.restype = ctypes.c_int
     lib.orc_frechet_dense.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int]
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    lib.orc_drag_apply_batched.restype = ctypes.c_int
+    lib.orc_drag_apply_batched.argtypes = [ctypes.c_int64, i64p, i64p, i64p, i32p, i32p, dp, dp, dp, dp, dp, dp,
+                                           ctypes.POINTER(ctypes.c_uint32)]
     for name in ("orc_table_mk", "orc_table_qk", "orc_table_rk"):
         getattr(lib, name).restype = ctypes.c_int
         getattr(lib, name).argtypes = [ctypes.c_int]
@@ -188,3 +193,28 @@ def drag_backward(rho_g, rho_d, t_s, dt, v_in, grad_v_out):
     if rc != 0:
         raise ValueError(f"oracle rejected sizes (rc={rc})")
     return gv, grg, grd, gts, st.value
+
+
+def drag_apply_batched(desc, rho_g, rho_d, t_s, v_in):
+    """Batched forward over packed block slabs.
+
+    desc: structured array with fields cell_offset, dust_offset, vel_offset
+    (int64), ncells, nspecies (int32), dt (float64). Returns (v_out, status).
+    """
+    f = lambda name, dt_: np.ascontiguousarray(desc[name], dtype=dt_)
+    co, do, vo = f("cell_offset", np.int64), f("dust_offset", np.int64), f("vel_offset", np.int64)
+    nc, ns, dts = f("ncells", np.int32), f("nspecies", np.int32), f("dt", np.float64)
+    rho_g = np.ascontiguousarray(rho_g, dtype=np.float64)
+    rho_d = np.ascontiguousarray(rho_d, dtype=np.float64)
+    t_s = np.ascontiguousarray(t_s, dtype=np.float64)
+    v_in = np.ascontiguousarray(v_in, dtype=np.float64)
+    v_out = v_in.copy()
+    st = ctypes.c_uint32(0)
+    p64 = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    p32 = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    rc = _load().orc_drag_apply_batched(len(desc), p64(co), p64(do), p64(vo), p32(nc), p32(ns), _dptr(dts),
+                                        _dptr(rho_g), _dptr(rho_d), _dptr(t_s), _dptr(v_in), _dptr(v_out),
+                                        ctypes.byref(st))
+    if rc != 0:
+        raise ValueError(f"oracle rejected a block (rc={rc})")
+    return v_out, st.value

@@ -544,6 +544,25 @@ int orc_drag_backward(int64_t C, int N, const double *rho_g, const double *rho_d
     return 0;
 }
 
+/* Batched forward: block b holds ncells[b] cells with nspecies[b] species and
+ * time step dt[b]; its gas densities start at rho_g[cell_offset[b]], its dust
+ * arrays at rho_d/t_s[dust_offset[b]] (species-major slab of N*ncells) and its
+ * velocities at v[vel_offset[b]] (slab of 3*(N+1)*ncells). Each block is an
+ * independent plain update (the drag step is cell local). */
+int orc_drag_apply_batched(int64_t nblocks, const int64_t *cell_offset, const int64_t *dust_offset,
+                           const int64_t *vel_offset, const int32_t *ncells, const int32_t *nspecies, const double *dt,
+                           const double *rho_g, const double *rho_d, const double *t_s, const double *v_in,
+                           double *v_out, uint32_t *status)
+{
+    for (int64_t b = 0; b < nblocks; b++) {
+        int rc = orc_drag_apply(ncells[b], nspecies[b], rho_g + cell_offset[b], rho_d + dust_offset[b],
+                                t_s + dust_offset[b], dt[b], v_in + vel_offset[b], v_out + vel_offset[b], 1, NULL,
+                                NULL, status);
+        if (rc != 0) return rc;
+    }
+    return 0;
+}
+
 /* Z = L(A^T, G) for one dense n x n pair (tests of the Frechet machinery).
  * structured != 0 only for A with zero row sums (column sums of exp(A^T) = 1). */
 int orc_frechet_dense(int n, const double *A, const double *G, double *Z, int structured)

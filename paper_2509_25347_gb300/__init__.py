@@ -13,7 +13,8 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["load_library", "apply", "backward", "select", "get_status", "theta", "DragExpm", "DragExpmError",
+__all__ = ["load_library", "apply", "backward", "apply_batched", "batched_workspace_bytes", "select", "get_status",
+           "theta", "DragExpm", "DragExpmError",
            "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -45,6 +46,10 @@ def load_library(path: str | None = None):
     lib.drag_expm_apply.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp]
     lib.drag_expm_backward.restype = ctypes.c_int
     lib.drag_expm_backward.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp, vp, vp, vp, vp]
+    lib.drag_expm_batched_workspace_bytes.restype = ctypes.c_size_t
+    lib.drag_expm_batched_workspace_bytes.argtypes = [i64, i64]
+    lib.drag_expm_apply_batched.restype = ctypes.c_int
+    lib.drag_expm_apply_batched.argtypes = [i64, vp, i64, i64, i64, i32, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     lib.drag_expm_select.restype = ctypes.c_int
     lib.drag_expm_select.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp]
     lib.drag_expm_get_status.restype = ctypes.c_int
@@ -173,6 +178,61 @@ class _LazyFunction:
 
 
 DragExpm = _LazyFunction()
+
+
+BLOCK_BYTES = 40   # sizeof(drag_block_t)
+
+
+def batched_workspace_bytes(nblocks: int, total_cells: int) -> int:
+    """Scratch bytes :func:`apply_batched` needs."""
+    return int(load_library().drag_expm_batched_workspace_bytes(int(nblocks), int(total_cells)))
+
+
+def _flat_f64(name, t):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise DragExpmError(f"{name} must be a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr()), t.numel()
+
+
+def apply_batched(blocks, rho_g, rho_d, t_s, v_in, v_out=None, nspecies_max=None, workspace=None, stream=None):
+    """Batched forward update over block slabs (drag_expm_apply_batched).
+
+    ``blocks``: a CUDA uint8 tensor of nblocks*40 bytes holding drag_block_t
+    records (with ``nspecies_max`` given), or a host numpy array of the
+    ``workloads.BLOCK_DTYPE`` record type (uploaded here). The arrays are flat
+    float64 CUDA tensors. ``workspace`` (uint8 CUDA tensor) is allocated if
+    not given. Returns v_out.
+    """
+    import numpy as np
+    import torch
+    if isinstance(blocks, np.ndarray):
+        if nspecies_max is None:
+            nspecies_max = int(blocks["nspecies"].max()) if len(blocks) else 1
+        blocks = torch.from_numpy(np.ascontiguousarray(blocks).view(np.uint8).copy()).to(rho_g.device)
+    if nspecies_max is None:
+        raise DragExpmError("nspecies_max is required when blocks are already on the device")
+    if not isinstance(blocks, torch.Tensor) or blocks.dtype != torch.uint8 or not blocks.is_cuda or \
+            blocks.numel() % BLOCK_BYTES:
+        raise DragExpmError("blocks must be a CUDA uint8 tensor of drag_block_t records")
+    nblocks = blocks.numel() // BLOCK_BYTES
+    if v_out is None:
+        v_out = torch.empty_like(v_in)
+    prg, C = _flat_f64("rho_g", rho_g)
+    prd, nd = _flat_f64("rho_d", rho_d)
+    pts, nt = _flat_f64("t_s", t_s)
+    pvi, nv = _flat_f64("v_in", v_in)
+    pvo, nvo = _flat_f64("v_out", v_out)
+    if nt != nd or nvo != nv:
+        raise DragExpmError("t_s must match rho_d and v_out must match v_in in length")
+    need = batched_workspace_bytes(nblocks, C)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=rho_g.device)
+    _check(load_library().drag_expm_apply_batched(nblocks, ctypes.c_void_p(blocks.data_ptr()), C, nd, nv,
+                                                  int(nspecies_max), prg, prd, pts, pvi, pvo,
+                                                  ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                                  _stream_handle(stream)))
+    return v_out
 
 
 def select(rho_g, rho_d, t_s, dt: float, stream=None):

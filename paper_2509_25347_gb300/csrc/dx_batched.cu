@@ -1,0 +1,410 @@
+// Batched forward drag update over AMR-like blocks whose cells differ in
+// species count N and time step dt, hence in Taylor order m* and squaring
+// count s* (Algorithm 2). The drag step is cell local (Sec. 3.5: each cell
+// solves its own drag equation), so the batch is re-ordered freely:
+//
+//   1. prepare  (1 CTA)  : validate descriptors, prefix-sum block sizes, clear counters;
+//   2. count    (grid)   : per cell, Algorithm 2 -> bin (n, k*, min(s*, 63)), histogram;
+//   3. bins     (1 CTA)  : prefix sums of bin counts and of work items per bin;
+//   4. scatter  (grid)   : cells -> bin-sorted permutation;
+//   5. main     (persistent grid) : warps pull work items from one atomic counter.
+//      An item is 32 cells of one bin run lane-per-cell (small n, the lanes
+//      of a warp share m* and s*, so no lane idles) or one cell run
+//      warp-per-cell (large n). The per-n choice comes from the mode table
+//      (drag_expm_autotune() measures it).
+//
+// Every launch goes to the caller's stream; there is no host synchronisation
+// and no allocation (scratch is the caller's workspace), so the whole call can
+// be captured in a CUDA graph and replayed.
+#include <cmath>
+
+#include "dx_lpc.cuh"
+#include "dx_modes.h"
+#include "dx_wpc.cuh"
+
+namespace {
+
+constexpr int kSBins = 64;
+constexpr int kBinsPerN = DX_K * kSBins;
+constexpr int kNBins = (DX_NMAXF - 1) * kBinsPerN;   // n = 2..32
+constexpr int kMainWarps = 2;                        // warps per CTA of the persistent kernel
+constexpr int kScanThreads = 1024;
+constexpr int kBatchLpcNMax = 9;                     // largest n run lane-per-cell in the batched kernel
+
+struct Desc {
+    long long cell_offset, dust_offset, vel_offset;
+    int ncells, nspecies;
+    double dt;
+};
+static_assert(sizeof(Desc) == sizeof(drag_block_t), "descriptor layout");
+
+struct Work {
+    unsigned long long *perm;   // (block << 32) | local cell, bin-sorted
+    unsigned int *key;          // bin of each enumerated cell
+    long long *blk_start;       // exclusive prefix of valid block sizes [nblocks + 1]
+    unsigned int *hist, *offs, *cursor, *item_offs;   // [kNBins + 1]
+    unsigned int *ctr;          // [0] work counter, [1] items, [2] enumerated cells
+};
+
+struct Modes {
+    int m[DX_NMAXF + 1];
+};
+
+__device__ __forceinline__ int bin_of(int n, int k, int s) {
+    return ((n - 2) * DX_K + (k - 1)) * kSBins + (s < kSBins - 1 ? s : kSBins - 1);
+}
+
+__device__ __forceinline__ bool desc_valid(const Desc &d, long long total_cells, long long rho_d_len, long long v_len) {
+    if (d.ncells < 0 || d.nspecies < 1 || d.nspecies > DRAG_EXPM_NMAX) return false;
+    const long long b = __double_as_longlong(d.dt);
+    if (!((b & 0x7fffffffffffffffLL) == 0 || (b > 0 && b < 0x7ff0000000000000LL))) return false;   // dt >= 0 finite
+    const long long C = d.ncells, N = d.nspecies;
+    if (d.cell_offset < 0 || d.cell_offset + C > total_cells) return false;
+    if (d.dust_offset < 0 || d.dust_offset + N * C > rho_d_len) return false;
+    if (d.vel_offset < 0 || d.vel_offset + 3 * (N + 1) * C > v_len) return false;
+    return true;
+}
+
+// Block-wide exclusive scan of one value per thread (kScanThreads threads).
+template <typename T>
+__device__ T block_exclusive_scan(T v, T *sh, T &total) {
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int o = 1; o < kScanThreads; o <<= 1) {
+        T add = t >= o ? sh[t - o] : T(0);
+        __syncthreads();
+        sh[t] += add;
+        __syncthreads();
+    }
+    total = sh[kScanThreads - 1];
+    T ex = sh[t] - v;
+    __syncthreads();
+    return ex;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+dx_batch_prepare(long long nblocks, const Desc *blocks, long long total_cells, long long rho_d_len, long long v_len,
+                 Work W, uint32_t *status) {
+    __shared__ long long sh[kScanThreads];
+    const int t = threadIdx.x;
+    for (int i = t; i < kNBins; i += kScanThreads) W.hist[i] = 0;
+    if (t < 4) W.ctr[t] = 0;
+    const long long per = (nblocks + kScanThreads - 1) / kScanThreads;
+    const long long b0 = t * per, b1 = b0 + per < nblocks ? b0 + per : nblocks;
+    long long sum = 0;
+    bool bad = false;
+    for (long long b = b0; b < b1; b++) {
+        const Desc d = blocks[b];
+        const bool ok = desc_valid(d, total_cells, rho_d_len, v_len);
+        bad |= !ok;
+        sum += ok ? d.ncells : 0;
+    }
+    long long total;
+    long long run = block_exclusive_scan(sum, sh, total);
+    for (long long b = b0; b < b1; b++) {
+        W.blk_start[b] = run;
+        const Desc d = blocks[b];
+        run += desc_valid(d, total_cells, rho_d_len, v_len) ? d.ncells : 0;
+    }
+    if (t == 0) {
+        W.blk_start[nblocks] = total;
+        // non-overlapping valid blocks never hold more cells than rho_g
+        W.ctr[2] = (unsigned int)(total < total_cells ? total : total_cells);
+        if (total > total_cells) bad = true;
+    }
+    if (bad) atomicOr(status, DRAG_STATUS_BAD_BLOCK);
+}
+
+// Block b with blk_start[b] <= g < blk_start[b + 1] (blocks of size 0 are skipped).
+__device__ __forceinline__ long long find_block(const long long *bs, long long nblocks, long long g) {
+    long long lo = 0, hi = nblocks;   // invariant: bs[lo] <= g < bs[hi]
+    while (hi - lo > 1) {
+        const long long mid = (lo + hi) >> 1;
+        if (bs[mid] <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void dx_batch_count(long long nblocks, const Desc *blocks, const double *rho_g, const double *rho_d,
+                               const double *t_s, Work W, DxConsts K) {
+    const long long total = W.ctr[2];
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long b = find_block(W.blk_start, nblocks, g);
+        const Desc d = blocks[b];
+        const long long c = g - W.blk_start[b], C = d.ncells;
+        const int N = d.nspecies;
+        const double rg = rho_g[d.cell_offset + c];
+        const double *rd = rho_d + d.dust_offset + c, *ts = t_s + d.dust_offset + c;
+        bool ok = dx_pos_finite(rg);
+        for (int i = 0; i < N && ok; i++) ok = dx_nonneg_finite(rd[i * C]) && dx_pos_or_inf(ts[i * C]);
+        int kk = 1, s = 0;
+        if (ok) {
+            // 1-norm of A = dt Omega_v in ascending species order (as the apply kernels do)
+            double s1 = 0.0, ai0s[DRAG_EXPM_NMAX];
+            long long cmax = 0;
+            for (int i = 0; i < N; i++) {
+                const double eps = __ddiv_rn(rd[i * C], rg), alpha = __ddiv_rn(1.0, ts[i * C]);
+                const double a0i = __dmul_rn(__dmul_rn(eps, alpha), d.dt), ai0 = __dmul_rn(alpha, d.dt);
+                s1 = __dadd_rn(s1, a0i);
+                ai0s[i] = ai0;
+                const long long cb = dx_bits(__dadd_rn(a0i, ai0));
+                cmax = cb > cmax ? cb : cmax;
+            }
+            double col0 = s1;
+            for (int i = 0; i < N; i++) col0 = __dadd_rn(col0, ai0s[i]);
+            const long long nb = dx_bits(col0) > cmax ? dx_bits(col0) : cmax;
+            dx_select(__longlong_as_double(nb), K, kk, s);
+        }
+        const unsigned int key = (unsigned int)bin_of(N + 1, kk, s);
+        W.key[g] = key;
+        atomicAdd(&W.hist[key], 1u);
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) dx_batch_bins(Work W, Modes M) {
+    __shared__ long long sh[kScanThreads];
+    const int t = threadIdx.x;
+    constexpr int per = (kNBins + kScanThreads - 1) / kScanThreads;
+    const int i0 = t * per, i1 = i0 + per < kNBins ? i0 + per : kNBins;
+    long long cs = 0, is = 0;
+    for (int i = i0; i < i1; i++) {
+        const unsigned int c = W.hist[i];
+        const int n = i / kBinsPerN + 2;
+        cs += c;
+        is += (M.m[n] == DX_MODE_WPC) ? c : (c + 31) / 32;
+    }
+    long long ctot, itot;
+    long long crun = block_exclusive_scan(cs, sh, ctot);
+    long long irun = block_exclusive_scan(is, sh, itot);
+    for (int i = i0; i < i1; i++) {
+        const unsigned int c = W.hist[i];
+        const int n = i / kBinsPerN + 2;
+        W.offs[i] = (unsigned int)crun;
+        W.cursor[i] = (unsigned int)crun;
+        W.item_offs[i] = (unsigned int)irun;
+        crun += c;
+        irun += (M.m[n] == DX_MODE_WPC) ? c : (c + 31) / 32;
+    }
+    if (t == 0) {
+        W.offs[kNBins] = (unsigned int)ctot;
+        W.item_offs[kNBins] = (unsigned int)itot;
+        W.ctr[1] = (unsigned int)itot;
+    }
+}
+
+__global__ void dx_batch_scatter(long long nblocks, Work W) {
+    const long long total = W.ctr[2];
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long b = find_block(W.blk_start, nblocks, g);
+        const unsigned long long local = (unsigned long long)(g - W.blk_start[b]);
+        const unsigned int pos = atomicAdd(&W.cursor[W.key[g]], 1u);
+        W.perm[pos] = ((unsigned long long)b << 32) | local;
+    }
+}
+
+struct MainArgs {
+    const Desc *blocks;
+    const double *rho_g, *rho_d, *t_s, *v_in;
+    double *v_out;
+    uint32_t *status;
+    int warp_doubles;   // per-warp shared-memory slice (doubles)
+};
+
+template <int NF, bool SMEM>
+__device__ __forceinline__ void lpc_item(int lane, const MainArgs &a, const Desc &d, long long c, const DxConsts &K,
+                                         const double *bsh, double *wsm) {
+    const long long C = d.ncells;
+    dx_lpc_forward_cell<NF, SMEM>(lane, a.rho_g + d.cell_offset + c, a.rho_d + d.dust_offset + c,
+                                  a.t_s + d.dust_offset + c, a.v_in + d.vel_offset + c, a.v_out + d.vel_offset + c, C,
+                                  d.dt, K, bsh, wsm, a.status);
+}
+
+__device__ __forceinline__ void lpc_dispatch(int n, int mode, int lane, const MainArgs &a, const Desc &d, long long c,
+                                             const DxConsts &K, const double *bsh, double *wsm) {
+    const bool reg = mode == DX_MODE_LPC_REG;
+    switch (n) {
+        case 2: reg ? lpc_item<2, false>(lane, a, d, c, K, bsh, wsm) : lpc_item<2, true>(lane, a, d, c, K, bsh, wsm); break;
+        case 3: reg ? lpc_item<3, false>(lane, a, d, c, K, bsh, wsm) : lpc_item<3, true>(lane, a, d, c, K, bsh, wsm); break;
+        case 4: reg ? lpc_item<4, false>(lane, a, d, c, K, bsh, wsm) : lpc_item<4, true>(lane, a, d, c, K, bsh, wsm); break;
+        case 5: reg ? lpc_item<5, false>(lane, a, d, c, K, bsh, wsm) : lpc_item<5, true>(lane, a, d, c, K, bsh, wsm); break;
+        case 6: reg ? lpc_item<6, false>(lane, a, d, c, K, bsh, wsm) : lpc_item<6, true>(lane, a, d, c, K, bsh, wsm); break;
+        case 7: lpc_item<7, true>(lane, a, d, c, K, bsh, wsm); break;
+        case 8: lpc_item<8, true>(lane, a, d, c, K, bsh, wsm); break;
+        case 9: lpc_item<9, true>(lane, a, d, c, K, bsh, wsm); break;
+        default: break;
+    }
+}
+
+__global__ void __launch_bounds__(kMainWarps * 32)
+dx_batch_main(long long nblocks, MainArgs a, Work W, Modes M, DxConsts K) {
+    extern __shared__ double smem[];
+    double *bsh = smem;
+    for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double *wsm = smem + 32 + wib * (a.warp_doubles + 2 * kPairSlots / 4);
+    unsigned short *od = reinterpret_cast<unsigned short *>(wsm + a.warp_doubles);
+    unsigned short *hp = od + kPairSlots;
+    int table_n = 0;
+    const unsigned int nitems = W.ctr[1];
+    // Each iteration claims a fresh item, so a warp runs at most nitems + 1 of them.
+    for (unsigned int guard = 0;; guard++) {
+        if (guard > nitems) {
+            if (lane == 0) atomicOr(a.status, DRAG_STATUS_QUEUE_GUARD);
+            break;
+        }
+        unsigned int item = 0;
+        if (lane == 0) item = atomicAdd(&W.ctr[0], 1u);
+        item = __shfl_sync(DX_FULL, item, 0);
+        if (item >= nitems) break;
+        // bin holding this item: last bin with item_offs[bin] <= item
+        int lo = 0, hi = kNBins;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (W.item_offs[mid] <= item) lo = mid; else hi = mid;
+        }
+        const int bin = lo, n = bin / kBinsPerN + 2, mode = M.m[n];
+        const unsigned int sub = item - W.item_offs[bin];
+        if (mode == DX_MODE_WPC) {
+            const unsigned long long p = W.perm[W.offs[bin] + sub];
+            const Desc d = a.blocks[p >> 32];
+            const long long c = (long long)(p & 0xffffffffull);
+            if (table_n != n) {
+                dx_build_pairs_warp(lane, n, od, hp);
+                table_n = n;
+            }
+            dx_wpc_forward_cell(lane, d.nspecies, a.rho_g + d.cell_offset + c, a.rho_d + d.dust_offset + c,
+                                a.t_s + d.dust_offset + c, a.v_in + d.vel_offset + c, a.v_out + d.vel_offset + c,
+                                d.ncells, d.dt, K, wsm, od, hp, a.status);
+        } else {
+            const unsigned int pos = W.offs[bin] + 32 * sub + lane;
+            if (pos < W.offs[bin + 1]) {
+                const unsigned long long p = W.perm[pos];
+                const Desc d = a.blocks[p >> 32];
+                lpc_dispatch(n, mode, lane, a, d, (long long)(p & 0xffffffffull), K, bsh, wsm);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t perm, key, blk_start, hist, offs, cursor, item_offs, ctr, total;
+};
+
+Layout layout(long long nblocks, long long total_cells) {
+    Layout L;
+    size_t o = 0;
+    L.perm = o; o += align256(sizeof(unsigned long long) * (size_t)total_cells);
+    L.key = o; o += align256(sizeof(unsigned int) * (size_t)total_cells);
+    L.blk_start = o; o += align256(sizeof(long long) * (size_t)(nblocks + 1));
+    L.hist = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
+    L.offs = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
+    L.cursor = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
+    L.item_offs = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
+    L.ctr = o; o += align256(sizeof(unsigned int) * 8);
+    L.total = o;
+    return L;
+}
+
+// Per-warp shared memory (doubles) the main kernel needs for matrices up to n_max.
+int warp_doubles_for(const Modes &M, int n_max) {
+    int w = 0;
+    for (int n = 2; n <= n_max; n++) {
+        int need = 0;
+        if (M.m[n] == DX_MODE_WPC) need = dx_wpc_fwd_warp_doubles(n);
+        else if (M.m[n] == DX_MODE_LPC_SMEM) {
+            switch (n) {
+                case 2: need = dx_lpc_warp_smem_doubles<2>(); break;
+                case 3: need = dx_lpc_warp_smem_doubles<3>(); break;
+                case 4: need = dx_lpc_warp_smem_doubles<4>(); break;
+                case 5: need = dx_lpc_warp_smem_doubles<5>(); break;
+                case 6: need = dx_lpc_warp_smem_doubles<6>(); break;
+                case 7: need = dx_lpc_warp_smem_doubles<7>(); break;
+                case 8: need = dx_lpc_warp_smem_doubles<8>(); break;
+                case 9: need = dx_lpc_warp_smem_doubles<9>(); break;
+                default: break;
+            }
+        }
+        w = need > w ? need : w;
+    }
+    return w;
+}
+
+bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
+
+}  // namespace
+
+Modes dx_batch_modes() {
+    Modes M;
+    for (int n = 0; n <= DX_NMAXF; n++) {
+        int m = n >= 2 ? dx_mode_for(n) : DX_MODE_WPC;
+        if (m != DX_MODE_WPC && n > kBatchLpcNMax) m = DX_MODE_WPC;
+        M.m[n] = m;
+    }
+    return M;
+}
+
+extern "C" size_t drag_expm_batched_workspace_bytes(int64_t nblocks, int64_t total_cells) {
+    if (nblocks < 0 || total_cells < 0) return 0;
+    return layout(nblocks, total_cells).total;
+}
+
+extern "C" int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *blocks, int64_t total_cells, int64_t rho_d_len,
+                                       int64_t v_len, int32_t nspecies_max, const double *rho_g, const double *rho_d,
+                                       const double *t_s, const double *v_in, double *v_out, void *workspace,
+                                       size_t workspace_bytes, cudaStream_t stream) {
+    if (nblocks < 0 || nblocks > (1LL << 31) - 1) return DRAG_EBLOCKS;
+    if (total_cells < 0 || total_cells > (1LL << 32) - 1 || rho_d_len < 0 || v_len < 0) return DRAG_EINVAL_SIZE;
+    if (nspecies_max < 1 || nspecies_max > DRAG_EXPM_NMAX) return DRAG_EINVAL_SIZE;
+    if (nblocks == 0 || total_cells == 0) return DRAG_OK;
+    if (!blocks || !rho_g || !rho_d || !t_s || !v_in || !v_out) return DRAG_ENULL;
+    if (!aligned8(blocks) || !aligned8(rho_g) || !aligned8(rho_d) || !aligned8(t_s) || !aligned8(v_in) ||
+        !aligned8(v_out))
+        return DRAG_EALIGN;
+    const Layout L = layout(nblocks, total_cells);
+    if (!workspace || workspace_bytes < L.total) return DRAG_EWORKSPACE;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return DRAG_EALIGN;
+    uint32_t *st = dx_status_ptr();
+    if (!st) return DRAG_ECUDA;
+
+    char *ws = static_cast<char *>(workspace);
+    Work W;
+    W.perm = reinterpret_cast<unsigned long long *>(ws + L.perm);
+    W.key = reinterpret_cast<unsigned int *>(ws + L.key);
+    W.blk_start = reinterpret_cast<long long *>(ws + L.blk_start);
+    W.hist = reinterpret_cast<unsigned int *>(ws + L.hist);
+    W.offs = reinterpret_cast<unsigned int *>(ws + L.offs);
+    W.cursor = reinterpret_cast<unsigned int *>(ws + L.cursor);
+    W.item_offs = reinterpret_cast<unsigned int *>(ws + L.item_offs);
+    W.ctr = reinterpret_cast<unsigned int *>(ws + L.ctr);
+
+    const Modes M = dx_batch_modes();
+    const DxConsts &K = dx_consts();
+    const Desc *D = reinterpret_cast<const Desc *>(blocks);
+    const int sms = dx_sm_count();
+    const long long cgrid_want = (total_cells + 255) / 256;
+    const int cgrid = (int)(cgrid_want < (long long)sms * 16 ? cgrid_want : (long long)sms * 16);
+
+    dx_batch_prepare<<<1, kScanThreads, 0, stream>>>(nblocks, D, total_cells, rho_d_len, v_len, W, st);
+    dx_batch_count<<<cgrid, 256, 0, stream>>>(nblocks, D, rho_g, rho_d, t_s, W, K);
+    dx_batch_bins<<<1, kScanThreads, 0, stream>>>(W, M);
+    dx_batch_scatter<<<cgrid, 256, 0, stream>>>(nblocks, W);
+
+    MainArgs a{D, rho_g, rho_d, t_s, v_in, v_out, st, warp_doubles_for(M, nspecies_max + 1)};
+    const size_t smem = sizeof(double) * (32 + (size_t)kMainWarps * (a.warp_doubles + 2 * kPairSlots / 4));
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(dx_batch_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return DRAG_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dx_batch_main, kMainWarps * 32, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    dx_batch_main<<<sms * per_sm, kMainWarps * 32, smem, stream>>>(nblocks, a, W, M, K);
+    return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
+}

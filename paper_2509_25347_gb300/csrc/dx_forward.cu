@@ -21,6 +21,7 @@
 //      P_ii = E_ii, P_ij = E_ij sigma_j / sigma_i.
 #include <cmath>
 
+#include "dx_modes.h"
 #include "dx_wpc.cuh"
 
 namespace {
@@ -36,101 +37,22 @@ struct FwdArgs {
     uint32_t *status;
 };
 
-// Per-warp shared-memory footprint (doubles): E0, E1, sigma, tau, X_0f, X_ff,
-// sigma v (3 components) and v (3 components).
-__host__ __device__ __forceinline__ int warp_smem_doubles(int n) {
-    return 2 * n * dx_stride(n) + 10 * DX_NMAXF;
-}
-
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 dx_forward_wpc(FwdArgs a, DxConsts K) {
     extern __shared__ double smem[];
-    const int n = a.N + 1, N = a.N, ns = dx_stride(n);
+    const int n = a.N + 1;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int n_od = n * (n - 1) / 2;
-    const int n_hp = n * (n + 1) / 2 - 1;
-
-    unsigned short *od = reinterpret_cast<unsigned short *>(smem + kWarpsPerBlock * warp_smem_doubles(n));
+    const int wd = dx_wpc_fwd_warp_doubles(n);
+    unsigned short *od = reinterpret_cast<unsigned short *>(smem + kWarpsPerBlock * wd);
     unsigned short *hp = od + kPairSlots;
     dx_build_pairs(n, od, hp);
     __syncthreads();
-
-    double *E0 = smem + wib * warp_smem_doubles(n);
-    double *E1 = E0 + n * ns;
-    DxVecs V;
-    V.sig = E1 + n * ns;
-    V.tau = V.sig + DX_NMAXF;
-    V.xs = V.tau + DX_NMAXF;
-    V.ds = V.xs + DX_NMAXF;
-    double *yv = V.ds + DX_NMAXF;      // sigma_f v_f, three components
-    double *vv = yv + 3 * DX_NMAXF;    // v_f, three components
-
+    double *wsm = smem + wib * wd;
     const long long C = a.C;
     const long long nwarps = (long long)gridDim.x * kWarpsPerBlock;
-    for (long long c = (long long)blockIdx.x * kWarpsPerBlock + wib; c < C; c += nwarps) {
-        const double rg = a.rho_g[c];
-        double rd = 0.0, ts = INFINITY;
-        if (lane >= 1 && lane <= N) {
-            rd = a.rho_d[(long long)(lane - 1) * C + c];
-            ts = a.t_s[(long long)(lane - 1) * C + c];
-        }
-        double vin[3] = {0.0, 0.0, 0.0};
-        if (lane < n) {
-#pragma unroll
-            for (int d = 0; d < 3; d++) vin[d] = a.v_in[((long long)d * n + lane) * C + c];
-        }
-        DxLane L;
-        if (!dx_wpc_setup(lane, N, rg, rd, ts, a.dt, K, V, L)) {
-            if (lane < n) {
-#pragma unroll
-                for (int d = 0; d < 3; d++) a.v_out[((long long)d * n + lane) * C + c] = NAN;
-            }
-            if (lane == 0) atomicOr(a.status, DRAG_STATUS_BAD_CELL);
-            continue;
-        }
-        const int m = K.mk[L.k];
-
-        // Taylor polynomial T_m(X) by Horner's rule in X
-        double *F = E0, *G = E1;
-        dx_wpc_taylor_init(lane, n, ns, m, K, V, F);
-        for (int j = m - 2; j >= 0; j--) {
-            dx_wpc_horner_step(lane, n, ns, n_hp, hp, V, K.b[j], F, G);
-            __syncwarp();
-            double *tmp = F; F = G; G = tmp;
-        }
-        dx_wpc_restore(lane, n, ns, V, F);
-        __syncwarp();
-
-        // s squarings (Eq. ExpEq1 with n = 2^s), row sums restored each time
-        for (int it = 0; it < L.s; it++) {
-            dx_wpc_square_offdiag(lane, n, ns, n_od, od, F, G);
-            __syncwarp();
-            dx_wpc_restore(lane, n, ns, V, G);
-            __syncwarp();
-            double *tmp = F; F = G; G = tmp;
-        }
-
-        // v_out_i = E_ii v_i + tau_i sum_{j != i} E_ij sigma_j v_j  (P = D_sigma^-1 E D_sigma)
-        if (lane < n) {
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                yv[d * DX_NMAXF + lane] = L.sg * vin[d];
-                vv[d * DX_NMAXF + lane] = vin[d];
-            }
-        }
-        __syncwarp();
-        for (int t = lane; t < 3 * n; t += 32) {
-            const int d = t / n, i = t - d * n;
-            const double *y = yv + d * DX_NMAXF;
-            double acc = 0.0;
-            for (int q = 0; q < n - 1; q++) {
-                const int k = q + (q >= i);
-                acc = fma(F[i * ns + k], y[k], acc);
-            }
-            a.v_out[((long long)d * n + i) * C + c] = fma(V.tau[i], acc, F[i * ns + i] * vv[d * DX_NMAXF + i]);
-        }
-        __syncwarp();
-    }
+    for (long long c = (long long)blockIdx.x * kWarpsPerBlock + wib; c < C; c += nwarps)
+        dx_wpc_forward_cell(lane, a.N, a.rho_g + c, a.rho_d + c, a.t_s + c, a.v_in + c, a.v_out + c, C, a.dt, K, wsm,
+                            od, hp, a.status);
 }
 
 // (k*, s*) per cell, one thread per cell (diagnostics and FLOP accounting).
@@ -183,7 +105,7 @@ int check_common(long long C, int N, const double *rho_g, const double *rho_d, c
 }  // namespace
 
 size_t dx_forward_smem_bytes(int n) {
-    return sizeof(double) * (size_t)kWarpsPerBlock * warp_smem_doubles(n) + 2 * kPairSlots * sizeof(unsigned short);
+    return sizeof(double) * (size_t)kWarpsPerBlock * dx_wpc_fwd_warp_doubles(n) + 2 * kPairSlots * sizeof(unsigned short);
 }
 
 extern "C" int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
@@ -196,6 +118,10 @@ extern "C" int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *r
     uint32_t *st = dx_status_ptr();
     if (!st) return DRAG_ECUDA;
     const int n = nspecies + 1;
+    const int mode = dx_mode_for(n);
+    if (mode != DX_MODE_WPC)
+        return dx_launch_forward_lpc(n, mode == DX_MODE_LPC_SMEM, ncells, rho_g, rho_d, t_s, v_in, v_out, dt, st,
+                                     stream);
     const size_t smem = dx_forward_smem_bytes(n);
     if (!dx_once_per_device(0, [] {
             return cudaFuncSetAttribute(dx_forward_wpc, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -5,6 +5,7 @@
 #include <mutex>
 
 #include "dx_common.cuh"
+#include "dx_modes.h"
 
 // Sticky status bits, one word per device (DRAG_STATUS_*).
 __device__ uint32_t g_dx_status;
@@ -68,6 +69,20 @@ std::mutex g_mu;
 uint32_t *g_status_ptr[64];
 int g_sm_count[64];
 bool g_once[64][16];
+int g_mode[64][DX_NMAXF + 1];
+bool g_mode_init[64];
+
+int default_mode(int n) {
+    if (n <= DX_LPC_REG_NMAX) return DX_MODE_LPC_REG;
+    if (n <= DX_LPC_NMAX) return DX_MODE_LPC_SMEM;
+    return DX_MODE_WPC;
+}
+
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    return dev;
+}
 
 }  // namespace
 
@@ -98,6 +113,32 @@ int dx_sm_count() {
         g_sm_count[dev] = v;
     }
     return g_sm_count[dev];
+}
+
+bool dx_mode_valid(int n, int mode) {
+    if (n < 2 || n > DX_NMAXF) return false;
+    if (mode == DX_MODE_WPC) return true;
+    if (mode == DX_MODE_LPC_REG) return n <= DX_LPC_REG_NMAX;
+    if (mode == DX_MODE_LPC_SMEM) return n <= DX_LPC_NMAX;
+    return false;
+}
+
+int dx_mode_for(int n) {
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_mode_init[dev]) {
+        for (int k = 0; k <= DX_NMAXF; k++) g_mode[dev][k] = default_mode(k);
+        g_mode_init[dev] = true;
+    }
+    return (n >= 0 && n <= DX_NMAXF) ? g_mode[dev][n] : DX_MODE_WPC;
+}
+
+void dx_set_mode(int n, int mode) {
+    if (!dx_mode_valid(n, mode)) return;
+    dx_mode_for(n);   // initialise the table
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_mode[dev][n] = mode;
 }
 
 bool dx_once_per_device(int slot, bool (*fn)()) {

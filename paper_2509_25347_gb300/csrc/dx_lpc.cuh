@@ -1,0 +1,221 @@
+// Lane-per-cell building block for small matrices (n = N + 1 <= 12).
+//
+// Each lane owns one cell and runs the whole update serially: set-up and
+// Algorithm 2, Horner Taylor in the symmetric arrowhead X, row-sum
+// restoration, squarings and the apply (same arithmetic as the warp-per-cell
+// path, see dx_wpc.cuh). Every FP64 instruction of a warp then does useful
+// work on 32 cells, instead of the n(n-1)/2 or n lanes a warp-per-cell round
+// keeps busy. Lanes of one warp run max(m*) Horner steps and max(s*)
+// squarings; the batched entry point bins cells by (N, k*, s*) so that the
+// lanes of a warp agree.
+//
+// The symmetric matrix is stored packed (upper triangle, NT = n(n+1)/2
+// doubles) either in registers (SMEM = false, fully unrolled, n <= 6) or in
+// shared memory with a stride of 32 doubles between entries so that the 32
+// lanes of a warp hit 32 different banks (SMEM = true).
+#pragma once
+
+#include "dx_common.cuh"
+
+template <int NF>
+struct DxPacked {
+    static constexpr int NT = NF * (NF + 1) / 2;
+    __host__ __device__ static constexpr int at(int i, int j) {
+        return i <= j ? i * NF - i * (i - 1) / 2 + (j - i) : j * NF - j * (j - 1) / 2 + (i - j);
+    }
+};
+
+// Storage of NT doubles per lane: registers or a strided shared-memory slice.
+template <int NT, bool SMEM>
+struct DxLaneArr;
+
+template <int NT>
+struct DxLaneArr<NT, false> {
+    double v[NT];
+    __device__ __forceinline__ void bind(double *, int) {}
+    __device__ __forceinline__ double &operator[](int e) { return v[e]; }
+};
+
+template <int NT>
+struct DxLaneArr<NT, true> {
+    double *p;
+    __device__ __forceinline__ void bind(double *base, int lane) { p = base + lane; }
+    __device__ __forceinline__ double &operator[](int e) { return p[e * 32]; }
+};
+
+// F <- G after a step: registers are copied, shared-memory slices swapped.
+template <int NT>
+__device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, false> &F, DxLaneArr<NT, false> &G) {
+#pragma unroll
+    for (int e = 0; e < NT; e++) F.v[e] = G.v[e];
+}
+template <int NT>
+__device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, true> &F, DxLaneArr<NT, true> &G) {
+    double *t = F.p;
+    F.p = G.p;
+    G.p = t;
+}
+
+// Shared-memory doubles one warp needs for the SMEM variant.
+template <int NF>
+__host__ __device__ constexpr int dx_lpc_warp_smem_doubles() {
+    return 32 * (2 * DxPacked<NF>::NT + 4 * NF);
+}
+
+// One cell per lane. Pointers address this cell; element (i) of a per-species
+// array is at p[i * stride]; velocity (d, f) at p[(d * NF + f) * stride].
+// smem_warp: this warp's slice (SMEM = true only); bsh: b_i = 1/i! in shared memory.
+template <int NF, bool SMEM>
+__device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp, const double *rdp, const double *tsp,
+                                                    const double *vip, double *vop, long long stride, double dt,
+                                                    const DxConsts &K, const double *bsh, double *smem_warp,
+                                                    uint32_t *status) {
+    constexpr int N = NF - 1;
+    constexpr int NT = DxPacked<NF>::NT;
+    using P = DxPacked<NF>;
+
+    // ---------------- load and validate (integer checks on bit patterns)
+    const double rg = *rgp;
+    bool ok = dx_pos_finite(rg);
+    double eps[N > 0 ? N : 1], alpha[N > 0 ? N : 1];
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const double rd = rdp[i * stride], ts = tsp[i * stride];
+        ok = ok && dx_nonneg_finite(rd) && dx_pos_or_inf(ts);
+        eps[i] = rd;
+        alpha[i] = ts;
+    }
+    if (!ok) {
+#pragma unroll
+        for (int e = 0; e < 3 * NF; e++) vop[e * stride] = NAN;
+        atomicOr(status, DRAG_STATUS_BAD_CELL);
+        return;
+    }
+
+    // ---------------- A = dt Omega_v entries and the 1-norm (ascending species order)
+    double s1 = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        eps[i] = __ddiv_rn(eps[i], rg);      // Eq. DragEqVar2
+        alpha[i] = __ddiv_rn(1.0, alpha[i]); // Eq. DragEqVar3
+        s1 = __dadd_rn(s1, __dmul_rn(__dmul_rn(eps[i], alpha[i]), dt));
+    }
+    double col0 = s1;
+    long long cmax = 0;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const double ai0 = __dmul_rn(alpha[i], dt);
+        col0 = __dadd_rn(col0, ai0);
+        const long long cb = dx_bits(__dadd_rn(__dmul_rn(__dmul_rn(eps[i], alpha[i]), dt), ai0));
+        cmax = cb > cmax ? cb : cmax;
+    }
+    const long long nb = dx_bits(col0) > cmax ? dx_bits(col0) : cmax;
+    int kk, s;
+    dx_select(__longlong_as_double(nb), K, kk, s);
+    const int m = K.mk[kk];
+    const double p2 = dx_pow2(-s);
+
+    // ---------------- symmetric arrowhead X = 2^-s D_sigma A D_sigma^-1
+    DxLaneArr<NF, SMEM> sig, tau, xs, ds;
+    DxLaneArr<NT, SMEM> Fm, Gm;
+    if constexpr (SMEM) {
+        Fm.bind(smem_warp, lane);
+        Gm.bind(smem_warp + 32 * NT, lane);
+        sig.bind(smem_warp + 64 * NT, lane);
+        tau.bind(smem_warp + 64 * NT + 32 * NF, lane);
+        xs.bind(smem_warp + 64 * NT + 64 * NF, lane);
+        ds.bind(smem_warp + 64 * NT + 96 * NF, lane);
+    }
+    sig[0] = 1.0;
+    tau[0] = 1.0;
+    xs[0] = -s1 * p2;
+    ds[0] = 0.0;
+#pragma unroll
+    for (int i = 1; i < NF; i++) {
+        const double e = dx_bits(eps[i - 1]) < dx_bits(DX_EPS_FLOOR) ? DX_EPS_FLOOR : eps[i - 1];
+        const double sg = __dsqrt_rn(e);
+        sig[i] = sg;
+        tau[i] = __ddiv_rn(1.0, sg);
+        xs[i] = __dmul_rn(__dmul_rn(sg, alpha[i - 1]), dt * p2);
+        ds[i] = -(__dmul_rn(alpha[i - 1], dt) * p2);
+    }
+
+    // ---------------- Taylor: F = b_m X + b_{m-1} I, then F <- F X + b_j I (Horner in X)
+    {
+        const double bm = bsh[m], bm1 = bsh[m - 1];
+#pragma unroll
+        for (int e = 0; e < NT; e++) Fm[e] = 0.0;
+        Fm[0] = fma(bm, xs[0], bm1);
+#pragma unroll
+        for (int i = 1; i < NF; i++) {
+            Fm[P::at(0, i)] = bm * xs[i];
+            Fm[P::at(i, i)] = fma(bm, ds[i], bm1);
+        }
+    }
+    for (int j = m - 2; j >= 0; j--) {
+        const double bj = bsh[j];
+        double g00 = fma(Fm[0], xs[0], bj);
+#pragma unroll
+        for (int k = 1; k < NF; k++) g00 = fma(Fm[P::at(0, k)], xs[k], g00);
+#pragma unroll
+        for (int jj = 1; jj < NF; jj++) {
+#pragma unroll
+            for (int i = 0; i <= jj; i++) {
+                double acc = fma(Fm[P::at(i, 0)], xs[jj], i == jj ? bj : 0.0);
+                Gm[P::at(i, jj)] = fma(Fm[P::at(i, jj)], ds[jj], acc);
+            }
+        }
+        Gm[0] = g00;
+        dx_lane_take(Fm, Gm);
+    }
+
+    // ---------------- restore E_ii = 1 - tau_i sum_{k != i} E_ik sigma_k, then s squarings
+#pragma unroll
+    for (int i = 0; i < NF; i++) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < NF; k++)
+            if (k != i) acc = fma(Fm[P::at(i, k)], sig[k], acc);
+        Fm[P::at(i, i)] = fma(-tau[i], acc, 1.0);
+    }
+    for (int it = 0; it < s; it++) {
+#pragma unroll
+        for (int i = 0; i < NF; i++) {
+#pragma unroll
+            for (int jj = i + 1; jj < NF; jj++) {
+                double acc = 0.0;
+#pragma unroll
+                for (int k = 0; k < NF; k++) acc = fma(Fm[P::at(i, k)], Fm[P::at(jj, k)], acc);
+                Gm[P::at(i, jj)] = acc;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NF; i++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < NF; k++)
+                if (k != i) acc = fma(Gm[P::at(i, k)], sig[k], acc);
+            Gm[P::at(i, i)] = fma(-tau[i], acc, 1.0);
+        }
+        dx_lane_take(Fm, Gm);
+    }
+
+    // ---------------- apply: v_out_i = E_ii v_i + tau_i sum_{k != i} E_ik sigma_k v_k
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        double v[NF], y[NF];
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            v[f] = vip[(d * NF + f) * stride];
+            y[f] = sig[f] * v[f];
+        }
+#pragma unroll
+        for (int i = 0; i < NF; i++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < NF; k++)
+                if (k != i) acc = fma(Fm[P::at(i, k)], y[k], acc);
+            vop[(d * NF + i) * stride] = fma(tau[i], acc, Fm[P::at(i, i)] * v[i]);
+        }
+    }
+}

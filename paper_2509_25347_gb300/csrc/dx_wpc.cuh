@@ -155,3 +155,108 @@ __device__ __forceinline__ void dx_wpc_square_offdiag(int lane, int n, int ns, i
         G[jj * ns + i] = acc;
     }
 }
+
+// Warp-cooperative pair tables (one warp builds its own; used when n varies per item).
+__device__ __forceinline__ void dx_build_pairs_warp(int lane, int n, unsigned short *od, unsigned short *hp) {
+    const int n_od = n * (n - 1) / 2, n_hp = n * (n + 1) / 2 - 1;
+    for (int t = lane; t < n_od; t += 32) {
+        int i = 0, r = t;
+        while (r >= n - 1 - i) { r -= n - 1 - i; i++; }
+        od[t] = (unsigned short)((i << 8) | (i + 1 + r));
+    }
+    for (int t = lane; t < n_hp; t += 32) {
+        int i = 0, r = t + 1;
+        while (r >= n - i) { r -= n - i; i++; }
+        hp[t] = (unsigned short)((i << 8) | (i + r));
+    }
+    __syncwarp();
+}
+
+// Per-warp shared-memory footprint of the forward cell routine (doubles).
+__host__ __device__ __forceinline__ int dx_wpc_fwd_warp_doubles(int n) { return 2 * n * dx_stride(n) + 10 * DX_NMAXF; }
+
+// Forward update of one cell by one warp (warp-uniform arguments). Element i
+// of a per-species array is at p[i * stride]; velocity (d, f) at
+// p[(d * n + f) * stride]. od/hp: pair tables for this n. v_out may alias v_in.
+__device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const double *rgp, const double *rdp,
+                                                    const double *tsp, const double *vip, double *vop,
+                                                    long long stride, double dt, const DxConsts &K, double *wsm,
+                                                    const unsigned short *od, const unsigned short *hp,
+                                                    uint32_t *status) {
+    const int n = N + 1, ns = dx_stride(n);
+    const int n_od = n * (n - 1) / 2;
+    const int n_hp = n * (n + 1) / 2 - 1;
+    double *E0 = wsm;
+    double *E1 = E0 + n * ns;
+    DxVecs V;
+    V.sig = E1 + n * ns;
+    V.tau = V.sig + DX_NMAXF;
+    V.xs = V.tau + DX_NMAXF;
+    V.ds = V.xs + DX_NMAXF;
+    double *yv = V.ds + DX_NMAXF;      // sigma_f v_f, three components
+    double *vv = yv + 3 * DX_NMAXF;    // v_f, three components
+
+    const double rg = *rgp;
+    double rd = 0.0, ts = INFINITY;
+    if (lane >= 1 && lane <= N) {
+        rd = rdp[(long long)(lane - 1) * stride];
+        ts = tsp[(long long)(lane - 1) * stride];
+    }
+    double vin[3] = {0.0, 0.0, 0.0};
+    if (lane < n) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) vin[d] = vip[((long long)d * n + lane) * stride];
+    }
+    DxLane L;
+    if (!dx_wpc_setup(lane, N, rg, rd, ts, dt, K, V, L)) {
+        if (lane < n) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) vop[((long long)d * n + lane) * stride] = NAN;
+        }
+        if (lane == 0) atomicOr(status, DRAG_STATUS_BAD_CELL);
+        __syncwarp();
+        return;
+    }
+    const int m = K.mk[L.k];
+
+    // Taylor polynomial T_m(X) by Horner's rule in X
+    double *F = E0, *G = E1;
+    dx_wpc_taylor_init(lane, n, ns, m, K, V, F);
+    for (int j = m - 2; j >= 0; j--) {
+        dx_wpc_horner_step(lane, n, ns, n_hp, hp, V, K.b[j], F, G);
+        __syncwarp();
+        double *tmp = F; F = G; G = tmp;
+    }
+    dx_wpc_restore(lane, n, ns, V, F);
+    __syncwarp();
+
+    // s squarings (Eq. ExpEq1 with n = 2^s), row sums restored each time
+    for (int it = 0; it < L.s; it++) {
+        dx_wpc_square_offdiag(lane, n, ns, n_od, od, F, G);
+        __syncwarp();
+        dx_wpc_restore(lane, n, ns, V, G);
+        __syncwarp();
+        double *tmp = F; F = G; G = tmp;
+    }
+
+    // v_out_i = E_ii v_i + tau_i sum_{j != i} E_ij sigma_j v_j  (P = D_sigma^-1 E D_sigma)
+    if (lane < n) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            yv[d * DX_NMAXF + lane] = L.sg * vin[d];
+            vv[d * DX_NMAXF + lane] = vin[d];
+        }
+    }
+    __syncwarp();
+    for (int t = lane; t < 3 * n; t += 32) {
+        const int d = t / n, i = t - d * n;
+        const double *y = yv + d * DX_NMAXF;
+        double acc = 0.0;
+        for (int q = 0; q < n - 1; q++) {
+            const int k = q + (q >= i);
+            acc = fma(F[i * ns + k], y[k], acc);
+        }
+        vop[((long long)d * n + i) * stride] = fma(V.tau[i], acc, F[i * ns + i] * vv[d * DX_NMAXF + i]);
+    }
+    __syncwarp();
+}

@@ -125,10 +125,40 @@ def adjoint_target(ncells: int, nspecies: int, seed: int = 4) -> np.ndarray:
     return _rng(seed + 1000).standard_normal((3, nspecies + 1, ncells))
 
 
+BLOCK_DTYPE = np.dtype([("cell_offset", "<i8"), ("dust_offset", "<i8"), ("vel_offset", "<i8"),
+                        ("ncells", "<i4"), ("nspecies", "<i4"), ("dt", "<f8")])
+
+
 @dataclass
 class Batch:
     """Blocks for the batched entry point: one SoA slab per block."""
     blocks: list          # list of (nspecies, dt, Cells)
+
+    def pack(self):
+        """Concatenate the blocks' slabs. Returns (desc, rho_g, rho_d, t_s, v)
+        with desc a BLOCK_DTYPE array: block b's gas densities start at
+        rho_g[cell_offset], its species-major dust slab (N x ncells) at
+        rho_d[dust_offset] and t_s[dust_offset], its velocity slab
+        (3 x (N+1) x ncells) at v[vel_offset]."""
+        desc = np.zeros(len(self.blocks), dtype=BLOCK_DTYPE)
+        rg, rd, ts, vv = [], [], [], []
+        co = do = vo = 0
+        for b, (N, dt, cells) in enumerate(self.blocks):
+            C = cells.ncells
+            desc[b] = (co, do, vo, C, N, dt)
+            rg.append(cells.rho_g)
+            rd.append(cells.rho_d.reshape(-1))
+            ts.append(cells.t_s.reshape(-1))
+            vv.append(cells.v.reshape(-1))
+            co += C
+            do += N * C
+            vo += 3 * (N + 1) * C
+        cat = lambda parts: np.ascontiguousarray(np.concatenate(parts)) if parts else np.zeros(0)
+        return desc, cat(rg), cat(rd), cat(ts), cat(vv)
+
+    @property
+    def ncells(self) -> int:
+        return int(sum(c.ncells for _, _, c in self.blocks))
 
 
 def batched(nblocks: int = 2048, block_cells: int = 512, seed: int = 3, species=(1, 4, 8, 16), kmax: int = 6) -> Batch:
