@@ -61,6 +61,7 @@ extern "C" {
 #define DRAG_ECUDA (-4)         /* a CUDA runtime call or kernel launch failed */
 #define DRAG_EWORKSPACE (-5)    /* workspace missing or smaller than required */
 #define DRAG_EBLOCKS (-6)       /* bad block count in the batched entry point */
+#define DRAG_ENOALLOC_LIMIT (-7) /* batch larger than drag_expm_apply_batched_noalloc's fixed scratch */
 
 /* Sticky device status bits (drag_expm_get_status). */
 #define DRAG_STATUS_BAD_CELL 0x1u      /* some cell had invalid data; its outputs are NaN */
@@ -170,6 +171,35 @@ int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *blocks, int64_t
                             int64_t v_len, int32_t nspecies_max, const double *rho_g, const double *rho_d,
                             const double *t_s, const double *v_in, double *v_out, void *workspace,
                             size_t workspace_bytes, cudaStream_t stream);
+
+/*
+ * drag_expm_apply_batched_noalloc — drag_expm_apply_batched for callers that
+ * cannot provide scratch memory. The paper has no counterpart; this is a
+ * library-integration entry point. Some host codes cannot allocate device
+ * memory for a library: their device memory is owned entirely by their own
+ * pool or arena allocator reserved at start-up, or they must not call
+ * cudaMalloc/cudaFree inside a time step because those calls synchronise the
+ * device and stall the step's other streams, or they reach this library
+ * through a thin binding that only passes the input and output arrays. This
+ * entry point allocates nothing: it runs the same pipeline on a fixed scratch
+ * array compiled into the library, which every GPU that loads the library
+ * holds in global memory until the process exits.
+ *   Limits: nblocks <= DRAG_NOALLOC_MAX_BLOCKS and total_cells <=
+ *   DRAG_NOALLOC_MAX_CELLS; larger batches return DRAG_ENOALLOC_LIMIT and
+ *   launch nothing. All other arguments and errors are those of
+ *   drag_expm_apply_batched.
+ *   The first call on each device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   Calls share the array: each call clears what must start at zero, but two
+ *   calls whose work overlaps on the GPU race on it, so order them (same
+ *   stream, or an event between streams).
+ */
+#define DRAG_NOALLOC_MAX_BLOCKS 16384
+#define DRAG_NOALLOC_MAX_CELLS 262144
+int drag_expm_apply_batched_noalloc(int64_t nblocks, const drag_block_t *blocks, int64_t total_cells,
+                                    int64_t rho_d_len, int64_t v_len, int32_t nspecies_max, const double *rho_g,
+                                    const double *rho_d, const double *t_s, const double *v_in, double *v_out,
+                                    cudaStream_t stream);
 
 /*
  * drag_expm_get_status — copy the current device's sticky status bits

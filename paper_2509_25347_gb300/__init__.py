@@ -50,6 +50,8 @@ def load_library(path: str | None = None):
     lib.drag_expm_batched_workspace_bytes.argtypes = [i64, i64]
     lib.drag_expm_apply_batched.restype = ctypes.c_int
     lib.drag_expm_apply_batched.argtypes = [i64, vp, i64, i64, i64, i32, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    lib.drag_expm_apply_batched_noalloc.restype = ctypes.c_int
+    lib.drag_expm_apply_batched_noalloc.argtypes = [i64, vp, i64, i64, i64, i32, vp, vp, vp, vp, vp, vp]
     lib.drag_expm_select.restype = ctypes.c_int
     lib.drag_expm_select.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp]
     lib.drag_expm_get_status.restype = ctypes.c_int

@@ -17,6 +17,7 @@
 // and no allocation (scratch is the caller's workspace), so the whole call can
 // be captured in a CUDA graph and replayed.
 #include <cmath>
+#include <mutex>
 
 #include "dx_lpc.cuh"
 #include "dx_modes.h"
@@ -407,4 +408,65 @@ extern "C" int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *bloc
         per_sm = 1;
     dx_batch_main<<<sms * per_sm, kMainWarps * 32, smem, stream>>>(nblocks, a, W, M, K);
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Batched update without caller scratch.
+//
+// Some callers cannot hand this library a workspace: host codes whose device
+// memory is owned entirely by their own pool or arena allocator (reserved at
+// start-up, with no hook through which a library could obtain scratch), codes
+// that must not call cudaMalloc/cudaFree inside a time step because those
+// calls synchronise the device and stall the other streams of the step, and
+// thin foreign-language bindings that only exchange the input and output
+// arrays. For them this entry point runs the same five-kernel pipeline as
+// drag_expm_apply_batched on a fixed scratch array compiled into the library.
+//
+// The array lives in device global memory of every GPU that loads the library
+// and stays there until the process exits. In host code its name only stands
+// in for it, so its device address is looked up once per device (first call on
+// that device, with that device current) and passed to the kernels. Every call
+// uses the same array: the first kernel of the pipeline clears the histogram
+// and the counters, and every other part is written before it is read, so no
+// stale contents leak from one call to the next; but two calls whose work
+// overlaps on the GPU (different streams, no ordering) would race on it.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kNoAllocBytes =
+    na_align(sizeof(unsigned long long) * (size_t)DRAG_NOALLOC_MAX_CELLS) +
+    na_align(sizeof(unsigned int) * (size_t)DRAG_NOALLOC_MAX_CELLS) +
+    na_align(sizeof(long long) * ((size_t)DRAG_NOALLOC_MAX_BLOCKS + 1)) +
+    4 * na_align(sizeof(unsigned int) * (kNBins + 1)) + na_align(sizeof(unsigned int) * 8);
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[64];
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+extern "C" int drag_expm_apply_batched_noalloc(int64_t nblocks, const drag_block_t *blocks, int64_t total_cells,
+                                               int64_t rho_d_len, int64_t v_len, int32_t nspecies_max,
+                                               const double *rho_g, const double *rho_d, const double *t_s,
+                                               const double *v_in, double *v_out, cudaStream_t stream) {
+    if (nblocks > DRAG_NOALLOC_MAX_BLOCKS || total_cells > DRAG_NOALLOC_MAX_CELLS) return DRAG_ENOALLOC_LIMIT;
+    if (nblocks >= 0 && total_cells >= 0 && drag_expm_batched_workspace_bytes(nblocks, total_cells) > kNoAllocBytes)
+        return DRAG_ENOALLOC_LIMIT;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DRAG_ECUDA;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DRAG_ECUDA;
+            g_noalloc_addr[dev] = p;
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    return drag_expm_apply_batched(nblocks, blocks, total_cells, rho_d_len, v_len, nspecies_max, rho_g, rho_d, t_s,
+                                   v_in, v_out, scratch, kNoAllocBytes, stream);
 }

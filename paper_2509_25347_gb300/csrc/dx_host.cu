@@ -182,6 +182,9 @@ const char *drag_expm_strerror(int code) {
         case DRAG_ECUDA: return "a CUDA runtime call or kernel launch failed";
         case DRAG_EWORKSPACE: return "workspace missing or too small";
         case DRAG_EBLOCKS: return "invalid block count or block descriptor array";
+        case DRAG_ENOALLOC_LIMIT:
+            return "batch exceeds the fixed scratch of drag_expm_apply_batched_noalloc "
+                   "(DRAG_NOALLOC_MAX_BLOCKS / DRAG_NOALLOC_MAX_CELLS); use drag_expm_apply_batched with a workspace";
         default: return "unknown error code";
     }
 }
