@@ -49,10 +49,29 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--ncells", type=int, default=None, help="truncate the workload (profiling runs only)")
+    p.add_argument("--nblocks", type=int, default=2048, help="blocks of the batched workload (profiling runs only)")
+    p.add_argument("--no-plain-baseline", action="store_true", help="batched workload: skip the per-block comparison")
     return p.parse_args()
 
 
 # ------------------------------------------------------------------ helpers ---
+
+def max_over_ranks(values, world, device="cpu"):
+    """Element-wise max of per-rank timings (ms) over all ranks; the job is as
+    slow as its slowest rank. Identity when world == 1."""
+    import torch
+    t = torch.tensor([float(x) for x in values], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Weak scaling: every rank processes its own full workload, so the
+    whole-job throughput is the units of all ranks over the slowest rank's time."""
+    return units_per_rank * world / (ms * 1e-3)
+
 
 def algorithmic_counts(N, k, s):
     """Per-cell algorithmic FLOPs (2 n^3 (k* + s*) + 6 n^2: k* + s* dense n x n
@@ -156,19 +175,60 @@ def cpu_oracle_rate(cells, seconds, steps=1):
 
 # ---------------------------------------------------------------- reference ---
 
+def _oracle_blocks(args):
+    import oracle
+    desc, rg, rd, ts, v = args
+    oracle.drag_apply_batched(desc, rg, rd, ts, v)
+    return int(desc["ncells"].sum())
+
+
+def cpu_oracle_batched_rate(batch, seconds, steps=1):
+    """Oracle cell-updates/s on the batched workload: a prefix of the blocks,
+    one contiguous group of blocks per spawned worker."""
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    t0 = time.perf_counter()
+    probe = W.Batch(batch.blocks[:8])
+    oracle.drag_apply_batched(*probe.pack())
+    per_cell = (time.perf_counter() - t0) / max(1, probe.ncells)
+    want_cells = seconds * cores / max(per_cell, 1e-9)
+    nb = int(min(len(batch.blocks), max(cores, want_cells / 512)))
+    groups = np.array_split(np.arange(nb), cores)
+    jobs = [W.Batch([batch.blocks[i] for i in g]).pack() for g in groups if len(g)]
+    ctx = mp.get_context("spawn")
+    walls = []
+    with ctx.Pool(cores) as pool:
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            done = sum(pool.map(_oracle_blocks, jobs))
+            walls.append(time.perf_counter() - t0)
+    wall = float(np.mean(walls))
+    return done / wall, cores, nb, wall
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
-    cells = W.workload(args.workload)
-    _, C, N, _ = W.WORKLOADS[args.workload]
-    rate, cores, sample, wall = cpu_oracle_rate(cells, seconds=max(2.0, 60.0 / max(1, args.steps + args.warmup)),
-                                                steps=args.steps)
+    secs = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    if args.workload == "batched_amr_1m":
+        batch = W.batched(nblocks=args.nblocks)
+        C, N = batch.ncells, "{1,4,8,16}"
+        rate, cores, nb, wall = cpu_oracle_batched_rate(batch, secs, steps=args.steps)
+        sample = nb * 512
+    else:
+        cells = W.workload(args.workload)
+        _, C, N, _ = W.WORKLOADS[args.workload]
+        rate, cores, sample, wall = cpu_oracle_rate(cells, seconds=secs, steps=args.steps)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "ncells": C, "nspecies": N, "step_sample_cells": sample},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"first {sample} cells of {args.workload} per step"},
+            "gpu_launches": 0,
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -281,13 +341,10 @@ def run_ours(args, rank, world):
     if dx.get_status():
         raise RuntimeError("device status set after forward + adjoint")
 
-    t_ms = torch.tensor([total_ms, e2e_ms, fb_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t_ms, op=torch.distributed.ReduceOp.MAX)
-    total_ms, e2e_ms, fb_ms = float(t_ms[0]), float(t_ms[1]), float(t_ms[2])
+    total_ms, e2e_ms, fb_ms = max_over_ranks([total_ms, e2e_ms, fb_ms], world, device="cuda")
     ms_per_step = total_ms / args.steps
-    value = C * world / (ms_per_step * 1e-3)
-    e2e_value = C * world / (e2e_ms * 1e-3)
+    value = whole_job_rate(C, world, ms_per_step)
+    e2e_value = whole_job_rate(C, world, e2e_ms)
 
     if rank != 0:
         if world > 1:
@@ -318,7 +375,7 @@ def run_ours(args, rank, world):
                      "algorithmic_flop_per_launch": flops_launch, "kernel_mean_ms": mean_launch_s * 1e3,
                      "hbm_gbs": gbs, "hbm_frac_of_measured": (gbs / hbm_peak) if hbm_peak else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "fwd_adjoint": {"value": C * world / (fb_ms * 1e-3), "unit": UNIT, "ms_per_step": fb_ms, "steps": fb_steps,
+        "fwd_adjoint": {"value": whole_job_rate(C, world, fb_ms), "unit": UNIT, "ms_per_step": fb_ms, "steps": fb_steps,
                         "note": "forward + dL/dv_out (torch sub) + drag_expm_backward, outside the headline timed region"},
         "gpu_launches": args.steps,
         "clocks": clocks,
@@ -353,7 +410,7 @@ def run_batched(args, rank, world):
         torch.distributed.barrier()
     dx.load_library()
 
-    batch = W.batched()
+    batch = W.batched(nblocks=args.nblocks)
     desc, rg_h, rd_h, ts_h, v_h = batch.pack()
     C = rg_h.size
     nmax = int(desc["nspecies"].max())
@@ -389,16 +446,19 @@ def run_batched(args, rank, world):
         for a, b_, c_, dt, vi, vo in views:
             dx.apply(a, b_, c_, dt, vi, vo, stream=stream)
 
+    plain = not args.no_plain_baseline
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             batched_call()
-            plain_calls()
+            if plain:
+                plain_calls()
     torch.cuda.synchronize()
     g_b, g_p = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
     with torch.cuda.graph(g_b, stream=stream):
         batched_call()
-    with torch.cuda.graph(g_p, stream=stream):
-        plain_calls()
+    if plain:
+        with torch.cuda.graph(g_p, stream=stream):
+            plain_calls()
     torch.cuda.synchronize()
     if dx.get_status():
         raise RuntimeError("device status set after warm-up")
@@ -429,8 +489,10 @@ def run_batched(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    plain_ms, _ = time_graph(g_p, max(1, min(args.steps, 5)))
-    plain_ms /= max(1, min(args.steps, 5))
+    plain_ms = float("nan")
+    if plain:
+        plain_ms, _ = time_graph(g_p, max(1, min(args.steps, 5)))
+        plain_ms /= max(1, min(args.steps, 5))
     if dx.get_status():
         raise RuntimeError("device status set after timed region")
 
@@ -453,10 +515,7 @@ def run_batched(args, rank, world):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
 
-    t_ms = torch.tensor([total_ms, e2e_ms, plain_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t_ms, op=torch.distributed.ReduceOp.MAX)
-    total_ms, e2e_ms, plain_ms = float(t_ms[0]), float(t_ms[1]), float(t_ms[2])
+    total_ms, e2e_ms, plain_ms = max_over_ranks([total_ms, e2e_ms, plain_ms], world, device="cuda")
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -466,19 +525,21 @@ def run_batched(args, rank, world):
     achieved = flops / mean_s / 1e12
     peak = FP64_FLOP_PER_CLK * SM_MAX_MHZ * 1e6 / 1e12
     line = {
-        "metric": METRIC, "value": C * world / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": whole_job_rate(C, world, ms), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "batched_amr_1m", "ncells": C, "nblocks": len(desc), "block_cells": 512,
+        "config": {"workload": "batched_amr_1m" if args.nblocks == 2048 else f"batched_amr_{args.nblocks}_blocks",
+                   "ncells": C, "nblocks": len(desc), "block_cells": 512,
                    "nspecies": "{1,4,8,16}", "dt": "2^-k, k in 0..6",
                    "l2": "inputs (%.2f GB) larger than L2, no flush" % (bytes_step / 1e9),
                    "launch": "one CUDA-graph replay: 4 binning kernels + 1 persistent kernel"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None, "algorithmic_flop_per_launch": flops, "step_mean_ms": mean_s * 1e3,
                      "peak_source": "FP64 pipe: 152 SMs x 608/152 flop/clk x 2070 MHz (unit count x max clock)"},
-        "plain_per_block": {"value": C * world / (plain_ms * 1e-3), "unit": UNIT, "ms_per_step": plain_ms,
-                            "note": "drag_expm_apply once per block (2048 launches), captured in one CUDA graph"},
-        "e2e": {"value": C * world / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "plain_per_block": ({"value": whole_job_rate(C, world, plain_ms), "unit": UNIT, "ms_per_step": plain_ms,
+                             "note": "drag_expm_apply once per block, all launches captured in one CUDA graph"}
+                            if plain else None),
+        "e2e": {"value": whole_job_rate(C, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": 5 * args.steps,
         "clocks": clocks,

@@ -202,6 +202,33 @@ int drag_expm_apply_batched_noalloc(int64_t nblocks, const drag_block_t *blocks,
                                     cudaStream_t stream);
 
 /*
+ * Execution modes. Each matrix size n = N + 1 runs in one of three kernel
+ * families (all compute the same update, Eq. ExacSolEqu by Algorithm 6):
+ * one lane per cell with the matrix in registers (n <= 6), one lane per cell
+ * with it in shared memory (n <= 12), or one warp per cell (any n). Defaults:
+ * registers up to n = 6, shared memory up to n = 12, warp above.
+ */
+#define DRAG_MODE_WARP_PER_CELL 0
+#define DRAG_MODE_LANE_REGISTERS 1
+#define DRAG_MODE_LANE_SHARED 2
+
+/* drag_expm_set_mode / drag_expm_get_mode — mode for nspecies on the current
+ * device (host only). set returns DRAG_EINVAL_SIZE for an invalid pair. */
+int drag_expm_set_mode(int32_t nspecies, int32_t mode);
+int drag_expm_get_mode(int32_t nspecies, int32_t *mode);
+
+/*
+ * drag_expm_autotune — time every valid mode for N = 1..nspecies_max on
+ * 32,768 synthetic MRN-like cells (dt/t_s over 1e-4..1e8) generated on the
+ * current device, and keep the fastest per N. cache_path (may be NULL): a
+ * text file; if it holds entries for this device (name, compute capability,
+ * SM count) they are loaded instead of measuring, otherwise the measured
+ * modes are appended. Allocates and frees ~12*(N+1)*256 KB of device memory
+ * and synchronises `stream`; call it outside timed or captured regions.
+ */
+int drag_expm_autotune(int32_t nspecies_max, const char *cache_path, cudaStream_t stream);
+
+/*
  * drag_expm_get_status — copy the current device's sticky status bits
  * (DRAG_STATUS_*) into *status_out and clear them. Synchronises `stream`.
  */

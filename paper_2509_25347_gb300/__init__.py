@@ -52,6 +52,12 @@ def load_library(path: str | None = None):
     lib.drag_expm_apply_batched.argtypes = [i64, vp, i64, i64, i64, i32, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     lib.drag_expm_apply_batched_noalloc.restype = ctypes.c_int
     lib.drag_expm_apply_batched_noalloc.argtypes = [i64, vp, i64, i64, i64, i32, vp, vp, vp, vp, vp, vp]
+    lib.drag_expm_set_mode.restype = ctypes.c_int
+    lib.drag_expm_set_mode.argtypes = [i32, i32]
+    lib.drag_expm_get_mode.restype = ctypes.c_int
+    lib.drag_expm_get_mode.argtypes = [i32, ctypes.POINTER(ctypes.c_int32)]
+    lib.drag_expm_autotune.restype = ctypes.c_int
+    lib.drag_expm_autotune.argtypes = [i32, ctypes.c_char_p, vp]
     lib.drag_expm_select.restype = ctypes.c_int
     lib.drag_expm_select.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp]
     lib.drag_expm_get_status.restype = ctypes.c_int
@@ -247,6 +253,29 @@ def select(rho_g, rho_d, t_s, dt: float, stream=None):
     _check(load_library().drag_expm_select(C, N, *args, float(dt), ctypes.c_void_p(k.data_ptr()),
                                            ctypes.c_void_p(s.data_ptr()), _stream_handle(stream)))
     return k, s
+
+
+MODE_WARP_PER_CELL = 0
+MODE_LANE_REGISTERS = 1
+MODE_LANE_SHARED = 2
+
+
+def set_mode(nspecies: int, mode: int) -> None:
+    """Force the kernel family used for ``nspecies`` on the current device."""
+    _check(load_library().drag_expm_set_mode(int(nspecies), int(mode)))
+
+
+def get_mode(nspecies: int) -> int:
+    out = ctypes.c_int32(0)
+    _check(load_library().drag_expm_get_mode(int(nspecies), ctypes.byref(out)))
+    return int(out.value)
+
+
+def autotune(nspecies_max: int, cache_path: str | None = None, stream=None) -> dict:
+    """Measure the fastest mode per N (1..nspecies_max); returns {N: mode}."""
+    p = cache_path.encode() if cache_path else None
+    _check(load_library().drag_expm_autotune(int(nspecies_max), p, _stream_handle(stream)))
+    return {N: get_mode(N) for N in range(1, int(nspecies_max) + 1)}
 
 
 def get_status(stream=None) -> int:
