@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import importlib.util
 import os
 import shutil
 import subprocess
@@ -19,7 +20,8 @@ OBJ_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libdragexpm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-I", INCLUDE]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-I", INCLUDE, "-I", OBJ_DIR]
+SCHED_INC = os.path.join(OBJ_DIR, "dx_sched_tables.inc")
 
 
 def nvcc() -> str:
@@ -33,7 +35,8 @@ def _stale(lib: str, sources: list[str]) -> bool:
     if not os.path.exists(lib):
         return True
     t = os.path.getmtime(lib)
-    deps = sources + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "drag_expm.h"), __file__]
+    deps = sources + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
+        [os.path.join(INCLUDE, "drag_expm.h"), __file__, os.path.join(HERE, "sched.py")]
     return any(os.path.getmtime(p) > t for p in deps)
 
 
@@ -42,6 +45,10 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     if not force and not _stale(LIB_PATH, sources):
         return LIB_PATH
     os.makedirs(OBJ_DIR, exist_ok=True)
+    spec = importlib.util.spec_from_file_location("dx_sched", os.path.join(HERE, "sched.py"))
+    sched = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(sched)
+    sched.write_header(SCHED_INC)            # squaring round schedules (static device tables)
     cc = nvcc()
     extra = list(extra or [])
 

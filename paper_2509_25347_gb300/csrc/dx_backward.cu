@@ -33,6 +33,7 @@
 namespace {
 
 constexpr int kWarpsPerBlock = 4;
+constexpr int kCellsPerBlock = 16;
 
 struct BwdArgs {
     long long C;
@@ -77,8 +78,17 @@ dx_backward_wpc(BwdArgs a, DxConsts K) {
     double *gg = wv + 4 * DX_NMAXF;    // g_d                                       [3][32]
 
     const long long C = a.C;
-    const long long nwarps = (long long)gridDim.x * kWarpsPerBlock;
-    for (long long c = (long long)blockIdx.x * kWarpsPerBlock + wib; c < C; c += nwarps) {
+    // Each block owns kCellsPerBlock consecutive cells, taken one at a time by
+    // its warps from a shared counter (balances cells of different s*).
+    __shared__ int next;
+    if (threadIdx.x == 0) next = 0;
+    __syncthreads();
+    for (int it = 0; it < kCellsPerBlock; it++) {
+        int kc = 0;
+        if (lane == 0) kc = atomicAdd(&next, 1);
+        kc = __shfl_sync(DX_FULL, kc, 0);
+        const long long c = (long long)blockIdx.x * kCellsPerBlock + kc;
+        if (kc >= kCellsPerBlock || c >= C) break;
         const double rg = a.rho_g[c];
         double rd = 0.0, ts = INFINITY;
         if (lane >= 1 && lane <= N) {
@@ -275,9 +285,7 @@ extern "C" int drag_expm_backward(int64_t ncells, int32_t nspecies, const double
     const int n = nspecies + 1;
     BwdArgs a{ncells, nspecies, rho_g, rho_d, t_s, v_in, grad_v_out, grad_v_in, grad_rho_g, grad_rho_d, grad_t_s,
               dt, st};
-    const long long want = (ncells + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    const long long cap = (long long)dx_sm_count() * 8;
-    const int grid = (int)(want < cap ? want : cap);
-    dx_backward_wpc<<<grid, kWarpsPerBlock * 32, bwd_smem_bytes(n), stream>>>(a, dx_consts());
+    const long long grid = (ncells + kCellsPerBlock - 1) / kCellsPerBlock;
+    dx_backward_wpc<<<(unsigned)grid, kWarpsPerBlock * 32, bwd_smem_bytes(n), stream>>>(a, dx_consts());
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }

@@ -27,6 +27,7 @@
 namespace {
 
 constexpr int kWarpsPerBlock = 4;
+constexpr int kCellsPerBlock = 16;
 
 struct FwdArgs {
     long long C;           // ncells
@@ -37,7 +38,7 @@ struct FwdArgs {
     uint32_t *status;
 };
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
 dx_forward_wpc(FwdArgs a, DxConsts K) {
     extern __shared__ double smem[];
     const int n = a.N + 1;
@@ -48,11 +49,23 @@ dx_forward_wpc(FwdArgs a, DxConsts K) {
     dx_build_pairs(n, od, hp);
     __syncthreads();
     double *wsm = smem + wib * wd;
-    const long long C = a.C;
-    const long long nwarps = (long long)gridDim.x * kWarpsPerBlock;
-    for (long long c = (long long)blockIdx.x * kWarpsPerBlock + wib; c < C; c += nwarps)
-        dx_wpc_forward_cell(lane, a.N, a.rho_g + c, a.rho_d + c, a.t_s + c, a.v_in + c, a.v_out + c, C, a.dt, K, wsm,
+    // Each block owns kCellsPerBlock consecutive cells; its warps take them one
+    // at a time from a shared counter, so cells of different cost (s* varies
+    // per cell) balance inside the block, and the hardware block scheduler
+    // balances blocks across the SMs. At most kCellsPerBlock iterations.
+    __shared__ int next;
+    if (threadIdx.x == 0) next = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kCellsPerBlock;
+    for (int it = 0; it < kCellsPerBlock; it++) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(&next, 1);
+        k = __shfl_sync(DX_FULL, k, 0);
+        const long long c = base + k;
+        if (k >= kCellsPerBlock || c >= a.C) break;
+        dx_wpc_forward_cell(lane, a.N, a.rho_g + c, a.rho_d + c, a.t_s + c, a.v_in + c, a.v_out + c, a.C, a.dt, K, wsm,
                             od, hp, a.status);
+    }
 }
 
 // (k*, s*) per cell, one thread per cell (diagnostics and FLOP accounting).
@@ -129,10 +142,8 @@ extern "C" int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *r
         }))
         return DRAG_ECUDA;
     FwdArgs a{ncells, nspecies, rho_g, rho_d, t_s, v_in, v_out, dt, st};
-    const long long want = (ncells + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    const long long cap = (long long)dx_sm_count() * 8;
-    const int grid = (int)(want < cap ? want : cap);
-    dx_forward_wpc<<<grid, kWarpsPerBlock * 32, smem, stream>>>(a, dx_consts());
+    const long long grid = (ncells + kCellsPerBlock - 1) / kCellsPerBlock;
+    dx_forward_wpc<<<(unsigned)grid, kWarpsPerBlock * 32, smem, stream>>>(a, dx_consts());
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }
 

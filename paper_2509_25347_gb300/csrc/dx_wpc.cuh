@@ -15,6 +15,7 @@
 #pragma once
 
 #include "dx_common.cuh"
+#include "dx_sched_tables.inc"   // generated at build time by sched.py
 
 constexpr int kPairSlots = 544;   // >= n(n+1)/2 for n <= 32
 
@@ -156,6 +157,57 @@ __device__ __forceinline__ void dx_wpc_square_offdiag(int lane, int n, int ns, i
     }
 }
 
+// Row-sum restoration of the starting matrix (t = 0) and s squarings with
+// restoration (t = 1..s), run on the round schedule generated by sched.py:
+// each round gives every lane one task of n FP64 operations, either an
+// off-diagonal dot product of squaring t (i < j, reads E_{t-1}, writes E_t)
+// or the restoration of row i of E_t (i == j). Restorations of squaring t
+// share rounds with the first products of squaring t + 1 whenever the rows
+// those need are complete. Chunks of at most DX_SCHED_H squarings each start
+// with a restoration (a no-op on an already restored matrix). The matrix
+// starts in B[p0]; returns the index of the buffer holding the result.
+__device__ __forceinline__ int dx_wpc_square_chain(int lane, int n, int ns, int s, double *B0, double *B1, int p0,
+                                                   const DxVecs &V) {
+    const unsigned short *tab = dx_sched_task + (size_t)dx_sched_off[n] * 32;
+    const unsigned short *endr = dx_sched_end + n * (DX_SCHED_H + 1);
+    int remaining = s, parity = p0;
+    do {
+        const int h = remaining < DX_SCHED_H ? remaining : DX_SCHED_H;
+        const int nr = endr[h];
+        for (int r = 0; r < nr; r++) {
+            const unsigned int code = tab[r * 32 + lane];
+            const int t = (int)(code >> 10);
+            if (code != 0xFFFFu && t <= h) {
+                const int i = code & 31, j = (code >> 5) & 31;
+                const bool isR = i == j;
+                double *dst = (parity ^ (t & 1)) ? B1 : B0;
+                const double *src = isR ? dst : ((parity ^ ((t - 1) & 1)) ? B1 : B0);
+                const double *pa = src + i * ns;
+                const double *pb = isR ? V.sig : src + j * ns;
+                double acc = 0.0;
+                for (int q = 0; q < n - 1; q++) {
+                    const int k = (isR && q >= i) ? q + 1 : q;
+                    acc = fma(pa[k], pb[k], acc);
+                }
+                const double x = isR ? -V.tau[i] : pa[n - 1];
+                const double y = isR ? acc : pb[n - 1];
+                const double z = isR ? 1.0 : acc;
+                const double res = fma(x, y, z);
+                if (isR) {
+                    dst[i * ns + i] = res;
+                } else {
+                    dst[i * ns + j] = res;
+                    dst[j * ns + i] = res;
+                }
+            }
+            __syncwarp();
+        }
+        parity ^= h & 1;
+        remaining -= h;
+    } while (remaining > 0);
+    return parity;
+}
+
 // Warp-cooperative pair tables (one warp builds its own; used when n varies per item).
 __device__ __forceinline__ void dx_build_pairs_warp(int lane, int n, unsigned short *od, unsigned short *hp) {
     const int n_od = n * (n - 1) / 2, n_hp = n * (n + 1) / 2 - 1;
@@ -227,17 +279,11 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
         __syncwarp();
         double *tmp = F; F = G; G = tmp;
     }
-    dx_wpc_restore(lane, n, ns, V, F);
-    __syncwarp();
 
-    // s squarings (Eq. ExpEq1 with n = 2^s), row sums restored each time
-    for (int it = 0; it < L.s; it++) {
-        dx_wpc_square_offdiag(lane, n, ns, n_od, od, F, G);
-        __syncwarp();
-        dx_wpc_restore(lane, n, ns, V, G);
-        __syncwarp();
-        double *tmp = F; F = G; G = tmp;
-    }
+    // row-sum restoration, then s squarings (Eq. ExpEq1 with n = 2^s), each restored
+    (void)od;
+    (void)n_od;
+    F = dx_wpc_square_chain(lane, n, ns, L.s, E0, E1, F == E1 ? 1 : 0, V) ? E1 : E0;
 
     // v_out_i = E_ii v_i + tau_i sum_{j != i} E_ij sigma_j v_j  (P = D_sigma^-1 E D_sigma)
     if (lane < n) {
