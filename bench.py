@@ -341,7 +341,20 @@ def run_ours(args, rank, world):
     if dx.get_status():
         raise RuntimeError("device status set after forward + adjoint")
 
-    total_ms, e2e_ms, fb_ms = max_over_ranks([total_ms, e2e_ms, fb_ms], world, device="cuda")
+    # analytic implicit RK1 (App. A.2): the paper's cost reference for EXP
+    rk_steps = max(3, args.steps)
+    for _ in range(2):
+        dx.rk1_apply(rg, rd, ts, cells.dt, v, vout)
+    torch.cuda.synchronize()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(rk_steps):
+        dx.rk1_apply(rg, rd, ts, cells.dt, v, vout)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    rk_ms = r0.elapsed_time(r1) / rk_steps
+
+    total_ms, e2e_ms, fb_ms, rk_ms = max_over_ranks([total_ms, e2e_ms, fb_ms, rk_ms], world, device="cuda")
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(C, world, ms_per_step)
     e2e_value = whole_job_rate(C, world, e2e_ms)
@@ -377,6 +390,10 @@ def run_ours(args, rank, world):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "fwd_adjoint": {"value": whole_job_rate(C, world, fb_ms), "unit": UNIT, "ms_per_step": fb_ms, "steps": fb_steps,
                         "note": "forward + dL/dv_out (torch sub) + drag_expm_backward, outside the headline timed region"},
+        "rk1": {"value": whole_job_rate(C, world, rk_ms), "unit": UNIT, "ms_per_step": rk_ms,
+                "exp_over_rk1_time": ms_per_step / rk_ms, "hbm_gbs": bytes_cell * C / (rk_ms * 1e-3) / 1e9,
+                "hbm_frac_of_measured": (bytes_cell * C / (rk_ms * 1e-3) / 1e9 / hbm_peak) if hbm_peak else None,
+                "note": "drag_rk1_apply (analytic implicit RK1, App. A.2), outside the headline timed region"},
         "gpu_launches": args.steps,
         "clocks": clocks,
     }

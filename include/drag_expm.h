@@ -138,6 +138,17 @@ typedef struct drag_block {
 } drag_block_t;
 
 /*
+ * drag_rk1_apply — first-order implicit drag step with the analytic solution
+ * of App. A.2 (Eqs. analytic_1-4), the paper's O(N) cost reference for EXP:
+ * v_out = (I - dt Omega_v)^-1 v_in per cell (backward Euler; drag-only split
+ * step, U^(n+1/2) = U^n in Eq. eq_rk1_2). First-order accurate in dt,
+ * unconditionally stable, conserves momentum. Arguments, layout, in-place use
+ * and error behaviour as drag_expm_apply.
+ */
+int drag_rk1_apply(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d, const double *t_s,
+                   double dt, const double *v_in, double *v_out, cudaStream_t stream);
+
+/*
  * drag_expm_batched_workspace_bytes — scratch bytes drag_expm_apply_batched
  * needs for nblocks blocks over arrays of total_cells gas cells (about
  * 12 bytes per cell plus 300 KB). Host only, no CUDA call.

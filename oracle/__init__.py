@@ -68,6 +68,9 @@ def _load():
     lib.orc_drag_apply_batched.restype = ctypes.c_int
     lib.orc_drag_apply_batched.argtypes = [ctypes.c_int64, i64p, i64p, i64p, i32p, i32p, dp, dp, dp, dp, dp, dp,
                                            ctypes.POINTER(ctypes.c_uint32)]
+    lib.orc_rk1_apply.restype = ctypes.c_int
+    lib.orc_rk1_apply.argtypes = [ctypes.c_int64, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp, dp,
+                                  ctypes.POINTER(ctypes.c_uint32)]
     for name in ("orc_table_mk", "orc_table_qk", "orc_table_rk"):
         getattr(lib, name).restype = ctypes.c_int
         getattr(lib, name).argtypes = [ctypes.c_int]
@@ -218,3 +221,19 @@ def drag_apply_batched(desc, rho_g, rho_d, t_s, v_in):
     if rc != 0:
         raise ValueError(f"oracle rejected a block (rc={rc})")
     return v_out, st.value
+
+
+def rk1_apply(rho_g, rho_d, t_s, dt, v_in):
+    """Analytic implicit RK1 drag step (App. A.2) over SoA arrays; returns v_out."""
+    rho_g = np.ascontiguousarray(rho_g, dtype=np.float64)
+    rho_d = np.ascontiguousarray(rho_d, dtype=np.float64)
+    t_s = np.ascontiguousarray(t_s, dtype=np.float64)
+    v_in = np.ascontiguousarray(v_in, dtype=np.float64)
+    C, N = rho_g.shape[0], rho_d.shape[0]
+    v_out = np.empty_like(v_in)
+    st = ctypes.c_uint32(0)
+    rc = _load().orc_rk1_apply(C, N, _dptr(rho_g), _dptr(rho_d), _dptr(t_s), float(dt), _dptr(v_in), _dptr(v_out),
+                               ctypes.byref(st))
+    if rc != 0:
+        raise ValueError(f"oracle rejected sizes (rc={rc})")
+    return v_out

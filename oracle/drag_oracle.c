@@ -563,6 +563,67 @@ int orc_drag_apply_batched(int64_t nblocks, const int64_t *cell_offset, const in
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Implicit RK1 with the analytic solution (App. A.2, Eqs. analytic_1-4)     */
+/* ------------------------------------------------------------------------ */
+
+/* One backward-Euler drag step: (I - dt Omega) q = b with b the momenta
+ * U^n = [rho_g v_g, rho_d,i v_d,i] (drag-only splitting, U^(n+1/2) = U^n in
+ * Eq. eq_rk1_2), solved as in the paper:
+ *   q_0 = (b_0 + dt B) / A,  A = 1 + sum_i (1 - 1/(1 + alpha_i dt)) eps_i,
+ *                            B = sum_i alpha_i b_i / (1 + alpha_i dt)      (Eq. analytic_4)
+ *   q_i = (b_i + eps_i alpha_i dt q_0) / (1 + alpha_i dt)                 (Eq. analytic_3)
+ * then v = q / rho. For a species with rho_d,i = 0 the momentum q_i carries no
+ * velocity; its velocity follows from row i of the same system in velocity
+ * form, v_i' = (v_i + alpha_i dt v_g') / (1 + alpha_i dt). */
+int orc_rk1_apply(int64_t C, int N, const double *rho_g, const double *rho_d, const double *t_s, double dt,
+                  const double *v_in, double *v_out, uint32_t *status)
+{
+    if (C < 0 || N < 1 || N + 1 > ORC_NMAX) return -1;
+    const int n = N + 1;
+    double rd[ORC_NMAX], ts[ORC_NMAX], eps[ORC_NMAX], alpha[ORC_NMAX];
+    uint32_t st = 0;
+    for (int64_t c = 0; c < C; c++) {
+        for (int i = 0; i < N; i++) {
+            rd[i] = rho_d[(int64_t)i * C + c];
+            ts[i] = t_s[(int64_t)i * C + c];
+        }
+        const int ok = orc_cell_valid(N, rho_g[c], rd, ts, dt);
+        for (int i = 0; i < N; i++) {
+            eps[i] = rd[i] / rho_g[c];
+            alpha[i] = 1.0 / ts[i];
+        }
+        for (int d = 0; d < 3; d++) {
+            double b[ORC_NMAX], q[ORC_NMAX];
+            b[0] = rho_g[c] * v_in[((int64_t)d * n + 0) * C + c];
+            for (int i = 1; i < n; i++) b[i] = rd[i - 1] * v_in[((int64_t)d * n + i) * C + c];
+            double Acoef = 1.0, Bcoef = 0.0;
+            for (int i = 1; i < n; i++) {
+                const double den = 1.0 + alpha[i - 1] * dt;
+                Acoef += (1.0 - 1.0 / den) * eps[i - 1];
+                Bcoef += (alpha[i - 1] / den) * b[i];
+            }
+            q[0] = (b[0] + dt * Bcoef) / Acoef;
+            const double vg = q[0] / rho_g[c];
+            v_out[((int64_t)d * n + 0) * C + c] = ok ? vg : NAN;
+            for (int i = 1; i < n; i++) {
+                const double den = 1.0 + alpha[i - 1] * dt;
+                double vi;
+                if (rd[i - 1] > 0.0) {
+                    q[i] = (b[i] + eps[i - 1] * alpha[i - 1] * dt * q[0]) / den;
+                    vi = q[i] / rd[i - 1];
+                } else {
+                    vi = (v_in[((int64_t)d * n + i) * C + c] + alpha[i - 1] * dt * vg) / den;
+                }
+                v_out[((int64_t)d * n + i) * C + c] = ok ? vi : NAN;
+            }
+        }
+        if (!ok) st |= 1u;
+    }
+    if (status) *status |= st;
+    return 0;
+}
+
 /* Z = L(A^T, G) for one dense n x n pair (tests of the Frechet machinery).
  * structured != 0 only for A with zero row sums (column sums of exp(A^T) = 1). */
 int orc_frechet_dense(int n, const double *A, const double *G, double *Z, int structured)
