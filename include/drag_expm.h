@@ -85,6 +85,22 @@ int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *rho_g, const
                     double dt, const double *v_in, double *v_out, cudaStream_t stream);
 
 /*
+ * drag_expm_apply_heat — drag_expm_apply plus the energy epilogue: heat_out[c]
+ * receives the kinetic energy (per unit volume) the drag step dissipates in
+ * cell c, sum_f 1/2 rho_f (|v_in,f - V|^2 - |v_out,f - V|^2) with V the
+ * centre-of-mass velocity (Eq. V_cm), which is >= 0. The frictional-heating
+ * term of Eqs. GenEq_3 / CompVar4 integrated over the exact step is w * heat;
+ * the gas energy changes by 1/2 rho_g (|v_g,out|^2 - |v_g,in|^2) + w * heat
+ * (w = 1 deposits all dissipation into the gas). The paper does not spell out
+ * EXP's energy update; this is the exact integral of its source terms.
+ *   heat_out : DEVICE, ncells doubles, written (NaN for invalid cells).
+ * Other arguments as drag_expm_apply (in place allowed).
+ */
+int drag_expm_apply_heat(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                         const double *t_s, double dt, const double *v_in, double *v_out, double *heat_out,
+                         cudaStream_t stream);
+
+/*
  * drag_expm_select — the (k*, s*) that drag_expm_apply uses for each cell:
  * Algorithm 2 with K = 9 on the 1-norm of A = dt Omega_v. The Taylor order is
  * m* = m_{k*} of Table B.1 and the cell costs k* + s* matrix products

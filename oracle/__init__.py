@@ -68,6 +68,8 @@ def _load():
     lib.orc_drag_apply_batched.restype = ctypes.c_int
     lib.orc_drag_apply_batched.argtypes = [ctypes.c_int64, i64p, i64p, i64p, i32p, i32p, dp, dp, dp, dp, dp, dp,
                                            ctypes.POINTER(ctypes.c_uint32)]
+    lib.orc_drag_heat.restype = ctypes.c_int
+    lib.orc_drag_heat.argtypes = [ctypes.c_int64, ctypes.c_int, dp, dp, dp, dp, dp]
     lib.orc_rk1_apply.restype = ctypes.c_int
     lib.orc_rk1_apply.argtypes = [ctypes.c_int64, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp, dp,
                                   ctypes.POINTER(ctypes.c_uint32)]
@@ -237,3 +239,17 @@ def rk1_apply(rho_g, rho_d, t_s, dt, v_in):
     if rc != 0:
         raise ValueError(f"oracle rejected sizes (rc={rc})")
     return v_out
+
+
+def drag_heat(rho_g, rho_d, v_in, v_out):
+    """Kinetic energy dissipated by a drag step, per cell (frictional heating)."""
+    rho_g = np.ascontiguousarray(rho_g, dtype=np.float64)
+    rho_d = np.ascontiguousarray(rho_d, dtype=np.float64)
+    v_in = np.ascontiguousarray(v_in, dtype=np.float64)
+    v_out = np.ascontiguousarray(v_out, dtype=np.float64)
+    C, N = rho_g.shape[0], rho_d.shape[0]
+    heat = np.empty(C)
+    rc = _load().orc_drag_heat(C, N, _dptr(rho_g), _dptr(rho_d), _dptr(v_in), _dptr(v_out), _dptr(heat))
+    if rc != 0:
+        raise ValueError(f"oracle rejected sizes (rc={rc})")
+    return heat

@@ -564,6 +564,45 @@ int orc_drag_apply_batched(int64_t nblocks, const int64_t *cell_offset, const in
 }
 
 /* ------------------------------------------------------------------------ */
+/* Frictional heating (energy epilogue)                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Kinetic energy the drag step dissipates, per cell:
+ *   heat = sum_f 1/2 rho_f (|v_in,f - V|^2 - |v_out,f - V|^2),
+ *   V = sum_f rho_f v_in,f / sum_f rho_f  (centre-of-mass velocity, Eq. V_cm).
+ * The drag terms of Eqs. GenEq_2/GenEq_5 change the mixture's kinetic energy at
+ * the rate -sum_i rho_d,i |v_d,i - v_g|^2 / T_s,i, which Eq. GenEq_3 returns
+ * to the gas as heat with weight w; over an exact step the integral is the
+ * kinetic-energy drop, and since momentum is conserved it can be measured
+ * about V (removing the common motion). The gas energy then changes by
+ * 1/2 rho_g (|v_g,out|^2 - |v_g,in|^2) + w heat. */
+int orc_drag_heat(int64_t C, int N, const double *rho_g, const double *rho_d, const double *v_in,
+                  const double *v_out, double *heat)
+{
+    if (C < 0 || N < 1 || N + 1 > ORC_NMAX) return -1;
+    const int n = N + 1;
+    for (int64_t c = 0; c < C; c++) {
+        double rho[ORC_NMAX], mass = 0.0;
+        rho[0] = rho_g[c];
+        for (int i = 1; i < n; i++) rho[i] = rho_d[(int64_t)(i - 1) * C + c];
+        for (int f = 0; f < n; f++) mass += rho[f];
+        double h = 0.0;
+        for (int d = 0; d < 3; d++) {
+            double mom = 0.0;
+            for (int f = 0; f < n; f++) mom += rho[f] * v_in[((int64_t)d * n + f) * C + c];
+            const double V = mom / mass;
+            for (int f = 0; f < n; f++) {
+                const double a = v_in[((int64_t)d * n + f) * C + c] - V;
+                const double b = v_out[((int64_t)d * n + f) * C + c] - V;
+                h += 0.5 * rho[f] * (a * a - b * b);
+            }
+        }
+        heat[c] = h;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Implicit RK1 with the analytic solution (App. A.2, Eqs. analytic_1-4)     */
 /* ------------------------------------------------------------------------ */
 

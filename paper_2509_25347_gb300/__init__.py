@@ -13,7 +13,7 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["load_library", "apply", "backward", "rk1_apply", "apply_batched", "batched_workspace_bytes", "select", "get_status",
+__all__ = ["load_library", "apply", "apply_heat", "backward", "rk1_apply", "apply_batched", "batched_workspace_bytes", "select", "get_status",
            "theta", "DragExpm", "DragExpmError",
            "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"]
 
@@ -58,6 +58,8 @@ def load_library(path: str | None = None):
     lib.drag_expm_get_mode.argtypes = [i32, ctypes.POINTER(ctypes.c_int32)]
     lib.drag_expm_autotune.restype = ctypes.c_int
     lib.drag_expm_autotune.argtypes = [i32, ctypes.c_char_p, vp]
+    lib.drag_expm_apply_heat.restype = ctypes.c_int
+    lib.drag_expm_apply_heat.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp, vp]
     lib.drag_rk1_apply.restype = ctypes.c_int
     lib.drag_rk1_apply.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp]
     lib.drag_expm_select.restype = ctypes.c_int
@@ -118,6 +120,22 @@ def apply(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, stream=None):
     vo = _f64_cuda("v_out", v_out, (3, N + 1, C))
     _check(load_library().drag_expm_apply(C, N, *args, float(dt), vi, vo, _stream_handle(stream)))
     return v_out
+
+
+def apply_heat(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, heat_out=None, stream=None):
+    """Forward update plus the dissipated kinetic energy per cell. Returns (v_out, heat)."""
+    import torch
+    C, N = _shapes(rho_g, rho_d)
+    if v_out is None:
+        v_out = torch.empty_like(v_in)
+    if heat_out is None:
+        heat_out = torch.empty((C,), dtype=torch.float64, device=v_in.device)
+    args = [_f64_cuda("rho_g", rho_g, (C,)), _f64_cuda("rho_d", rho_d, (N, C)), _f64_cuda("t_s", t_s, (N, C))]
+    vi = _f64_cuda("v_in", v_in, (3, N + 1, C))
+    vo = _f64_cuda("v_out", v_out, (3, N + 1, C))
+    ho = _f64_cuda("heat_out", heat_out, (C,))
+    _check(load_library().drag_expm_apply_heat(C, N, *args, float(dt), vi, vo, ho, _stream_handle(stream)))
+    return v_out, heat_out
 
 
 def rk1_apply(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, stream=None):

@@ -36,6 +36,7 @@ struct FwdArgs {
     double *v_out;
     double dt;
     uint32_t *status;
+    double *heat;          // optional per-cell dissipated kinetic energy
 };
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
@@ -64,7 +65,7 @@ dx_forward_wpc(FwdArgs a, DxConsts K) {
         const long long c = base + k;
         if (k >= kCellsPerBlock || c >= a.C) break;
         dx_wpc_forward_cell(lane, a.N, a.rho_g + c, a.rho_d + c, a.t_s + c, a.v_in + c, a.v_out + c, a.C, a.dt, K, wsm,
-                            od, hp, a.status);
+                            od, hp, a.status, a.heat ? a.heat + c : nullptr);
     }
 }
 
@@ -121,19 +122,19 @@ size_t dx_forward_smem_bytes(int n) {
     return sizeof(double) * (size_t)kWarpsPerBlock * dx_wpc_fwd_warp_doubles(n) + 2 * kPairSlots * sizeof(unsigned short);
 }
 
-extern "C" int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
-                               const double *t_s, double dt, const double *v_in, double *v_out,
-                               cudaStream_t stream) {
+static int apply_impl(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                      const double *t_s, double dt, const double *v_in, double *v_out, double *heat,
+                      cudaStream_t stream) {
     int rc = check_common(ncells, nspecies, rho_g, rho_d, t_s, dt);
     if (rc != DRAG_OK || ncells == 0) return rc;
     if (!v_in || !v_out) return DRAG_ENULL;
-    if (!aligned8(v_in) || !aligned8(v_out)) return DRAG_EALIGN;
+    if (!aligned8(v_in) || !aligned8(v_out) || (heat && !aligned8(heat))) return DRAG_EALIGN;
     uint32_t *st = dx_status_ptr();
     if (!st) return DRAG_ECUDA;
     const int n = nspecies + 1;
     const int mode = dx_mode_for(n);
     if (mode != DX_MODE_WPC)
-        return dx_launch_forward_lpc(n, mode == DX_MODE_LPC_SMEM, ncells, rho_g, rho_d, t_s, v_in, v_out, dt, st,
+        return dx_launch_forward_lpc(n, mode == DX_MODE_LPC_SMEM, ncells, rho_g, rho_d, t_s, v_in, v_out, dt, st, heat,
                                      stream);
     const size_t smem = dx_forward_smem_bytes(n);
     if (!dx_once_per_device(0, [] {
@@ -141,10 +142,23 @@ extern "C" int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *r
                                         (int)dx_forward_smem_bytes(DX_NMAXF)) == cudaSuccess;
         }))
         return DRAG_ECUDA;
-    FwdArgs a{ncells, nspecies, rho_g, rho_d, t_s, v_in, v_out, dt, st};
+    FwdArgs a{ncells, nspecies, rho_g, rho_d, t_s, v_in, v_out, dt, st, heat};
     const long long grid = (ncells + kCellsPerBlock - 1) / kCellsPerBlock;
     dx_forward_wpc<<<(unsigned)grid, kWarpsPerBlock * 32, smem, stream>>>(a, dx_consts());
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
+}
+
+extern "C" int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                               const double *t_s, double dt, const double *v_in, double *v_out,
+                               cudaStream_t stream) {
+    return apply_impl(ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, nullptr, stream);
+}
+
+extern "C" int drag_expm_apply_heat(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                                    const double *t_s, double dt, const double *v_in, double *v_out, double *heat_out,
+                                    cudaStream_t stream) {
+    if (!heat_out && ncells > 0) return DRAG_ENULL;
+    return apply_impl(ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, heat_out, stream);
 }
 
 extern "C" int drag_expm_select(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,

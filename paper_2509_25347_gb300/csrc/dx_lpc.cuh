@@ -69,7 +69,7 @@ template <int NF, bool SMEM>
 __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp, const double *rdp, const double *tsp,
                                                     const double *vip, double *vop, long long stride, double dt,
                                                     const DxConsts &K, const double *bsh, double *smem_warp,
-                                                    uint32_t *status) {
+                                                    uint32_t *status, double *heat = nullptr) {
     constexpr int N = NF - 1;
     constexpr int NT = DxPacked<NF>::NT;
     using P = DxPacked<NF>;
@@ -88,6 +88,7 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
     if (!ok) {
 #pragma unroll
         for (int e = 0; e < 3 * NF; e++) vop[e * stride] = NAN;
+        if (heat) *heat = NAN;
         atomicOr(status, DRAG_STATUS_BAD_CELL);
         return;
     }
@@ -201,6 +202,16 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
     }
 
     // ---------------- apply: v_out_i = E_ii v_i + tau_i sum_{k != i} E_ik sigma_k v_k
+    double rho[NF];
+    double mass = 0.0;
+    if (heat) {
+        rho[0] = rg;
+#pragma unroll
+        for (int i = 1; i < NF; i++) rho[i] = rdp[(i - 1) * stride];
+#pragma unroll
+        for (int f = 0; f < NF; f++) mass += rho[f];
+    }
+    double hsum = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         double v[NF], y[NF];
@@ -209,13 +220,25 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
             v[f] = vip[(d * NF + f) * stride];
             y[f] = sig[f] * v[f];
         }
+        double vc = 0.0;
+        if (heat) {
+#pragma unroll
+            for (int f = 0; f < NF; f++) vc = fma(rho[f], v[f], vc);
+            vc = __ddiv_rn(vc, mass);
+        }
 #pragma unroll
         for (int i = 0; i < NF; i++) {
             double acc = 0.0;
 #pragma unroll
             for (int k = 0; k < NF; k++)
                 if (k != i) acc = fma(Fm[P::at(i, k)], y[k], acc);
-            vop[(d * NF + i) * stride] = fma(tau[i], acc, Fm[P::at(i, i)] * v[i]);
+            const double out = fma(tau[i], acc, Fm[P::at(i, i)] * v[i]);
+            vop[(d * NF + i) * stride] = out;
+            if (heat) {
+                const double a = v[i] - vc, b = out - vc;
+                hsum = fma(0.5 * rho[i], (a - b) * (a + b), hsum);
+            }
         }
     }
+    if (heat) *heat = hsum;
 }

@@ -17,4 +17,5 @@ void dx_set_mode(int n, int mode);  // used by the autotuner
 bool dx_mode_valid(int n, int mode);
 
 int dx_launch_forward_lpc(int n, bool smem, long long C, const double *rho_g, const double *rho_d, const double *t_s,
-                          const double *v_in, double *v_out, double dt, uint32_t *status, cudaStream_t stream);
+                          const double *v_in, double *v_out, double dt, uint32_t *status, double *heat,
+                          cudaStream_t stream);

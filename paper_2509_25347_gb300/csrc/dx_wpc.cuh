@@ -230,11 +230,14 @@ __host__ __device__ __forceinline__ int dx_wpc_fwd_warp_doubles(int n) { return 
 // Forward update of one cell by one warp (warp-uniform arguments). Element i
 // of a per-species array is at p[i * stride]; velocity (d, f) at
 // p[(d * n + f) * stride]. od/hp: pair tables for this n. v_out may alias v_in.
+// heat (may be null, warp uniform): receives the kinetic energy the step
+// dissipates, sum_f 1/2 rho_f (|v_in,f - V|^2 - |v_out,f - V|^2) with V the
+// centre-of-mass velocity (frictional heating of Eq. GenEq_3, weight w = 1).
 __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const double *rgp, const double *rdp,
                                                     const double *tsp, const double *vip, double *vop,
                                                     long long stride, double dt, const DxConsts &K, double *wsm,
                                                     const unsigned short *od, const unsigned short *hp,
-                                                    uint32_t *status) {
+                                                    uint32_t *status, double *heat = nullptr) {
     const int n = N + 1, ns = dx_stride(n);
     const int n_od = n * (n - 1) / 2;
     const int n_hp = n * (n + 1) / 2 - 1;
@@ -265,7 +268,10 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
 #pragma unroll
             for (int d = 0; d < 3; d++) vop[((long long)d * n + lane) * stride] = NAN;
         }
-        if (lane == 0) atomicOr(status, DRAG_STATUS_BAD_CELL);
+        if (lane == 0) {
+            atomicOr(status, DRAG_STATUS_BAD_CELL);
+            if (heat) *heat = NAN;
+        }
         __syncwarp();
         return;
     }
@@ -294,6 +300,26 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
         }
     }
     __syncwarp();
+    double vcm[3] = {0.0, 0.0, 0.0};
+    if (heat) {
+        // centre-of-mass velocity: masses rho_f (lane f), momenta rho_f v_f
+        double mass = lane == 0 ? rg : (lane < n ? rd : 0.0);
+        double mom[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) mom[d] = mass * vin[d];
+        if (lane < n) V.ds[lane] = mass;          // X_ff is no longer needed: reuse as the mass table
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mass += __shfl_xor_sync(DX_FULL, mass, o);
+#pragma unroll
+            for (int d = 0; d < 3; d++) mom[d] += __shfl_xor_sync(DX_FULL, mom[d], o);
+        }
+        const double inv = __ddiv_rn(1.0, mass);
+#pragma unroll
+        for (int d = 0; d < 3; d++) vcm[d] = mom[d] * inv;
+        __syncwarp();
+    }
+    double hsum = 0.0;
     for (int t = lane; t < 3 * n; t += 32) {
         const int d = t / n, i = t - d * n;
         const double *y = yv + d * DX_NMAXF;
@@ -302,7 +328,19 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
             const int k = q + (q >= i);
             acc = fma(F[i * ns + k], y[k], acc);
         }
-        vop[((long long)d * n + i) * stride] = fma(V.tau[i], acc, F[i * ns + i] * vv[d * DX_NMAXF + i]);
+        const double vi = vv[d * DX_NMAXF + i];
+        const double out = fma(V.tau[i], acc, F[i * ns + i] * vi);
+        vop[((long long)d * n + i) * stride] = out;
+        if (heat) {
+            const double vc = d == 0 ? vcm[0] : (d == 1 ? vcm[1] : vcm[2]);
+            const double a = vi - vc, b = out - vc;
+            hsum = fma(0.5 * V.ds[i], (a - b) * (a + b), hsum);
+        }
+    }
+    if (heat) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) hsum += __shfl_xor_sync(DX_FULL, hsum, o);
+        if (lane == 0) *heat = hsum;
     }
     __syncwarp();
 }
