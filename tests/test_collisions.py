@@ -1,0 +1,50 @@
+"""Collisions tests B, C and the 20-species case (Sec. 3.1) driven through the
+GPU drag update, with Er1 (Eq. Error1_eq) against the exact solution."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2509_25347_gb300 import collisions as CO
+from tests.conftest import read_golden_table
+
+
+def test_exact_solution_matches_table1():
+    """V(t) from the eigenpairs reproduces Table 1's printed modes (CPU)."""
+    T = {r[0]: (float(r[1]), float(r[2])) for r in read_golden_table("collisions_table1.txt")}
+    for col, setup in ((0, CO.collisions_b()), (1, CO.collisions_c())):
+        lam = [T["lambda1"][col], T["lambda2"][col]]
+        coef = [(T["c_g1"][col], T["c_g2"][col]), (T["c_d11"][col], T["c_d12"][col]),
+                (T["c_d21"][col], T["c_d22"][col])]
+        times = np.linspace(0.0, 0.05 if col == 0 else 2.0, 9)
+        got = CO.exact_solution(setup, times)
+        for k, tt in enumerate(times):
+            ref = [T["V_CM"][col] + sum(c * math.exp(l * tt) for c, l in zip(coef[f], lam)) for f in range(3)]
+            assert np.allclose(got[k], ref, atol=2e-5, rtol=0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("which,dt0,t_final", [("b", 1e-4, 0.1), ("c", 1e-3, 2.0)])
+def test_er1_exp_flat_and_rk1_first_order(which, dt0, t_final):
+    """EXP stays at machine precision for every dt of the Fig. 2 sweep (the
+    paper reports a flat ~1e-8); RK1's Er1 falls linearly with dt."""
+    setup = CO.collisions_b() if which == "b" else CO.collisions_c()
+    exp = CO.convergence(setup, dt0, t_final, "exp")
+    assert max(e for _, e in exp) < 1e-12                # M steps accumulate ~M u at worst
+    rk1 = CO.convergence(setup, dt0, t_final, "rk1")
+    (d0, e0), (d1, e1) = rk1[0], rk1[1]
+    assert 1.6 < e1 / e0 < 2.4                           # halving dt halves the error at small dt
+    assert all(e_rk > 1e3 * e_exp for (_, e_rk), (_, e_exp) in zip(rk1, exp))
+
+
+@pytest.mark.gpu
+def test_20_species_collision():
+    """20 dust species, stopping times 1e-3..10, eps by Eq. dust_to_gas_ratio:
+    the EXP trajectory stays within 1e-13 of the exact solution (the paper
+    reports errors ~1e-7)."""
+    setup = CO.collisions_20_species()
+    assert abs(setup.rho_d.sum() - 1.0) < 1e-14
+    dt, steps = 0.01, 300
+    num = CO.integrate(setup, dt, steps, "exp")
+    ref = CO.exact_solution(setup, dt * np.arange(1, steps + 1))
+    assert np.max(np.abs(num - ref)) <= 1e-13 * np.max(np.abs(setup.v0))
