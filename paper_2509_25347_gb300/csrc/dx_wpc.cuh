@@ -224,8 +224,17 @@ __device__ __forceinline__ void dx_build_pairs_warp(int lane, int n, unsigned sh
     __syncwarp();
 }
 
-// Per-warp shared-memory footprint of the forward cell routine (doubles).
-__host__ __device__ __forceinline__ int dx_wpc_fwd_warp_doubles(int n) { return 2 * n * dx_stride(n) + 10 * DX_NMAXF; }
+// Per-warp shared-memory footprint of the forward cell routine (doubles):
+// E0, E1, then sigma, tau, X_0f, X_ff, the input velocities (3 x 32) and two
+// buffers of (v, sigma o v) for the repeated apply (2 x 2 x 3 x 32).
+__host__ __device__ __forceinline__ int dx_wpc_fwd_warp_doubles(int n) { return 2 * n * dx_stride(n) + 19 * DX_NMAXF; }
+
+// The last squarings are replaced by repeated applications: P^(2^q) v is
+// computed as P (P (... P v)) with q = min(s*, DX_APPLY_Q). One squaring costs
+// n(n+1)/2 tasks of n FP64 operations, one application 3n tasks of n + 2, so
+// for n = 17 two squarings and one application (~206 warp-level FP64
+// instructions) become four applications (~152).
+#define DX_APPLY_Q 2
 
 // Forward update of one cell by one warp (warp-uniform arguments). Element i
 // of a per-species array is at p[i * stride]; velocity (d, f) at
@@ -248,8 +257,9 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
     V.tau = V.sig + DX_NMAXF;
     V.xs = V.tau + DX_NMAXF;
     V.ds = V.xs + DX_NMAXF;
-    double *yv = V.ds + DX_NMAXF;      // sigma_f v_f, three components
-    double *vv = yv + 3 * DX_NMAXF;    // v_f, three components
+    double *v0 = V.ds + DX_NMAXF;      // input velocities v_f, three components
+    double *const wv0 = v0 + 3 * DX_NMAXF, *const wv1 = v0 + 9 * DX_NMAXF;    // current v, two buffers
+    double *const wy0 = v0 + 6 * DX_NMAXF, *const wy1 = v0 + 12 * DX_NMAXF;   // sigma o current v
 
     const double rg = *rgp;
     double rd = 0.0, ts = INFINITY;
@@ -286,17 +296,21 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
         double *tmp = F; F = G; G = tmp;
     }
 
-    // row-sum restoration, then s squarings (Eq. ExpEq1 with n = 2^s), each restored
+    // row-sum restoration, then s - q squarings (Eq. ExpEq1 with n = 2^s), each
+    // restored; the remaining q squarings become 2^q applications below
     (void)od;
     (void)n_od;
-    F = dx_wpc_square_chain(lane, n, ns, L.s, E0, E1, F == E1 ? 1 : 0, V) ? E1 : E0;
+    const int q = L.s < DX_APPLY_Q ? L.s : DX_APPLY_Q;
+    F = dx_wpc_square_chain(lane, n, ns, L.s - q, E0, E1, F == E1 ? 1 : 0, V) ? E1 : E0;
 
-    // v_out_i = E_ii v_i + tau_i sum_{j != i} E_ij sigma_j v_j  (P = D_sigma^-1 E D_sigma)
+    // v <- P v, 2^q times, P_ii = E_ii, P_ij = E_ij sigma_j / sigma_i (P = D_sigma^-1 E D_sigma):
+    // v_i' = E_ii v_i + tau_i sum_{j != i} E_ij sigma_j v_j
     if (lane < n) {
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            yv[d * DX_NMAXF + lane] = L.sg * vin[d];
-            vv[d * DX_NMAXF + lane] = vin[d];
+            v0[d * DX_NMAXF + lane] = vin[d];
+            wv0[d * DX_NMAXF + lane] = vin[d];
+            wy0[d * DX_NMAXF + lane] = L.sg * vin[d];
         }
     }
     __syncwarp();
@@ -319,23 +333,35 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
         for (int d = 0; d < 3; d++) vcm[d] = mom[d] * inv;
         __syncwarp();
     }
+    const int napply = 1 << q;
     double hsum = 0.0;
-    for (int t = lane; t < 3 * n; t += 32) {
-        const int d = t / n, i = t - d * n;
-        const double *y = yv + d * DX_NMAXF;
-        double acc = 0.0;
-        for (int q = 0; q < n - 1; q++) {
-            const int k = q + (q >= i);
-            acc = fma(F[i * ns + k], y[k], acc);
+    for (int ap = 0; ap < napply; ap++) {
+        const bool last = ap == napply - 1;
+        const bool odd = ap & 1;
+        const double *cv = odd ? wv1 : wv0, *cy = odd ? wy1 : wy0;
+        double *nv = odd ? wv0 : wv1, *ny = odd ? wy0 : wy1;
+        for (int t = lane; t < 3 * n; t += 32) {
+            const int d = t / n, i = t - d * n;
+            const double *y = cy + d * DX_NMAXF;
+            double acc = 0.0;
+            for (int qq = 0; qq < n - 1; qq++) {
+                const int k = qq + (qq >= i);
+                acc = fma(F[i * ns + k], y[k], acc);
+            }
+            const double out = fma(V.tau[i], acc, F[i * ns + i] * cv[d * DX_NMAXF + i]);
+            if (!last) {
+                nv[d * DX_NMAXF + i] = out;
+                ny[d * DX_NMAXF + i] = V.sig[i] * out;
+                continue;
+            }
+            vop[((long long)d * n + i) * stride] = out;
+            if (heat) {
+                const double vc = d == 0 ? vcm[0] : (d == 1 ? vcm[1] : vcm[2]);
+                const double a = v0[d * DX_NMAXF + i] - vc, b = out - vc;
+                hsum = fma(0.5 * V.ds[i], (a - b) * (a + b), hsum);
+            }
         }
-        const double vi = vv[d * DX_NMAXF + i];
-        const double out = fma(V.tau[i], acc, F[i * ns + i] * vi);
-        vop[((long long)d * n + i) * stride] = out;
-        if (heat) {
-            const double vc = d == 0 ? vcm[0] : (d == 1 ? vcm[1] : vcm[2]);
-            const double a = vi - vc, b = out - vc;
-            hsum = fma(0.5 * V.ds[i], (a - b) * (a + b), hsum);
-        }
+        __syncwarp();
     }
     if (heat) {
 #pragma unroll
