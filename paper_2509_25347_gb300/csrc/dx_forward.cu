@@ -39,7 +39,7 @@ struct FwdArgs {
     double *heat;          // optional per-cell dissipated kinetic energy
 };
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 7)
 dx_forward_wpc(FwdArgs a, DxConsts K) {
     extern __shared__ double smem[];
     const int n = a.N + 1;

@@ -114,22 +114,100 @@ __device__ __forceinline__ void dx_wpc_taylor_init(int lane, int n, int ns, int 
     __syncwarp();
 }
 
+// Lanes given to the dot product G_00 = sum_k F_0k X_k0 + bj in a Horner
+// step: a power-of-two group g at the top of the warp, idle in the step's last
+// round (32 rounds - n_hp >= g), each lane summing every g-th term, followed
+// by log2 g shuffle levels. The group is chosen to minimise the FP64
+// instructions the step adds beyond the two of its last round; 0 means the
+// plain full-warp reduction (7 instructions) is cheaper.
+__host__ __device__ __forceinline__ int dx_horner_g00_group(int n) {
+    const int n_hp = n * (n + 1) / 2 - 1;
+    const int idle = 32 * ((n_hp + 31) / 32) - n_hp;
+    int best = 7, group = 0;
+    for (int g = 1, lg = 0; g <= idle; g *= 2, lg++) {
+        const int per = (n + g - 1) / g;
+        const int cost = (per > 2 ? per - 2 : 0) + lg;
+        if (cost < best) {
+            best = cost;
+            group = g;
+        }
+    }
+    return group;
+}
+
 // One Horner step G = F X + bj I (F, G symmetric; X the arrowhead):
 //   G_ij = F_i0 X_0j + F_ij X_jj (+ bj if i == j) for i <= j, (i,j) != (0,0),
 //   G_00 = sum_k F_0k X_k0 + bj.
 __device__ __forceinline__ void dx_wpc_horner_step(int lane, int n, int ns, int n_hp, const unsigned short *hp,
                                                    const DxVecs &V, double bj, const double *F, double *G) {
-    for (int t = lane; t < n_hp; t += 32) {
-        const int p = hp[t], i = p >> 8, jj = p & 255;
+    const int g = dx_horner_g00_group(n);
+    if (g == 0) {
+        for (int t = lane; t < n_hp; t += 32) {
+            const int p = hp[t], i = p >> 8, jj = p & 255;
+            double acc = fma(F[i * ns], V.xs[jj], i == jj ? bj : 0.0);
+            acc = fma(F[i * ns + jj], V.ds[jj], acc);
+            G[i * ns + jj] = acc;
+            G[jj * ns + i] = acc;
+        }
+        double part = lane < n ? F[lane] * V.xs[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(DX_FULL, part, o);
+        if (lane == 0) G[0] = part + bj;
+        return;
+    }
+    // Rounds before the last: two FMAs per entry on every lane.
+    const int last = (n_hp - 1) >> 5;
+    for (int r = 0; r < last; r++) {
+        const int p = hp[r * 32 + lane], i = p >> 8, jj = p & 255;
         double acc = fma(F[i * ns], V.xs[jj], i == jj ? bj : 0.0);
         acc = fma(F[i * ns + jj], V.ds[jj], acc);
         G[i * ns + jj] = acc;
         G[jj * ns + i] = acc;
     }
-    double part = lane < n ? F[lane] * V.xs[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(DX_FULL, part, o);
-    if (lane == 0) G[0] = part + bj;
+    // Last round: the remaining entries, and on the g lanes at the top of the
+    // warp the partial sums of G_00 (lane 32 - g + phi takes the terms
+    // k = phi, phi + g, ...). Every lane issues the same, warp-uniform number
+    // of FMAs, absent terms being 0 * 0.
+    const int t = last * 32 + lane;
+    const bool task = t < n_hp;
+    const int phi = lane - (32 - g);
+    const bool grp = !task && phi >= 0;
+    const int cmax = (n + g - 1) / g;
+    double a0 = 0.0, b0 = 0.0, a1 = 0.0, b1 = 0.0, c = 0.0;
+    int dst = 0, dstT = 0;
+    if (task) {
+        const int p = hp[t], i = p >> 8, jj = p & 255;
+        a0 = F[i * ns];
+        b0 = V.xs[jj];
+        a1 = F[i * ns + jj];
+        b1 = V.ds[jj];
+        c = i == jj ? bj : 0.0;
+        dst = i * ns + jj;
+        dstT = jj * ns + i;
+    } else if (grp) {
+        if (phi < n) {
+            a0 = F[phi];
+            b0 = V.xs[phi];
+        }
+        if (phi + g < n) {
+            a1 = F[phi + g];
+            b1 = V.xs[phi + g];
+        }
+        c = phi == 0 ? bj : 0.0;
+    }
+    double acc = fma(a0, b0, c);
+    acc = fma(a1, b1, acc);
+    for (int u = 2; u < cmax; u++) {
+        const int k = phi + u * g;
+        const bool on = grp && k < n;
+        acc = fma(on ? F[on ? k : 0] : 0.0, on ? V.xs[on ? k : 0] : 0.0, acc);
+    }
+    if (task) {
+        G[dst] = acc;
+        G[dstT] = acc;
+    }
+    for (int o = g >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(DX_FULL, acc, o);
+    if (lane == 32 - g) G[0] = acc;
 }
 
 // Row-sum restoration in symmetric form: E_ii = 1 - tau_i sum_{k != i} E_ik sigma_k.
@@ -225,9 +303,9 @@ __device__ __forceinline__ void dx_build_pairs_warp(int lane, int n, unsigned sh
 }
 
 // Per-warp shared-memory footprint of the forward cell routine (doubles):
-// E0, E1, then sigma, tau, X_0f, X_ff, the input velocities (3 x 32) and two
-// buffers of (v, sigma o v) for the repeated apply (2 x 2 x 3 x 32).
-__host__ __device__ __forceinline__ int dx_wpc_fwd_warp_doubles(int n) { return 2 * n * dx_stride(n) + 19 * DX_NMAXF; }
+// E0, E1, then n-vectors: sigma, tau, X_0f, X_ff, the input velocities (3 of
+// them) and two buffers of (v, sigma o v) for the repeated apply (2 x 2 x 3).
+__host__ __device__ __forceinline__ int dx_wpc_fwd_warp_doubles(int n) { return 2 * n * dx_stride(n) + 19 * n; }
 
 // The last squarings are replaced by repeated applications: P^(2^q) v is
 // computed as P (P (... P v)) with q = min(s*, DX_APPLY_Q). One squaring costs
@@ -254,12 +332,12 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
     double *E1 = E0 + n * ns;
     DxVecs V;
     V.sig = E1 + n * ns;
-    V.tau = V.sig + DX_NMAXF;
-    V.xs = V.tau + DX_NMAXF;
-    V.ds = V.xs + DX_NMAXF;
-    double *v0 = V.ds + DX_NMAXF;      // input velocities v_f, three components
-    double *const wv0 = v0 + 3 * DX_NMAXF, *const wv1 = v0 + 9 * DX_NMAXF;    // current v, two buffers
-    double *const wy0 = v0 + 6 * DX_NMAXF, *const wy1 = v0 + 12 * DX_NMAXF;   // sigma o current v
+    V.tau = V.sig + n;
+    V.xs = V.tau + n;
+    V.ds = V.xs + n;
+    double *v0 = V.ds + n;      // input velocities v_f, three components
+    double *const wv0 = v0 + 3 * n, *const wv1 = v0 + 9 * n;    // current v, two buffers
+    double *const wy0 = v0 + 6 * n, *const wy1 = v0 + 12 * n;   // sigma o current v
 
     const double rg = *rgp;
     double rd = 0.0, ts = INFINITY;
@@ -308,9 +386,9 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
     if (lane < n) {
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            v0[d * DX_NMAXF + lane] = vin[d];
-            wv0[d * DX_NMAXF + lane] = vin[d];
-            wy0[d * DX_NMAXF + lane] = L.sg * vin[d];
+            v0[d * n + lane] = vin[d];
+            wv0[d * n + lane] = vin[d];
+            wy0[d * n + lane] = L.sg * vin[d];
         }
     }
     __syncwarp();
@@ -342,22 +420,22 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
         double *nv = odd ? wv0 : wv1, *ny = odd ? wy0 : wy1;
         for (int t = lane; t < 3 * n; t += 32) {
             const int d = t / n, i = t - d * n;
-            const double *y = cy + d * DX_NMAXF;
+            const double *y = cy + d * n;
             double acc = 0.0;
             for (int qq = 0; qq < n - 1; qq++) {
                 const int k = qq + (qq >= i);
                 acc = fma(F[i * ns + k], y[k], acc);
             }
-            const double out = fma(V.tau[i], acc, F[i * ns + i] * cv[d * DX_NMAXF + i]);
+            const double out = fma(V.tau[i], acc, F[i * ns + i] * cv[d * n + i]);
             if (!last) {
-                nv[d * DX_NMAXF + i] = out;
-                ny[d * DX_NMAXF + i] = V.sig[i] * out;
+                nv[d * n + i] = out;
+                ny[d * n + i] = V.sig[i] * out;
                 continue;
             }
             vop[((long long)d * n + i) * stride] = out;
             if (heat) {
                 const double vc = d == 0 ? vcm[0] : (d == 1 ? vcm[1] : vcm[2]);
-                const double a = v0[d * DX_NMAXF + i] - vc, b = out - vc;
+                const double a = v0[d * n + i] - vc, b = out - vc;
                 hsum = fma(0.5 * V.ds[i], (a - b) * (a + b), hsum);
             }
         }
