@@ -7,11 +7,14 @@
 //   2. count    (grid)   : per cell, Algorithm 2 -> bin (n, k*, min(s*, 63)), histogram;
 //   3. bins     (1 CTA)  : prefix sums of bin counts and of work items per bin;
 //   4. scatter  (grid)   : cells -> bin-sorted permutation;
-//   5. main     (persistent grid) : warps pull work items from one atomic counter.
+//   5. main     (persistent grids) : warps pull work items from atomic counters.
 //      An item is 32 cells of one bin run lane-per-cell (small n, the lanes
 //      of a warp share m* and s*, so no lane idles) or one cell run
 //      warp-per-cell (large n). The per-n choice comes from the mode table
-//      (drag_expm_autotune() measures it).
+//      (drag_expm_autotune() measures it). The two kinds of item run in two
+//      kernels, each with its own queue, so that the register-heavy
+//      lane-per-cell code does not set the occupancy of the warp-per-cell
+//      work.
 //
 // Every launch goes to the caller's stream; there is no host synchronisation
 // and no allocation (scratch is the caller's workspace), so the whole call can
@@ -28,7 +31,9 @@ namespace {
 constexpr int kSBins = 64;
 constexpr int kBinsPerN = DX_K * kSBins;
 constexpr int kNBins = (DX_NMAXF - 1) * kBinsPerN;   // n = 2..32
-constexpr int kMainWarps = 2;                        // warps per CTA of the persistent kernel
+constexpr int kLpcWarps = 2;                         // warps per CTA, lane-per-cell kernel
+constexpr int kWpcWarps = 4;                         // warps per CTA, warp-per-cell kernel
+constexpr int kWpcMinBlocks = 6;                     // resident CTAs per SM the latter is compiled for
 constexpr int kScanThreads = 1024;
 constexpr int kBatchLpcNMax = 9;                     // largest n run lane-per-cell in the batched kernel
 
@@ -43,8 +48,10 @@ struct Work {
     unsigned long long *perm;   // (block << 32) | local cell, bin-sorted
     unsigned int *key;          // bin of each enumerated cell
     long long *blk_start;       // exclusive prefix of valid block sizes [nblocks + 1]
-    unsigned int *hist, *offs, *cursor, *item_offs;   // [kNBins + 1]
-    unsigned int *ctr;          // [0] work counter, [1] items, [2] enumerated cells
+    unsigned int *hist, *offs, *cursor;               // [kNBins + 1]
+    unsigned int *item_w, *item_l;   // [kNBins + 1] first item of each bin among warp- / lane-per-cell items
+    unsigned int *ctr;   // [0] / [1] warp-per-cell queue counter / items, [2] enumerated cells,
+                         // [3] / [4] lane-per-cell queue counter / items
 };
 
 struct Modes {
@@ -90,7 +97,7 @@ dx_batch_prepare(long long nblocks, const Desc *blocks, long long total_cells, l
     __shared__ long long sh[kScanThreads];
     const int t = threadIdx.x;
     for (int i = t; i < kNBins; i += kScanThreads) W.hist[i] = 0;
-    if (t < 4) W.ctr[t] = 0;
+    if (t < 8) W.ctr[t] = 0;
     const long long per = (nblocks + kScanThreads - 1) / kScanThreads;
     const long long b0 = t * per, b1 = b0 + per < nblocks ? b0 + per : nblocks;
     long long sum = 0;
@@ -169,29 +176,35 @@ __global__ void __launch_bounds__(kScanThreads) dx_batch_bins(Work W, Modes M) {
     const int t = threadIdx.x;
     constexpr int per = (kNBins + kScanThreads - 1) / kScanThreads;
     const int i0 = t * per, i1 = i0 + per < kNBins ? i0 + per : kNBins;
-    long long cs = 0, is = 0;
+    long long cs = 0, ws = 0, ls = 0;
     for (int i = i0; i < i1; i++) {
         const unsigned int c = W.hist[i];
-        const int n = i / kBinsPerN + 2;
+        const bool wpc = M.m[i / kBinsPerN + 2] == DX_MODE_WPC;
         cs += c;
-        is += (M.m[n] == DX_MODE_WPC) ? c : (c + 31) / 32;
+        ws += wpc ? c : 0;
+        ls += wpc ? 0 : (c + 31) / 32;
     }
-    long long ctot, itot;
+    long long ctot, wtot, ltot;
     long long crun = block_exclusive_scan(cs, sh, ctot);
-    long long irun = block_exclusive_scan(is, sh, itot);
+    long long wrun = block_exclusive_scan(ws, sh, wtot);
+    long long lrun = block_exclusive_scan(ls, sh, ltot);
     for (int i = i0; i < i1; i++) {
         const unsigned int c = W.hist[i];
-        const int n = i / kBinsPerN + 2;
+        const bool wpc = M.m[i / kBinsPerN + 2] == DX_MODE_WPC;
         W.offs[i] = (unsigned int)crun;
         W.cursor[i] = (unsigned int)crun;
-        W.item_offs[i] = (unsigned int)irun;
+        W.item_w[i] = (unsigned int)wrun;
+        W.item_l[i] = (unsigned int)lrun;
         crun += c;
-        irun += (M.m[n] == DX_MODE_WPC) ? c : (c + 31) / 32;
+        wrun += wpc ? c : 0;
+        lrun += wpc ? 0 : (c + 31) / 32;
     }
     if (t == 0) {
         W.offs[kNBins] = (unsigned int)ctot;
-        W.item_offs[kNBins] = (unsigned int)itot;
-        W.ctr[1] = (unsigned int)itot;
+        W.item_w[kNBins] = (unsigned int)wtot;
+        W.item_l[kNBins] = (unsigned int)ltot;
+        W.ctr[1] = (unsigned int)wtot;
+        W.ctr[4] = (unsigned int)ltot;
     }
 }
 
@@ -239,63 +252,80 @@ __device__ __forceinline__ void lpc_dispatch(int n, int mode, int lane, const Ma
     }
 }
 
-__global__ void __launch_bounds__(kMainWarps * 32)
-dx_batch_main(long long nblocks, MainArgs a, Work W, Modes M, DxConsts K) {
-    extern __shared__ double smem[];
-    double *bsh = smem;
-    for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    double *wsm = smem + 32 + wib * (a.warp_doubles + 2 * kPairSlots / 4);
-    unsigned short *od = reinterpret_cast<unsigned short *>(wsm + a.warp_doubles);
-    unsigned short *hp = od + kPairSlots;
-    int table_n = 0;
-    const unsigned int nitems = W.ctr[1];
-    // Each iteration claims a fresh item, so a warp runs at most nitems + 1 of them.
+// Pulls items of one kind (warp- or lane-per-cell) from that kind's queue;
+// item_offs numbers the items of that kind bin by bin. Returns when the queue
+// is empty. Each claim takes a fresh item, so a warp runs at most nitems + 1
+// of them.
+template <typename F>
+__device__ __forceinline__ void dx_batch_queue(unsigned int *counter, unsigned int nitems,
+                                               const unsigned int *item_offs, uint32_t *status, F &&run) {
+    const int lane = threadIdx.x & 31;
     for (unsigned int guard = 0;; guard++) {
         if (guard > nitems) {
-            if (lane == 0) atomicOr(a.status, DRAG_STATUS_QUEUE_GUARD);
+            if (lane == 0) atomicOr(status, DRAG_STATUS_QUEUE_GUARD);
             break;
         }
         unsigned int item = 0;
-        if (lane == 0) item = atomicAdd(&W.ctr[0], 1u);
+        if (lane == 0) item = atomicAdd(counter, 1u);
         item = __shfl_sync(DX_FULL, item, 0);
         if (item >= nitems) break;
         // bin holding this item: last bin with item_offs[bin] <= item
         int lo = 0, hi = kNBins;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (W.item_offs[mid] <= item) lo = mid; else hi = mid;
+            if (item_offs[mid] <= item) lo = mid; else hi = mid;
         }
-        const int bin = lo, n = bin / kBinsPerN + 2, mode = M.m[n];
-        const unsigned int sub = item - W.item_offs[bin];
-        if (mode == DX_MODE_WPC) {
-            const unsigned long long p = W.perm[W.offs[bin] + sub];
-            const Desc d = a.blocks[p >> 32];
-            const long long c = (long long)(p & 0xffffffffull);
-            if (table_n != n) {
-                dx_build_pairs_warp(lane, n, od, hp);
-                table_n = n;
-            }
-            dx_wpc_forward_cell(lane, d.nspecies, a.rho_g + d.cell_offset + c, a.rho_d + d.dust_offset + c,
-                                a.t_s + d.dust_offset + c, a.v_in + d.vel_offset + c, a.v_out + d.vel_offset + c,
-                                d.ncells, d.dt, K, wsm, od, hp, a.status);
-        } else {
-            const unsigned int pos = W.offs[bin] + 32 * sub + lane;
-            if (pos < W.offs[bin + 1]) {
-                const unsigned long long p = W.perm[pos];
-                const Desc d = a.blocks[p >> 32];
-                lpc_dispatch(n, mode, lane, a, d, (long long)(p & 0xffffffffull), K, bsh, wsm);
-            }
-            __syncwarp();
-        }
+        run(lo, item - item_offs[lo]);
     }
+}
+
+__global__ void __launch_bounds__(kWpcWarps * 32, kWpcMinBlocks)
+dx_batch_main_wpc(MainArgs a, Work W, DxConsts K) {
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double *wsm = smem + wib * (a.warp_doubles + 2 * kPairSlots / 4);
+    unsigned short *od = reinterpret_cast<unsigned short *>(wsm + a.warp_doubles);
+    unsigned short *hp = od + kPairSlots;
+    int table_n = 0;
+    dx_batch_queue(&W.ctr[0], W.ctr[1], W.item_w, a.status, [&](int bin, unsigned int sub) {
+        const int n = bin / kBinsPerN + 2;
+        const unsigned long long p = W.perm[W.offs[bin] + sub];
+        const Desc d = a.blocks[p >> 32];
+        const long long c = (long long)(p & 0xffffffffull);
+        if (table_n != n) {
+            dx_build_pairs_warp(lane, n, od, hp);
+            table_n = n;
+        }
+        dx_wpc_forward_cell(lane, d.nspecies, a.rho_g + d.cell_offset + c, a.rho_d + d.dust_offset + c,
+                            a.t_s + d.dust_offset + c, a.v_in + d.vel_offset + c, a.v_out + d.vel_offset + c,
+                            d.ncells, d.dt, K, wsm, od, hp, a.status);
+    });
+}
+
+__global__ void __launch_bounds__(kLpcWarps * 32)
+dx_batch_main_lpc(MainArgs a, Work W, Modes M, DxConsts K) {
+    extern __shared__ double smem[];
+    double *bsh = smem;
+    for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double *wsm = smem + 32 + wib * a.warp_doubles;
+    dx_batch_queue(&W.ctr[3], W.ctr[4], W.item_l, a.status, [&](int bin, unsigned int sub) {
+        const int n = bin / kBinsPerN + 2;
+        const unsigned int pos = W.offs[bin] + 32 * sub + lane;
+        if (pos < W.offs[bin + 1]) {
+            const unsigned long long p = W.perm[pos];
+            const Desc d = a.blocks[p >> 32];
+            lpc_dispatch(n, M.m[n], lane, a, d, (long long)(p & 0xffffffffull), K, bsh, wsm);
+        }
+        __syncwarp();
+    });
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t perm, key, blk_start, hist, offs, cursor, item_offs, ctr, total;
+    size_t perm, key, blk_start, hist, offs, cursor, item_w, item_l, ctr, total;
 };
 
 Layout layout(long long nblocks, long long total_cells) {
@@ -307,19 +337,28 @@ Layout layout(long long nblocks, long long total_cells) {
     L.hist = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
     L.offs = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
     L.cursor = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
-    L.item_offs = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
+    L.item_w = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
+    L.item_l = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
     L.ctr = o; o += align256(sizeof(unsigned int) * 8);
     L.total = o;
     return L;
 }
 
-// Per-warp shared memory (doubles) the main kernel needs for matrices up to n_max.
-int warp_doubles_for(const Modes &M, int n_max) {
-    int w = 0;
+// Per-warp shared memory (doubles) each main kernel needs for matrices up to
+// n_max; *has_wpc / *has_lpc tell whether any n <= n_max runs that way.
+void warp_doubles_for(const Modes &M, int n_max, int *wpc, int *lpc, bool *has_wpc, bool *has_lpc) {
+    *wpc = *lpc = 0;
+    *has_wpc = *has_lpc = false;
     for (int n = 2; n <= n_max; n++) {
         int need = 0;
-        if (M.m[n] == DX_MODE_WPC) need = dx_wpc_fwd_warp_doubles(n);
-        else if (M.m[n] == DX_MODE_LPC_SMEM) {
+        if (M.m[n] == DX_MODE_WPC) {
+            *has_wpc = true;
+            need = dx_wpc_fwd_warp_doubles(n);
+            *wpc = need > *wpc ? need : *wpc;
+            continue;
+        }
+        *has_lpc = true;
+        if (M.m[n] == DX_MODE_LPC_SMEM) {
             switch (n) {
                 case 2: need = dx_lpc_warp_smem_doubles<2>(); break;
                 case 3: need = dx_lpc_warp_smem_doubles<3>(); break;
@@ -332,9 +371,8 @@ int warp_doubles_for(const Modes &M, int n_max) {
                 default: break;
             }
         }
-        w = need > w ? need : w;
+        *lpc = need > *lpc ? need : *lpc;
     }
-    return w;
 }
 
 bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
@@ -382,7 +420,8 @@ extern "C" int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *bloc
     W.hist = reinterpret_cast<unsigned int *>(ws + L.hist);
     W.offs = reinterpret_cast<unsigned int *>(ws + L.offs);
     W.cursor = reinterpret_cast<unsigned int *>(ws + L.cursor);
-    W.item_offs = reinterpret_cast<unsigned int *>(ws + L.item_offs);
+    W.item_w = reinterpret_cast<unsigned int *>(ws + L.item_w);
+    W.item_l = reinterpret_cast<unsigned int *>(ws + L.item_l);
     W.ctr = reinterpret_cast<unsigned int *>(ws + L.ctr);
 
     const Modes M = dx_batch_modes();
@@ -397,16 +436,34 @@ extern "C" int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *bloc
     dx_batch_bins<<<1, kScanThreads, 0, stream>>>(W, M);
     dx_batch_scatter<<<cgrid, 256, 0, stream>>>(nblocks, W);
 
-    MainArgs a{D, rho_g, rho_d, t_s, v_in, v_out, st, warp_doubles_for(M, nspecies_max + 1)};
-    const size_t smem = sizeof(double) * (32 + (size_t)kMainWarps * (a.warp_doubles + 2 * kPairSlots / 4));
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(dx_batch_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return DRAG_ECUDA;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dx_batch_main, kMainWarps * 32, smem) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    dx_batch_main<<<sms * per_sm, kMainWarps * 32, smem, stream>>>(nblocks, a, W, M, K);
+    int wd_wpc = 0, wd_lpc = 0;
+    bool has_wpc = false, has_lpc = false;
+    warp_doubles_for(M, nspecies_max + 1, &wd_wpc, &wd_lpc, &has_wpc, &has_lpc);
+    if (has_lpc) {
+        MainArgs a{D, rho_g, rho_d, t_s, v_in, v_out, st, wd_lpc};
+        const size_t smem = sizeof(double) * (32 + (size_t)kLpcWarps * wd_lpc);
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(dx_batch_main_lpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return DRAG_ECUDA;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dx_batch_main_lpc, kLpcWarps * 32, smem) !=
+                cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        dx_batch_main_lpc<<<sms * per_sm, kLpcWarps * 32, smem, stream>>>(a, W, M, K);
+        if (cudaGetLastError() != cudaSuccess) return DRAG_ECUDA;
+    }
+    if (has_wpc) {
+        MainArgs a{D, rho_g, rho_d, t_s, v_in, v_out, st, wd_wpc};
+        const size_t smem = sizeof(double) * (size_t)kWpcWarps * (wd_wpc + 2 * kPairSlots / 4);
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(dx_batch_main_wpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return DRAG_ECUDA;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dx_batch_main_wpc, kWpcWarps * 32, smem) !=
+                cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        dx_batch_main_wpc<<<sms * per_sm, kWpcWarps * 32, smem, stream>>>(a, W, K);
+    }
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }
 
@@ -439,7 +496,7 @@ constexpr size_t kNoAllocBytes =
     na_align(sizeof(unsigned long long) * (size_t)DRAG_NOALLOC_MAX_CELLS) +
     na_align(sizeof(unsigned int) * (size_t)DRAG_NOALLOC_MAX_CELLS) +
     na_align(sizeof(long long) * ((size_t)DRAG_NOALLOC_MAX_BLOCKS + 1)) +
-    4 * na_align(sizeof(unsigned int) * (kNBins + 1)) + na_align(sizeof(unsigned int) * 8);
+    5 * na_align(sizeof(unsigned int) * (kNBins + 1)) + na_align(sizeof(unsigned int) * 8);
 
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[64];
