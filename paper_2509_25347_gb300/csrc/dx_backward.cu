@@ -44,17 +44,122 @@ struct BwdArgs {
     uint32_t *status;
 };
 
-// Per-warp shared memory (doubles): E0, E1, L0, L1 and 19 vectors of 32.
-__host__ __device__ __forceinline__ int bwd_warp_smem_doubles(int n) { return 4 * n * dx_stride(n) + 19 * DX_NMAXF; }
+// Per-warp shared memory (doubles): E0, E1, L0, L1, then n-vectors: sigma,
+// tau, X_0f, X_ff, a_d and b_d (4 each), two buffers of y_d (3 each) and g_d (3).
+__host__ __device__ __forceinline__ int bwd_warp_smem_doubles(int n) { return 4 * n * dx_stride(n) + 21 * n; }
 
 constexpr int kRank = 4;   // rank of the Frechet direction H
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+// yo_d = c1 X y_d + c0 a_d for d = 0, 1, 2 (X the arrowhead; vectors at stride n).
+// Entries f >= 1 take two FMAs each; entry 0 is a dot product over the row
+// X_0k, split over three groups of eight lanes (one per d) and reduced.
+__device__ __forceinline__ void bwd_xvec(int lane, int n, const DxVecs &V, double c1, double c0, const double *a,
+                                         const double *y, double *yo) {
+    const int m1 = n - 1;
+    for (int t = lane; t < 3 * m1; t += 32) {
+        const int d = t >= m1 ? (t >= 2 * m1 ? 2 : 1) : 0;
+        const int f = t - d * m1 + 1;
+        const double *yd = y + d * n;
+        yo[d * n + f] = fma(c1, fma(V.xs[f], yd[0], V.ds[f] * yd[f]), c0 * a[d * n + f]);
+    }
+    const int d = lane >> 3, phi = lane & 7;
+    const bool on = d < 3;
+    const double *yd = y + (on ? d : 0) * n;
+    double acc = 0.0;
+    const int cnt = (n + 7) >> 3;
+    for (int u = 0; u < cnt; u++) {
+        const int k = phi + 8 * u;
+        const bool ok = on && k < n;
+        acc = fma(ok ? V.xs[ok ? k : 0] : 0.0, ok ? yd[ok ? k : 0] : 0.0, acc);
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(DX_FULL, acc, o);
+    if (on && phi == 0) yo[d * n] = fma(c1, acc, c0 * a[d * n]);
+}
+
+// One squaring of (E, L): (E, L) <- (E^2, E L + L E), E^2 restored, as tasks
+// of n FP64 operations dealt 32 per round:
+//   O (i < j): En_ij = En_ji = sum_k E_ik E_jk;
+//   A (i, j) : Ln_ij = sum_k E_ik L_kj;
+//   B (i, j) : Ln_ij = Ln_ij + sum_k L_ik E_jk  (at least one round after its A);
+//   R (i)    : En_ii = 1 - tau_i sum_{k != i} En_ik sigma_k  (after every O).
+// trimmed: only the entries of E L + L E in row 0, column 0 and on the
+// diagonal, and no E^2 (the gradients read only those entries of the last L).
+__device__ __forceinline__ void bwd_square(int lane, int n, int ns, const unsigned short *od, const DxVecs &V,
+                                           const double *E, const double *L, double *En, double *Ln, bool trimmed) {
+    const int nO = trimmed ? 0 : n * (n - 1) / 2;
+    const int nL = trimmed ? 3 * n - 2 : n * n;
+    const int nR = trimmed ? 0 : n;
+    const int a0 = nO;
+    const int b0 = nL >= 32 ? nO + nL : ((nO + nL + 31) & ~31);
+    const int r0 = b0 + nL;
+    const int ntask = r0 + nR;
+    const int inv = (65536 + n - 1) / n;   // (e * inv) >> 16 == e / n for e < n^2 + 64, n <= 32
+    for (int base = 0; base < ntask; base += 32) {
+        const int t = base + lane;
+        const double *pa = E, *pb = E;
+        int sb = 1, skip = 32, kind = 0, i = 0, j = 0;
+        double acc = 0.0;
+        if (t < nO) {
+            const int p = od[t];
+            i = p >> 8;
+            j = p & 255;
+            pa = E + i * ns;
+            pb = E + j * ns;
+            kind = 1;
+        } else if ((t >= a0 && t < a0 + nL) || (t >= b0 && t < r0)) {
+            const bool isB = t >= b0;
+            const int e = isB ? t - b0 : t - a0;
+            if (!trimmed) {
+                i = (e * inv) >> 16;
+                j = e - i * n;
+            } else if (e < n) {
+                j = e;
+            } else if (e < 2 * n - 1) {
+                i = e - n + 1;
+            } else {
+                i = j = e - 2 * n + 2;
+            }
+            if (isB) {
+                pa = L + i * ns;
+                pb = E + j * ns;
+                acc = Ln[i * ns + j];
+            } else {
+                pa = E + i * ns;
+                pb = L + j;
+                sb = ns;
+            }
+            kind = 2;
+        } else if (t >= r0 && t < ntask) {
+            i = t - r0;
+            pa = En + i * ns;
+            pb = V.sig;
+            skip = i;
+            kind = 3;
+        }
+        for (int q = 0; q < n - 1; q++) {
+            const int k = q + (q >= skip);
+            acc = fma(pa[k], pb[k * sb], acc);
+        }
+        const bool isR = kind == 3;
+        const double res = fma(isR ? -V.tau[i] : pa[n - 1], isR ? acc : pb[(n - 1) * sb], isR ? 1.0 : acc);
+        if (kind == 1) {
+            En[i * ns + j] = res;
+            En[j * ns + i] = res;
+        } else if (kind == 2) {
+            Ln[i * ns + j] = res;
+        } else if (kind == 3) {
+            En[i * ns + i] = res;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
 dx_backward_wpc(BwdArgs a, DxConsts K) {
     extern __shared__ double smem[];
     const int n = a.N + 1, N = a.N, ns = dx_stride(n);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int n_od = n * (n - 1) / 2;
     const int n_hp = n * (n + 1) / 2 - 1;
     const int nn = n * n;
 
@@ -69,13 +174,14 @@ dx_backward_wpc(BwdArgs a, DxConsts K) {
     double *L1 = L0 + n * ns;
     DxVecs V;
     V.sig = L1 + n * ns;
-    V.tau = V.sig + DX_NMAXF;
-    V.xs = V.tau + DX_NMAXF;
-    V.ds = V.xs + DX_NMAXF;
-    double *av = V.ds + DX_NMAXF;      // a_d = g_d / sigma, a_3 = -kappa sigma     [4][32]
-    double *bv = av + 4 * DX_NMAXF;    // 2^-s sigma o v_d, b_3 = sigma             [4][32]
-    double *wv = bv + 4 * DX_NMAXF;    // F a_d                                     [4][32]
-    double *gg = wv + 4 * DX_NMAXF;    // g_d                                       [3][32]
+    V.tau = V.sig + n;
+    V.xs = V.tau + n;
+    V.ds = V.xs + n;
+    double *av = V.ds + n;       // a_d = g_d / sigma, a_3 = -kappa sigma     [4][n]
+    double *bv = av + 4 * n;     // 2^-s sigma o v_d, b_3 = sigma             [4][n]
+    double *yv0 = bv + 4 * n;    // y_d = F a_d (d < 3), two buffers          [3][n] x 2
+    double *yv1 = yv0 + 3 * n;
+    double *gg = yv1 + 3 * n;    // g_d                                       [3][n]
 
     const long long C = a.C;
     // Each block owns kCellsPerBlock consecutive cells, taken one at a time by
@@ -121,13 +227,13 @@ dx_backward_wpc(BwdArgs a, DxConsts K) {
         const double p2 = dx_pow2(-L.s);
         {
             // rank-3 direction and its stationary block (kappa)
-            double a[3], b[3], sa[3], sb[3];
+            double ad[3], bd[3], sa[3], sb[3];
 #pragma unroll
             for (int d = 0; d < 3; d++) {
-                a[d] = lane < n ? gin[d] * L.tu : 0.0;
-                b[d] = lane < n ? (L.sg * vin[d]) * p2 : 0.0;
-                sa[d] = L.sg * a[d];
-                sb[d] = L.sg * b[d];
+                ad[d] = lane < n ? gin[d] * L.tu : 0.0;
+                bd[d] = lane < n ? (L.sg * vin[d]) * p2 : 0.0;
+                sa[d] = L.sg * ad[d];
+                sb[d] = L.sg * bd[d];
             }
             double ss = lane < n ? L.sg * L.sg : 0.0;
 #pragma unroll
@@ -143,97 +249,105 @@ dx_backward_wpc(BwdArgs a, DxConsts K) {
             if (lane < n) {
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
-                    av[d * DX_NMAXF + lane] = a[d];
-                    bv[d * DX_NMAXF + lane] = b[d];
-                    gg[d * DX_NMAXF + lane] = gin[d];
+                    av[d * n + lane] = ad[d];
+                    bv[d * n + lane] = bd[d];
+                    gg[d * n + lane] = gin[d];
                 }
-                av[3 * DX_NMAXF + lane] = -kappa * L.sg;
-                bv[3 * DX_NMAXF + lane] = L.sg;
+                av[3 * n + lane] = -kappa * L.sg;
+                bv[3 * n + lane] = L.sg;
             }
         }
 
-        // ---- Taylor and its derivative: F = b_m X + b_{m-1} I, dF = b_m H
-        double *F = E0, *Fn = E1, *dF = L0, *dFn = L1;
+        // ---- Taylor and its derivative: F = b_m X + b_{m-1} I, dF = b_m H,
+        // y_d = F a_d
+        double *F = E0, *Fn = E1, *dF = L0, *dFn = L1, *y = yv0, *yn = yv1;
         dx_wpc_taylor_init(lane, n, ns, m, K, V, F);
         for (int t = lane; t < nn; t += 32) {
             const int i = t / n, j = t - i * n;
             double acc = av[i] * bv[j];
 #pragma unroll
-            for (int d = 1; d < kRank; d++) acc = fma(av[d * DX_NMAXF + i], bv[d * DX_NMAXF + j], acc);
+            for (int d = 1; d < kRank; d++) acc = fma(av[d * n + i], bv[d * n + j], acc);
             dF[i * ns + j] = K.b[m] * acc;
         }
+        bwd_xvec(lane, n, V, K.b[m], K.b[m - 1], av, av, y);
         __syncwarp();
         for (int jb = m - 2; jb >= 0; jb--) {
-            // w_d = F a_d (F before this step)
-            for (int t = lane; t < kRank * n; t += 32) {
-                const int d = t / n, i = t - d * n;
-                const double *ad = av + d * DX_NMAXF;
-                double acc = 0.0;
-                for (int k = 0; k < n; k++) acc = fma(F[i * ns + k], ad[k], acc);
-                wv[d * DX_NMAXF + i] = acc;
-            }
+            // F_jb = F X + b_jb I (Horner), dF_jb = dF X + F H with
+            // F H = sum_d (F a_d) b_d^T: F a_d = y_d for d < 3 and, as F is a
+            // polynomial in X with constant term b_{jb+1} and X sigma = 0,
+            // F a_3 = b_{jb+1} a_3. Finally y_d <- F_jb a_d = X y_d + b_jb a_d
+            // (F_jb = X F + b_jb I: polynomials in X commute with X).
             dx_wpc_horner_step(lane, n, ns, n_hp, hp, V, K.b[jb], F, Fn);
-            __syncwarp();
-            // dFn = dF X + F H. Columns j >= 1 (5 FMAs each: X has two
-            // nonzeros per column there) and column 0 (n + 3 FMAs) are dealt
-            // in separate rounds so short and long tasks do not share a round.
+            const double b3 = K.b[jb + 1];
+            // columns j >= 1 (6 FMAs each: X has two nonzeros per column there)
+            // and column 0 (n + 4 FMAs) are dealt in separate rounds
             for (int t = lane; t < n * (n - 1); t += 32) {
                 const int i = t / (n - 1), j = t - i * (n - 1) + 1;
-                double acc = wv[i] * bv[j];
-#pragma unroll
-                for (int d = 1; d < kRank; d++) acc = fma(wv[d * DX_NMAXF + i], bv[d * DX_NMAXF + j], acc);
+                double acc = y[i] * bv[j];
+                acc = fma(y[n + i], bv[n + j], acc);
+                acc = fma(y[2 * n + i], bv[2 * n + j], acc);
+                acc = fma(b3 * av[3 * n + i], bv[3 * n + j], acc);
                 acc = fma(dF[i * ns], V.xs[j], acc);
                 acc = fma(dF[i * ns + j], V.ds[j], acc);
                 dFn[i * ns + j] = acc;
             }
             for (int i = lane; i < n; i += 32) {
-                double acc = wv[i] * bv[0];
-#pragma unroll
-                for (int d = 1; d < kRank; d++) acc = fma(wv[d * DX_NMAXF + i], bv[d * DX_NMAXF], acc);
+                double acc = y[i] * bv[0];
+                acc = fma(y[n + i], bv[n], acc);
+                acc = fma(y[2 * n + i], bv[2 * n], acc);
+                acc = fma(b3 * av[3 * n + i], bv[3 * n], acc);
                 const double *ri = dF + i * ns;
                 for (int k = 0; k < n; k++) acc = fma(ri[k], V.xs[k], acc);
                 dFn[i * ns] = acc;
             }
+            bwd_xvec(lane, n, V, 1.0, K.b[jb], av, y, yn);
             __syncwarp();
             double *t1 = F; F = Fn; Fn = t1;
             double *t2 = dF; dF = dFn; dFn = t2;
+            double *t3 = y; y = yn; yn = t3;
         }
         dx_wpc_restore(lane, n, ns, V, F);
         __syncwarp();
 
-        // ---- squarings: (E, L) <- (E^2, E L + L E)
-        for (int it = 0; it < L.s; it++) {
-            dx_wpc_square_offdiag(lane, n, ns, n_od, od, F, Fn);
-            for (int t = lane; t < nn; t += 32) {
-                const int i = t / n, j = t - i * n;
-                const double *ei = F + i * ns, *ej = F + j * ns, *li = dF + i * ns;
-                double acc = 0.0;
-                for (int k = 0; k < n; k++) {
-                    acc = fma(ei[k], dF[k * ns + j], acc);
-                    acc = fma(li[k], ej[k], acc);
-                }
-                dFn[i * ns + j] = acc;
+        // ---- squarings: (E, L) <- (E^2, E L + L E); the last one only forms
+        // the entries of L the gradients read and leaves E at E_{s-1}
+        for (int sq = 0; sq < L.s; sq++) {
+            const bool trimmed = sq == L.s - 1;
+            bwd_square(lane, n, ns, od, V, F, dF, Fn, dFn, trimmed);
+            if (!trimmed) {
+                double *t1 = F; F = Fn; Fn = t1;
             }
-            __syncwarp();
-            dx_wpc_restore(lane, n, ns, V, Fn);
-            __syncwarp();
-            double *t1 = F; F = Fn; Fn = t1;
             double *t2 = dF; dF = dFn; dFn = t2;
         }
 
         // ---- outputs
         if (a.g_vin) {
-            // (P^T g)_i = E_ii g_i + sigma_i sum_{j != i} E_ij a_j
-            for (int t = lane; t < 3 * n; t += 32) {
-                const int d = t / n, i = t - d * n;
-                const double *ad = av + d * DX_NMAXF;
-                double acc = 0.0;
-                for (int q = 0; q < n - 1; q++) {
-                    const int k = q + (q >= i);
-                    acc = fma(F[i * ns + k], ad[k], acc);
+            // P^T g with P^T = D_sigma E D_sigma^-1: (P^T g)_i = E_ii g_i +
+            // sigma_i sum_{j != i} E_ij a_j, a = g / sigma. After s >= 1
+            // squarings E holds E_{s-1} and P^T = (D_sigma E D_sigma^-1)^2:
+            // two applications, the first into (yv0, yv1) = (g', g' / sigma).
+            const int napply = L.s >= 1 ? 2 : 1;
+            for (int ap = 0; ap < napply; ap++) {
+                const bool last = ap == napply - 1;
+                const double *cg = ap == 0 ? gg : yv0, *ca = ap == 0 ? av : yv1;
+                for (int t = lane; t < 3 * n; t += 32) {
+                    const int d = t >= n ? (t >= 2 * n ? 2 : 1) : 0;
+                    const int i = t - d * n;
+                    const double *adv = ca + d * n;
+                    double acc = 0.0;
+                    for (int q = 0; q < n - 1; q++) {
+                        const int k = q + (q >= i);
+                        acc = fma(F[i * ns + k], adv[k], acc);
+                    }
+                    const double out = fma(V.sig[i], acc, F[i * ns + i] * cg[d * n + i]);
+                    if (last) {
+                        a.g_vin[((long long)d * n + i) * C + c] = out;
+                    } else {
+                        yv0[d * n + i] = out;
+                        yv1[d * n + i] = V.tau[i] * out;
+                    }
                 }
-                a.g_vin[((long long)d * n + i) * C + c] =
-                    fma(V.sig[i], acc, F[i * ns + i] * gg[d * DX_NMAXF + i]);
+                __syncwarp();
             }
         }
         double geps = 0.0;
