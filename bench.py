@@ -38,6 +38,39 @@ UNIT = "cell-updates/s"
 FP64_FLOP_PER_CLK = 152 * 4 * 0.5 * 2
 SM_MAX_MHZ = 2070.0
 
+# DRAM traffic of the dominant kernel per cell, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one 262,144-cell launch of
+# the same kernel and launch shape, divided by its cells; the summary under
+# profiles/ gives the command). It holds only for the sources it was taken on:
+# the entry carries a SHA-256 of them and is reported as null once they change.
+KERNEL_SOURCES = {
+    "dx_forward_wpc": ["csrc/dx_forward.cu", "csrc/dx_wpc.cuh", "csrc/dx_common.cuh", "csrc/dx_modes.h", "sched.py"],
+}
+MEASURED_TRAFFIC = {
+    ("mrn_n16_128cube", "dx_forward_wpc"): {
+        "sources_sha256": "da3860a215f080b6c41b754e710541b018fdc0ded1d05ac1ed642a75c89e8ccc",
+        "bytes_per_cell": (186.644992e6 + 80.977920e6) / 262144,
+        "capture": "profiles/dx_forward_wpc_mrn_n16.md",
+    },
+}
+
+
+def sources_digest(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2509_25347_gb300", rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload, kernel, cells):
+    """Per-launch DRAM bytes of `kernel` on `cells` cells of `workload`, or None."""
+    e = MEASURED_TRAFFIC.get((workload, kernel))
+    if e is None or kernel not in KERNEL_SOURCES or sources_digest(kernel) != e["sources_sha256"]:
+        return None
+    return e["bytes_per_cell"] * cells
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -383,7 +416,11 @@ def run_ours(args, rank, world):
                    "l2": "inputs (%.2f GB) larger than L2, no flush" % (bytes_cell * C / 1e9),
                    "mean_k_star": float(k.mean()), "mean_s_star": float(s.mean()), "max_s_star": int(s.max())},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved_tf / peak_tf, "traffic": None,
+                     "frac": achieved_tf / peak_tf,
+                     "traffic": measured_traffic(args.workload, "dx_forward_wpc", C) if dx.get_mode(N) == dx.MODE_WARP_PER_CELL
+                     else None,
+                     "traffic_unit": "bytes per launch (ncu dram read + write, per cell x cells)",
+                     "algorithmic_bytes_per_launch": float(bytes_cell * C),
                      "peak_source": "FP64 pipe: 152 SMs x 608/152 flop/clk x 2070 MHz (unit count x max clock)",
                      "algorithmic_flop_per_launch": flops_launch, "kernel_mean_ms": mean_launch_s * 1e3,
                      "hbm_gbs": gbs, "hbm_frac_of_measured": (gbs / hbm_peak) if hbm_peak else None},
