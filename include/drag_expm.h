@@ -62,6 +62,7 @@ extern "C" {
 #define DRAG_EWORKSPACE (-5)    /* workspace missing or smaller than required */
 #define DRAG_EBLOCKS (-6)       /* bad block count in the batched entry point */
 #define DRAG_ENOALLOC_LIMIT (-7) /* batch larger than drag_expm_apply_batched_noalloc's fixed scratch */
+#define DRAG_EINVAL_TARGET (-8)  /* unit round-off target other than 53, 24 or 11 bits */
 
 /* Sticky device status bits (drag_expm_get_status). */
 #define DRAG_STATUS_BAD_CELL 0x1u      /* some cell had invalid data; its outputs are NaN */
@@ -83,6 +84,22 @@ extern "C" {
  */
 int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d, const double *t_s,
                     double dt, const double *v_in, double *v_out, cudaStream_t stream);
+
+/*
+ * drag_expm_apply_target — drag_expm_apply for a lower accuracy target.
+ * Eq. B8 defines theta_m for any unit round-off u (the paper names 2^-11,
+ * 2^-24, 2^-113 and 2^-237 besides 2^-53); this entry point runs Algorithm 2
+ * on the theta_{m_k} table of u = 2^-ubits, so cells take fewer Taylor terms
+ * and squarings, and then the same FP64 arithmetic as drag_expm_apply. The
+ * result is exp(dt Omega_v + dA) v_in with a backward error |dA| <= u |A| of
+ * the Taylor step (App. B), plus FP64 rounding.
+ *   ubits : 53 (same as drag_expm_apply), 24 (single-precision target) or
+ *           11 (half-precision target); other values return DRAG_EINVAL_TARGET.
+ * Other arguments as drag_expm_apply (in place allowed).
+ */
+int drag_expm_apply_target(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                           const double *t_s, double dt, const double *v_in, double *v_out, int32_t ubits,
+                           cudaStream_t stream);
 
 /*
  * drag_expm_apply_heat — drag_expm_apply plus the energy epilogue: heat_out[c]
@@ -110,6 +127,15 @@ int drag_expm_apply_heat(int64_t ncells, int32_t nspecies, const double *rho_g, 
  */
 int drag_expm_select(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d, const double *t_s,
                      double dt, int8_t *k_out, int16_t *s_out, cudaStream_t stream);
+
+/*
+ * drag_expm_select_target — drag_expm_select with the theta table of
+ * u = 2^-ubits (the (k*, s*) drag_expm_apply_target uses). ubits as
+ * drag_expm_apply_target; other values return DRAG_EINVAL_TARGET.
+ */
+int drag_expm_select_target(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                            const double *t_s, double dt, int32_t ubits, int8_t *k_out, int16_t *s_out,
+                            cudaStream_t stream);
 
 /*
  * drag_expm_backward — adjoint of drag_expm_apply (reverse mode). Given
@@ -266,6 +292,12 @@ int drag_expm_get_status(cudaStream_t stream, uint32_t *status_out);
  * for k = 1..9 (Table B.1 prints these to five digits). Host only.
  */
 int drag_expm_theta(int32_t k, double *theta_out);
+
+/*
+ * drag_expm_theta_target — theta_{m_k} of Eq. B8 for u = 2^-ubits (53, 24 or
+ * 11; DRAG_EINVAL_TARGET otherwise), k = 1..9. Host only.
+ */
+int drag_expm_theta_target(int32_t k, int32_t ubits, double *theta_out);
 
 /* drag_expm_strerror — static text for a DRAG_E* code. */
 const char *drag_expm_strerror(int code);

@@ -54,6 +54,14 @@ def _load():
     lib.orc_expm_dense.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
     lib.orc_assemble.restype = None
     lib.orc_assemble.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_double, ctypes.c_int, dp]
+    lib.orc_theta_table_u.restype = None
+    lib.orc_theta_table_u.argtypes = [ctypes.c_double, dp]
+    lib.orc_select_alg2_u.restype = ctypes.c_int
+    lib.orc_select_alg2_u.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_double] + [ctypes.POINTER(ctypes.c_int)] * 3
+    lib.orc_drag_apply_u.restype = ctypes.c_int
+    lib.orc_drag_apply_u.argtypes = [ctypes.c_int64, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp, dp, ctypes.c_int,
+                                     ctypes.c_double, ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int16),
+                                     ctypes.POINTER(ctypes.c_uint32)]
     lib.orc_drag_apply.restype = ctypes.c_int
     lib.orc_drag_apply.argtypes = [ctypes.c_int64, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp, dp, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int16),
@@ -87,10 +95,17 @@ def _dptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def theta_table() -> np.ndarray:
-    """theta_{m_k} for k = 0..9 (index 0 unused), Eq. B8 with u = 2^-53."""
+U_DOUBLE = 2.0 ** -53
+
+
+def theta_table(u: float = U_DOUBLE) -> np.ndarray:
+    """theta_{m_k} for k = 0..9 (index 0 unused), Eq. B8 with unit round-off u
+    (2^-53 by default; Eq. B8 also names 2^-11, 2^-24, 2^-113, 2^-237)."""
     out = np.zeros(K_MAX + 1)
-    _load().orc_theta_table(_dptr(out))
+    if u == U_DOUBLE:
+        _load().orc_theta_table(_dptr(out))
+    else:
+        _load().orc_theta_table_u(float(u), _dptr(out))
     return out
 
 
@@ -105,10 +120,14 @@ def table_b1(k: int) -> tuple[int, int, int]:
     return lib.orc_table_mk(k), lib.orc_table_qk(k), lib.orc_table_rk(k)
 
 
-def select(norm: float) -> tuple[int, int, int]:
-    """Algorithm 2 (K = 9): returns (k*, m*, s*) for a given 1-norm."""
+def select(norm: float, u: float = U_DOUBLE) -> tuple[int, int, int]:
+    """Algorithm 2 (K = 9) with the theta table of unit round-off u: returns
+    (k*, m*, s*) for a given 1-norm."""
     k, m, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _load().orc_select_alg2(float(norm), K_MAX, ctypes.byref(k), ctypes.byref(m), ctypes.byref(s))
+    if u == U_DOUBLE:
+        _load().orc_select_alg2(float(norm), K_MAX, ctypes.byref(k), ctypes.byref(m), ctypes.byref(s))
+    else:
+        _load().orc_select_alg2_u(float(norm), K_MAX, float(u), ctypes.byref(k), ctypes.byref(m), ctypes.byref(s))
     return k.value, m.value, s.value
 
 
@@ -135,11 +154,14 @@ def assemble(rho_g: float, rho_d: np.ndarray, t_s: np.ndarray, dt: float, struct
     return A
 
 
-def drag_apply(rho_g, rho_d, t_s, dt, v_in, structured: bool = True, return_ks: bool = False):
+def drag_apply(rho_g, rho_d, t_s, dt, v_in, structured: bool = True, return_ks: bool = False,
+               u: float = U_DOUBLE):
     """Forward drag update over SoA arrays (layout of the CUDA library).
 
     rho_g: (C,), rho_d: (N, C), t_s: (N, C), v_in: (3, N+1, C). Returns v_out of
     the same shape as v_in (and, with return_ks, k*, s* per cell and the status word).
+    u: unit round-off whose theta table Algorithm 2 selects (k*, s*) from; the
+    arithmetic is FP64 whatever u is.
     """
     rho_g = np.ascontiguousarray(rho_g, dtype=np.float64)
     rho_d = np.ascontiguousarray(rho_d, dtype=np.float64)
@@ -152,9 +174,14 @@ def drag_apply(rho_g, rho_d, t_s, dt, v_in, structured: bool = True, return_ks: 
     k_out = np.zeros(C, dtype=np.int8)
     s_out = np.zeros(C, dtype=np.int16)
     st = ctypes.c_uint32(0)
-    rc = _load().orc_drag_apply(C, N, _dptr(rho_g), _dptr(rho_d), _dptr(t_s), float(dt), _dptr(v_in), _dptr(v_out),
-                                int(structured), k_out.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
-                                s_out.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), ctypes.byref(st))
+    kp = k_out.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
+    sp = s_out.ctypes.data_as(ctypes.POINTER(ctypes.c_int16))
+    if u == U_DOUBLE:
+        rc = _load().orc_drag_apply(C, N, _dptr(rho_g), _dptr(rho_d), _dptr(t_s), float(dt), _dptr(v_in),
+                                    _dptr(v_out), int(structured), kp, sp, ctypes.byref(st))
+    else:
+        rc = _load().orc_drag_apply_u(C, N, _dptr(rho_g), _dptr(rho_d), _dptr(t_s), float(dt), _dptr(v_in),
+                                      _dptr(v_out), int(structured), float(u), kp, sp, ctypes.byref(st))
     if rc != 0:
         raise ValueError(f"oracle rejected sizes (rc={rc})")
     if return_ks:

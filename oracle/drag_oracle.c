@@ -116,6 +116,31 @@ static const double *orc_thetas(void)
     return g_theta;
 }
 
+/* theta_{m_k}, k = 1..9, for another unit round-off u (Eq. B8 names 2^-11,
+ * 2^-24, 2^-113 and 2^-237 besides 2^-53). */
+void orc_theta_table_u(double u, double *theta /* [ORC_K + 1] */)
+{
+    theta[0] = 0.0;
+    for (int k = 1; k <= ORC_K; k++) theta[k] = orc_theta_m(orc_mk[k], u);
+}
+
+/* Tables for the last few distinct u asked for (computed once each). */
+enum { ORC_U_SLOTS = 8 };
+static double g_theta_u[ORC_U_SLOTS][ORC_K + 1];
+static double g_theta_u_key[ORC_U_SLOTS];
+static int g_theta_u_used = 0;
+
+static const double *orc_thetas_u(double u)
+{
+    if (u == ldexp(1.0, -53)) return orc_thetas();
+    for (int i = 0; i < g_theta_u_used; i++)
+        if (g_theta_u_key[i] == u) return g_theta_u[i];
+    int slot = g_theta_u_used < ORC_U_SLOTS ? g_theta_u_used++ : ORC_U_SLOTS - 1;
+    orc_theta_table_u(u, g_theta_u[slot]);
+    g_theta_u_key[slot] = u;
+    return g_theta_u[slot];
+}
+
 /* ------------------------------------------------------------------------ */
 /* Algorithm 2: polynomial order and scale factor                           */
 /* ------------------------------------------------------------------------ */
@@ -131,9 +156,8 @@ static const double *orc_thetas(void)
  *    max() gives v3 priority over v2 over v1.
  *  - "m* = m_k*" means m* = m_{k*}.
  * Returns 0, or -1 if |A| is not finite (the caller marks the cell invalid). */
-int orc_select_alg2(double normA, int K, int *kstar, int *mstar, int *sstar)
+static int orc_select_alg2_th(const double *th, double normA, int K, int *kstar, int *mstar, int *sstar)
 {
-    const double *th = orc_thetas();
     if (!isfinite(normA) || normA < 0.0) {
         *kstar = K; *mstar = orc_mk[K]; *sstar = 0;
         return -1;
@@ -172,6 +196,17 @@ int orc_select_alg2(double normA, int K, int *kstar, int *mstar, int *sstar)
     }
     *kstar = ks; *mstar = ms; *sstar = ss;
     return 0;
+}
+
+int orc_select_alg2(double normA, int K, int *kstar, int *mstar, int *sstar)
+{
+    return orc_select_alg2_th(orc_thetas(), normA, K, kstar, mstar, sstar);
+}
+
+/* Algorithm 2 with the theta table of unit round-off u. */
+int orc_select_alg2_u(double normA, int K, double u, int *kstar, int *mstar, int *sstar)
+{
+    return orc_select_alg2_th(orc_thetas_u(u), normA, K, kstar, mstar, sstar);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -222,10 +257,11 @@ static void orc_restore(int n, double *P)
  * evaluated by Horner in X^q with the stored powers X, X^2, ..., X^q.
  * With structured != 0 the diagonal is restored after the Taylor step and
  * after every squaring. Returns 0, or -1 when |A| is not finite. */
-int orc_expm(int n, const double *A, double *P, int structured, int *k_out, int *m_out, int *s_out)
+static int orc_expm_u(int n, const double *A, double *P, int structured, double u, int *k_out, int *m_out,
+                      int *s_out)
 {
     int k, m, s;
-    int rc = orc_select_alg2(orc_norm1(n, A), ORC_K, &k, &m, &s);
+    int rc = orc_select_alg2_u(orc_norm1(n, A), ORC_K, u, &k, &m, &s);
     if (k_out) *k_out = k;
     if (m_out) *m_out = m;
     if (s_out) *s_out = s;
@@ -271,6 +307,11 @@ int orc_expm(int n, const double *A, double *P, int structured, int *k_out, int 
     }
     free(pw); free(F); free(T); free(Bb);
     return 0;
+}
+
+int orc_expm(int n, const double *A, double *P, int structured, int *k_out, int *m_out, int *s_out)
+{
+    return orc_expm_u(n, A, P, structured, ldexp(1.0, -53), k_out, m_out, s_out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -321,9 +362,9 @@ void orc_assemble(int N, double rho_g, const double *rho_d, const double *t_s, d
  *   v[(d*n + f)*C + c]  (d = x,y,z; f = 0 gas, f = i dust species i).
  * Invalid cells get NaN outputs and set bit 0 of *status.
  * k_out / s_out (optional) receive k* and s* per cell. */
-int orc_drag_apply(int64_t C, int N, const double *rho_g, const double *rho_d, const double *t_s, double dt,
-                   const double *v_in, double *v_out, int structured, int8_t *k_out, int16_t *s_out,
-                   uint32_t *status)
+int orc_drag_apply_u(int64_t C, int N, const double *rho_g, const double *rho_d, const double *t_s, double dt,
+                     const double *v_in, double *v_out, int structured, double u, int8_t *k_out, int16_t *s_out,
+                     uint32_t *status)
 {
     if (C < 0 || N < 1 || N + 1 > ORC_NMAX) return -1;
     const int n = N + 1;
@@ -340,7 +381,7 @@ int orc_drag_apply(int64_t C, int N, const double *rho_g, const double *rho_d, c
         int ok = orc_cell_valid(N, rho_g[c], rd, ts, dt);
         if (ok) {
             orc_assemble(N, rho_g[c], rd, ts, dt, structured, A);
-            ok = orc_expm(n, A, P, structured, &k, &m, &s) == 0;
+            ok = orc_expm_u(n, A, P, structured, u, &k, &m, &s) == 0;
         }
         if (k_out) k_out[c] = (int8_t)k;
         if (s_out) s_out[c] = (int16_t)s;
@@ -357,6 +398,14 @@ int orc_drag_apply(int64_t C, int N, const double *rho_g, const double *rho_d, c
     free(A); free(P);
     if (status) *status |= st;
     return 0;
+}
+
+int orc_drag_apply(int64_t C, int N, const double *rho_g, const double *rho_d, const double *t_s, double dt,
+                   const double *v_in, double *v_out, int structured, int8_t *k_out, int16_t *s_out,
+                   uint32_t *status)
+{
+    return orc_drag_apply_u(C, N, rho_g, rho_d, t_s, dt, v_in, v_out, structured, ldexp(1.0, -53), k_out, s_out,
+                            status);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -68,6 +68,12 @@ def load_library(path: str | None = None):
     lib.drag_expm_get_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
     lib.drag_expm_theta.restype = ctypes.c_int
     lib.drag_expm_theta.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+    lib.drag_expm_theta_target.restype = ctypes.c_int
+    lib.drag_expm_theta_target.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
+    lib.drag_expm_apply_target.restype = ctypes.c_int
+    lib.drag_expm_apply_target.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, i32, vp]
+    lib.drag_expm_select_target.restype = ctypes.c_int
+    lib.drag_expm_select_target.argtypes = [i64, i32, vp, vp, vp, dbl, i32, vp, vp, vp]
     lib.drag_expm_strerror.restype = ctypes.c_char_p
     lib.drag_expm_strerror.argtypes = [ctypes.c_int]
     lib.drag_expm_version.restype = ctypes.c_int
@@ -106,10 +112,15 @@ def _shapes(rho_g, rho_d):
     return C, N
 
 
-def apply(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, stream=None):
+UBITS_TARGETS = (53, 24, 11)
+
+
+def apply(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, stream=None, ubits: int = 53):
     """v_out = exp(dt Omega_v) v_in per cell (forward drag update). Returns v_out.
 
     ``v_out`` may be ``v_in`` (in place) or None (a new tensor is allocated).
+    ``ubits`` selects the accuracy target u = 2^-ubits whose theta table
+    Algorithm 2 uses (53, 24 or 11; the arithmetic is FP64 in every case).
     """
     import torch
     C, N = _shapes(rho_g, rho_d)
@@ -118,7 +129,11 @@ def apply(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, stream=None):
     args = [_f64_cuda("rho_g", rho_g, (C,)), _f64_cuda("rho_d", rho_d, (N, C)), _f64_cuda("t_s", t_s, (N, C))]
     vi = _f64_cuda("v_in", v_in, (3, N + 1, C))
     vo = _f64_cuda("v_out", v_out, (3, N + 1, C))
-    _check(load_library().drag_expm_apply(C, N, *args, float(dt), vi, vo, _stream_handle(stream)))
+    if ubits == 53:
+        _check(load_library().drag_expm_apply(C, N, *args, float(dt), vi, vo, _stream_handle(stream)))
+    else:
+        _check(load_library().drag_expm_apply_target(C, N, *args, float(dt), vi, vo, int(ubits),
+                                                     _stream_handle(stream)))
     return v_out
 
 
@@ -276,15 +291,16 @@ def apply_batched(blocks, rho_g, rho_d, t_s, v_in, v_out=None, nspecies_max=None
     return v_out
 
 
-def select(rho_g, rho_d, t_s, dt: float, stream=None):
-    """(k*, s*) per cell as chosen by Algorithm 2: int8 and int16 CUDA tensors."""
+def select(rho_g, rho_d, t_s, dt: float, stream=None, ubits: int = 53):
+    """(k*, s*) per cell as chosen by Algorithm 2 (theta table of u = 2^-ubits):
+    int8 and int16 CUDA tensors."""
     import torch
     C, N = _shapes(rho_g, rho_d)
     k = torch.empty(C, dtype=torch.int8, device=rho_g.device)
     s = torch.empty(C, dtype=torch.int16, device=rho_g.device)
     args = [_f64_cuda("rho_g", rho_g, (C,)), _f64_cuda("rho_d", rho_d, (N, C)), _f64_cuda("t_s", t_s, (N, C))]
-    _check(load_library().drag_expm_select(C, N, *args, float(dt), ctypes.c_void_p(k.data_ptr()),
-                                           ctypes.c_void_p(s.data_ptr()), _stream_handle(stream)))
+    _check(load_library().drag_expm_select_target(C, N, *args, float(dt), int(ubits), ctypes.c_void_p(k.data_ptr()),
+                                                  ctypes.c_void_p(s.data_ptr()), _stream_handle(stream)))
     return k, s
 
 
@@ -318,8 +334,8 @@ def get_status(stream=None) -> int:
     return int(st.value)
 
 
-def theta(k: int) -> float:
-    """theta_{m_k} (Eq. B8, u = 2^-53) as used by the library, k = 1..9."""
+def theta(k: int, ubits: int = 53) -> float:
+    """theta_{m_k} (Eq. B8, u = 2^-ubits) as used by the library, k = 1..9."""
     out = ctypes.c_double(0.0)
-    _check(load_library().drag_expm_theta(int(k), ctypes.byref(out)))
+    _check(load_library().drag_expm_theta_target(int(k), int(ubits), ctypes.byref(out)))
     return out.value

@@ -31,6 +31,8 @@ struct DxConsts {
 
 // Host side (dx_host.cu)
 const DxConsts &dx_consts();
+// Tables for unit round-off u = 2^-ubits, ubits in {53, 24, 11}; nullptr otherwise.
+const DxConsts *dx_consts_for(int ubits);
 uint32_t *dx_status_ptr();     // device address of the sticky status word (current device)
 int dx_sm_count();
 // Runs fn() once per (device, slot); returns false if it failed (it is retried next time).

@@ -122,7 +122,7 @@ size_t dx_forward_smem_bytes(int n) {
     return sizeof(double) * (size_t)kWarpsPerBlock * dx_wpc_fwd_warp_doubles(n) + 2 * kPairSlots * sizeof(unsigned short);
 }
 
-static int apply_impl(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+static int apply_impl(const DxConsts &K, int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
                       const double *t_s, double dt, const double *v_in, double *v_out, double *heat,
                       cudaStream_t stream) {
     int rc = check_common(ncells, nspecies, rho_g, rho_d, t_s, dt);
@@ -134,7 +134,7 @@ static int apply_impl(int64_t ncells, int32_t nspecies, const double *rho_g, con
     const int n = nspecies + 1;
     const int mode = dx_mode_for(n);
     if (mode != DX_MODE_WPC)
-        return dx_launch_forward_lpc(n, mode == DX_MODE_LPC_SMEM, ncells, rho_g, rho_d, t_s, v_in, v_out, dt, st, heat,
+        return dx_launch_forward_lpc(K, n, mode == DX_MODE_LPC_SMEM, ncells, rho_g, rho_d, t_s, v_in, v_out, dt, st, heat,
                                      stream);
     const size_t smem = dx_forward_smem_bytes(n);
     if (!dx_once_per_device(0, [] {
@@ -144,25 +144,41 @@ static int apply_impl(int64_t ncells, int32_t nspecies, const double *rho_g, con
         return DRAG_ECUDA;
     FwdArgs a{ncells, nspecies, rho_g, rho_d, t_s, v_in, v_out, dt, st, heat};
     const long long grid = (ncells + kCellsPerBlock - 1) / kCellsPerBlock;
-    dx_forward_wpc<<<(unsigned)grid, kWarpsPerBlock * 32, smem, stream>>>(a, dx_consts());
+    dx_forward_wpc<<<(unsigned)grid, kWarpsPerBlock * 32, smem, stream>>>(a, K);
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }
 
 extern "C" int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
                                const double *t_s, double dt, const double *v_in, double *v_out,
                                cudaStream_t stream) {
-    return apply_impl(ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, nullptr, stream);
+    return apply_impl(dx_consts(), ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, nullptr, stream);
+}
+
+extern "C" int drag_expm_apply_target(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                                      const double *t_s, double dt, const double *v_in, double *v_out, int32_t ubits,
+                                      cudaStream_t stream) {
+    const DxConsts *K = dx_consts_for(ubits);
+    if (!K) return DRAG_EINVAL_TARGET;
+    return apply_impl(*K, ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, nullptr, stream);
 }
 
 extern "C" int drag_expm_apply_heat(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
                                     const double *t_s, double dt, const double *v_in, double *v_out, double *heat_out,
                                     cudaStream_t stream) {
     if (!heat_out && ncells > 0) return DRAG_ENULL;
-    return apply_impl(ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, heat_out, stream);
+    return apply_impl(dx_consts(), ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, heat_out, stream);
 }
 
 extern "C" int drag_expm_select(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
                                 const double *t_s, double dt, int8_t *k_out, int16_t *s_out, cudaStream_t stream) {
+    return drag_expm_select_target(ncells, nspecies, rho_g, rho_d, t_s, dt, 53, k_out, s_out, stream);
+}
+
+extern "C" int drag_expm_select_target(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                                       const double *t_s, double dt, int32_t ubits, int8_t *k_out, int16_t *s_out,
+                                       cudaStream_t stream) {
+    const DxConsts *K = dx_consts_for(ubits);
+    if (!K) return DRAG_EINVAL_TARGET;
     int rc = check_common(ncells, nspecies, rho_g, rho_d, t_s, dt);
     if (rc != DRAG_OK || ncells == 0) return rc;
     uint32_t *st = dx_status_ptr();
@@ -170,6 +186,6 @@ extern "C" int drag_expm_select(int64_t ncells, int32_t nspecies, const double *
     const int threads = 256;
     const long long blocks = (ncells + threads - 1) / threads;
     dx_select_kernel<<<(unsigned)blocks, threads, 0, stream>>>(ncells, nspecies, rho_g, rho_d, t_s, dt, k_out, s_out,
-                                                              st, dx_consts());
+                                                              st, *K);
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }

@@ -26,7 +26,7 @@ dx_forward_lpc(long long C, const double *rho_g, const double *rho_d, const doub
 }
 
 template <int NF, bool SMEM>
-int launch_one(long long C, const double *rho_g, const double *rho_d, const double *t_s, const double *v_in,
+int launch_one(const DxConsts &K, long long C, const double *rho_g, const double *rho_d, const double *t_s, const double *v_in,
                double *v_out, double dt, uint32_t *status, double *heat, cudaStream_t stream) {
     const size_t smem = sizeof(double) * (32 + (SMEM ? (kThreads / 32) * dx_lpc_warp_smem_doubles<NF>() : 0));
     if (smem > 48 * 1024 &&
@@ -35,20 +35,20 @@ int launch_one(long long C, const double *rho_g, const double *rho_d, const doub
         return DRAG_ECUDA;
     const long long blocks = (C + kThreads - 1) / kThreads;
     dx_forward_lpc<NF, SMEM><<<(unsigned)blocks, kThreads, smem, stream>>>(C, rho_g, rho_d, t_s, v_in, v_out, dt,
-                                                                          status, heat, dx_consts());
+                                                                          status, heat, K);
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }
 
 }  // namespace
 
-int dx_launch_forward_lpc(int n, bool smem, long long C, const double *rho_g, const double *rho_d, const double *t_s,
+int dx_launch_forward_lpc(const DxConsts &K, int n, bool smem, long long C, const double *rho_g, const double *rho_d, const double *t_s,
                           const double *v_in, double *v_out, double dt, uint32_t *status, double *heat,
                           cudaStream_t stream) {
 #define DX_CASE_REG(NF) \
-    case NF: return smem ? launch_one<NF, true>(C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream) \
-                         : launch_one<NF, false>(C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream);
+    case NF: return smem ? launch_one<NF, true>(K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream) \
+                         : launch_one<NF, false>(K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream);
 #define DX_CASE_SMEM(NF) \
-    case NF: return launch_one<NF, true>(C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream);
+    case NF: return launch_one<NF, true>(K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream);
     switch (n) {
         DX_CASE_REG(2)
         DX_CASE_REG(3)

@@ -49,10 +49,10 @@ long long bits(double x) {
     return b;
 }
 
-DxConsts make_consts() {
+DxConsts make_consts(int ubits) {
     DxConsts K;
     std::memset(&K, 0, sizeof K);
-    const double u = std::ldexp(1.0, -53);
+    const double u = std::ldexp(1.0, -ubits);
     for (int k = 1; k <= DX_K; k++) {
         double th = theta_of(kMk[k], u);
         K.th[k] = bits(th);
@@ -72,9 +72,15 @@ bool g_once[64][16];
 int g_mode[64][DX_NMAXF + 1];
 bool g_mode_init[64];
 
+// Measured on GB300 (MRN-like cells): lane per cell with the matrix in
+// registers is fastest up to n = 6, in shared memory up to n = 8 (its shared
+// memory per warp grows as 32 n(n+1) doubles and limits residency), warp per
+// cell above.
+constexpr int kDefaultLpcSmemNMax = 8;
+
 int default_mode(int n) {
     if (n <= DX_LPC_REG_NMAX) return DX_MODE_LPC_REG;
-    if (n <= DX_LPC_NMAX) return DX_MODE_LPC_SMEM;
+    if (n <= kDefaultLpcSmemNMax) return DX_MODE_LPC_SMEM;
     return DX_MODE_WPC;
 }
 
@@ -87,8 +93,18 @@ int current_device() {
 }  // namespace
 
 const DxConsts &dx_consts() {
-    static const DxConsts K = make_consts();
+    static const DxConsts K = make_consts(53);
     return K;
+}
+
+const DxConsts *dx_consts_for(int ubits) {
+    static const DxConsts K24 = make_consts(24), K11 = make_consts(11);
+    switch (ubits) {
+        case 53: return &dx_consts();
+        case 24: return &K24;
+        case 11: return &K11;
+        default: return nullptr;
+    }
 }
 
 uint32_t *dx_status_ptr() {
@@ -165,10 +181,14 @@ int drag_expm_get_status(cudaStream_t stream, uint32_t *status_out) {
     return DRAG_OK;
 }
 
-int drag_expm_theta(int32_t k, double *theta_out) {
+int drag_expm_theta(int32_t k, double *theta_out) { return drag_expm_theta_target(k, 53, theta_out); }
+
+int drag_expm_theta_target(int32_t k, int32_t ubits, double *theta_out) {
     if (!theta_out) return DRAG_ENULL;
     if (k < 1 || k > DX_K) return DRAG_EINVAL_SIZE;
-    long long b = dx_consts().th[k];
+    const DxConsts *K = dx_consts_for(ubits);
+    if (!K) return DRAG_EINVAL_TARGET;
+    long long b = K->th[k];
     std::memcpy(theta_out, &b, sizeof b);
     return DRAG_OK;
 }
@@ -182,6 +202,7 @@ const char *drag_expm_strerror(int code) {
         case DRAG_ECUDA: return "a CUDA runtime call or kernel launch failed";
         case DRAG_EWORKSPACE: return "workspace missing or too small";
         case DRAG_EBLOCKS: return "invalid block count or block descriptor array";
+        case DRAG_EINVAL_TARGET: return "unsupported unit round-off target (use 53, 24 or 11)";
         case DRAG_ENOALLOC_LIMIT:
             return "batch exceeds the fixed scratch of drag_expm_apply_batched_noalloc "
                    "(DRAG_NOALLOC_MAX_BLOCKS / DRAG_NOALLOC_MAX_CELLS); use drag_expm_apply_batched with a workspace";

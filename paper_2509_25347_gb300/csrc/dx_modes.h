@@ -7,6 +7,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dx_common.cuh"
+
 enum DxMode : int { DX_MODE_WPC = 0, DX_MODE_LPC_REG = 1, DX_MODE_LPC_SMEM = 2 };
 
 #define DX_LPC_NMAX 12   // largest n with a lane-per-cell kernel
@@ -16,6 +18,6 @@ int dx_mode_for(int n);            // current mode for matrix size n (current de
 void dx_set_mode(int n, int mode);  // used by the autotuner
 bool dx_mode_valid(int n, int mode);
 
-int dx_launch_forward_lpc(int n, bool smem, long long C, const double *rho_g, const double *rho_d, const double *t_s,
+int dx_launch_forward_lpc(const DxConsts &K, int n, bool smem, long long C, const double *rho_g, const double *rho_d, const double *t_s,
                           const double *v_in, double *v_out, double dt, uint32_t *status, double *heat,
                           cudaStream_t stream);

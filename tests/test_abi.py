@@ -45,7 +45,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_version_and_strerror(lib):
     assert lib.drag_expm_version() >= 1
-    for code in (0, -1, -2, -3, -4, -5, -6):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
         assert len(lib.drag_expm_strerror(code)) > 0
     assert b"unknown" in lib.drag_expm_strerror(-999)
 
@@ -60,6 +60,24 @@ def test_theta_matches_oracle_bitwise(lib):
     assert lib.drag_expm_theta(0, ctypes.byref(out)) == -1
     assert lib.drag_expm_theta(10, ctypes.byref(out)) == -1
     assert lib.drag_expm_theta(1, None) == -2
+
+
+def test_theta_targets_match_oracle(lib):
+    """theta_{m_k} for the lower accuracy targets of Eq. B8 (u = 2^-24, 2^-11):
+    the library's closed-form route against the oracle's Cauchy-product route
+    (bisection on the same bound, so they agree to the last bits)."""
+    for ubits in (53, 24, 11):
+        th = oracle.theta_table(2.0 ** -ubits)
+        for k in range(1, 10):
+            got = dx.theta(k, ubits)
+            assert abs(got - th[k]) <= 2 * 2.0 ** -52 * th[k], (ubits, k, got, th[k])
+    out = ctypes.c_double()
+    assert lib.drag_expm_theta_target(3, 20, ctypes.byref(out)) == -8
+    assert lib.drag_expm_theta_target(3, 64, ctypes.byref(out)) == -8
+    assert lib.drag_expm_theta_target(10, 24, ctypes.byref(out)) == -1
+    # a lower target never needs a smaller theta
+    for k in range(1, 10):
+        assert dx.theta(k, 53) < dx.theta(k, 24) < dx.theta(k, 11)
 
 
 def test_host_argument_errors(lib):
@@ -78,6 +96,13 @@ def test_host_argument_errors(lib):
     assert apply(10, 4, null, good, good, 1.0, good, good, s) == -2
     assert apply(10, 4, good, good, good, 1.0, null, good, s) == -2
     assert apply(10, 4, good, bad_align, good, 1.0, good, good, s) == -3
+    at = lib.drag_expm_apply_target
+    assert at(10, 4, good, good, good, 1.0, good, good, 20, s) == -8
+    assert at(10, 4, good, good, good, 1.0, good, good, 0, s) == -8
+    assert at(-1, 4, good, good, good, 1.0, good, good, 24, s) == -1
+    assert at(10, 4, null, good, good, 1.0, good, good, 24, s) == -2
+    st = lib.drag_expm_select_target
+    assert st(10, 4, good, good, good, 1.0, 12, good, good, s) == -8
     assert apply(10, 4, good, good, good, 1.0, good, bad_align, s) == -3
     assert apply(0, 4, null, null, null, 1.0, null, null, s) == 0          # empty: no-op
     sel = lib.drag_expm_select
