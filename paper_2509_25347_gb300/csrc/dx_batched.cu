@@ -379,13 +379,17 @@ bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0;
 
 }  // namespace
 
+// Kernel family per n for the batched path. Items are binned by (n, k*, s*),
+// so the 32 lanes of a lane-per-cell item run exactly their own Taylor order
+// and squaring count; the standalone kernels' mode table (measured on
+// unsorted cells, whose warps run the largest s* of 32 cells) does not
+// carry over. Lane per cell up to n = kBatchLpcNMax (matrix in registers up to
+// DX_LPC_REG_NMAX), warp per cell above.
 Modes dx_batch_modes() {
     Modes M;
-    for (int n = 0; n <= DX_NMAXF; n++) {
-        int m = n >= 2 ? dx_mode_for(n) : DX_MODE_WPC;
-        if (m != DX_MODE_WPC && n > kBatchLpcNMax) m = DX_MODE_WPC;
-        M.m[n] = m;
-    }
+    for (int n = 0; n <= DX_NMAXF; n++)
+        M.m[n] = (n < 2 || n > kBatchLpcNMax) ? DX_MODE_WPC
+                                               : (n <= DX_LPC_REG_NMAX ? DX_MODE_LPC_REG : DX_MODE_LPC_SMEM);
     return M;
 }
 

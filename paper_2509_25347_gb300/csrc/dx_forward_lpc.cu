@@ -8,21 +8,71 @@
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kMaxTileRounds = 4;                   // cells per thread and tile (at most)
+constexpr int kTile = kThreads * kMaxTileRounds;    // largest tile a block sorts and runs
+
+// A warp runs the largest Taylor order and squaring count of its 32 cells, so
+// each block first orders a tile of rounds x kThreads consecutive cells (the
+// launcher shrinks the tile when the grid would leave SMs idle) by a cost proxy
+// (the 1-norm of A = dt Omega_v in FP32, whose binary exponent tracks s*) and
+// hands every warp 32 cells of similar cost. The proxy only groups cells; the
+// cell routine still selects (k*, s*) from the FP64 norm.
+template <int N>
+__device__ __forceinline__ unsigned int cost_proxy(const double *rgp, const double *rdp, const double *tsp,
+                                                   long long stride, double dt) {
+    const float rg = (float)*rgp, fdt = (float)dt;
+    float col0 = 0.0f, cmax = 0.0f;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const float a = fdt / (float)tsp[i * stride];
+        const float ea = a * ((float)rdp[i * stride] / rg);
+        col0 += ea + a;
+        cmax = fmaxf(cmax, ea + a);
+    }
+    const float nrm = fmaxf(col0, cmax);
+    const unsigned int b = __float_as_uint(nrm);
+    return (nrm >= 0.0f && b < 0x7f800000u) ? b : 0x7f800000u;   // non-finite and NaN last among valid cells
+}
 
 template <int NF, bool SMEM>
 __global__ void __launch_bounds__(kThreads)
-dx_forward_lpc(long long C, const double *rho_g, const double *rho_d, const double *t_s, const double *v_in,
-               double *v_out, double dt, uint32_t *status, double *heat, DxConsts K) {
+dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d, const double *t_s,
+               const double *v_in, double *v_out, double dt, uint32_t *status, double *heat, DxConsts K) {
     extern __shared__ double smem[];
+    __shared__ unsigned long long key[kTile];     // (proxy << 32) | tile index, unique
+    __shared__ unsigned short order[kTile];       // sorted position -> tile index
     double *bsh = smem;
     for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
+    const int tile = rounds * kThreads;
+    const long long base = (long long)blockIdx.x * tile;
+    if (rounds > 1) {
+        for (int r = 0; r < rounds; r++) {
+            const int e = r * kThreads + threadIdx.x;
+            const long long c = base + e;
+            const unsigned int p = c < C ? cost_proxy<NF - 1>(rho_g + c, rho_d + c, t_s + c, C, dt) : 0xffffffffu;
+            key[e] = ((unsigned long long)p << 32) | (unsigned int)e;
+        }
+        __syncthreads();
+        // rank sort: position of each key among the tile's distinct keys
+        for (int r = 0; r < rounds; r++) {
+            const int e = r * kThreads + threadIdx.x;
+            const unsigned long long me = key[e];
+            int rank = 0;
+            for (int j = 0; j < tile; j++) rank += key[j] < me;
+            order[rank] = (unsigned short)e;
+        }
+    } else {
+        order[threadIdx.x] = (unsigned short)threadIdx.x;   // one round: grid-sized for small inputs, no sort
+    }
     __syncthreads();
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
     const int lane = threadIdx.x & 31;
     double *wsm = SMEM ? smem + 32 + (threadIdx.x >> 5) * dx_lpc_warp_smem_doubles<NF>() : nullptr;
-    dx_lpc_forward_cell<NF, SMEM>(lane, rho_g + c, rho_d + c, t_s + c, v_in + c, v_out + c, C, dt, K, bsh, wsm,
-                                  status, heat ? heat + c : nullptr);
+    for (int r = 0; r < rounds; r++) {
+        const long long c = base + order[r * kThreads + threadIdx.x];
+        if (c < C)
+            dx_lpc_forward_cell<NF, SMEM>(lane, rho_g + c, rho_d + c, t_s + c, v_in + c, v_out + c, C, dt, K, bsh,
+                                          wsm, status, heat ? heat + c : nullptr);
+    }
 }
 
 template <int NF, bool SMEM>
@@ -33,9 +83,11 @@ int launch_one(const DxConsts &K, long long C, const double *rho_g, const double
         cudaFuncSetAttribute(dx_forward_lpc<NF, SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
         return DRAG_ECUDA;
-    const long long blocks = (C + kThreads - 1) / kThreads;
-    dx_forward_lpc<NF, SMEM><<<(unsigned)blocks, kThreads, smem, stream>>>(C, rho_g, rho_d, t_s, v_in, v_out, dt,
-                                                                          status, heat, K);
+    int rounds = kMaxTileRounds;
+    while (rounds > 1 && (C + rounds * kThreads - 1) / (rounds * kThreads) < 4LL * dx_sm_count()) rounds >>= 1;
+    const long long blocks = (C + rounds * kThreads - 1) / (rounds * kThreads);
+    dx_forward_lpc<NF, SMEM><<<(unsigned)blocks, kThreads, smem, stream>>>(C, rounds, rho_g, rho_d, t_s, v_in, v_out,
+                                                                          dt, status, heat, K);
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }
 

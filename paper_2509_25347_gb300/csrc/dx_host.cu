@@ -72,11 +72,11 @@ bool g_once[64][16];
 int g_mode[64][DX_NMAXF + 1];
 bool g_mode_init[64];
 
-// Measured on GB300 (MRN-like cells): lane per cell with the matrix in
-// registers is fastest up to n = 6, in shared memory up to n = 8 (its shared
-// memory per warp grows as 32 n(n+1) doubles and limits residency), warp per
-// cell above.
-constexpr int kDefaultLpcSmemNMax = 8;
+// Measured on GB300 (stiff MRN-like cells, cost-sorted lane-per-cell tiles):
+// lane per cell with the matrix in registers is fastest up to n = 6, in
+// shared memory up to n = 10 (its shared memory per warp grows as
+// 32 n(n+1) doubles and limits residency), warp per cell above.
+constexpr int kDefaultLpcSmemNMax = 10;
 
 int default_mode(int n) {
     if (n <= DX_LPC_REG_NMAX) return DX_MODE_LPC_REG;
