@@ -62,6 +62,17 @@ def _load():
     lib.orc_drag_apply_u.argtypes = [ctypes.c_int64, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp, dp, ctypes.c_int,
                                      ctypes.c_double, ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int16),
                                      ctypes.POINTER(ctypes.c_uint32)]
+    lib.orc_pade_coeffs.restype = None
+    lib.orc_pade_coeffs.argtypes = [ctypes.c_int, dp]
+    lib.orc_pade_theta.restype = ctypes.c_double
+    lib.orc_pade_theta.argtypes = [ctypes.c_int, ctypes.c_double]
+    lib.orc_select_pade.restype = ctypes.c_int
+    lib.orc_select_pade.argtypes = [ctypes.c_double, ctypes.c_double] + [ctypes.POINTER(ctypes.c_int)] * 2
+    lib.orc_drag_apply_opts.restype = ctypes.c_int
+    lib.orc_drag_apply_opts.argtypes = [ctypes.c_int64, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp, dp,
+                                        ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int8),
+                                        ctypes.POINTER(ctypes.c_int16), dp, ctypes.POINTER(ctypes.c_uint32)]
     lib.orc_drag_apply.restype = ctypes.c_int
     lib.orc_drag_apply.argtypes = [ctypes.c_int64, ctypes.c_int, dp, dp, dp, ctypes.c_double, dp, dp, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(ctypes.c_int16),
@@ -187,6 +198,61 @@ def drag_apply(rho_g, rho_d, t_s, dt, v_in, structured: bool = True, return_ks: 
     if return_ks:
         return v_out, k_out, s_out, st.value
     return v_out
+
+
+PADE_DEGREES = (3, 5, 7, 9, 13)
+
+
+def pade_coeffs(m: int) -> np.ndarray:
+    """c_0..c_m of N_mm (Eq. PadeEqu, p = q = m); D_mm(x) = N_mm(-x)."""
+    out = np.zeros(32)
+    _load().orc_pade_coeffs(int(m), _dptr(out))
+    return out[:m + 1].copy()
+
+
+def pade_theta(m: int, u: float = U_DOUBLE) -> float:
+    """theta of the [m/m] Pade approximant: Eqs. B5-B8 with T_m replaced by R_mm."""
+    return _load().orc_pade_theta(int(m), float(u))
+
+
+def select_pade(norm: float, u: float = U_DOUBLE) -> tuple[int, int]:
+    """(m, s) of the Pade variant for a given 1-norm."""
+    m, s = ctypes.c_int(), ctypes.c_int()
+    _load().orc_select_pade(float(norm), float(u), ctypes.byref(m), ctypes.byref(s))
+    return m.value, s.value
+
+
+def drag_apply_opts(rho_g, rho_d, t_s, dt, v_in, u: float = U_DOUBLE, method: str = "taylor",
+                    bound_test: bool = False, structured: bool = True):
+    """Forward update with the options of the CUDA library's drag_expm_apply_opts.
+
+    method 'taylor' (Algorithm 2; bound_test adds the second modification,
+    Eqs. Pat_Stk4-7) or 'pade' (Eq. PadeEqu). Returns (v_out, k, m, s, ratio,
+    status): k* (Taylor) or the Pade degree, the degree actually evaluated,
+    s*, and for the bound test its left side over u for the top block.
+    """
+    rho_g = np.ascontiguousarray(rho_g, dtype=np.float64)
+    rho_d = np.ascontiguousarray(rho_d, dtype=np.float64)
+    t_s = np.ascontiguousarray(t_s, dtype=np.float64)
+    v_in = np.ascontiguousarray(v_in, dtype=np.float64)
+    C, N = rho_g.shape[0], rho_d.shape[0]
+    assert rho_d.shape == (N, C) and t_s.shape == (N, C) and v_in.shape == (3, N + 1, C)
+    v_out = np.empty_like(v_in)
+    k = np.zeros(C, dtype=np.int8)
+    m = np.zeros(C, dtype=np.int8)
+    s = np.zeros(C, dtype=np.int16)
+    ratio = np.zeros(C)
+    st = ctypes.c_uint32(0)
+    meth = {"taylor": 0, "pade": 1}[method]
+    rc = _load().orc_drag_apply_opts(C, N, _dptr(rho_g), _dptr(rho_d), _dptr(t_s), float(dt), _dptr(v_in),
+                                     _dptr(v_out), int(structured), float(u), meth, int(bound_test),
+                                     k.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                     m.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                     s.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), _dptr(ratio),
+                                     ctypes.byref(st))
+    if rc != 0:
+        raise ValueError(f"oracle rejected sizes (rc={rc})")
+    return v_out, k, m, s, ratio, st.value
 
 
 def frechet_T(A: np.ndarray, G: np.ndarray, structured: bool = False) -> np.ndarray:

@@ -257,8 +257,60 @@ static void orc_restore(int n, double *P)
  * evaluated by Horner in X^q with the stored powers X, X^2, ..., X^q.
  * With structured != 0 the diagonal is restored after the Taylor step and
  * after every squaring. Returns 0, or -1 when |A| is not finite. */
-static int orc_expm_u(int n, const double *A, double *P, int structured, double u, int *k_out, int *m_out,
-                      int *s_out)
+/* ------------------------------------------------------------------------ */
+/* Second modification: the bound test (Eqs. Pat_Stk4-Pat_Stk7, Alg. 8/9)   */
+/* ------------------------------------------------------------------------ */
+
+/* Number of Paterson-Stockmeyer blocks to keep. pw[j] = X^j (j = 1..q, each
+ * n x n), b[i] = 1/i!, T_m(X) = I + sum_{l<r} Bbar_l (X^q)^l with
+ * Bbar_l = sum_{j=1}^{q} b_{ql+j} X^j.
+ *   b_exp = |b_0 I + Bhat_0| + sum_{l=1}^{r-1} |Bhat_l| |X^q|^l     (Eq. Pat_Stk6)
+ *   Bhat_l = sum_{j=1}^{q} (-1)^{ql+j} b_{ql+j} X^j                 (so b_exp >= |T_m(-X)|)
+ * The highest block is dropped while
+ *   b_exp |Bbar_{keep-1}| |X^q|^{keep-1} <= u                       (Eq. Pat_Stk5)
+ * holds (reading of Algorithm 9's per-block condition; at least one block is
+ * kept). ratio_out (optional) receives the left side for the top block / u. */
+static int orc_bound_test_keep(int n, const double *pw, int q, int r, const double *b, double u, double *ratio_out)
+{
+    const size_t nn = (size_t)n * n;
+    double *T = (double *)malloc(sizeof(double) * nn);
+    const double xq = orc_norm1(n, pw + (size_t)q * nn);
+    double bexp = 0.0, xql = 1.0;
+    for (int l = 0; l < r; l++) {
+        for (size_t e = 0; e < nn; e++) {
+            double acc = 0.0;
+            for (int j = 1; j <= q; j++) {
+                const double c = ((q * l + j) & 1) ? -b[q * l + j] : b[q * l + j];
+                acc += c * pw[(size_t)j * nn + e];
+            }
+            T[e] = acc;
+        }
+        if (l == 0)
+            for (int i = 0; i < n; i++) T[(size_t)i * n + i] += b[0];
+        bexp += orc_norm1(n, T) * xql;
+        xql *= xq;
+    }
+    int keep = r;
+    if (ratio_out) *ratio_out = 0.0;
+    while (keep > 1) {
+        const int l = keep - 1;
+        for (size_t e = 0; e < nn; e++) {
+            double acc = 0.0;
+            for (int j = 1; j <= q; j++) acc += b[q * l + j] * pw[(size_t)j * nn + e];
+            T[e] = acc;
+        }
+        double val = bexp * orc_norm1(n, T);
+        for (int t = 0; t < l; t++) val *= xq;
+        if (keep == r && ratio_out) *ratio_out = val / u;
+        if (!(val <= u)) break;
+        keep--;
+    }
+    free(T);
+    return keep;
+}
+
+static int orc_expm_u(int n, const double *A, double *P, int structured, double u, int bound_test, int *k_out,
+                      int *m_out, int *s_out, double *ratio_out)
 {
     int k, m, s;
     int rc = orc_select_alg2_u(orc_norm1(n, A), ORC_K, u, &k, &m, &s);
@@ -281,15 +333,20 @@ static int orc_expm_u(int n, const double *A, double *P, int structured, double 
 
     for (size_t e = 0; e < nn; e++) pw[nn + e] = ldexp(A[e], -s);       /* X = 2^-s A */
     for (int j = 2; j <= q; j++) orc_matmul(n, pw + (size_t)(j - 1) * nn, pw + nn, pw + (size_t)j * nn);
+    int rb = r;                                                          /* blocks kept */
+    if (bound_test) {
+        rb = orc_bound_test_keep(n, pw, q, r, b, u, ratio_out);
+        if (m_out) *m_out = q * rb;
+    }
 
-    /* Horner in X^q: F = Bbar_{r-1}; F = Bbar_k + F X^q for k = r-2..0 */
-    for (int kk = r - 1; kk >= 0; kk--) {
+    /* Horner in X^q: F = Bbar_{rb-1}; F = Bbar_k + F X^q for k = rb-2..0 */
+    for (int kk = rb - 1; kk >= 0; kk--) {
         for (size_t e = 0; e < nn; e++) {
             double acc = 0.0;
             for (int j = 1; j <= q; j++) acc += b[q * kk + j] * pw[(size_t)j * nn + e];
             Bb[e] = acc;
         }
-        if (kk == r - 1) {
+        if (kk == rb - 1) {
             memcpy(F, Bb, nn * sizeof(double));
         } else {
             orc_matmul(n, F, pw + (size_t)q * nn, T);
@@ -311,7 +368,229 @@ static int orc_expm_u(int n, const double *A, double *P, int structured, double 
 
 int orc_expm(int n, const double *A, double *P, int structured, int *k_out, int *m_out, int *s_out)
 {
-    return orc_expm_u(n, A, P, structured, ldexp(1.0, -53), k_out, m_out, s_out);
+    return orc_expm_u(n, A, P, structured, ldexp(1.0, -53), 0, k_out, m_out, s_out, NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pade variant (Eq. PadeEqu): R_mm = D_mm^-1 N_mm, scaling and squaring      */
+/* ------------------------------------------------------------------------ */
+
+/* Coefficients of N_mm (Eq. PadeEqu with p = q = m):
+ * c_j = (2m - j)! m! / ((2m)! j! (m - j)!), j = 0..m; D_mm(X) = N_mm(-X). */
+void orc_pade_coeffs(int m, double *c)
+{
+    for (int j = 0; j <= m; j++) {
+        double v = 1.0;
+        for (int a = 2 * m - j + 1; a <= 2 * m; a++) v /= a;   /* (2m-j)!/(2m)! */
+        for (int a = m - j + 1; a <= m; a++) v *= a;           /* m!/(m-j)! */
+        for (int a = 2; a <= j; a++) v /= a;                   /* 1/j! */
+        c[j] = v;
+    }
+}
+
+/* Double-double numbers (hi + lo, |lo| <= ulp(hi)/2) for the Pade series:
+ * error-free sum (Knuth) and product (explicit fma), so results are the same
+ * on every IEEE platform. */
+typedef struct { double hi, lo; } orc_dd;
+
+static orc_dd orc_dd_add(orc_dd a, orc_dd b)
+{
+    double s = a.hi + b.hi, bb = s - a.hi;
+    double e = (a.hi - (s - bb)) + (b.hi - bb) + a.lo + b.lo;
+    orc_dd r;
+    r.hi = s + e;
+    r.lo = e - (r.hi - s);
+    return r;
+}
+
+static orc_dd orc_dd_mul(orc_dd a, orc_dd b)
+{
+    double p = a.hi * b.hi;
+    double e = fma(a.hi, b.hi, -p) + (a.hi * b.lo + a.lo * b.hi);
+    orc_dd r;
+    r.hi = p + e;
+    r.lo = e - (r.hi - p);
+    return r;
+}
+
+static orc_dd orc_dd_div_int(orc_dd a, int k)   /* a / k, k > 0 */
+{
+    double q = a.hi / k;
+    double e = fma(-q, (double)k, a.hi) + a.lo;    /* remainder a - q k */
+    double q2 = e / k;
+    orc_dd r;
+    r.hi = q + q2;
+    r.lo = q2 - (r.hi - q);
+    return r;
+}
+
+static orc_dd orc_dd_neg(orc_dd a) { a.hi = -a.hi; a.lo = -a.lo; return a; }
+
+/* Series of rho(x) = e^-x N_mm(x) / D_mm(x) - 1 up to x^(L-1): the inverse
+ * series of D (D(0) = 1), times N, times e^-x, in double-double (the terms of
+ * order <= 2m cancel, rho_j = 0 there, and the leading rho_j are ~10 orders
+ * below the partial sums). */
+static void orc_pade_rho(int m, int L, double *rho)
+{
+    orc_dd c[32], w[256], y[256], fac[256];
+    for (int j = 0; j <= m; j++) {                 /* c_j = (2m-j)! m! / ((2m)! j! (m-j)!) */
+        orc_dd v = {1.0, 0.0};
+        for (int a = 2 * m - j + 1; a <= 2 * m; a++) v = orc_dd_div_int(v, a);
+        for (int a = m - j + 1; a <= m; a++) v = orc_dd_mul(v, (orc_dd){(double)a, 0.0});
+        for (int a = 2; a <= j; a++) v = orc_dd_div_int(v, a);
+        c[j] = v;
+    }
+    fac[0] = (orc_dd){1.0, 0.0};                    /* 1/i! */
+    for (int i = 1; i < L; i++) fac[i] = orc_dd_div_int(fac[i - 1], i);
+    for (int k = 0; k < L; k++) {                 /* w = 1 / D, D_i = (-1)^i c_i */
+        orc_dd acc = {k == 0 ? 1.0 : 0.0, 0.0};
+        for (int i = 1; i <= m && i <= k; i++) {
+            orc_dd t = orc_dd_mul(c[i], w[k - i]);
+            acc = orc_dd_add(acc, (i & 1) ? t : orc_dd_neg(t));
+        }
+        w[k] = acc;
+    }
+    for (int k = 0; k < L; k++) {                 /* y = N w */
+        orc_dd acc = {0.0, 0.0};
+        for (int i = 0; i <= m && i <= k; i++) acc = orc_dd_add(acc, orc_dd_mul(c[i], w[k - i]));
+        y[k] = acc;
+    }
+    for (int k = 0; k < L; k++) {                 /* rho = e^-x y - 1 */
+        orc_dd acc = {k == 0 ? -1.0 : 0.0, 0.0};
+        for (int i = 0; i <= k; i++) {
+            orc_dd t = orc_dd_mul(fac[i], y[k - i]);
+            acc = orc_dd_add(acc, (i & 1) ? orc_dd_neg(t) : t);
+        }
+        rho[k] = acc.hi + acc.lo;
+    }
+}
+
+/* theta of the [m/m] Pade approximant: the construction of Eqs. B5-B8 with
+ * T_m replaced by R_mm, i.e. the largest theta with
+ * -log(1 - f(theta))/theta <= u, f(theta) = sum_{j>2m} |rho_j| theta^j. */
+double orc_pade_theta(int m, double u)
+{
+    enum { L = 200 };
+    double rho[L];
+    orc_pade_rho(m, L, rho);
+    double lo = 0.0, hi = 16.0;
+    for (int it = 0; it < 400; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double f = 0.0, p = pow(mid, 2.0 * m + 1.0);
+        for (int j = 2 * m + 1; j < L; j++) {
+            f += fabs(rho[j]) * p;
+            p *= mid;
+        }
+        double bound = (f < 1.0) ? -log1p(-f) / mid : INFINITY;
+        if (bound <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+static const int orc_pade_m[5] = {3, 5, 7, 9, 13};
+
+/* Degree and scaling for the Pade variant: the smallest m in {3, 5, 7, 9}
+ * with |A| <= theta_m and s = 0, else m = 13 and the smallest s with
+ * 2^-s |A| <= theta_13 (the paper gives no selection for Pade; this is the
+ * usual choice of the Pade scaling and squaring it cites). */
+int orc_select_pade(double normA, double u, int *m_out, int *s_out)
+{
+    if (!isfinite(normA) || normA < 0.0) {
+        *m_out = 13; *s_out = 0;
+        return -1;
+    }
+    for (int i = 0; i < 4; i++)
+        if (normA <= orc_pade_theta(orc_pade_m[i], u)) {
+            *m_out = orc_pade_m[i]; *s_out = 0;
+            return 0;
+        }
+    const double th = orc_pade_theta(13, u);
+    int s = 0;
+    while (ldexp(normA, -s) > th) s++;
+    *m_out = 13; *s_out = s;
+    return 0;
+}
+
+/* Solve D R = N for R (n x n), Gaussian elimination with partial pivoting
+ * on copies of D and N. Returns -1 if a pivot is zero. */
+static int orc_solve(int n, const double *Dm, const double *Nm, double *R)
+{
+    const size_t nn = (size_t)n * n;
+    double *M = (double *)malloc(sizeof(double) * nn);
+    memcpy(M, Dm, sizeof(double) * nn);
+    memcpy(R, Nm, sizeof(double) * nn);
+    int rc = 0;
+    for (int j = 0; j < n && rc == 0; j++) {
+        int p = j;
+        for (int i = j + 1; i < n; i++)
+            if (fabs(M[(size_t)i * n + j]) > fabs(M[(size_t)p * n + j])) p = i;
+        if (M[(size_t)p * n + j] == 0.0) { rc = -1; break; }
+        if (p != j)
+            for (int c = 0; c < n; c++) {
+                double t = M[(size_t)j * n + c]; M[(size_t)j * n + c] = M[(size_t)p * n + c]; M[(size_t)p * n + c] = t;
+                t = R[(size_t)j * n + c]; R[(size_t)j * n + c] = R[(size_t)p * n + c]; R[(size_t)p * n + c] = t;
+            }
+        for (int i = j + 1; i < n; i++) {
+            const double l = M[(size_t)i * n + j] / M[(size_t)j * n + j];
+            for (int c = j; c < n; c++) M[(size_t)i * n + c] -= l * M[(size_t)j * n + c];
+            for (int c = 0; c < n; c++) R[(size_t)i * n + c] -= l * R[(size_t)j * n + c];
+        }
+    }
+    for (int j = n - 1; j >= 0 && rc == 0; j--)
+        for (int c = 0; c < n; c++) {
+            double acc = R[(size_t)j * n + c];
+            for (int k = j + 1; k < n; k++) acc -= M[(size_t)j * n + k] * R[(size_t)k * n + c];
+            R[(size_t)j * n + c] = acc / M[(size_t)j * n + j];
+        }
+    free(M);
+    return rc;
+}
+
+/* P = R_mm(X)^(2^s), X = 2^-s A, with the structured restoration after the
+ * Pade step and every squaring (as the Taylor path). */
+static int orc_expm_pade(int n, const double *A, double *P, int structured, double u, int *m_out, int *s_out)
+{
+    int m, s;
+    int rc = orc_select_pade(orc_norm1(n, A), u, &m, &s);
+    if (m_out) *m_out = m;
+    if (s_out) *s_out = s;
+    const size_t nn = (size_t)n * n;
+    if (rc != 0) {
+        for (size_t e = 0; e < nn; e++) P[e] = NAN;
+        return -1;
+    }
+    double c[32];
+    orc_pade_coeffs(m, c);
+    double *X = (double *)malloc(sizeof(double) * nn), *Xj = (double *)malloc(sizeof(double) * nn);
+    double *T = (double *)malloc(sizeof(double) * nn), *Nm = (double *)calloc(nn, sizeof(double));
+    double *Dm = (double *)calloc(nn, sizeof(double));
+    for (size_t e = 0; e < nn; e++) X[e] = ldexp(A[e], -s);
+    for (size_t e = 0; e < nn; e++) Xj[e] = 0.0;
+    for (int i = 0; i < n; i++) Xj[(size_t)i * n + i] = 1.0;             /* X^0 */
+    for (int j = 0; j <= m; j++) {
+        if (j > 0) {
+            orc_matmul(n, Xj, X, T);
+            memcpy(Xj, T, sizeof(double) * nn);
+        }
+        for (size_t e = 0; e < nn; e++) {
+            Nm[e] += c[j] * Xj[e];
+            Dm[e] += ((j & 1) ? -c[j] : c[j]) * Xj[e];
+        }
+    }
+    rc = orc_solve(n, Dm, Nm, P);
+    if (rc == 0) {
+        if (structured) orc_restore(n, P);
+        for (int t = 0; t < s; t++) {
+            orc_matmul(n, P, P, T);
+            memcpy(P, T, sizeof(double) * nn);
+            if (structured) orc_restore(n, P);
+        }
+    } else {
+        for (size_t e = 0; e < nn; e++) P[e] = NAN;
+    }
+    free(X); free(Xj); free(T); free(Nm); free(Dm);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -381,10 +660,60 @@ int orc_drag_apply_u(int64_t C, int N, const double *rho_g, const double *rho_d,
         int ok = orc_cell_valid(N, rho_g[c], rd, ts, dt);
         if (ok) {
             orc_assemble(N, rho_g[c], rd, ts, dt, structured, A);
-            ok = orc_expm_u(n, A, P, structured, u, &k, &m, &s) == 0;
+            ok = orc_expm_u(n, A, P, structured, u, 0, &k, &m, &s, NULL) == 0;
         }
         if (k_out) k_out[c] = (int8_t)k;
         if (s_out) s_out[c] = (int16_t)s;
+        for (int d = 0; d < 3; d++) {
+            for (int f = 0; f < n; f++) vin[f] = v_in[((int64_t)d * n + f) * C + c];
+            for (int i = 0; i < n; i++) {
+                double acc = 0.0;
+                for (int j = 0; j < n; j++) acc += P[i * n + j] * vin[j];
+                v_out[((int64_t)d * n + i) * C + c] = ok ? acc : NAN;
+            }
+        }
+        if (!ok) st |= 1u;
+    }
+    free(A); free(P);
+    if (status) *status |= st;
+    return 0;
+}
+
+/* Forward drag update with the options of the CUDA library: unit round-off
+ * u of the theta tables, method 0 = Taylor (Algorithm 2; bound_test != 0
+ * adds the second modification), 1 = Pade. k_out: k* (Taylor) or the Pade
+ * degree; m_out: the polynomial degree actually evaluated; s_out: s*. */
+int orc_drag_apply_opts(int64_t C, int N, const double *rho_g, const double *rho_d, const double *t_s, double dt,
+                        const double *v_in, double *v_out, int structured, double u, int method, int bound_test,
+                        int8_t *k_out, int8_t *m_out, int16_t *s_out, double *ratio_out, uint32_t *status)
+{
+    if (C < 0 || N < 1 || N + 1 > ORC_NMAX || method < 0 || method > 1) return -1;
+    const int n = N + 1;
+    double *A = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double *P = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double rd[ORC_NMAX], ts[ORC_NMAX], vin[ORC_NMAX];
+    uint32_t st = 0;
+    for (int64_t c = 0; c < C; c++) {
+        for (int i = 0; i < N; i++) {
+            rd[i] = rho_d[(int64_t)i * C + c];
+            ts[i] = t_s[(int64_t)i * C + c];
+        }
+        int k = 0, m = 0, s = 0;
+        double ratio = 0.0;
+        int ok = orc_cell_valid(N, rho_g[c], rd, ts, dt);
+        if (ok) {
+            orc_assemble(N, rho_g[c], rd, ts, dt, structured, A);
+            if (method == 0) {
+                ok = orc_expm_u(n, A, P, structured, u, bound_test, &k, &m, &s, &ratio) == 0;
+            } else {
+                ok = orc_expm_pade(n, A, P, structured, u, &m, &s) == 0;
+                k = m;
+            }
+        }
+        if (k_out) k_out[c] = (int8_t)k;
+        if (m_out) m_out[c] = (int8_t)m;
+        if (s_out) s_out[c] = (int16_t)s;
+        if (ratio_out) ratio_out[c] = ratio;
         for (int d = 0; d < 3; d++) {
             for (int f = 0; f < n; f++) vin[f] = v_in[((int64_t)d * n + f) * C + c];
             for (int i = 0; i < n; i++) {
