@@ -405,9 +405,27 @@ def run_ours(args, rank, world):
     if dx.get_status():
         raise RuntimeError("device status set after the accuracy-target runs")
 
-    total_ms, e2e_ms, fb_ms, rk_ms, t24_ms, t11_ms = max_over_ranks(
-        [total_ms, e2e_ms, fb_ms, rk_ms, target_ms[24], target_ms[11]], world, device="cuda")
+    # the paper's variants: second modification (bound test) and Pade
+    variant_ms, variant_deg = {}, {}
+    for name, kw in (("taylor_bound_test", {"bound_test": True}), ("pade", {"method": "pade"})):
+        _, mdeg, _ = dx.apply_opts(rg, rd, ts, cells.dt, v, vout, return_ms=True, **kw)
+        variant_deg[name] = float(mdeg.double().mean())
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(rk_steps):
+            dx.apply_opts(rg, rd, ts, cells.dt, v, vout, **kw)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        variant_ms[name] = t0.elapsed_time(t1) / rk_steps
+    if dx.get_status():
+        raise RuntimeError("device status set after the variant runs")
+
+    total_ms, e2e_ms, fb_ms, rk_ms, t24_ms, t11_ms, bt_ms, pd_ms = max_over_ranks(
+        [total_ms, e2e_ms, fb_ms, rk_ms, target_ms[24], target_ms[11], variant_ms["taylor_bound_test"],
+         variant_ms["pade"]], world, device="cuda")
     target_ms = {24: t24_ms, 11: t11_ms}
+    variant_ms = {"taylor_bound_test": bt_ms, "pade": pd_ms}
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(C, world, ms_per_step)
     e2e_value = whole_job_rate(C, world, e2e_ms)
@@ -458,6 +476,12 @@ def run_ours(args, rank, world):
                                "ms_per_step": target_ms[ub], "mean_k_star": target_ks[ub][0],
                                "mean_s_star": target_ks[ub][1]}
                for ub in (24, 11)}},
+        "variants": {
+            "note": "drag_expm_apply_opts: the paper's second modification (bound test) and the Pade variant "
+                    "(Eq. PadeEqu), warp per cell; outside the headline timed region",
+            **{name: {"value": whole_job_rate(C, world, variant_ms[name]), "unit": UNIT,
+                      "ms_per_step": variant_ms[name], "mean_degree": variant_deg[name]}
+               for name in ("taylor_bound_test", "pade")}},
         "gpu_launches": args.steps,
         "clocks": clocks,
     }

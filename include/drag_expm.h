@@ -62,7 +62,8 @@ extern "C" {
 #define DRAG_EWORKSPACE (-5)    /* workspace missing or smaller than required */
 #define DRAG_EBLOCKS (-6)       /* bad block count in the batched entry point */
 #define DRAG_ENOALLOC_LIMIT (-7) /* batch larger than drag_expm_apply_batched_noalloc's fixed scratch */
-#define DRAG_EINVAL_TARGET (-8)  /* unit round-off target other than 53, 24 or 11 bits */
+#define DRAG_EINVAL_TARGET (-8)  /* unit round-off target other than 53, 24 or 11 bits (Pade: 53, 24) */
+#define DRAG_EINVAL_OPTION (-9)  /* bad drag_expm_options_t (method, bound_test with Pade, reserved != 0) */
 
 /* Sticky device status bits (drag_expm_get_status). */
 #define DRAG_STATUS_BAD_CELL 0x1u      /* some cell had invalid data; its outputs are NaN */
@@ -100,6 +101,45 @@ int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *rho_g, const
 int drag_expm_apply_target(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
                            const double *t_s, double dt, const double *v_in, double *v_out, int32_t ubits,
                            cudaStream_t stream);
+
+/* Methods of drag_expm_apply_opts. */
+#define DRAG_METHOD_TAYLOR 0   /* the paper's Taylor scaling and squaring (Algorithm 2) */
+#define DRAG_METHOD_PADE 1     /* diagonal Pade approximant (Eq. PadeEqu) with scaling and squaring */
+
+typedef struct {
+    int32_t ubits;       /* accuracy target u = 2^-ubits: 53, 24 or 11 (Pade: 53 or 24) */
+    int32_t method;      /* DRAG_METHOD_TAYLOR or DRAG_METHOD_PADE */
+    int32_t bound_test;  /* Taylor only: 1 = the paper's second modification (bound test) */
+    int32_t reserved;    /* must be 0 */
+} drag_expm_options_t;
+
+/*
+ * drag_expm_apply_opts — forward update with the paper's variants of the
+ * Taylor method and its Pade alternative. Host-side validation as
+ * drag_expm_apply; opts is a HOST pointer.
+ *   method = DRAG_METHOD_TAYLOR, bound_test = 0: drag_expm_apply_target.
+ *   method = DRAG_METHOD_TAYLOR, bound_test = 1: after Algorithm 2, the
+ *     Paterson-Stockmeyer blocks of T_m are bounded as in Eqs. Pat_Stk5 and
+ *     Pat_Stk6 (Algorithm 8's b_exp) and the highest ones dropped while the
+ *     bound holds, so the Taylor step has fewer terms (App. B, second
+ *     modification); the 1-norms are those of the velocity-form matrices.
+ *   method = DRAG_METHOD_PADE: R_mm(X) = D_mm(X)^-1 N_mm(X) (Eq. PadeEqu),
+ *     m in {3, 5, 7, 9, 13} and the scaling s chosen with theta_m from the
+ *     construction of Eqs. B5-B8 applied to R_mm (drag_expm_pade_theta): the
+ *     smallest m with |A|_1 <= theta_m and s = 0, else m = 13 and the smallest
+ *     s with 2^-s |A|_1 <= theta_13.
+ *   All variants restore the row sums after the approximant and every squaring.
+ *   m_out : DEVICE int8[ncells] or NULL, receives the polynomial degree
+ *           evaluated per cell (Taylor: m_{k*} or fewer terms after the bound
+ *           test; Pade: m); 0 for invalid cells.
+ *   s_out : DEVICE int16[ncells] or NULL, receives s* (-1 for invalid cells).
+ * These variants run one warp per cell whatever the mode table says.
+ * Returns DRAG_ENULL (opts NULL), DRAG_EINVAL_OPTION, DRAG_EINVAL_TARGET, or as
+ * drag_expm_apply.
+ */
+int drag_expm_apply_opts(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                         const double *t_s, double dt, const double *v_in, double *v_out,
+                         const drag_expm_options_t *opts, int8_t *m_out, int16_t *s_out, cudaStream_t stream);
 
 /*
  * drag_expm_apply_heat — drag_expm_apply plus the energy epilogue: heat_out[c]
@@ -298,6 +338,14 @@ int drag_expm_theta(int32_t k, double *theta_out);
  * 11; DRAG_EINVAL_TARGET otherwise), k = 1..9. Host only.
  */
 int drag_expm_theta_target(int32_t k, int32_t ubits, double *theta_out);
+
+/*
+ * drag_expm_pade_theta — theta_m of the Pade variant (Eq. PadeEqu; the
+ * construction of Eqs. B5-B8 applied to the [m/m] approximant) for
+ * m in {3, 5, 7, 9, 13} and u = 2^-ubits, ubits in {53, 24}. Host only.
+ * Returns DRAG_EINVAL_SIZE for another m, DRAG_EINVAL_TARGET for another ubits.
+ */
+int drag_expm_pade_theta(int32_t m, int32_t ubits, double *theta_out);
 
 /* drag_expm_strerror — static text for a DRAG_E* code. */
 const char *drag_expm_strerror(int code);

@@ -14,7 +14,7 @@ import ctypes
 import os
 
 __all__ = ["load_library", "apply", "apply_heat", "backward", "rk1_apply", "apply_batched", "batched_workspace_bytes", "select", "get_status",
-           "theta", "DragExpm", "DragExpmError",
+           "theta", "DragExpm", "DragExpmError", "apply_opts", "pade_theta",
            "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -72,6 +72,10 @@ def load_library(path: str | None = None):
     lib.drag_expm_theta_target.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
     lib.drag_expm_apply_target.restype = ctypes.c_int
     lib.drag_expm_apply_target.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, i32, vp]
+    lib.drag_expm_apply_opts.restype = ctypes.c_int
+    lib.drag_expm_apply_opts.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, ctypes.POINTER(DragOptions), vp, vp, vp]
+    lib.drag_expm_pade_theta.restype = ctypes.c_int
+    lib.drag_expm_pade_theta.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
     lib.drag_expm_select_target.restype = ctypes.c_int
     lib.drag_expm_select_target.argtypes = [i64, i32, vp, vp, vp, dbl, i32, vp, vp, vp]
     lib.drag_expm_strerror.restype = ctypes.c_char_p
@@ -113,6 +117,14 @@ def _shapes(rho_g, rho_d):
 
 
 UBITS_TARGETS = (53, 24, 11)
+METHOD_TAYLOR = 0
+METHOD_PADE = 1
+
+
+class DragOptions(ctypes.Structure):
+    """drag_expm_options_t of include/drag_expm.h."""
+    _fields_ = [("ubits", ctypes.c_int32), ("method", ctypes.c_int32), ("bound_test", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 def apply(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, stream=None, ubits: int = 53):
@@ -135,6 +147,37 @@ def apply(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, stream=None, ubits: in
         _check(load_library().drag_expm_apply_target(C, N, *args, float(dt), vi, vo, int(ubits),
                                                      _stream_handle(stream)))
     return v_out
+
+
+def apply_opts(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, ubits: int = 53, method: str = "taylor",
+               bound_test: bool = False, return_ms: bool = False, stream=None):
+    """Forward update with the paper's variants (drag_expm_apply_opts): method
+    'taylor' (bound_test adds the second modification) or 'pade'. With
+    return_ms, also returns the degree evaluated (int8) and s* (int16) per cell."""
+    import torch
+    C, N = _shapes(rho_g, rho_d)
+    if v_out is None:
+        v_out = torch.empty_like(v_in)
+    args = [_f64_cuda("rho_g", rho_g, (C,)), _f64_cuda("rho_d", rho_d, (N, C)), _f64_cuda("t_s", t_s, (N, C))]
+    vi = _f64_cuda("v_in", v_in, (3, N + 1, C))
+    vo = _f64_cuda("v_out", v_out, (3, N + 1, C))
+    opts = DragOptions(int(ubits), {"taylor": METHOD_TAYLOR, "pade": METHOD_PADE}[method], int(bool(bound_test)), 0)
+    m = s = None
+    mp = sp = ctypes.c_void_p(0)
+    if return_ms:
+        m = torch.empty(C, dtype=torch.int8, device=v_in.device)
+        s = torch.empty(C, dtype=torch.int16, device=v_in.device)
+        mp, sp = ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(s.data_ptr())
+    _check(load_library().drag_expm_apply_opts(C, N, *args, float(dt), vi, vo, ctypes.byref(opts), mp, sp,
+                                               _stream_handle(stream)))
+    return (v_out, m, s) if return_ms else v_out
+
+
+def pade_theta(m: int, ubits: int = 53) -> float:
+    """theta_m of the Pade variant as used by the library (m in 3, 5, 7, 9, 13)."""
+    out = ctypes.c_double(0.0)
+    _check(load_library().drag_expm_pade_theta(int(m), int(ubits), ctypes.byref(out)))
+    return out.value
 
 
 def apply_heat(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, heat_out=None, stream=None):

@@ -27,12 +27,25 @@ struct DxConsts {
     long long th4[DX_K + 1];   // 4 theta_{m_k}
     double b[32];              // Taylor coefficients b_i = 1/i!, i = 0..31
     int mk[DX_K + 1];          // m_k of Table B.1
+    int qk[DX_K + 1];          // q_k, r_k of Table B.1 (m_k = q_k r_k; the bound test's blocks)
+    int rk[DX_K + 1];
+    double u;                  // unit round-off the theta tables were made for
+};
+
+// Pade variant (Eq. PadeEqu, diagonal [m/m] approximants).
+#define DX_PADE_NM 5
+struct DxPade {
+    long long th[DX_PADE_NM];      // bit patterns of theta_m, m = 3, 5, 7, 9, 13
+    int m[DX_PADE_NM];
+    double c[DX_PADE_NM][14];      // N_mm(x) = sum_j c_j x^j, D_mm(x) = N_mm(-x)
 };
 
 // Host side (dx_host.cu)
 const DxConsts &dx_consts();
 // Tables for unit round-off u = 2^-ubits, ubits in {53, 24, 11}; nullptr otherwise.
 const DxConsts *dx_consts_for(int ubits);
+// Pade tables for u = 2^-ubits, ubits in {53, 24}; nullptr otherwise.
+const DxPade *dx_pade_for(int ubits);
 uint32_t *dx_status_ptr();     // device address of the sticky status word (current device)
 int dx_sm_count();
 // Runs fn() once per (device, slot); returns false if it failed (it is retried next time).
@@ -92,6 +105,23 @@ __device__ __forceinline__ void dx_select(double norm, const DxConsts &K, int &k
     }
     kstar = ks;
     sstar = ss;
+}
+
+// Pade degree and scaling: the smallest m in {3, 5, 7, 9} with |A| <= theta_m
+// (s = 0), else m = 13 with the smallest s >= 0 such that 2^-s |A| <= theta_13.
+// Integer compares of bit patterns; returns the index of m in DxPade::m.
+__device__ __forceinline__ void dx_select_pade(double norm, const DxPade &P, int &idx, int &sstar) {
+    const long long nb = dx_bits(norm);
+    idx = DX_PADE_NM - 1;
+#pragma unroll
+    for (int i = DX_PADE_NM - 2; i >= 0; i--)
+        if (nb <= P.th[i]) idx = i;
+    sstar = 0;
+    const long long th = P.th[DX_PADE_NM - 1];
+    if (idx == DX_PADE_NM - 1 && nb > th) {
+        const long long mask = (1LL << 52) - 1;
+        sstar = (int)(nb >> 52) - (int)(th >> 52) + (((nb & mask) > (th & mask)) ? 1 : 0);
+    }
 }
 
 // 2^e as a double for -1022 <= e <= 1023 (exact).

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "dx_common.cuh"
 #include "dx_modes.h"
@@ -12,8 +13,10 @@ __device__ uint32_t g_dx_status;
 
 namespace {
 
-// Table B.1: m_k for k = 1..9.
+// Table B.1: m_k, q_k, r_k for k = 1..9.
 const int kMk[DX_K + 1] = {0, 2, 4, 6, 9, 12, 16, 20, 25, 30};
+const int kQk[DX_K + 1] = {0, 1, 2, 2, 3, 3, 4, 4, 5, 5};
+const int kRk[DX_K + 1] = {0, 2, 2, 3, 3, 4, 4, 5, 5, 6};
 
 // f_m(theta)/theta with f_m of Eq. B6. The coefficients of
 // rho(x) = e^-x T_m(x) - 1 (Eq. B5) satisfy |c_j| = C(j-1, m)/j!, so
@@ -59,10 +62,112 @@ DxConsts make_consts(int ubits) {
         K.th2[k] = bits(2.0 * th);
         K.th4[k] = bits(4.0 * th);
         K.mk[k] = kMk[k];
+        K.qk[k] = kQk[k];
+        K.rk[k] = kRk[k];
     }
     K.b[0] = 1.0;
     for (int i = 1; i < 32; i++) K.b[i] = K.b[i - 1] / i;
+    K.u = u;
     return K;
+}
+
+// ---- Pade variant: coefficients and theta_m (host, double-double series)
+
+// Unevaluated sum hi + lo with |lo| <= ulp(hi)/2; the operations are
+// error-free transformations (two-sum, fma two-product), identical on every
+// IEEE-754 host.
+struct Dd {
+    double hi = 0.0, lo = 0.0;
+};
+Dd dd_norm(double a, double b) {
+    Dd r;
+    r.hi = a + b;
+    r.lo = b - (r.hi - a);
+    return r;
+}
+Dd operator+(Dd a, Dd b) {
+    const double s = a.hi + b.hi, v = s - a.hi;
+    const double err = (a.hi - (s - v)) + (b.hi - v);
+    return dd_norm(s, err + a.lo + b.lo);
+}
+Dd operator-(Dd a) { return Dd{-a.hi, -a.lo}; }
+Dd operator*(Dd a, Dd b) {
+    const double p = a.hi * b.hi;
+    return dd_norm(p, std::fma(a.hi, b.hi, -p) + a.hi * b.lo + a.lo * b.hi);
+}
+Dd dd_from_ratio(double num, double den) {       // num / den for integers below 2^53
+    const double q = num / den;
+    return dd_norm(q, std::fma(-q, den, num) / den);
+}
+
+// rho(x) = e^-x R_mm(x) - 1 = -E(x) G(x) with
+//   E(x) = e^x D(x) - N(x) = (-1)^m x^(2m+1)/(2m)! int_0^1 e^(tx) t^m (1-t)^m dt
+//        = sum_k e_k x^(2m+1+k),  e_k = (-1)^m m! (m+k)! / ((2m)! k! (2m+k+1)!)
+//   G(x) = e^-x / D(x):  D G = e^-x, i.e. G_k = (-1)^k/k! - sum_{i>=1} d_i G_{k-i}.
+// Returns |rho_j| for j = 2m+1 .. 2m+L (index j - 2m - 1).
+void pade_rho_abs(int m, int L, double *out) {
+    std::vector<Dd> d(m + 1), G(L), e(L);
+    for (int j = 0; j <= m; j++) {             // d_j = (-1)^j (2m-j)! m! / ((2m)! j! (m-j)!)
+        Dd v{1.0, 0.0};
+        for (int a = 0; a < j; a++) v = v * dd_from_ratio(m - a, (2 * m - a) * (double)(a + 1));
+        d[j] = (j & 1) ? -v : v;
+    }
+    Dd inv_fact{1.0, 0.0};
+    for (int k = 0; k < L; k++) {
+        if (k > 0) inv_fact = inv_fact * dd_from_ratio(1.0, k);
+        Dd g = (k & 1) ? -inv_fact : inv_fact;
+        for (int i = 1; i <= m && i <= k; i++) g = g + -(d[i] * G[k - i]);
+        G[k] = g;
+    }
+    Dd ek{1.0, 0.0};                          // |e_0| = m! m! / ((2m)! (2m+1)!)
+    for (int a = 1; a <= m; a++) ek = ek * dd_from_ratio(a, m + a);        // m! m! / (2m)!
+    for (int a = 2; a <= 2 * m + 1; a++) ek = ek * dd_from_ratio(1.0, a);   // / (2m+1)!
+    for (int k = 0; k < L; k++) {
+        e[k] = (m & 1) ? -ek : ek;
+        ek = ek * dd_from_ratio(m + k + 1, (double)(k + 1) * (2 * m + k + 2));   // e_{k+1}/e_k
+    }
+    for (int j = 0; j < L; j++) {
+        Dd acc;
+        for (int k = 0; k <= j; k++) acc = acc + e[k] * G[j - k];
+        out[j] = std::fabs(acc.hi + acc.lo);
+    }
+}
+
+double pade_theta_of(int m, double u) {
+    const int L = 200;
+    std::vector<double> a(L);
+    pade_rho_abs(m, L, a.data());
+    double lo = 0.0, hi = 16.0;
+    for (int it = 0; it < 300; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double f = 0.0, p = std::pow(mid, 2 * m + 1);
+        for (int j = 0; j < L; j++) {
+            f += a[j] * p;
+            p *= mid;
+        }
+        const bool ok = f < 1.0 && -std::log1p(-f) / mid <= u;
+        (ok ? lo : hi) = mid;
+    }
+    return lo;
+}
+
+DxPade make_pade(int ubits) {
+    static const int kPm[DX_PADE_NM] = {3, 5, 7, 9, 13};
+    DxPade P;
+    std::memset(&P, 0, sizeof P);
+    const double u = std::ldexp(1.0, -ubits);
+    for (int i = 0; i < DX_PADE_NM; i++) {
+        const int m = kPm[i];
+        P.m[i] = m;
+        P.th[i] = bits(pade_theta_of(m, u));
+        double v = 1.0;                       // c_j = (2m-j)! m! / ((2m)! j! (m-j)!)
+        for (int j = 0; j <= m; j++) {
+            P.c[i][j] = v;
+            v = v * (m - j) / ((2.0 * m - j) * (j + 1));
+        }
+    }
+    return P;
 }
 
 std::mutex g_mu;
@@ -95,6 +200,15 @@ int current_device() {
 const DxConsts &dx_consts() {
     static const DxConsts K = make_consts(53);
     return K;
+}
+
+const DxPade *dx_pade_for(int ubits) {
+    static const DxPade P53 = make_pade(53), P24 = make_pade(24);
+    switch (ubits) {
+        case 53: return &P53;
+        case 24: return &P24;
+        default: return nullptr;
+    }
 }
 
 const DxConsts *dx_consts_for(int ubits) {
@@ -193,6 +307,19 @@ int drag_expm_theta_target(int32_t k, int32_t ubits, double *theta_out) {
     return DRAG_OK;
 }
 
+int drag_expm_pade_theta(int32_t m, int32_t ubits, double *theta_out) {
+    if (!theta_out) return DRAG_ENULL;
+    const DxPade *P = dx_pade_for(ubits);
+    if (!P) return DRAG_EINVAL_TARGET;
+    for (int i = 0; i < DX_PADE_NM; i++)
+        if (P->m[i] == m) {
+            const long long b = P->th[i];
+            std::memcpy(theta_out, &b, sizeof b);
+            return DRAG_OK;
+        }
+    return DRAG_EINVAL_SIZE;
+}
+
 const char *drag_expm_strerror(int code) {
     switch (code) {
         case DRAG_OK: return "success";
@@ -202,7 +329,8 @@ const char *drag_expm_strerror(int code) {
         case DRAG_ECUDA: return "a CUDA runtime call or kernel launch failed";
         case DRAG_EWORKSPACE: return "workspace missing or too small";
         case DRAG_EBLOCKS: return "invalid block count or block descriptor array";
-        case DRAG_EINVAL_TARGET: return "unsupported unit round-off target (use 53, 24 or 11)";
+        case DRAG_EINVAL_TARGET: return "unsupported unit round-off target (use 53, 24 or 11; Pade: 53 or 24)";
+        case DRAG_EINVAL_OPTION: return "invalid option combination (method, bound_test, reserved)";
         case DRAG_ENOALLOC_LIMIT:
             return "batch exceeds the fixed scratch of drag_expm_apply_batched_noalloc "
                    "(DRAG_NOALLOC_MAX_BLOCKS / DRAG_NOALLOC_MAX_CELLS); use drag_expm_apply_batched with a workspace";

@@ -54,11 +54,13 @@ struct DxLane {
 };
 
 // Set-up of one cell: A = dt Omega_v entries, the 1-norm (summed in ascending
-// species order, as the oracle does, so (k*, s*) are reproducible), Algorithm 2,
-// and the scaled symmetric arrowhead X = 2^-s* S. Returns false (warp uniform)
-// when the cell's data are invalid.
+// species order, as the oracle does, so (k*, s*) are reproducible), Algorithm 2
+// (or, with a Pade table, the Pade degree and scaling), and the scaled
+// symmetric arrowhead X = 2^-s* S. Returns false (warp uniform) when the cell's
+// data are invalid.
 __device__ __forceinline__ bool dx_wpc_setup(int lane, int N, double rg, double rd, double ts, double dt,
-                                             const DxConsts &K, const DxVecs &V, DxLane &L) {
+                                             const DxConsts &K, const DxVecs &V, DxLane &L,
+                                             const DxPade *pade = nullptr) {
     const int n = N + 1;
     const bool okl = (lane == 0 || lane > N) || (dx_nonneg_finite(rd) && dx_pos_or_inf(ts));
     const bool ok = __all_sync(DX_FULL, okl) && dx_pos_finite(rg);
@@ -75,7 +77,10 @@ __device__ __forceinline__ bool dx_wpc_setup(int lane, int N, double rg, double 
     const double colj = sp ? __dadd_rn(a0i, ai0) : 0.0;
     long long nb = dx_warp_max_ll(dx_bits(colj));
     nb = nb > dx_bits(col0) ? nb : dx_bits(col0);
-    dx_select(__longlong_as_double(nb), K, L.k, L.s);
+    if (pade)
+        dx_select_pade(__longlong_as_double(nb), *pade, L.k, L.s);   // L.k: index of the Pade degree
+    else
+        dx_select(__longlong_as_double(nb), K, L.k, L.s);
     const double p2 = dx_pow2(-L.s);
     double sg = 1.0, tu = 1.0;
     if (sp) {
@@ -314,73 +319,73 @@ __host__ __device__ __forceinline__ int dx_wpc_fwd_warp_doubles(int n) { return 
 // instructions) become four applications (~152).
 #define DX_APPLY_Q 2
 
-// Forward update of one cell by one warp (warp-uniform arguments). Element i
-// of a per-species array is at p[i * stride]; velocity (d, f) at
-// p[(d * n + f) * stride]. od/hp: pair tables for this n. v_out may alias v_in.
-// heat (may be null, warp uniform): receives the kinetic energy the step
-// dissipates, sum_f 1/2 rho_f (|v_in,f - V|^2 - |v_out,f - V|^2) with V the
-// centre-of-mass velocity (frictional heating of Eq. GenEq_3, weight w = 1).
-__device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const double *rgp, const double *rdp,
-                                                    const double *tsp, const double *vip, double *vop,
-                                                    long long stride, double dt, const DxConsts &K, double *wsm,
-                                                    const unsigned short *od, const unsigned short *hp,
-                                                    uint32_t *status, double *heat = nullptr) {
-    const int n = N + 1, ns = dx_stride(n);
-    const int n_od = n * (n - 1) / 2;
-    const int n_hp = n * (n + 1) / 2 - 1;
-    double *E0 = wsm;
-    double *E1 = E0 + n * ns;
-    DxVecs V;
-    V.sig = E1 + n * ns;
+// Per-cell vectors of the forward routines, laid out from vbase: sigma, tau,
+// X_0f, X_ff (4 n), the input velocities (3 n) and two buffers of
+// (v, sigma o v) for the repeated applications (12 n): 19 n doubles.
+struct DxFwdBufs {
+    double *v0;          // input velocities v_f, three components
+    double *wv0, *wv1;   // current v, two buffers
+    double *wy0, *wy1;   // sigma o current v
+};
+
+__device__ __forceinline__ void dx_wpc_fwd_layout(double *vbase, int n, DxVecs &V, DxFwdBufs &B) {
+    V.sig = vbase;
     V.tau = V.sig + n;
     V.xs = V.tau + n;
     V.ds = V.xs + n;
-    double *v0 = V.ds + n;      // input velocities v_f, three components
-    double *const wv0 = v0 + 3 * n, *const wv1 = v0 + 9 * n;    // current v, two buffers
-    double *const wy0 = v0 + 6 * n, *const wy1 = v0 + 12 * n;   // sigma o current v
+    B.v0 = V.ds + n;
+    B.wv0 = B.v0 + 3 * n;
+    B.wy0 = B.v0 + 6 * n;
+    B.wv1 = B.v0 + 9 * n;
+    B.wy1 = B.v0 + 12 * n;
+}
 
-    const double rg = *rgp;
-    double rd = 0.0, ts = INFINITY;
+// One cell's inputs on the lanes: lane f holds fluid f (species i on lane i).
+struct DxCellIn {
+    double rg, rd, ts, vin[3];
+};
+
+__device__ __forceinline__ void dx_wpc_load_cell(int lane, int N, const double *rgp, const double *rdp,
+                                                 const double *tsp, const double *vip, long long stride,
+                                                 DxCellIn &c) {
+    const int n = N + 1;
+    c.rg = *rgp;
+    c.rd = 0.0;
+    c.ts = INFINITY;
     if (lane >= 1 && lane <= N) {
-        rd = rdp[(long long)(lane - 1) * stride];
-        ts = tsp[(long long)(lane - 1) * stride];
+        c.rd = rdp[(long long)(lane - 1) * stride];
+        c.ts = tsp[(long long)(lane - 1) * stride];
     }
-    double vin[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int d = 0; d < 3; d++) c.vin[d] = lane < n ? vip[((long long)d * n + lane) * stride] : 0.0;
+}
+
+// Invalid cell: NaN outputs and the status bit.
+__device__ __forceinline__ void dx_wpc_fail_cell(int lane, int n, double *vop, long long stride, uint32_t *status,
+                                                 double *heat) {
     if (lane < n) {
 #pragma unroll
-        for (int d = 0; d < 3; d++) vin[d] = vip[((long long)d * n + lane) * stride];
+        for (int d = 0; d < 3; d++) vop[((long long)d * n + lane) * stride] = NAN;
     }
-    DxLane L;
-    if (!dx_wpc_setup(lane, N, rg, rd, ts, dt, K, V, L)) {
-        if (lane < n) {
-#pragma unroll
-            for (int d = 0; d < 3; d++) vop[((long long)d * n + lane) * stride] = NAN;
-        }
-        if (lane == 0) {
-            atomicOr(status, DRAG_STATUS_BAD_CELL);
-            if (heat) *heat = NAN;
-        }
-        __syncwarp();
-        return;
+    if (lane == 0) {
+        atomicOr(status, DRAG_STATUS_BAD_CELL);
+        if (heat) *heat = NAN;
     }
-    const int m = K.mk[L.k];
+    __syncwarp();
+}
 
-    // Taylor polynomial T_m(X) by Horner's rule in X
-    double *F = E0, *G = E1;
-    dx_wpc_taylor_init(lane, n, ns, m, K, V, F);
-    for (int j = m - 2; j >= 0; j--) {
-        dx_wpc_horner_step(lane, n, ns, n_hp, hp, V, K.b[j], F, G);
-        __syncwarp();
-        double *tmp = F; F = G; G = tmp;
-    }
-
-    // row-sum restoration, then s - q squarings (Eq. ExpEq1 with n = 2^s), each
-    // restored; the remaining q squarings become 2^q applications below
-    (void)od;
-    (void)n_od;
-    const int q = L.s < DX_APPLY_Q ? L.s : DX_APPLY_Q;
-    F = dx_wpc_square_chain(lane, n, ns, L.s - q, E0, E1, F == E1 ? 1 : 0, V) ? E1 : E0;
-
+// Apply P^(2^q) (P = D_sigma^-1 F D_sigma, F the restored symmetric form after
+// s - q squarings) to the three velocity components and store v_out. heat
+// (may be null, warp uniform): the kinetic energy the step dissipates,
+// sum_f 1/2 rho_f (|v_in,f - V|^2 - |v_out,f - V|^2) with V the centre-of-mass
+// velocity (frictional heating of Eq. GenEq_3, weight w = 1).
+__device__ __forceinline__ void dx_wpc_apply_tail(int lane, int n, int ns, const DxVecs &V, const DxFwdBufs &B,
+                                                  const double *F, int q, const DxCellIn &c, double sg, double *vop,
+                                                  long long stride, double *heat) {
+    double *const v0 = B.v0;
+    double *const wv0 = B.wv0, *const wv1 = B.wv1, *const wy0 = B.wy0, *const wy1 = B.wy1;
+    const double rg = c.rg, rd = c.rd;
+    const double *vin = c.vin;
     // v <- P v, 2^q times, P_ii = E_ii, P_ij = E_ij sigma_j / sigma_i (P = D_sigma^-1 E D_sigma):
     // v_i' = E_ii v_i + tau_i sum_{j != i} E_ij sigma_j v_j
     if (lane < n) {
@@ -388,7 +393,7 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
         for (int d = 0; d < 3; d++) {
             v0[d * n + lane] = vin[d];
             wv0[d * n + lane] = vin[d];
-            wy0[d * n + lane] = L.sg * vin[d];
+            wy0[d * n + lane] = sg * vin[d];
         }
     }
     __syncwarp();
@@ -447,4 +452,47 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
         if (lane == 0) *heat = hsum;
     }
     __syncwarp();
+}
+
+// Forward update of one cell by one warp (warp-uniform arguments). Element i
+// of a per-species array is at p[i * stride]; velocity (d, f) at
+// p[(d * n + f) * stride]. od/hp: pair tables for this n. v_out may alias v_in.
+// heat: see dx_wpc_apply_tail.
+__device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const double *rgp, const double *rdp,
+                                                    const double *tsp, const double *vip, double *vop,
+                                                    long long stride, double dt, const DxConsts &K, double *wsm,
+                                                    const unsigned short *od, const unsigned short *hp,
+                                                    uint32_t *status, double *heat = nullptr) {
+    const int n = N + 1, ns = dx_stride(n);
+    const int n_hp = n * (n + 1) / 2 - 1;
+    double *E0 = wsm;
+    double *E1 = E0 + n * ns;
+    DxVecs V;
+    DxFwdBufs B;
+    dx_wpc_fwd_layout(E1 + n * ns, n, V, B);
+    (void)od;
+
+    DxCellIn c;
+    dx_wpc_load_cell(lane, N, rgp, rdp, tsp, vip, stride, c);
+    DxLane L;
+    if (!dx_wpc_setup(lane, N, c.rg, c.rd, c.ts, dt, K, V, L)) {
+        dx_wpc_fail_cell(lane, n, vop, stride, status, heat);
+        return;
+    }
+    const int m = K.mk[L.k];
+
+    // Taylor polynomial T_m(X) by Horner's rule in X
+    double *F = E0, *G = E1;
+    dx_wpc_taylor_init(lane, n, ns, m, K, V, F);
+    for (int j = m - 2; j >= 0; j--) {
+        dx_wpc_horner_step(lane, n, ns, n_hp, hp, V, K.b[j], F, G);
+        __syncwarp();
+        double *tmp = F; F = G; G = tmp;
+    }
+
+    // row-sum restoration, then s - q squarings (Eq. ExpEq1 with n = 2^s), each
+    // restored; the remaining q squarings become 2^q applications
+    const int q = L.s < DX_APPLY_Q ? L.s : DX_APPLY_Q;
+    F = dx_wpc_square_chain(lane, n, ns, L.s - q, E0, E1, F == E1 ? 1 : 0, V) ? E1 : E0;
+    dx_wpc_apply_tail(lane, n, ns, V, B, F, q, c, L.sg, vop, stride, heat);
 }

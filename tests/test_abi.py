@@ -45,7 +45,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_version_and_strerror(lib):
     assert lib.drag_expm_version() >= 1
-    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8, -9):
         assert len(lib.drag_expm_strerror(code)) > 0
     assert b"unknown" in lib.drag_expm_strerror(-999)
 
@@ -80,6 +80,18 @@ def test_theta_targets_match_oracle(lib):
         assert dx.theta(k, 53) < dx.theta(k, 24) < dx.theta(k, 11)
 
 
+def test_pade_theta_matches_oracle(lib):
+    """theta_m of the Pade variant: the library's route (closed-form remainder
+    e^x D - N times e^-x/D) against the oracle's (series division), both in
+    double-double."""
+    for ubits in (53, 24):
+        for m in oracle.PADE_DEGREES:
+            assert dx.pade_theta(m, ubits) == oracle.pade_theta(m, 2.0 ** -ubits)
+    out = ctypes.c_double()
+    assert lib.drag_expm_pade_theta(4, 53, ctypes.byref(out)) == -1
+    assert lib.drag_expm_pade_theta(13, 11, ctypes.byref(out)) == -8
+
+
 def test_host_argument_errors(lib):
     """Bad sizes, NULL and misaligned pointers are rejected before any CUDA call."""
     good = ctypes.c_void_p(4096)
@@ -101,6 +113,20 @@ def test_host_argument_errors(lib):
     assert at(10, 4, good, good, good, 1.0, good, good, 0, s) == -8
     assert at(-1, 4, good, good, good, 1.0, good, good, 24, s) == -1
     assert at(10, 4, null, good, good, 1.0, good, good, 24, s) == -2
+    ao = lib.drag_expm_apply_opts
+    opts = dx.DragOptions(53, 1, 1, 0)                 # Pade with the bound test
+    assert ao(ctypes.c_int64(10), 4, good, good, good, ctypes.c_double(1.0), good, good, ctypes.byref(opts), null,
+              null, s) == -9
+    opts = dx.DragOptions(11, 1, 0, 0)                 # Pade at 2^-11
+    assert ao(ctypes.c_int64(10), 4, good, good, good, ctypes.c_double(1.0), good, good, ctypes.byref(opts), null,
+              null, s) == -8
+    opts = dx.DragOptions(53, 0, 1, 7)                 # reserved != 0
+    assert ao(ctypes.c_int64(10), 4, good, good, good, ctypes.c_double(1.0), good, good, ctypes.byref(opts), null,
+              null, s) == -9
+    assert ao(ctypes.c_int64(10), 4, good, good, good, ctypes.c_double(1.0), good, good, None, null, null, s) == -2
+    opts = dx.DragOptions(53, 0, 1, 0)
+    assert ao(ctypes.c_int64(10), 4, good, bad_align, good, ctypes.c_double(1.0), good, good, ctypes.byref(opts),
+              null, null, s) == -3
     st = lib.drag_expm_select_target
     assert st(10, 4, good, good, good, 1.0, 12, good, good, s) == -8
     assert apply(10, 4, good, good, good, 1.0, good, bad_align, s) == -3

@@ -1,0 +1,139 @@
+"""GPU parity of the forward variants behind drag_expm_apply_opts: the
+paper's second modification (bound test) on the Taylor path and the Pade
+approximant of Eq. PadeEqu, against the oracle's drag_apply_opts.
+
+* v_out: |v_gpu - v_oracle| <= 1e-13 max_f |v_in[d, f]| (the forward bar).
+* Pade (m, s): bit-exact (same norm summation order, theta tables that agree
+  bit for bit, integer compares).
+* Bound test: the degree kept agrees with the oracle except where the test's
+  value sits within 1e-9 of u (the two sides form the block norms in
+  different orders: the symmetric form versus the velocity form).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_25347_gb300 import workloads as W
+from tests.test_forward_gpu import assert_parity, dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dx():
+    import torch  # noqa: F401
+    from paper_2509_25347_gb300 import build
+    build.build()
+    import paper_2509_25347_gb300 as m
+    m.load_library()
+    m.get_status()
+    return m
+
+
+CASES = [("dustybox_n1_32k", 1201), ("mrn_n4_128cube", 801), ("mrn_n8_128cube_adjoint", 401),
+         ("mrn_n16_128cube", 201)]
+
+
+def run(dx, cells, **kw):
+    rg, rd, ts, v = dev(cells)
+    out, m, s = dx.apply_opts(rg, rd, ts, cells.dt, v, return_ms=True, **kw)
+    return out.cpu().numpy(), m.cpu().numpy(), s.cpu().numpy()
+
+
+def theta_table_matches(dx):
+    for ub in (53, 24):
+        for m in oracle.PADE_DEGREES:
+            assert dx.pade_theta(m, ub) == oracle.pade_theta(m, 2.0 ** -ub)
+
+
+@pytest.mark.parametrize("ubits", (53, 24))
+@pytest.mark.parametrize("name,C", CASES)
+def test_pade_parity(dx, ubits, name, C):
+    theta_table_matches(dx)
+    cells = W.workload(name, ncells=C)
+    out, m, s = run(dx, cells, ubits=ubits, method="pade")
+    ref, _, mo, so, _, st = oracle.drag_apply_opts(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v,
+                                                   u=2.0 ** -ubits, method="pade")
+    assert st == 0
+    assert np.array_equal(m, mo) and np.array_equal(s, so)
+    assert_parity(out, ref, cells.v)
+    assert dx.get_status() == 0
+
+
+@pytest.mark.parametrize("ubits", (53, 24, 11))
+@pytest.mark.parametrize("name,C", CASES)
+def test_bound_test_parity(dx, ubits, name, C):
+    cells = W.workload(name, ncells=C)
+    out, m, s = run(dx, cells, ubits=ubits, bound_test=True)
+    ref, ko, mo, so, ratio, st = oracle.drag_apply_opts(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v,
+                                                        u=2.0 ** -ubits, bound_test=True)
+    assert st == 0
+    assert np.array_equal(s, so)
+    diff = m != mo
+    assert np.all(np.abs(ratio[diff] - 1.0) < 1e-9), (np.flatnonzero(diff), ratio[diff])
+    assert_parity(out, ref, cells.v)
+    assert dx.get_status() == 0
+
+
+@pytest.mark.parametrize("N", [1, 2, 4, 6, 9, 12, 16, 20, 31])
+def test_variants_every_size(dx, N):
+    cells = W.mrn(53 + N, N, seed=600 + N, stiff_lo=-4.0, stiff_hi=8.0)
+    for kw, okw in (({"method": "pade"}, {"method": "pade"}), ({"bound_test": True}, {"bound_test": True})):
+        out, m, s = run(dx, cells, **kw)
+        ref, _, mo, so, ratio, _ = oracle.drag_apply_opts(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v,
+                                                          **okw)
+        assert np.array_equal(s, so)
+        assert np.all((m == mo) | (np.abs(ratio - 1.0) < 1e-9))
+        assert_parity(out, ref, cells.v)
+
+
+def test_plain_taylor_through_opts(dx):
+    """method taylor without the bound test is the default method; asking for
+    the degrees runs the variant kernel, which must give the same numbers."""
+    cells = W.workload("mrn_n16_128cube", ncells=150)
+    rg, rd, ts, v = dev(cells)
+    a = dx.apply(rg, rd, ts, cells.dt, v).cpu().numpy()
+    b = dx.apply_opts(rg, rd, ts, cells.dt, v).cpu().numpy()
+    out, m, s = run(dx, cells)
+    assert np.array_equal(a, b)
+    _, ko, so, _ = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, return_ks=True)
+    assert np.array_equal(s, so)
+    assert np.array_equal(m, np.array([oracle.table_b1(int(k))[0] for k in ko]))
+    assert_parity(out, a, cells.v, tol=1e-13)
+
+
+def test_variants_invalid_and_edge(dx):
+    cells = W.workload("mrn_n4_128cube", ncells=64)
+    rg, rd, ts, v = dev(cells)
+    with pytest.raises(dx.DragExpmError):
+        dx.apply_opts(rg, rd, ts, cells.dt, v, method="pade", bound_test=True)
+    with pytest.raises(dx.DragExpmError):
+        dx.apply_opts(rg, rd, ts, cells.dt, v, method="pade", ubits=11)
+    with pytest.raises(dx.DragExpmError):
+        dx.apply_opts(rg, rd, ts, cells.dt, v, ubits=7)
+    # dt = 0: identity, in place
+    out = dx.apply_opts(rg, rd, ts, 0.0, v, method="pade").cpu().numpy()
+    assert np.array_equal(out, cells.v)
+    ref = oracle.drag_apply_opts(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, method="pade")[0]
+    dx.apply_opts(rg, rd, ts, cells.dt, v, v, method="pade")
+    assert_parity(v.cpu().numpy(), ref, cells.v)
+    # invalid cells: NaN and the status bit, degree 0 and s = -1
+    bad = W.workload("mrn_n4_128cube", ncells=40)
+    bad.t_s[1, 7] = -1.0
+    out, m, s = run(dx, bad, bound_test=True)
+    assert np.all(np.isnan(out[:, :, 7])) and m[7] == 0 and s[7] == -1
+    assert dx.get_status() & dx.STATUS_BAD_CELL
+
+
+@pytest.mark.parametrize("kw", [{"method": "pade"}, {"bound_test": True}])
+def test_variants_full_size_sampled(dx, kw):
+    import torch
+    cells = W.workload("mrn_n16_128cube")
+    rg, rd, ts, v = dev(cells)
+    out = dx.apply_opts(rg, rd, ts, cells.dt, v, **kw)
+    idx = np.random.default_rng(17).choice(cells.ncells, 300, replace=False)
+    sub = cells.subset(idx)
+    ref = oracle.drag_apply_opts(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v, **kw)[0]
+    got = out[:, :, torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert_parity(got, ref, sub.v)
+    assert dx.get_status() == 0
