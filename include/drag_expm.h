@@ -63,7 +63,7 @@ extern "C" {
 #define DRAG_EBLOCKS (-6)       /* bad block count in the batched entry point */
 #define DRAG_ENOALLOC_LIMIT (-7) /* batch larger than drag_expm_apply_batched_noalloc's fixed scratch */
 #define DRAG_EINVAL_TARGET (-8)  /* unit round-off target other than 53, 24 or 11 bits (Pade: 53, 24) */
-#define DRAG_EINVAL_OPTION (-9)  /* bad drag_expm_options_t (method, bound_test with Pade, reserved != 0) */
+#define DRAG_EINVAL_OPTION (-9)  /* bad drag_expm_options_t combination (see drag_expm_apply_opts) */
 
 /* Sticky device status bits (drag_expm_get_status). */
 #define DRAG_STATUS_BAD_CELL 0x1u      /* some cell had invalid data; its outputs are NaN */
@@ -106,12 +106,17 @@ int drag_expm_apply_target(int64_t ncells, int32_t nspecies, const double *rho_g
 #define DRAG_METHOD_TAYLOR 0   /* the paper's Taylor scaling and squaring (Algorithm 2) */
 #define DRAG_METHOD_PADE 1     /* diagonal Pade approximant (Eq. PadeEqu) with scaling and squaring */
 
+
 typedef struct {
     int32_t ubits;       /* accuracy target u = 2^-ubits: 53, 24 or 11 (Pade: 53 or 24) */
     int32_t method;      /* DRAG_METHOD_TAYLOR or DRAG_METHOD_PADE */
     int32_t bound_test;  /* Taylor only: 1 = the paper's second modification (bound test) */
-    int32_t reserved;    /* must be 0 */
+    int32_t arith;       /* DRAG_ARITH_FP64 (0) or DRAG_ARITH_FP32 (1, the mixed-precision path) */
 } drag_expm_options_t;
+
+/* Arithmetic of the matrix work in drag_expm_apply_opts. */
+#define DRAG_ARITH_FP64 0
+#define DRAG_ARITH_FP32 1   /* FP64 in/out, set-up and selection; FP32 Taylor, squarings, applications */
 
 /*
  * drag_expm_apply_opts — forward update with the paper's variants of the
@@ -128,6 +133,12 @@ typedef struct {
  *     construction of Eqs. B5-B8 applied to R_mm (drag_expm_pade_theta): the
  *     smallest m with |A|_1 <= theta_m and s = 0, else m = 13 and the smallest
  *     s with 2^-s |A|_1 <= theta_13.
+ *   arith = DRAG_ARITH_FP32 (the mixed-precision path of the lower targets):
+ *     Taylor without the bound test at ubits = 24 only (Eq. B8 pairs
+ *     u = 2^-24 with single precision), and no m_out / s_out. Inputs, outputs, the set-up and Algorithm 2 stay FP64; the Taylor
+ *     step, the squarings and the applications run in FP32 (dust-to-gas ratios
+ *     below 1e-30 are raised to it there, as 1e-200 in FP64). The result then
+ *     carries FP32 rounding, ~1e-6 of the velocity scale.
  *   All variants restore the row sums after the approximant and every squaring.
  *   m_out : DEVICE int8[ncells] or NULL, receives the polynomial degree
  *           evaluated per cell (Taylor: m_{k*} or fewer terms after the bound

@@ -124,7 +124,7 @@ METHOD_PADE = 1
 class DragOptions(ctypes.Structure):
     """drag_expm_options_t of include/drag_expm.h."""
     _fields_ = [("ubits", ctypes.c_int32), ("method", ctypes.c_int32), ("bound_test", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("arith", ctypes.c_int32)]
 
 
 def apply(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, stream=None, ubits: int = 53):
@@ -150,10 +150,11 @@ def apply(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, stream=None, ubits: in
 
 
 def apply_opts(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, ubits: int = 53, method: str = "taylor",
-               bound_test: bool = False, return_ms: bool = False, stream=None):
+               bound_test: bool = False, arith: str = "fp64", return_ms: bool = False, stream=None):
     """Forward update with the paper's variants (drag_expm_apply_opts): method
-    'taylor' (bound_test adds the second modification) or 'pade'. With
-    return_ms, also returns the degree evaluated (int8) and s* (int16) per cell."""
+    'taylor' (bound_test adds the second modification) or 'pade'; arith 'fp32'
+    is the mixed-precision path (Taylor at ubits 24 or 11). With return_ms,
+    also returns the degree evaluated (int8) and s* (int16) per cell."""
     import torch
     C, N = _shapes(rho_g, rho_d)
     if v_out is None:
@@ -161,7 +162,8 @@ def apply_opts(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, ubits: int = 53, 
     args = [_f64_cuda("rho_g", rho_g, (C,)), _f64_cuda("rho_d", rho_d, (N, C)), _f64_cuda("t_s", t_s, (N, C))]
     vi = _f64_cuda("v_in", v_in, (3, N + 1, C))
     vo = _f64_cuda("v_out", v_out, (3, N + 1, C))
-    opts = DragOptions(int(ubits), {"taylor": METHOD_TAYLOR, "pade": METHOD_PADE}[method], int(bool(bound_test)), 0)
+    opts = DragOptions(int(ubits), {"taylor": METHOD_TAYLOR, "pade": METHOD_PADE}[method], int(bool(bound_test)),
+                       {"fp64": 0, "fp32": 1}[arith])
     m = s = None
     mp = sp = ctypes.c_void_p(0)
     if return_ms:

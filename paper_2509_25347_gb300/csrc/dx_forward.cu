@@ -69,6 +69,36 @@ dx_forward_wpc(FwdArgs a, DxConsts K) {
     }
 }
 
+// Mixed-precision forward: FP64 inputs, outputs, set-up and Algorithm 2 (on
+// the theta table of u = 2^-24, Eq. B8's single-precision target), FP32
+// Taylor, squarings and applications. FP32 issues 64x faster than FP64 on this
+// part; the result carries FP32 rounding.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
+dx_forward_wpc_f32(FwdArgs a, DxConsts K) {
+    extern __shared__ float smemf[];
+    const int n = a.N + 1;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int wd = dx_wpc_fwd_warp_doubles(n);
+    unsigned short *od = reinterpret_cast<unsigned short *>(smemf + kWarpsPerBlock * wd);
+    unsigned short *hp = od + kPairSlots;
+    dx_build_pairs(n, od, hp);
+    __syncthreads();
+    float *wsm = smemf + wib * wd;
+    __shared__ int next;
+    if (threadIdx.x == 0) next = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kCellsPerBlock;
+    for (int it = 0; it < kCellsPerBlock; it++) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(&next, 1);
+        k = __shfl_sync(DX_FULL, k, 0);
+        const long long c = base + k;
+        if (k >= kCellsPerBlock || c >= a.C) break;
+        dx_wpc_forward_cell(lane, a.N, a.rho_g + c, a.rho_d + c, a.t_s + c, a.v_in + c, a.v_out + c, a.C, a.dt, K, wsm,
+                            od, hp, a.status);
+    }
+}
+
 // (k*, s*) per cell, one thread per cell (diagnostics and FLOP accounting).
 __global__ void dx_select_kernel(long long C, int N, const double *rho_g, const double *rho_d, const double *t_s,
                                  double dt, int8_t *k_out, int16_t *s_out, uint32_t *status, DxConsts K) {
@@ -122,6 +152,11 @@ size_t dx_forward_smem_bytes(int n) {
     return sizeof(double) * (size_t)kWarpsPerBlock * dx_wpc_fwd_warp_doubles(n) + 2 * kPairSlots * sizeof(unsigned short);
 }
 
+size_t dx_forward_f32_smem_bytes(int n) {
+    return sizeof(float) * (size_t)kWarpsPerBlock * dx_wpc_fwd_warp_doubles(n) +
+           2 * kPairSlots * sizeof(unsigned short);
+}
+
 static int apply_impl(const DxConsts &K, int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
                       const double *t_s, double dt, const double *v_in, double *v_out, double *heat,
                       cudaStream_t stream) {
@@ -152,6 +187,25 @@ extern "C" int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *r
                                const double *t_s, double dt, const double *v_in, double *v_out,
                                cudaStream_t stream) {
     return apply_impl(dx_consts(), ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, nullptr, stream);
+}
+
+int dx_launch_forward_f32(const DxConsts &K, long long ncells, int nspecies, const double *rho_g, const double *rho_d,
+                          const double *t_s, double dt, const double *v_in, double *v_out, cudaStream_t stream) {
+    int rc = check_common(ncells, nspecies, rho_g, rho_d, t_s, dt);
+    if (rc != DRAG_OK || ncells == 0) return rc;
+    if (!v_in || !v_out) return DRAG_ENULL;
+    if (!aligned8(v_in) || !aligned8(v_out)) return DRAG_EALIGN;
+    uint32_t *st = dx_status_ptr();
+    if (!st) return DRAG_ECUDA;
+    if (!dx_once_per_device(4, [] {
+            return cudaFuncSetAttribute(dx_forward_wpc_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)dx_forward_f32_smem_bytes(DX_NMAXF)) == cudaSuccess;
+        }))
+        return DRAG_ECUDA;
+    FwdArgs a{ncells, nspecies, rho_g, rho_d, t_s, v_in, v_out, dt, st, nullptr};
+    const long long grid = (ncells + kCellsPerBlock - 1) / kCellsPerBlock;
+    dx_forward_wpc_f32<<<(unsigned)grid, kWarpsPerBlock * 32, dx_forward_f32_smem_bytes(nspecies + 1), stream>>>(a, K);
+    return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }
 
 extern "C" int drag_expm_apply_target(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,

@@ -330,7 +330,7 @@ const char *drag_expm_strerror(int code) {
         case DRAG_EWORKSPACE: return "workspace missing or too small";
         case DRAG_EBLOCKS: return "invalid block count or block descriptor array";
         case DRAG_EINVAL_TARGET: return "unsupported unit round-off target (use 53, 24 or 11; Pade: 53 or 24)";
-        case DRAG_EINVAL_OPTION: return "invalid option combination (method, bound_test, reserved)";
+        case DRAG_EINVAL_OPTION: return "invalid option combination (method, bound_test, arith)";
         case DRAG_ENOALLOC_LIMIT:
             return "batch exceeds the fixed scratch of drag_expm_apply_batched_noalloc "
                    "(DRAG_NOALLOC_MAX_BLOCKS / DRAG_NOALLOC_MAX_CELLS); use drag_expm_apply_batched with a workspace";

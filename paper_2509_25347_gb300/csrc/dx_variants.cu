@@ -277,11 +277,18 @@ extern "C" int drag_expm_apply_opts(int64_t ncells, int32_t nspecies, const doub
                                     const drag_expm_options_t *opts, int8_t *m_out, int16_t *s_out,
                                     cudaStream_t stream) {
     if (!opts) return DRAG_ENULL;
-    if (opts->reserved != 0 || opts->method < DRAG_METHOD_TAYLOR || opts->method > DRAG_METHOD_PADE ||
-        (opts->method == DRAG_METHOD_PADE && opts->bound_test))
+    if (opts->arith < DRAG_ARITH_FP64 || opts->arith > DRAG_ARITH_FP32 || opts->method < DRAG_METHOD_TAYLOR ||
+        opts->method > DRAG_METHOD_PADE || (opts->method == DRAG_METHOD_PADE && opts->bound_test))
         return DRAG_EINVAL_OPTION;
     const DxConsts *K = dx_consts_for(opts->ubits);
     if (!K) return DRAG_EINVAL_TARGET;
+    if (opts->arith == DRAG_ARITH_FP32) {
+        // mixed precision: plain Taylor at the single-precision target (Eq. B8 pairs u = 2^-24 with single
+        // precision; at 2^-11, theta reaches ~8 and the Taylor sum's cancellation costs up to e^theta FP32 ulps)
+        if (opts->method != DRAG_METHOD_TAYLOR || opts->bound_test || opts->ubits != 24 || m_out || s_out)
+            return DRAG_EINVAL_OPTION;
+        return dx_launch_forward_f32(*K, ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, stream);
+    }
     const DxPade *P = opts->method == DRAG_METHOD_PADE ? dx_pade_for(opts->ubits) : dx_pade_for(53);
     if (!P) return DRAG_EINVAL_TARGET;
     if (opts->method == DRAG_METHOD_TAYLOR && !opts->bound_test && !m_out && !s_out)

@@ -38,13 +38,17 @@ __device__ __forceinline__ void dx_build_pairs(int n, unsigned short *od, unsign
     }
 }
 
-// Per-cell vectors of the symmetric form, kept in shared memory.
-struct DxVecs {
-    double *sig;   // sigma_f
-    double *tau;   // 1 / sigma_f
-    double *xs;    // xs[0] = X_00, xs[f] = X_0f (f >= 1)
-    double *ds;    // ds[f] = X_ff (f >= 1)
+// Per-cell vectors of the symmetric form, kept in shared memory. T is the
+// arithmetic type of the matrix work: double, or float on the mixed-precision
+// path (set-up and selection stay FP64 there).
+template <typename T>
+struct DxVecsT {
+    T *sig;   // sigma_f
+    T *tau;   // 1 / sigma_f
+    T *xs;    // xs[0] = X_00, xs[f] = X_0f (f >= 1)
+    T *ds;    // ds[f] = X_ff (f >= 1)
 };
+using DxVecs = DxVecsT<double>;
 
 // Lane-resident cell quantities after set-up (lane f = fluid f; species i on lane i).
 struct DxLane {
@@ -58,8 +62,9 @@ struct DxLane {
 // (or, with a Pade table, the Pade degree and scaling), and the scaled
 // symmetric arrowhead X = 2^-s* S. Returns false (warp uniform) when the cell's
 // data are invalid.
+template <typename T>
 __device__ __forceinline__ bool dx_wpc_setup(int lane, int N, double rg, double rd, double ts, double dt,
-                                             const DxConsts &K, const DxVecs &V, DxLane &L,
+                                             const DxConsts &K, const DxVecsT<T> &V, DxLane &L,
                                              const DxPade *pade = nullptr) {
     const int n = N + 1;
     const bool okl = (lane == 0 || lane > N) || (dx_nonneg_finite(rd) && dx_pos_or_inf(ts));
@@ -84,15 +89,17 @@ __device__ __forceinline__ bool dx_wpc_setup(int lane, int N, double rg, double 
     const double p2 = dx_pow2(-L.s);
     double sg = 1.0, tu = 1.0;
     if (sp) {
-        const double e = dx_bits(eps) < dx_bits(DX_EPS_FLOOR) ? DX_EPS_FLOOR : eps;
+        // FP32 work keeps sigma and 1/sigma inside its range: 1e-30 instead of 1e-200
+        const double floor_eps = sizeof(T) == sizeof(double) ? DX_EPS_FLOOR : 1e-30;
+        const double e = dx_bits(eps) < dx_bits(floor_eps) ? floor_eps : eps;
         sg = __dsqrt_rn(e);
         tu = __ddiv_rn(1.0, sg);
     }
     if (lane < n) {
-        V.sig[lane] = sg;
-        V.tau[lane] = tu;
-        V.xs[lane] = lane == 0 ? -s1 * p2 : __dmul_rn(__dmul_rn(sg, alpha), dt * p2);
-        V.ds[lane] = -(ai0 * p2);
+        V.sig[lane] = (T)sg;
+        V.tau[lane] = (T)tu;
+        V.xs[lane] = (T)(lane == 0 ? -s1 * p2 : __dmul_rn(__dmul_rn(sg, alpha), dt * p2));
+        V.ds[lane] = (T)(-(ai0 * p2));
     }
     L.eps = eps;
     L.alpha = alpha;
@@ -103,17 +110,19 @@ __device__ __forceinline__ bool dx_wpc_setup(int lane, int N, double rg, double 
 }
 
 // F = b_m X + b_{m-1} I (arrowhead), written into a zeroed n x n buffer.
+template <typename T>
 __device__ __forceinline__ void dx_wpc_taylor_init(int lane, int n, int ns, int m, const DxConsts &K,
-                                                   const DxVecs &V, double *F) {
-    for (int t = lane; t < n * ns; t += 32) F[t] = 0.0;
+                                                   const DxVecsT<T> &V, T *F) {
+    for (int t = lane; t < n * ns; t += 32) F[t] = T(0);
     __syncwarp();
+    const T bm = (T)K.b[m], bm1 = (T)K.b[m - 1];
     if (lane < n) {
-        const double x = V.xs[lane];
+        const T x = V.xs[lane];
         if (lane == 0) {
-            F[0] = fma(K.b[m], x, K.b[m - 1]);
+            F[0] = fma(bm, x, bm1);
         } else {
-            F[lane] = F[lane * ns] = K.b[m] * x;
-            F[lane * ns + lane] = fma(K.b[m], V.ds[lane], K.b[m - 1]);
+            F[lane] = F[lane * ns] = bm * x;
+            F[lane * ns + lane] = fma(bm, V.ds[lane], bm1);
         }
     }
     __syncwarp();
@@ -143,18 +152,19 @@ __host__ __device__ __forceinline__ int dx_horner_g00_group(int n) {
 // One Horner step G = F X + bj I (F, G symmetric; X the arrowhead):
 //   G_ij = F_i0 X_0j + F_ij X_jj (+ bj if i == j) for i <= j, (i,j) != (0,0),
 //   G_00 = sum_k F_0k X_k0 + bj.
+template <typename T>
 __device__ __forceinline__ void dx_wpc_horner_step(int lane, int n, int ns, int n_hp, const unsigned short *hp,
-                                                   const DxVecs &V, double bj, const double *F, double *G) {
+                                                   const DxVecsT<T> &V, T bj, const T *F, T *G) {
     const int g = dx_horner_g00_group(n);
     if (g == 0) {
         for (int t = lane; t < n_hp; t += 32) {
             const int p = hp[t], i = p >> 8, jj = p & 255;
-            double acc = fma(F[i * ns], V.xs[jj], i == jj ? bj : 0.0);
+            T acc = fma(F[i * ns], V.xs[jj], i == jj ? bj : T(0));
             acc = fma(F[i * ns + jj], V.ds[jj], acc);
             G[i * ns + jj] = acc;
             G[jj * ns + i] = acc;
         }
-        double part = lane < n ? F[lane] * V.xs[lane] : 0.0;
+        T part = lane < n ? F[lane] * V.xs[lane] : T(0);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(DX_FULL, part, o);
         if (lane == 0) G[0] = part + bj;
@@ -164,7 +174,7 @@ __device__ __forceinline__ void dx_wpc_horner_step(int lane, int n, int ns, int 
     const int last = (n_hp - 1) >> 5;
     for (int r = 0; r < last; r++) {
         const int p = hp[r * 32 + lane], i = p >> 8, jj = p & 255;
-        double acc = fma(F[i * ns], V.xs[jj], i == jj ? bj : 0.0);
+        T acc = fma(F[i * ns], V.xs[jj], i == jj ? bj : T(0));
         acc = fma(F[i * ns + jj], V.ds[jj], acc);
         G[i * ns + jj] = acc;
         G[jj * ns + i] = acc;
@@ -178,7 +188,7 @@ __device__ __forceinline__ void dx_wpc_horner_step(int lane, int n, int ns, int 
     const int phi = lane - (32 - g);
     const bool grp = !task && phi >= 0;
     const int cmax = (n + g - 1) / g;
-    double a0 = 0.0, b0 = 0.0, a1 = 0.0, b1 = 0.0, c = 0.0;
+    T a0 = T(0), b0 = T(0), a1 = T(0), b1 = T(0), c = T(0);
     int dst = 0, dstT = 0;
     if (task) {
         const int p = hp[t], i = p >> 8, jj = p & 255;
@@ -186,7 +196,7 @@ __device__ __forceinline__ void dx_wpc_horner_step(int lane, int n, int ns, int 
         b0 = V.xs[jj];
         a1 = F[i * ns + jj];
         b1 = V.ds[jj];
-        c = i == jj ? bj : 0.0;
+        c = i == jj ? bj : T(0);
         dst = i * ns + jj;
         dstT = jj * ns + i;
     } else if (grp) {
@@ -198,14 +208,14 @@ __device__ __forceinline__ void dx_wpc_horner_step(int lane, int n, int ns, int 
             a1 = F[phi + g];
             b1 = V.xs[phi + g];
         }
-        c = phi == 0 ? bj : 0.0;
+        c = phi == 0 ? bj : T(0);
     }
-    double acc = fma(a0, b0, c);
+    T acc = fma(a0, b0, c);
     acc = fma(a1, b1, acc);
     for (int u = 2; u < cmax; u++) {
         const int k = phi + u * g;
         const bool on = grp && k < n;
-        acc = fma(on ? F[on ? k : 0] : 0.0, on ? V.xs[on ? k : 0] : 0.0, acc);
+        acc = fma(on ? F[on ? k : 0] : T(0), on ? V.xs[on ? k : 0] : T(0), acc);
     }
     if (task) {
         G[dst] = acc;
@@ -216,24 +226,26 @@ __device__ __forceinline__ void dx_wpc_horner_step(int lane, int n, int ns, int 
 }
 
 // Row-sum restoration in symmetric form: E_ii = 1 - tau_i sum_{k != i} E_ik sigma_k.
-__device__ __forceinline__ void dx_wpc_restore(int lane, int n, int ns, const DxVecs &V, double *E) {
+template <typename T>
+__device__ __forceinline__ void dx_wpc_restore(int lane, int n, int ns, const DxVecsT<T> &V, T *E) {
     if (lane < n) {
-        double acc = 0.0;
+        T acc = T(0);
         for (int q = 0; q < n - 1; q++) {
             const int k = q + (q >= lane);
             acc = fma(E[lane * ns + k], V.sig[k], acc);
         }
-        E[lane * ns + lane] = fma(-V.tau[lane], acc, 1.0);
+        E[lane * ns + lane] = fma(-V.tau[lane], acc, T(1));
     }
 }
 
 // Strict upper triangle of E^2 (symmetric), mirrored: G_ij = G_ji = sum_k E_ik E_jk.
+template <typename T>
 __device__ __forceinline__ void dx_wpc_square_offdiag(int lane, int n, int ns, int n_od, const unsigned short *od,
-                                                      const double *E, double *G) {
+                                                      const T *E, T *G) {
     for (int t = lane; t < n_od; t += 32) {
         const int p = od[t], i = p >> 8, jj = p & 255;
-        const double *ri = E + i * ns, *rj = E + jj * ns;
-        double acc = 0.0;
+        const T *ri = E + i * ns, *rj = E + jj * ns;
+        T acc = T(0);
         for (int k = 0; k < n; k++) acc = fma(ri[k], rj[k], acc);
         G[i * ns + jj] = acc;
         G[jj * ns + i] = acc;
@@ -249,8 +261,9 @@ __device__ __forceinline__ void dx_wpc_square_offdiag(int lane, int n, int ns, i
 // those need are complete. Chunks of at most DX_SCHED_H squarings each start
 // with a restoration (a no-op on an already restored matrix). The matrix
 // starts in B[p0]; returns the index of the buffer holding the result.
-__device__ __forceinline__ int dx_wpc_square_chain(int lane, int n, int ns, int s, double *B0, double *B1, int p0,
-                                                   const DxVecs &V) {
+template <typename T>
+__device__ __forceinline__ int dx_wpc_square_chain(int lane, int n, int ns, int s, T *B0, T *B1, int p0,
+                                                   const DxVecsT<T> &V) {
     const unsigned short *tab = dx_sched_task + (size_t)dx_sched_off[n] * 32;
     const unsigned short *endr = dx_sched_end + n * (DX_SCHED_H + 1);
     int remaining = s, parity = p0;
@@ -263,19 +276,19 @@ __device__ __forceinline__ int dx_wpc_square_chain(int lane, int n, int ns, int 
             if (code != 0xFFFFu && t <= h) {
                 const int i = code & 31, j = (code >> 5) & 31;
                 const bool isR = i == j;
-                double *dst = (parity ^ (t & 1)) ? B1 : B0;
-                const double *src = isR ? dst : ((parity ^ ((t - 1) & 1)) ? B1 : B0);
-                const double *pa = src + i * ns;
-                const double *pb = isR ? V.sig : src + j * ns;
-                double acc = 0.0;
+                T *dst = (parity ^ (t & 1)) ? B1 : B0;
+                const T *src = isR ? dst : ((parity ^ ((t - 1) & 1)) ? B1 : B0);
+                const T *pa = src + i * ns;
+                const T *pb = isR ? V.sig : src + j * ns;
+                T acc = T(0);
                 for (int q = 0; q < n - 1; q++) {
                     const int k = (isR && q >= i) ? q + 1 : q;
                     acc = fma(pa[k], pb[k], acc);
                 }
-                const double x = isR ? -V.tau[i] : pa[n - 1];
-                const double y = isR ? acc : pb[n - 1];
-                const double z = isR ? 1.0 : acc;
-                const double res = fma(x, y, z);
+                const T x = isR ? -V.tau[i] : pa[n - 1];
+                const T y = isR ? acc : pb[n - 1];
+                const T z = isR ? T(1) : acc;
+                const T res = fma(x, y, z);
                 if (isR) {
                     dst[i * ns + i] = res;
                 } else {
@@ -322,13 +335,16 @@ __host__ __device__ __forceinline__ int dx_wpc_fwd_warp_doubles(int n) { return 
 // Per-cell vectors of the forward routines, laid out from vbase: sigma, tau,
 // X_0f, X_ff (4 n), the input velocities (3 n) and two buffers of
 // (v, sigma o v) for the repeated applications (12 n): 19 n doubles.
-struct DxFwdBufs {
-    double *v0;          // input velocities v_f, three components
-    double *wv0, *wv1;   // current v, two buffers
-    double *wy0, *wy1;   // sigma o current v
+template <typename T>
+struct DxFwdBufsT {
+    T *v0;          // input velocities v_f, three components
+    T *wv0, *wv1;   // current v, two buffers
+    T *wy0, *wy1;   // sigma o current v
 };
+using DxFwdBufs = DxFwdBufsT<double>;
 
-__device__ __forceinline__ void dx_wpc_fwd_layout(double *vbase, int n, DxVecs &V, DxFwdBufs &B) {
+template <typename T>
+__device__ __forceinline__ void dx_wpc_fwd_layout(T *vbase, int n, DxVecsT<T> &V, DxFwdBufsT<T> &B) {
     V.sig = vbase;
     V.tau = V.sig + n;
     V.xs = V.tau + n;
@@ -379,11 +395,12 @@ __device__ __forceinline__ void dx_wpc_fail_cell(int lane, int n, double *vop, l
 // (may be null, warp uniform): the kinetic energy the step dissipates,
 // sum_f 1/2 rho_f (|v_in,f - V|^2 - |v_out,f - V|^2) with V the centre-of-mass
 // velocity (frictional heating of Eq. GenEq_3, weight w = 1).
-__device__ __forceinline__ void dx_wpc_apply_tail(int lane, int n, int ns, const DxVecs &V, const DxFwdBufs &B,
-                                                  const double *F, int q, const DxCellIn &c, double sg, double *vop,
-                                                  long long stride, double *heat) {
-    double *const v0 = B.v0;
-    double *const wv0 = B.wv0, *const wv1 = B.wv1, *const wy0 = B.wy0, *const wy1 = B.wy1;
+template <typename T>
+__device__ __forceinline__ void dx_wpc_apply_tail(int lane, int n, int ns, const DxVecsT<T> &V,
+                                                  const DxFwdBufsT<T> &B, const T *F, int q, const DxCellIn &c,
+                                                  double sg, double *vop, long long stride, double *heat) {
+    T *const v0 = B.v0;
+    T *const wv0 = B.wv0, *const wv1 = B.wv1, *const wy0 = B.wy0, *const wy1 = B.wy1;
     const double rg = c.rg, rd = c.rd;
     const double *vin = c.vin;
     // v <- P v, 2^q times, P_ii = E_ii, P_ij = E_ij sigma_j / sigma_i (P = D_sigma^-1 E D_sigma):
@@ -391,9 +408,9 @@ __device__ __forceinline__ void dx_wpc_apply_tail(int lane, int n, int ns, const
     if (lane < n) {
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            v0[d * n + lane] = vin[d];
-            wv0[d * n + lane] = vin[d];
-            wy0[d * n + lane] = sg * vin[d];
+            v0[d * n + lane] = (T)vin[d];
+            wv0[d * n + lane] = (T)vin[d];
+            wy0[d * n + lane] = (T)(sg * vin[d]);
         }
     }
     __syncwarp();
@@ -404,7 +421,7 @@ __device__ __forceinline__ void dx_wpc_apply_tail(int lane, int n, int ns, const
         double mom[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) mom[d] = mass * vin[d];
-        if (lane < n) V.ds[lane] = mass;          // X_ff is no longer needed: reuse as the mass table
+        if (lane < n) V.ds[lane] = (T)mass;       // X_ff is no longer needed: reuse as the mass table
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             mass += __shfl_xor_sync(DX_FULL, mass, o);
@@ -421,23 +438,23 @@ __device__ __forceinline__ void dx_wpc_apply_tail(int lane, int n, int ns, const
     for (int ap = 0; ap < napply; ap++) {
         const bool last = ap == napply - 1;
         const bool odd = ap & 1;
-        const double *cv = odd ? wv1 : wv0, *cy = odd ? wy1 : wy0;
-        double *nv = odd ? wv0 : wv1, *ny = odd ? wy0 : wy1;
+        const T *cv = odd ? wv1 : wv0, *cy = odd ? wy1 : wy0;
+        T *nv = odd ? wv0 : wv1, *ny = odd ? wy0 : wy1;
         for (int t = lane; t < 3 * n; t += 32) {
             const int d = t / n, i = t - d * n;
-            const double *y = cy + d * n;
-            double acc = 0.0;
+            const T *y = cy + d * n;
+            T acc = T(0);
             for (int qq = 0; qq < n - 1; qq++) {
                 const int k = qq + (qq >= i);
                 acc = fma(F[i * ns + k], y[k], acc);
             }
-            const double out = fma(V.tau[i], acc, F[i * ns + i] * cv[d * n + i]);
+            const T out = fma(V.tau[i], acc, F[i * ns + i] * cv[d * n + i]);
             if (!last) {
                 nv[d * n + i] = out;
                 ny[d * n + i] = V.sig[i] * out;
                 continue;
             }
-            vop[((long long)d * n + i) * stride] = out;
+            vop[((long long)d * n + i) * stride] = (double)out;
             if (heat) {
                 const double vc = d == 0 ? vcm[0] : (d == 1 ? vcm[1] : vcm[2]);
                 const double a = v0[d * n + i] - vc, b = out - vc;
@@ -458,17 +475,18 @@ __device__ __forceinline__ void dx_wpc_apply_tail(int lane, int n, int ns, const
 // of a per-species array is at p[i * stride]; velocity (d, f) at
 // p[(d * n + f) * stride]. od/hp: pair tables for this n. v_out may alias v_in.
 // heat: see dx_wpc_apply_tail.
+template <typename T>
 __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const double *rgp, const double *rdp,
                                                     const double *tsp, const double *vip, double *vop,
-                                                    long long stride, double dt, const DxConsts &K, double *wsm,
+                                                    long long stride, double dt, const DxConsts &K, T *wsm,
                                                     const unsigned short *od, const unsigned short *hp,
                                                     uint32_t *status, double *heat = nullptr) {
     const int n = N + 1, ns = dx_stride(n);
     const int n_hp = n * (n + 1) / 2 - 1;
-    double *E0 = wsm;
-    double *E1 = E0 + n * ns;
-    DxVecs V;
-    DxFwdBufs B;
+    T *E0 = wsm;
+    T *E1 = E0 + n * ns;
+    DxVecsT<T> V;
+    DxFwdBufsT<T> B;
     dx_wpc_fwd_layout(E1 + n * ns, n, V, B);
     (void)od;
 
@@ -482,12 +500,12 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
     const int m = K.mk[L.k];
 
     // Taylor polynomial T_m(X) by Horner's rule in X
-    double *F = E0, *G = E1;
+    T *F = E0, *G = E1;
     dx_wpc_taylor_init(lane, n, ns, m, K, V, F);
     for (int j = m - 2; j >= 0; j--) {
-        dx_wpc_horner_step(lane, n, ns, n_hp, hp, V, K.b[j], F, G);
+        dx_wpc_horner_step(lane, n, ns, n_hp, hp, V, (T)K.b[j], F, G);
         __syncwarp();
-        double *tmp = F; F = G; G = tmp;
+        T *tmp = F; F = G; G = tmp;
     }
 
     // row-sum restoration, then s - q squarings (Eq. ExpEq1 with n = 2^s), each

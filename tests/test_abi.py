@@ -120,10 +120,17 @@ def test_host_argument_errors(lib):
     opts = dx.DragOptions(11, 1, 0, 0)                 # Pade at 2^-11
     assert ao(ctypes.c_int64(10), 4, good, good, good, ctypes.c_double(1.0), good, good, ctypes.byref(opts), null,
               null, s) == -8
-    opts = dx.DragOptions(53, 0, 1, 7)                 # reserved != 0
+    opts = dx.DragOptions(53, 0, 1, 7)                 # arith outside {0, 1}
     assert ao(ctypes.c_int64(10), 4, good, good, good, ctypes.c_double(1.0), good, good, ctypes.byref(opts), null,
               null, s) == -9
     assert ao(ctypes.c_int64(10), 4, good, good, good, ctypes.c_double(1.0), good, good, None, null, null, s) == -2
+    for bad in (dx.DragOptions(53, 0, 0, 1), dx.DragOptions(11, 0, 0, 1), dx.DragOptions(24, 1, 0, 1),
+                dx.DragOptions(24, 0, 1, 1)):
+        assert ao(ctypes.c_int64(10), 4, good, good, good, ctypes.c_double(1.0), good, good, ctypes.byref(bad),
+                  null, null, s) == -9                   # FP32 arithmetic: Taylor, no bound test, ubits 24
+    opts = dx.DragOptions(24, 0, 0, 1)
+    assert ao(ctypes.c_int64(10), 4, good, good, good, ctypes.c_double(1.0), good, good, ctypes.byref(opts),
+              good, null, s) == -9                       # no per-cell degrees on the FP32 path
     opts = dx.DragOptions(53, 0, 1, 0)
     assert ao(ctypes.c_int64(10), 4, good, bad_align, good, ctypes.c_double(1.0), good, good, ctypes.byref(opts),
               null, null, s) == -3
