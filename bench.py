@@ -48,8 +48,8 @@ KERNEL_SOURCES = {
 }
 MEASURED_TRAFFIC = {
     ("mrn_n16_128cube", "dx_forward_wpc"): {
-        "sources_sha256": "da3860a215f080b6c41b754e710541b018fdc0ded1d05ac1ed642a75c89e8ccc",
-        "bytes_per_cell": (186.644992e6 + 80.977920e6) / 262144,
+        "sources_sha256": "8d8f9e4a2bf43d8a3d3cb7ca289ec2df92bea32f1495dcbc96d50c6e05c36df0",
+        "bytes_per_cell": (187.130624e6 + 80.892416e6) / 262144,
         "capture": "profiles/dx_forward_wpc_mrn_n16.md",
     },
 }
