@@ -7,12 +7,17 @@
 
 namespace {
 
-constexpr int kThreads = 128;
-constexpr int kMaxTileRounds = 4;                   // cells per thread and tile (at most)
-constexpr int kTile = kThreads * kMaxTileRounds;    // largest tile a block sorts and runs
+constexpr int kTile = 512;   // largest tile of cells a block sorts and runs
+
+// Threads per block: 4 warps, or 2 warps when the matrix lives in shared
+// memory and n >= 9: there the slices (32 doubles per packed entry, 32 KB per
+// warp at n = 9) set the residency and smaller blocks pack more warps onto an
+// SM (measured: 1.3x at n = 9; 4-warp blocks stay faster up to n = 8).
+template <int NF, bool SMEM>
+__host__ __device__ constexpr int lpc_threads() { return (SMEM && NF >= 9) ? 64 : 128; }
 
 // A warp runs the largest Taylor order and squaring count of its 32 cells, so
-// each block first orders a tile of rounds x kThreads consecutive cells (the
+// each block first orders a tile of rounds x threads consecutive cells (the
 // launcher shrinks the tile when the grid would leave SMs idle) by a cost proxy
 // (the 1-norm of A = dt Omega_v in FP32, whose binary exponent tracks s*) and
 // hands every warp 32 cells of similar cost. The proxy only groups cells; the
@@ -35,7 +40,7 @@ __device__ __forceinline__ unsigned int cost_proxy(const double *rgp, const doub
 }
 
 template <int NF, bool SMEM>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(lpc_threads<NF, SMEM>())
 dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d, const double *t_s,
                const double *v_in, double *v_out, double dt, uint32_t *status, double *heat, DxConsts K) {
     extern __shared__ double smem[];
@@ -43,6 +48,7 @@ dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d
     __shared__ unsigned short order[kTile];       // sorted position -> tile index
     double *bsh = smem;
     for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
+    constexpr int kThreads = lpc_threads<NF, SMEM>();
     const int tile = rounds * kThreads;
     const long long base = (long long)blockIdx.x * tile;
     if (rounds > 1) {
@@ -78,12 +84,13 @@ dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d
 template <int NF, bool SMEM>
 int launch_one(const DxConsts &K, long long C, const double *rho_g, const double *rho_d, const double *t_s, const double *v_in,
                double *v_out, double dt, uint32_t *status, double *heat, cudaStream_t stream) {
+    constexpr int kThreads = lpc_threads<NF, SMEM>();
     const size_t smem = sizeof(double) * (32 + (SMEM ? (kThreads / 32) * dx_lpc_warp_smem_doubles<NF>() : 0));
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(dx_forward_lpc<NF, SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
         return DRAG_ECUDA;
-    int rounds = kMaxTileRounds;
+    int rounds = kTile / kThreads;
     while (rounds > 1 && (C + rounds * kThreads - 1) / (rounds * kThreads) < 4LL * dx_sm_count()) rounds >>= 1;
     const long long blocks = (C + rounds * kThreads - 1) / (rounds * kThreads);
     dx_forward_lpc<NF, SMEM><<<(unsigned)blocks, kThreads, smem, stream>>>(C, rounds, rho_g, rho_d, t_s, v_in, v_out,

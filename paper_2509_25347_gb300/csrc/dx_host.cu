@@ -179,9 +179,9 @@ bool g_mode_init[64];
 
 // Measured on GB300 (stiff MRN-like cells, cost-sorted lane-per-cell tiles):
 // lane per cell with the matrix in registers is fastest up to n = 6, in
-// shared memory up to n = 10 (its shared memory per warp grows as
+// shared memory up to n = 11 (its shared memory per warp grows as
 // 32 n(n+1) doubles and limits residency), warp per cell above.
-constexpr int kDefaultLpcSmemNMax = 10;
+constexpr int kDefaultLpcSmemNMax = 11;
 
 int default_mode(int n) {
     if (n <= DX_LPC_REG_NMAX) return DX_MODE_LPC_REG;
