@@ -153,6 +153,27 @@ int drag_expm_apply_opts(int64_t ncells, int32_t nspecies, const double *rho_g, 
                          const drag_expm_options_t *opts, int8_t *m_out, int16_t *s_out, cudaStream_t stream);
 
 /*
+ * drag_expm_apply_host — drag_expm_apply on HOST arrays (same SoA layout,
+ * stride ncells): the cells are processed in chunks of chunk_cells (0: 131072)
+ * through a two-stream pipeline, so the host-to-device copies of one chunk
+ * and the device-to-host copy of another overlap the update of a third. The
+ * copies are asynchronous only from page-locked (pinned) host memory; with
+ * pageable memory the call still works but the copies do not overlap.
+ *   rho_g, rho_d, t_s, v_in : HOST, read only;  v_out : HOST, written (may be v_in).
+ *   workspace : DEVICE, 256-byte aligned, >= drag_expm_host_workspace_bytes(nspecies,
+ *               chunk_cells) bytes (two chunk slabs), owned by the caller.
+ *   stream    : the work is ordered after the work already on `stream`, and
+ *               `stream` waits for it (fork and join through internal streams of the
+ *               library). v_out is valid once `stream` has reached that point.
+ * Calls from several host threads on one device are serialised while they enqueue.
+ * Returns as drag_expm_apply, or DRAG_EWORKSPACE / DRAG_EALIGN for the workspace.
+ */
+size_t drag_expm_host_workspace_bytes(int32_t nspecies, int64_t chunk_cells);
+int drag_expm_apply_host(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                         const double *t_s, double dt, const double *v_in, double *v_out, int64_t chunk_cells,
+                         void *workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/*
  * drag_expm_apply_heat — drag_expm_apply plus the energy epilogue: heat_out[c]
  * receives the kinetic energy (per unit volume) the drag step dissipates in
  * cell c, sum_f 1/2 rho_f (|v_in,f - V|^2 - |v_out,f - V|^2) with V the

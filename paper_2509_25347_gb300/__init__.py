@@ -14,7 +14,7 @@ import ctypes
 import os
 
 __all__ = ["load_library", "apply", "apply_heat", "backward", "rk1_apply", "apply_batched", "batched_workspace_bytes", "select", "get_status",
-           "theta", "DragExpm", "DragExpmError", "apply_opts", "pade_theta",
+           "theta", "DragExpm", "DragExpmError", "apply_opts", "pade_theta", "apply_host", "host_workspace_bytes",
            "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -72,6 +72,10 @@ def load_library(path: str | None = None):
     lib.drag_expm_theta_target.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
     lib.drag_expm_apply_target.restype = ctypes.c_int
     lib.drag_expm_apply_target.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, i32, vp]
+    lib.drag_expm_host_workspace_bytes.restype = ctypes.c_size_t
+    lib.drag_expm_host_workspace_bytes.argtypes = [i32, i64]
+    lib.drag_expm_apply_host.restype = ctypes.c_int
+    lib.drag_expm_apply_host.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, i64, vp, ctypes.c_size_t, vp]
     lib.drag_expm_apply_opts.restype = ctypes.c_int
     lib.drag_expm_apply_opts.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, ctypes.POINTER(DragOptions), vp, vp, vp]
     lib.drag_expm_pade_theta.restype = ctypes.c_int
@@ -146,6 +150,40 @@ def apply(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, stream=None, ubits: in
     else:
         _check(load_library().drag_expm_apply_target(C, N, *args, float(dt), vi, vo, int(ubits),
                                                      _stream_handle(stream)))
+    return v_out
+
+
+def _f64_host(name, t, shape):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or t.is_cuda:
+        raise DragExpmError(f"{name} must be a float64 CPU tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise DragExpmError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise DragExpmError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def host_workspace_bytes(nspecies: int, chunk_cells: int = 0) -> int:
+    return int(load_library().drag_expm_host_workspace_bytes(int(nspecies), int(chunk_cells)))
+
+
+def apply_host(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, chunk_cells: int = 0, workspace=None, stream=None):
+    """Forward update on host (CPU, ideally pinned) float64 tensors, pipelined
+    through the GPU in chunks (drag_expm_apply_host). Returns v_out (host)."""
+    import torch
+    C, N = _shapes(rho_g, rho_d)
+    if v_out is None:
+        v_out = torch.empty_like(v_in)
+    args = [_f64_host("rho_g", rho_g, (C,)), _f64_host("rho_d", rho_d, (N, C)), _f64_host("t_s", t_s, (N, C))]
+    vi = _f64_host("v_in", v_in, (3, N + 1, C))
+    vo = _f64_host("v_out", v_out, (3, N + 1, C))
+    nbytes = host_workspace_bytes(N, chunk_cells)
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    _check(load_library().drag_expm_apply_host(C, N, *args, float(dt), vi, vo, int(chunk_cells),
+                                               ctypes.c_void_p(workspace.data_ptr()), nbytes,
+                                               _stream_handle(stream)))
     return v_out
 
 

@@ -134,6 +134,13 @@ def test_host_argument_errors(lib):
     opts = dx.DragOptions(53, 0, 1, 0)
     assert ao(ctypes.c_int64(10), 4, good, bad_align, good, ctypes.c_double(1.0), good, good, ctypes.byref(opts),
               null, null, s) == -3
+    ah = lib.drag_expm_apply_host
+    assert ah(-1, 4, good, good, good, 1.0, good, good, 0, good, 1 << 30, s) == -1
+    assert ah(10, 4, good, good, good, float("nan"), good, good, 0, good, 1 << 30, s) == -1
+    assert ah(10, 4, good, null, good, 1.0, good, good, 0, good, 1 << 30, s) == -2
+    assert ah(10, 4, good, good, good, 1.0, good, good, 0, null, 1 << 30, s) == -2
+    assert ah(10, 4, good, good, good, 1.0, good, good, 64, good, 16, s) == -5
+    assert ah(10, 4, good, good, good, 1.0, good, good, 64, ctypes.c_void_p(4104), 1 << 30, s) == -3
     st = lib.drag_expm_select_target
     assert st(10, 4, good, good, good, 1.0, 12, good, good, s) == -8
     assert apply(10, 4, good, good, good, 1.0, good, bad_align, s) == -3
