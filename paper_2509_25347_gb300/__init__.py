@@ -13,9 +13,11 @@ from __future__ import annotations
 import ctypes
 import os
 
-__all__ = ["load_library", "apply", "apply_heat", "backward", "rk1_apply", "apply_batched", "batched_workspace_bytes", "select", "get_status",
-           "theta", "DragExpm", "DragExpmError", "apply_opts", "pade_theta", "apply_host", "host_workspace_bytes",
-           "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"]
+__all__ = [
+    "load_library", "apply", "apply_heat", "backward", "rk1_apply", "apply_batched", "batched_workspace_bytes",
+    "select", "get_status", "theta", "DragExpm", "DragExpmError", "apply_opts", "pade_theta", "apply_host",
+    "host_workspace_bytes", "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"
+]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdragexpm.so")

@@ -189,8 +189,9 @@ extern "C" int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *r
     return apply_impl(dx_consts(), ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, nullptr, stream);
 }
 
-int dx_launch_forward_f32(const DxConsts &K, long long ncells, int nspecies, const double *rho_g, const double *rho_d,
-                          const double *t_s, double dt, const double *v_in, double *v_out, cudaStream_t stream) {
+int dx_launch_forward_f32(const DxConsts &K, long long ncells, int nspecies, const double *rho_g,
+                          const double *rho_d, const double *t_s, double dt, const double *v_in, double *v_out,
+                          cudaStream_t stream) {
     int rc = check_common(ncells, nspecies, rho_g, rho_d, t_s, dt);
     if (rc != DRAG_OK || ncells == 0) return rc;
     if (!v_in || !v_out) return DRAG_ENULL;
@@ -204,7 +205,8 @@ int dx_launch_forward_f32(const DxConsts &K, long long ncells, int nspecies, con
         return DRAG_ECUDA;
     FwdArgs a{ncells, nspecies, rho_g, rho_d, t_s, v_in, v_out, dt, st, nullptr};
     const long long grid = (ncells + kCellsPerBlock - 1) / kCellsPerBlock;
-    dx_forward_wpc_f32<<<(unsigned)grid, kWarpsPerBlock * 32, dx_forward_f32_smem_bytes(nspecies + 1), stream>>>(a, K);
+    const size_t smem = dx_forward_f32_smem_bytes(nspecies + 1);
+    dx_forward_wpc_f32<<<(unsigned)grid, kWarpsPerBlock * 32, smem, stream>>>(a, K);
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }
 

@@ -82,8 +82,8 @@ dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d
 }
 
 template <int NF, bool SMEM>
-int launch_one(const DxConsts &K, long long C, const double *rho_g, const double *rho_d, const double *t_s, const double *v_in,
-               double *v_out, double dt, uint32_t *status, double *heat, cudaStream_t stream) {
+int launch_one(const DxConsts &K, long long C, const double *rho_g, const double *rho_d, const double *t_s,
+               const double *v_in, double *v_out, double dt, uint32_t *status, double *heat, cudaStream_t stream) {
     constexpr int kThreads = lpc_threads<NF, SMEM>();
     const size_t smem = sizeof(double) * (32 + (SMEM ? (kThreads / 32) * dx_lpc_warp_smem_doubles<NF>() : 0));
     if (smem > 48 * 1024 &&
@@ -100,9 +100,9 @@ int launch_one(const DxConsts &K, long long C, const double *rho_g, const double
 
 }  // namespace
 
-int dx_launch_forward_lpc(const DxConsts &K, int n, bool smem, long long C, const double *rho_g, const double *rho_d, const double *t_s,
-                          const double *v_in, double *v_out, double dt, uint32_t *status, double *heat,
-                          cudaStream_t stream) {
+int dx_launch_forward_lpc(const DxConsts &K, int n, bool smem, long long C, const double *rho_g,
+                          const double *rho_d, const double *t_s, const double *v_in, double *v_out, double dt,
+                          uint32_t *status, double *heat, cudaStream_t stream) {
 #define DX_CASE_REG(NF) \
     case NF: return smem ? launch_one<NF, true>(K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream) \
                          : launch_one<NF, false>(K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream);

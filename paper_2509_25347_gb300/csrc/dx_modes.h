@@ -18,8 +18,9 @@ int dx_mode_for(int n);            // current mode for matrix size n (current de
 void dx_set_mode(int n, int mode);  // used by the autotuner
 bool dx_mode_valid(int n, int mode);
 
-int dx_launch_forward_f32(const DxConsts &K, long long ncells, int nspecies, const double *rho_g, const double *rho_d,
-                          const double *t_s, double dt, const double *v_in, double *v_out, cudaStream_t stream);
-int dx_launch_forward_lpc(const DxConsts &K, int n, bool smem, long long C, const double *rho_g, const double *rho_d, const double *t_s,
-                          const double *v_in, double *v_out, double dt, uint32_t *status, double *heat,
+int dx_launch_forward_f32(const DxConsts &K, long long ncells, int nspecies, const double *rho_g,
+                          const double *rho_d, const double *t_s, double dt, const double *v_in, double *v_out,
                           cudaStream_t stream);
+int dx_launch_forward_lpc(const DxConsts &K, int n, bool smem, long long C, const double *rho_g,
+                          const double *rho_d, const double *t_s, const double *v_in, double *v_out, double dt,
+                          uint32_t *status, double *heat, cudaStream_t stream);

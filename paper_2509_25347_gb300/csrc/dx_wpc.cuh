@@ -238,20 +238,6 @@ __device__ __forceinline__ void dx_wpc_restore(int lane, int n, int ns, const Dx
     }
 }
 
-// Strict upper triangle of E^2 (symmetric), mirrored: G_ij = G_ji = sum_k E_ik E_jk.
-template <typename T>
-__device__ __forceinline__ void dx_wpc_square_offdiag(int lane, int n, int ns, int n_od, const unsigned short *od,
-                                                      const T *E, T *G) {
-    for (int t = lane; t < n_od; t += 32) {
-        const int p = od[t], i = p >> 8, jj = p & 255;
-        const T *ri = E + i * ns, *rj = E + jj * ns;
-        T acc = T(0);
-        for (int k = 0; k < n; k++) acc = fma(ri[k], rj[k], acc);
-        G[i * ns + jj] = acc;
-        G[jj * ns + i] = acc;
-    }
-}
-
 // Row-sum restoration of the starting matrix (t = 0) and s squarings with
 // restoration (t = 1..s), run on the round schedule generated by sched.py:
 // each round gives every lane one task of n FP64 operations, either an
