@@ -224,14 +224,13 @@ dx_backward_wpc(BwdArgs a, DxConsts K) {
             continue;
         }
         const int m = K.mk[L.k];
-        const double p2 = dx_pow2(-L.s);
         {
             // rank-3 direction and its stationary block (kappa)
             double ad[3], bd[3], sa[3], sb[3];
 #pragma unroll
             for (int d = 0; d < 3; d++) {
                 ad[d] = lane < n ? gin[d] * L.tu : 0.0;
-                bd[d] = lane < n ? (L.sg * vin[d]) * p2 : 0.0;
+                bd[d] = lane < n ? dx_scale2(L.sg * vin[d], L.s) : 0.0;
                 sa[d] = L.sg * ad[d];
                 sb[d] = L.sg * bd[d];
             }

@@ -163,7 +163,7 @@ __global__ void dx_batch_count(long long nblocks, const Desc *blocks, const doub
             double col0 = s1;
             for (int i = 0; i < N; i++) col0 = __dadd_rn(col0, ai0s[i]);
             const long long nb = dx_bits(col0) > cmax ? dx_bits(col0) : cmax;
-            dx_select(__longlong_as_double(nb), K, kk, s);
+            if (dx_norm_ok(nb)) dx_select(__longlong_as_double(nb), K, kk, s);   // else the cell routine flags it
         }
         const unsigned int key = (unsigned int)bin_of(N + 1, kk, s);
         W.key[g] = key;

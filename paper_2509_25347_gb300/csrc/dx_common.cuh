@@ -127,6 +127,17 @@ __device__ __forceinline__ void dx_select_pade(double norm, const DxPade &P, int
 // 2^e as a double for -1022 <= e <= 1023 (exact).
 __device__ __forceinline__ double dx_pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 
+// x 2^-s for 0 <= s <= 1100 (Algorithm 2 returns up to ~1025 for norms near the
+// top of the double range): through two factors once 2^-s leaves the normal range.
+__device__ __forceinline__ double dx_scale2(double x, int s) {
+    return s <= 1022 ? x * dx_pow2(-s) : (x * dx_pow2(-1022)) * dx_pow2(-(s - 1022));
+}
+
+// A usable 1-norm (finite; the bit pattern of a non-negative double). An
+// overflowing norm, e.g. alpha = 1/t_s beyond the double range, makes the
+// cell invalid, as in the oracle.
+__device__ __forceinline__ bool dx_norm_ok(long long nb) { return nb >= 0 && nb < 0x7ff0000000000000LL; }
+
 __device__ __forceinline__ double dx_shfl(double x, int src) { return __shfl_sync(DX_FULL, x, src); }
 
 __device__ __forceinline__ long long dx_warp_max_ll(long long v) {

@@ -128,10 +128,12 @@ __global__ void dx_select_kernel(long long C, int N, const double *rho_g, const 
             cmax = dx_bits(cj) > dx_bits(cmax) ? cj : cmax;
         }
         const double norm = dx_bits(col0) > dx_bits(cmax) ? col0 : cmax;
-        dx_select(norm, K, kk, s);
-    } else {
-        atomicOr(status, DRAG_STATUS_BAD_CELL);
+        if (dx_norm_ok(dx_bits(norm)))
+            dx_select(norm, K, kk, s);
+        else
+            ok = false;
     }
+    if (!ok) atomicOr(status, DRAG_STATUS_BAD_CELL);
     if (k_out) k_out[c] = (int8_t)kk;
     if (s_out) s_out[c] = (int16_t)s;
 }

@@ -111,10 +111,16 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
         cmax = cb > cmax ? cb : cmax;
     }
     const long long nb = dx_bits(col0) > cmax ? dx_bits(col0) : cmax;
+    if (!dx_norm_ok(nb)) {
+#pragma unroll
+        for (int e = 0; e < 3 * NF; e++) vop[e * stride] = NAN;
+        if (heat) *heat = NAN;
+        atomicOr(status, DRAG_STATUS_BAD_CELL);
+        return;
+    }
     int kk, s;
     dx_select(__longlong_as_double(nb), K, kk, s);
     const int m = K.mk[kk];
-    const double p2 = dx_pow2(-s);
 
     // ---------------- symmetric arrowhead X = 2^-s D_sigma A D_sigma^-1
     DxLaneArr<NF, SMEM> sig, tau, xs, ds;
@@ -129,7 +135,7 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
     }
     sig[0] = 1.0;
     tau[0] = 1.0;
-    xs[0] = -s1 * p2;
+    xs[0] = dx_scale2(-s1, s);
     ds[0] = 0.0;
 #pragma unroll
     for (int i = 1; i < NF; i++) {
@@ -137,8 +143,8 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
         const double sg = __dsqrt_rn(e);
         sig[i] = sg;
         tau[i] = __ddiv_rn(1.0, sg);
-        xs[i] = __dmul_rn(__dmul_rn(sg, alpha[i - 1]), dt * p2);
-        ds[i] = -(__dmul_rn(alpha[i - 1], dt) * p2);
+        xs[i] = __dmul_rn(__dmul_rn(sg, alpha[i - 1]), dx_scale2(dt, s));
+        ds[i] = -dx_scale2(__dmul_rn(alpha[i - 1], dt), s);
     }
 
     // ---------------- Taylor: F = b_m X + b_{m-1} I, then F <- F X + b_j I (Horner in X)

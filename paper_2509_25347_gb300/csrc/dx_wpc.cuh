@@ -82,11 +82,11 @@ __device__ __forceinline__ bool dx_wpc_setup(int lane, int N, double rg, double 
     const double colj = sp ? __dadd_rn(a0i, ai0) : 0.0;
     long long nb = dx_warp_max_ll(dx_bits(colj));
     nb = nb > dx_bits(col0) ? nb : dx_bits(col0);
+    if (!dx_norm_ok(nb)) return false;                          // warp uniform
     if (pade)
         dx_select_pade(__longlong_as_double(nb), *pade, L.k, L.s);   // L.k: index of the Pade degree
     else
         dx_select(__longlong_as_double(nb), K, L.k, L.s);
-    const double p2 = dx_pow2(-L.s);
     double sg = 1.0, tu = 1.0;
     if (sp) {
         // FP32 work keeps sigma and 1/sigma inside its range: 1e-30 instead of 1e-200
@@ -98,8 +98,8 @@ __device__ __forceinline__ bool dx_wpc_setup(int lane, int N, double rg, double 
     if (lane < n) {
         V.sig[lane] = (T)sg;
         V.tau[lane] = (T)tu;
-        V.xs[lane] = (T)(lane == 0 ? -s1 * p2 : __dmul_rn(__dmul_rn(sg, alpha), dt * p2));
-        V.ds[lane] = (T)(-(ai0 * p2));
+        V.xs[lane] = (T)(lane == 0 ? dx_scale2(-s1, L.s) : __dmul_rn(__dmul_rn(sg, alpha), dx_scale2(dt, L.s)));
+        V.ds[lane] = (T)(-dx_scale2(ai0, L.s));
     }
     L.eps = eps;
     L.alpha = alpha;

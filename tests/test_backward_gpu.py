@@ -181,3 +181,25 @@ def test_backward_full_size_sampled(dx, name):
     ref = oracle.drag_backward(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v, gs)[:4]
     got = (gv[:, :, ti].cpu().numpy(), grg[ti].cpu().numpy(), grd[:, ti].cpu().numpy(), gts[:, ti].cpu().numpy())
     assert_adjoint_parity(sub, gs, got, ref)
+
+
+def test_backward_extreme_norms(dx):
+    """The adjoint at very large norms. dL/dv_in = P^T g must match the oracle
+    up to norms of 1.5e308 (s* ~ 1023, every cell fully relaxed). The parameter
+    gradients come from the chain rule alpha dt (Z_0i - Z_00) etc., in which
+    alpha dt multiplies the rounding of Z: they are checked in full up to
+    |A| ~ 1e14 (alpha dt u << 1); beyond ~1/u both implementations return
+    rounding-dominated values, as the design notes state."""
+    from tests.test_forward_gpu import extreme_cells
+    cells = extreme_cells(8, [1e250, 1e300, 1.5e308])
+    g = np.random.default_rng(8).standard_normal(cells.v.shape)
+    gv = gpu_backward(dx, cells, g)[0]
+    rv = oracle.drag_backward(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, g)[0]
+    assert np.all(np.isfinite(gv))
+    assert np.max(np.abs(gv - rv) / np.abs(g).sum(axis=1, keepdims=True)) <= TOL_V
+    cells = extreme_cells(8, [1e8, 1e11, 1e14])
+    g = np.random.default_rng(9).standard_normal(cells.v.shape)
+    got = gpu_backward(dx, cells, g)
+    ref = oracle.drag_backward(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, g)[:4]
+    assert_adjoint_parity(cells, g, got, ref)
+    assert dx.get_status() == 0

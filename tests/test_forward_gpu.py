@@ -180,3 +180,38 @@ def test_sorted_tiles_parity(dx, N):
     ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v)
     assert_parity(out, ref, cells.v)
     assert dx.get_status() == 0
+
+
+def extreme_cells(N, norms, seed=3):
+    """Cells whose 1-norm |A|_1 is about `norms[c]` (rho_d = rho_g = 1, dt = 1,
+    stopping times spread over a factor 2): s* up to ~1023."""
+    rng = np.random.default_rng(seed)
+    C = len(norms)
+    t_s = np.empty((N, C))
+    for c, nrm in enumerate(norms):
+        t_s[:, c] = 2.0 * N / nrm * (1.0 + np.arange(N) / N)
+    return W.Cells(np.ones(C), np.ones((N, C)), t_s, rng.standard_normal((3, N + 1, C)), 1.0)
+
+
+@pytest.mark.parametrize("N", [4, 16])
+def test_extreme_norms(dx, N):
+    """Norms from 1e250 to 1.5e308: the scaling 2^-s* leaves the normal range
+    past s* = 1022; every cell must still match the oracle. A norm that
+    overflows (a stopping time below 1/DBL_MAX) is an invalid cell on both
+    sides: NaN outputs and the status bit."""
+    norms = [1e250, 1e300, 5e306, 1.5e308]
+    cells = extreme_cells(N, norms)
+    out = gpu_apply(dx, cells)
+    ref, k, s, st = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, return_ks=True)
+    assert st == 0 and s.max() >= 1022, s
+    assert_parity(out, ref, cells.v)
+    kg, sg = dx.select(*dev(cells)[:3], cells.dt)
+    assert np.array_equal(kg.cpu().numpy(), k) and np.array_equal(sg.cpu().numpy(), s)
+    assert dx.get_status() == 0
+    bad = extreme_cells(N, [1e300, 1e300])
+    bad.t_s[0, 1] = 1e-310
+    out = gpu_apply(dx, bad)
+    ref, _, _, st = oracle.drag_apply(bad.rho_g, bad.rho_d, bad.t_s, bad.dt, bad.v, return_ks=True)
+    assert st == 1 and np.all(np.isnan(ref[:, :, 1]))
+    assert np.all(np.isnan(out[:, :, 1])) and np.all(np.isfinite(out[:, :, 0]))
+    assert dx.get_status() & dx.STATUS_BAD_CELL
