@@ -78,12 +78,13 @@ dx_forward_wpc_f32(FwdArgs a, DxConsts K) {
     extern __shared__ float smemf[];
     const int n = a.N + 1;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int wd = dx_wpc_fwd_warp_doubles(n);
+    const int wd = dx_wpc_fwd_warp_doubles(n) + n * dx_stride(n);   // + the restoration weight table
     unsigned short *od = reinterpret_cast<unsigned short *>(smemf + kWarpsPerBlock * wd);
     unsigned short *hp = od + kPairSlots;
     dx_build_pairs(n, od, hp);
     __syncthreads();
     float *wsm = smemf + wib * wd;
+    float *wz = wsm + dx_wpc_fwd_warp_doubles(n);
     __shared__ int next;
     if (threadIdx.x == 0) next = 0;
     __syncthreads();
@@ -95,7 +96,7 @@ dx_forward_wpc_f32(FwdArgs a, DxConsts K) {
         const long long c = base + k;
         if (k >= kCellsPerBlock || c >= a.C) break;
         dx_wpc_forward_cell(lane, a.N, a.rho_g + c, a.rho_d + c, a.t_s + c, a.v_in + c, a.v_out + c, a.C, a.dt, K, wsm,
-                            od, hp, a.status);
+                            od, hp, a.status, (double *)nullptr, wz);
     }
 }
 
@@ -155,7 +156,7 @@ size_t dx_forward_smem_bytes(int n) {
 }
 
 size_t dx_forward_f32_smem_bytes(int n) {
-    return sizeof(float) * (size_t)kWarpsPerBlock * dx_wpc_fwd_warp_doubles(n) +
+    return sizeof(float) * (size_t)kWarpsPerBlock * (dx_wpc_fwd_warp_doubles(n) + n * dx_stride(n)) +
            2 * kPairSlots * sizeof(unsigned short);
 }
 

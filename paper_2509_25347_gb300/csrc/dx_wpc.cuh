@@ -247,9 +247,14 @@ __device__ __forceinline__ void dx_wpc_restore(int lane, int n, int ns, const Dx
 // those need are complete. Chunks of at most DX_SCHED_H squarings each start
 // with a restoration (a no-op on an already restored matrix). The matrix
 // starts in B[p0]; returns the index of the buffer holding the result.
+// wz (FP32 work only, may be null): an n x ns table whose row i is sigma with
+// a zero at i. With it a restoration runs the same plain n-term loop as a
+// product (the stale diagonal of the destination is multiplied by an exact 0),
+// which costs one more FMA per round but drops the per-term index select that
+// dominates instruction issue once the arithmetic is FP32.
 template <typename T>
 __device__ __forceinline__ int dx_wpc_square_chain(int lane, int n, int ns, int s, T *B0, T *B1, int p0,
-                                                   const DxVecsT<T> &V) {
+                                                   const DxVecsT<T> &V, const T *wz = nullptr) {
     const unsigned short *tab = dx_sched_task + (size_t)dx_sched_off[n] * 32;
     const unsigned short *endr = dx_sched_end + n * (DX_SCHED_H + 1);
     int remaining = s, parity = p0;
@@ -265,16 +270,25 @@ __device__ __forceinline__ int dx_wpc_square_chain(int lane, int n, int ns, int 
                 T *dst = (parity ^ (t & 1)) ? B1 : B0;
                 const T *src = isR ? dst : ((parity ^ ((t - 1) & 1)) ? B1 : B0);
                 const T *pa = src + i * ns;
-                const T *pb = isR ? V.sig : src + j * ns;
-                T acc = T(0);
-                for (int q = 0; q < n - 1; q++) {
-                    const int k = (isR && q >= i) ? q + 1 : q;
-                    acc = fma(pa[k], pb[k], acc);
+                T res;
+                if (sizeof(T) == sizeof(float) && wz) {
+                    const T *pb = isR ? wz + i * ns : src + j * ns;
+                    T acc = T(0);
+#pragma unroll 4
+                    for (int k = 0; k < n; k++) acc = fma(pa[k], pb[k], acc);
+                    res = isR ? fma(-V.tau[i], acc, T(1)) : acc;
+                } else {
+                    const T *pb = isR ? V.sig : src + j * ns;
+                    T acc = T(0);
+                    for (int q = 0; q < n - 1; q++) {
+                        const int k = (isR && q >= i) ? q + 1 : q;
+                        acc = fma(pa[k], pb[k], acc);
+                    }
+                    const T x = isR ? -V.tau[i] : pa[n - 1];
+                    const T y = isR ? acc : pb[n - 1];
+                    const T z = isR ? T(1) : acc;
+                    res = fma(x, y, z);
                 }
-                const T x = isR ? -V.tau[i] : pa[n - 1];
-                const T y = isR ? acc : pb[n - 1];
-                const T z = isR ? T(1) : acc;
-                const T res = fma(x, y, z);
                 if (isR) {
                     dst[i * ns + i] = res;
                 } else {
@@ -430,11 +444,20 @@ __device__ __forceinline__ void dx_wpc_apply_tail(int lane, int n, int ns, const
             const int d = t / n, i = t - d * n;
             const T *y = cy + d * n;
             T acc = T(0);
-            for (int qq = 0; qq < n - 1; qq++) {
-                const int k = qq + (qq >= i);
-                acc = fma(F[i * ns + k], y[k], acc);
+            T out;
+            if (sizeof(T) == sizeof(float)) {
+                // FP32: the plain form tau_i sum_j E_ij sigma_j v_j (its j = i term is E_ii v_i) as
+                // one unmasked loop; FP64 keeps E_ii v_i apart so that dt = 0 returns v_in exactly
+#pragma unroll 4
+                for (int k = 0; k < n; k++) acc = fma(F[i * ns + k], y[k], acc);
+                out = V.tau[i] * acc;
+            } else {
+                for (int qq = 0; qq < n - 1; qq++) {
+                    const int k = qq + (qq >= i);
+                    acc = fma(F[i * ns + k], y[k], acc);
+                }
+                out = fma(V.tau[i], acc, F[i * ns + i] * cv[d * n + i]);
             }
-            const T out = fma(V.tau[i], acc, F[i * ns + i] * cv[d * n + i]);
             if (!last) {
                 nv[d * n + i] = out;
                 ny[d * n + i] = V.sig[i] * out;
@@ -466,7 +489,7 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
                                                     const double *tsp, const double *vip, double *vop,
                                                     long long stride, double dt, const DxConsts &K, T *wsm,
                                                     const unsigned short *od, const unsigned short *hp,
-                                                    uint32_t *status, double *heat = nullptr) {
+                                                    uint32_t *status, double *heat = nullptr, T *wz = nullptr) {
     const int n = N + 1, ns = dx_stride(n);
     const int n_hp = n * (n + 1) / 2 - 1;
     T *E0 = wsm;
@@ -497,6 +520,14 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
     // row-sum restoration, then s - q squarings (Eq. ExpEq1 with n = 2^s), each
     // restored; the remaining q squarings become 2^q applications
     const int q = L.s < DX_APPLY_Q ? L.s : DX_APPLY_Q;
-    F = dx_wpc_square_chain(lane, n, ns, L.s - q, E0, E1, F == E1 ? 1 : 0, V) ? E1 : E0;
+    if (wz) {
+        // row i of wz: sigma with a zero at i (restorations as plain n-term loops)
+        for (int t = lane; t < n * n; t += 32) {
+            const int i = t / n, k = t - i * n;
+            wz[i * ns + k] = i == k ? T(0) : V.sig[k];
+        }
+        __syncwarp();
+    }
+    F = dx_wpc_square_chain(lane, n, ns, L.s - q, E0, E1, F == E1 ? 1 : 0, V, wz) ? E1 : E0;
     dx_wpc_apply_tail(lane, n, ns, V, B, F, q, c, L.sg, vop, stride, heat);
 }

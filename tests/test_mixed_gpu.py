@@ -79,9 +79,11 @@ def test_mixed_conserves_momentum_and_stays_convex(dx):
 
 def test_mixed_edge_cases(dx):
     cells = W.workload("mrn_n8_128cube_adjoint", ncells=100)
-    # dt = 0: the identity, up to the FP32 rounding of v_in
+    # dt = 0: the identity up to FP32 rounding. The FP32 apply forms
+    # v_i' = tau_i sum_j E_ij sigma_j v_j, so v_i comes back through sigma_i, its
+    # reciprocal and two products: at most a few FP32 roundings of v_i.
     out = mixed(dx, cells, 24, dt=0.0)
-    assert np.all(np.abs(out - cells.v) <= U32 * np.abs(cells.v))
+    assert np.all(np.abs(out - cells.v) <= 8 * U32 * np.abs(cells.v))
     # in place
     rg, rd, ts, v = dev(cells)
     dx.apply_opts(rg, rd, ts, cells.dt, v, v, ubits=24, arith="fp32")
