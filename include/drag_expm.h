@@ -234,6 +234,58 @@ int drag_expm_backward(int64_t ncells, int32_t nspecies, const double *rho_g, co
                        cudaStream_t stream);
 
 /*
+ * Adjoint tape. The adjoint needs every restored iterate E_t = exp(2^(t-s*) S)
+ * (S the symmetric similarity form of A = dt Omega_v, t = 0 .. s*-1) that the
+ * forward's Taylor step and squarings (Algorithm 2 choices, Eq. ExpEq1) form;
+ * drag_expm_backward recomputes them. drag_expm_apply_taped stores the ones
+ * the forward forms, E_0 .. E_{s*-2} (E_0 alone for s* <= 1), in a tape, and
+ * drag_expm_backward_taped reads them instead: it then forms neither the
+ * Taylor polynomial nor those products, and its gradients are identical to
+ * drag_expm_backward's. The tape trades HBM for FP64 work:
+ *   drag_expm_tape_bytes(ncells, nspecies, levels) bytes, about
+ *   ncells * levels * 8 * (N+1)(N+2)/2 (rounded up to 128-byte slots),
+ * where `levels` is the capacity per cell; a cell needs
+ * drag_expm_tape_levels(s*) = max(s* - 1, 1) of them (drag_expm_select gives
+ * s*). A cell that needs more is not recorded and its adjoint recomputes.
+ * Layout (opaque to callers): ncells 8-byte fingerprint words, padded to a
+ * 256-byte multiple, then per cell `levels` slots of packed upper triangles.
+ * Each cell's fingerprint covers rho_g, rho_d, t_s, dt and the tape geometry;
+ * the adjoint uses a cell's entries only if its own inputs reproduce the
+ * fingerprint, so a stale or foreign tape gives correct gradients (at the
+ * recomputing cost), up to 64-bit hash collisions.
+ * drag_expm_tape_bytes returns 0 for bad sizes or levels outside
+ * [1, DRAG_TAPE_MAX_LEVELS]; drag_expm_tape_levels returns 0 for s* < 0.
+ */
+#define DRAG_TAPE_MAX_LEVELS 2048
+size_t drag_expm_tape_bytes(int64_t ncells, int32_t nspecies, int32_t levels);
+int32_t drag_expm_tape_levels(int32_t sstar);
+
+/*
+ * drag_expm_apply_taped — drag_expm_apply (bit-identical v_out), run one warp
+ * per cell for every nspecies, that also writes the adjoint tape.
+ *   levels : tape capacity per cell, 1 .. DRAG_TAPE_MAX_LEVELS.
+ *   tape   : DEVICE, 256-byte aligned, >= drag_expm_tape_bytes(ncells,
+ *            nspecies, levels) bytes, owned by the caller, written; must not
+ *            overlap the other arrays.
+ * Returns as drag_expm_apply, or DRAG_EINVAL_SIZE (levels), DRAG_ENULL (tape),
+ * DRAG_EALIGN (tape alignment), DRAG_EWORKSPACE (tape_bytes too small).
+ */
+int drag_expm_apply_taped(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                          const double *t_s, double dt, const double *v_in, double *v_out, int32_t levels,
+                          void *tape, size_t tape_bytes, cudaStream_t stream);
+
+/*
+ * drag_expm_backward_taped — drag_expm_backward reading the tape written by
+ * drag_expm_apply_taped with the same ncells, nspecies and levels (read only).
+ * Arguments and errors as drag_expm_backward, plus those of the tape as in
+ * drag_expm_apply_taped.
+ */
+int drag_expm_backward_taped(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                             const double *t_s, double dt, const double *v_in, const double *grad_v_out,
+                             double *grad_v_in, double *grad_rho_g, double *grad_rho_d, double *grad_t_s,
+                             int32_t levels, const void *tape, size_t tape_bytes, cudaStream_t stream);
+
+/*
  * Batched drag update over AMR-like blocks. Block b holds ncells cells that
  * share nspecies N and time step dt. Its data live in slabs of the caller's
  * arrays, each laid out like a plain call with C = ncells:

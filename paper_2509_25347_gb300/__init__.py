@@ -16,7 +16,8 @@ import os
 __all__ = [
     "load_library", "apply", "apply_heat", "backward", "rk1_apply", "apply_batched", "batched_workspace_bytes",
     "select", "get_status", "theta", "DragExpm", "DragExpmError", "apply_opts", "pade_theta", "apply_host",
-    "host_workspace_bytes", "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"
+    "host_workspace_bytes", "apply_taped", "Tape", "tape_bytes", "tape_levels", "tape_levels_needed",
+    "DragExpmTaped", "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -84,6 +85,15 @@ def load_library(path: str | None = None):
     lib.drag_expm_pade_theta.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
     lib.drag_expm_select_target.restype = ctypes.c_int
     lib.drag_expm_select_target.argtypes = [i64, i32, vp, vp, vp, dbl, i32, vp, vp, vp]
+    lib.drag_expm_tape_bytes.restype = ctypes.c_size_t
+    lib.drag_expm_tape_bytes.argtypes = [i64, i32, i32]
+    lib.drag_expm_tape_levels.restype = ctypes.c_int32
+    lib.drag_expm_tape_levels.argtypes = [i32]
+    lib.drag_expm_apply_taped.restype = ctypes.c_int
+    lib.drag_expm_apply_taped.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, i32, vp, ctypes.c_size_t, vp]
+    lib.drag_expm_backward_taped.restype = ctypes.c_int
+    lib.drag_expm_backward_taped.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp, vp, vp, vp, i32, vp,
+                                             ctypes.c_size_t, vp]
     lib.drag_expm_strerror.restype = ctypes.c_char_p
     lib.drag_expm_strerror.argtypes = [ctypes.c_int]
     lib.drag_expm_version.restype = ctypes.c_int
@@ -257,11 +267,74 @@ def _opt_ptr(name, t, shape):
     return _f64_cuda(name, t, shape)
 
 
+class Tape:
+    """Adjoint tape written by :func:`apply_taped` (a uint8 CUDA tensor of
+    drag_expm_tape_bytes bytes) with the geometry it was written for."""
+
+    __slots__ = ("buf", "ncells", "nspecies", "levels")
+
+    def __init__(self, buf, ncells: int, nspecies: int, levels: int):
+        self.buf, self.ncells, self.nspecies, self.levels = buf, int(ncells), int(nspecies), int(levels)
+
+    @property
+    def nbytes(self) -> int:
+        return int(self.buf.numel())
+
+
+def tape_bytes(ncells: int, nspecies: int, levels: int) -> int:
+    """Bytes of an adjoint tape (0 for bad arguments)."""
+    return int(load_library().drag_expm_tape_bytes(int(ncells), int(nspecies), int(levels)))
+
+
+def tape_levels(sstar: int) -> int:
+    """Tape levels a cell with s* = sstar needs, max(s* - 1, 1)."""
+    return int(load_library().drag_expm_tape_levels(int(sstar)))
+
+
+def tape_levels_needed(rho_g, rho_d, t_s, dt: float, stream=None) -> int:
+    """The capacity that records every cell: tape_levels(max s*) over the cells
+    (runs drag_expm_select; synchronises with the device)."""
+    C, _ = _shapes(rho_g, rho_d)
+    if C == 0:
+        return 1
+    _, s = select(rho_g, rho_d, t_s, dt, stream=stream)
+    return max(tape_levels(int(s.max().item())), 1)
+
+
+def apply_taped(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, levels: int | None = None, tape=None,
+                stream=None):
+    """:func:`apply` (bit-identical v_out, one warp per cell) that also records
+    the adjoint tape; returns (v_out, Tape). ``levels`` is the tape capacity per
+    cell (default: :func:`tape_levels_needed`); ``tape`` may pass a Tape to reuse
+    (its buffer must be large enough)."""
+    import torch
+    C, N = _shapes(rho_g, rho_d)
+    if levels is None:
+        levels = tape_levels_needed(rho_g, rho_d, t_s, dt, stream=stream)
+    nbytes = tape_bytes(C, N, levels)
+    if C > 0 and nbytes == 0:
+        raise DragExpmError(f"bad tape geometry: ncells={C} nspecies={N} levels={levels}")
+    if tape is None or tape.nbytes < nbytes:
+        tape = Tape(torch.empty((max(nbytes, 1),), dtype=torch.uint8, device=rho_g.device), C, N, levels)
+    else:
+        tape = Tape(tape.buf, C, N, levels)
+    if v_out is None:
+        v_out = torch.empty_like(v_in)
+    args = [_f64_cuda("rho_g", rho_g, (C,)), _f64_cuda("rho_d", rho_d, (N, C)), _f64_cuda("t_s", t_s, (N, C))]
+    _check(load_library().drag_expm_apply_taped(C, N, *args, float(dt), _f64_cuda("v_in", v_in, (3, N + 1, C)),
+                                                _f64_cuda("v_out", v_out, (3, N + 1, C)), int(levels),
+                                                ctypes.c_void_p(tape.buf.data_ptr()), tape.nbytes,
+                                                _stream_handle(stream)))
+    return v_out, tape
+
+
 def backward(rho_g, rho_d, t_s, dt: float, v_in, grad_v_out, need_v_in=True, need_rho_g=True, need_rho_d=True,
-             need_t_s=True, out=None, stream=None):
+             need_t_s=True, out=None, stream=None, tape=None):
     """Adjoint of :func:`apply`: returns (grad_v_in, grad_rho_g, grad_rho_d, grad_t_s),
     None for the ones not requested. ``out`` may pass preallocated output tensors
-    (a 4-tuple, None entries are not computed)."""
+    (a 4-tuple, None entries are not computed). ``tape``: a Tape from
+    :func:`apply_taped` on these inputs (drag_expm_backward_taped; same gradients,
+    less FP64 work)."""
     import torch
     C, N = _shapes(rho_g, rho_d)
     dev = rho_g.device
@@ -275,9 +348,17 @@ def backward(rho_g, rho_d, t_s, dt: float, v_in, grad_v_out, need_v_in=True, nee
     args = [_f64_cuda("rho_g", rho_g, (C,)), _f64_cuda("rho_d", rho_d, (N, C)), _f64_cuda("t_s", t_s, (N, C))]
     vi = _f64_cuda("v_in", v_in, (3, N + 1, C))
     go = _f64_cuda("grad_v_out", grad_v_out, (3, N + 1, C))
-    _check(load_library().drag_expm_backward(C, N, *args, float(dt), vi, go, _opt_ptr("grad_v_in", gvi, (3, N + 1, C)),
-                                             _opt_ptr("grad_rho_g", grg, (C,)), _opt_ptr("grad_rho_d", grd, (N, C)),
-                                             _opt_ptr("grad_t_s", gts, (N, C)), _stream_handle(stream)))
+    outs = [_opt_ptr("grad_v_in", gvi, (3, N + 1, C)), _opt_ptr("grad_rho_g", grg, (C,)),
+            _opt_ptr("grad_rho_d", grd, (N, C)), _opt_ptr("grad_t_s", gts, (N, C))]
+    if tape is None:
+        _check(load_library().drag_expm_backward(C, N, *args, float(dt), vi, go, *outs, _stream_handle(stream)))
+    else:
+        if (tape.ncells, tape.nspecies) != (C, N):
+            raise DragExpmError(f"tape written for ncells={tape.ncells} nspecies={tape.nspecies}, "
+                                f"called with ncells={C} nspecies={N}")
+        _check(load_library().drag_expm_backward_taped(C, N, *args, float(dt), vi, go, *outs, tape.levels,
+                                                       ctypes.c_void_p(tape.buf.data_ptr()), tape.nbytes,
+                                                       _stream_handle(stream)))
     return gvi, grg, grd, gts
 
 
@@ -306,19 +387,49 @@ def _autograd_function():
                                           need_rho_g=need[0], need_rho_d=need[1], need_t_s=need[2])
             return grg, grd, gts, None, gvi
 
-    return _DragExpm
+    class _DragExpmTaped(torch.autograd.Function):
+        """DragExpm whose forward records the adjoint tape (apply_taped) and whose
+        backward reads it: identical values and gradients, less FP64 work in the
+        backward for a tape of about ncells * levels * 4 (N+1)(N+2) bytes.
+
+        forward(rho_g, rho_d, t_s, dt, v_in, levels=None)."""
+
+        @staticmethod
+        def forward(ctx, rho_g, rho_d, t_s, dt, v_in, levels=None):
+            rg, rd, ts = rho_g.contiguous(), rho_d.contiguous(), t_s.contiguous()
+            v_out, tape = apply_taped(rg, rd, ts, float(dt), v_in.contiguous(), levels=levels)
+            ctx.save_for_backward(rho_g, rho_d, t_s, v_in)
+            ctx.dt = float(dt)
+            ctx.tape = tape
+            return v_out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            rho_g, rho_d, t_s, v_in = ctx.saved_tensors
+            need = ctx.needs_input_grad
+            gvi, grg, grd, gts = backward(rho_g.contiguous(), rho_d.contiguous(), t_s.contiguous(), ctx.dt,
+                                          v_in.contiguous(), grad_out.contiguous(), need_v_in=need[4],
+                                          need_rho_g=need[0], need_rho_d=need[1], need_t_s=need[2], tape=ctx.tape)
+            ctx.tape = None
+            return grg, grd, gts, None, gvi, None
+
+    return _DragExpm, _DragExpmTaped
 
 
 class _LazyFunction:
-    _fn = None
+    _fns = None
+
+    def __init__(self, which: int):
+        self._which = which
 
     def apply(self, *args):
-        if _LazyFunction._fn is None:
-            _LazyFunction._fn = _autograd_function()
-        return _LazyFunction._fn.apply(*args)
+        if _LazyFunction._fns is None:
+            _LazyFunction._fns = _autograd_function()
+        return _LazyFunction._fns[self._which].apply(*args)
 
 
-DragExpm = _LazyFunction()
+DragExpm = _LazyFunction(0)
+DragExpmTaped = _LazyFunction(1)
 
 
 BLOCK_BYTES = 40   # sizeof(drag_block_t)

@@ -42,7 +42,40 @@ struct BwdArgs {
     double *g_vin, *g_rho_g, *g_rho_d, *g_ts;
     double dt;
     uint32_t *status;
+    // adjoint tape written by the forward (taped kernel only): cell c's
+    // fingerprint at thdr[c], its level t at tm + (c * levels + t) * P
+    const long long *thdr;
+    const double *tm;
+    int levels, P;
 };
+
+// 8-byte asynchronous copy global -> shared (no register staging), and the
+// wait for all of this thread's outstanding copies.
+__device__ __forceinline__ void cp_async8(double *sdst, const double *gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Starts copying one tape level (packed upper triangle) into the full
+// symmetric n x n matrix E; complete after cp_async_wait_all() + __syncwarp().
+// hp[p - 1] is entry p of the packing (p = 0 is (0, 0)).
+__device__ __forceinline__ void tape_load(int lane, int n, int ns, const unsigned short *hp, const double *src,
+                                          double *E) {
+    const int np = n * (n + 1) / 2;
+    for (int p = lane; p < np; p += 32) {
+        int i = 0, j = 0;
+        if (p > 0) {
+            const int c = hp[p - 1];
+            i = c >> 8;
+            j = c & 255;
+        }
+        cp_async8(E + i * ns + j, src + p);
+        if (i != j) cp_async8(E + j * ns + i, src + p);
+    }
+    cp_async_commit();
+}
 
 // Per-warp shared memory (doubles): E0, E1, L0, L1, then n-vectors: sigma,
 // tau, X_0f, X_ff, a_d and b_d (4 each), two buffers of y_d (3 each) and g_d (3).
@@ -83,13 +116,18 @@ __device__ __forceinline__ void bwd_xvec(int lane, int n, const DxVecs &V, doubl
 //   A (i, j) : Ln_ij = sum_k E_ik L_kj;
 //   B (i, j) : Ln_ij = Ln_ij + sum_k L_ik E_jk  (at least one round after its A);
 //   R (i)    : En_ii = 1 - tau_i sum_{k != i} En_ik sigma_k  (after every O).
-// trimmed: only the entries of E L + L E in row 0, column 0 and on the
-// diagonal, and no E^2 (the gradients read only those entries of the last L).
+// mode kSqFull: all of the above. kSqTrimmed: only the entries of E L + L E in
+// row 0, column 0 and on the diagonal, and no E^2 (the gradients read only
+// those entries of the last L). kSqLOnly: E L + L E, and no E^2 (read from the
+// tape instead).
+constexpr int kSqFull = 0, kSqTrimmed = 1, kSqLOnly = 2;
 __device__ __forceinline__ void bwd_square(int lane, int n, int ns, const unsigned short *od, const DxVecs &V,
-                                           const double *E, const double *L, double *En, double *Ln, bool trimmed) {
-    const int nO = trimmed ? 0 : n * (n - 1) / 2;
+                                           const double *E, const double *L, double *En, double *Ln, int mode) {
+    const bool trimmed = mode == kSqTrimmed;
+    const bool noE2 = mode != kSqFull;
+    const int nO = noE2 ? 0 : n * (n - 1) / 2;
     const int nL = trimmed ? 3 * n - 2 : n * n;
-    const int nR = trimmed ? 0 : n;
+    const int nR = noE2 ? 0 : n;
     const int a0 = nO;
     const int b0 = nL >= 32 ? nO + nL : ((nO + nL + 31) & ~31);
     const int r0 = b0 + nL;
@@ -155,8 +193,8 @@ __device__ __forceinline__ void bwd_square(int lane, int n, int ns, const unsign
     }
 }
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
-dx_backward_wpc(BwdArgs a, DxConsts K) {
+template <bool TAPE>
+__device__ __forceinline__ void bwd_wpc_body(const BwdArgs &a, const DxConsts &K) {
     extern __shared__ double smem[];
     const int n = a.N + 1, N = a.N, ns = dx_stride(n);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -224,6 +262,21 @@ dx_backward_wpc(BwdArgs a, DxConsts K) {
             continue;
         }
         const int m = K.mk[L.k];
+        // Taped cell: E_0 .. E_{s-2} come from the forward's tape, so neither
+        // the Taylor polynomial F nor the products E^2 before the last two
+        // squarings are formed here (E_0 streams in during the Taylor step).
+        bool taped = false;
+        const double *tcell = nullptr;
+        if (TAPE) {
+            const long long h = dx_cell_fingerprint(lane, N, rg, rd, ts, a.dt,
+                                                    ((unsigned long long)a.levels << 8) | (unsigned long long)n);
+            long long stored = 0;
+            if (lane == 0) stored = a.thdr[c];
+            stored = __shfl_sync(DX_FULL, stored, 0);
+            taped = stored == h && dx_tape_levels(L.s) <= a.levels;
+            tcell = a.tm + (size_t)c * a.levels * a.P;
+            if (taped) tape_load(lane, n, ns, hp, tcell, E0);
+        }
         {
             // rank-3 direction and its stationary block (kappa)
             double ad[3], bd[3], sa[3], sb[3];
@@ -260,7 +313,7 @@ dx_backward_wpc(BwdArgs a, DxConsts K) {
         // ---- Taylor and its derivative: F = b_m X + b_{m-1} I, dF = b_m H,
         // y_d = F a_d
         double *F = E0, *Fn = E1, *dF = L0, *dFn = L1, *y = yv0, *yn = yv1;
-        dx_wpc_taylor_init(lane, n, ns, m, K, V, F);
+        if (!taped) dx_wpc_taylor_init(lane, n, ns, m, K, V, F);
         for (int t = lane; t < nn; t += 32) {
             const int i = t / n, j = t - i * n;
             double acc = av[i] * bv[j];
@@ -276,7 +329,7 @@ dx_backward_wpc(BwdArgs a, DxConsts K) {
             // polynomial in X with constant term b_{jb+1} and X sigma = 0,
             // F a_3 = b_{jb+1} a_3. Finally y_d <- F_jb a_d = X y_d + b_jb a_d
             // (F_jb = X F + b_jb I: polynomials in X commute with X).
-            dx_wpc_horner_step(lane, n, ns, n_hp, hp, V, K.b[jb], F, Fn);
+            if (!taped) dx_wpc_horner_step(lane, n, ns, n_hp, hp, V, K.b[jb], F, Fn);
             const double b3 = K.b[jb + 1];
             // columns j >= 1 (6 FMAs each: X has two nonzeros per column there)
             // and column 0 (n + 4 FMAs) are dealt in separate rounds
@@ -305,14 +358,27 @@ dx_backward_wpc(BwdArgs a, DxConsts K) {
             double *t2 = dF; dF = dFn; dFn = t2;
             double *t3 = y; y = yn; yn = t3;
         }
-        dx_wpc_restore(lane, n, ns, V, F);
+        if (taped) {
+            F = E0;
+            Fn = E1;
+            cp_async_wait_all();
+        } else {
+            dx_wpc_restore(lane, n, ns, V, F);
+        }
         __syncwarp();
 
         // ---- squarings: (E, L) <- (E^2, E L + L E); the last one only forms
-        // the entries of L the gradients read and leaves E at E_{s-1}
+        // the entries of L the gradients read and leaves E at E_{s-1}. Taped,
+        // E_{sq+1} is loaded while the squaring forms L whenever the tape holds it.
         for (int sq = 0; sq < L.s; sq++) {
             const bool trimmed = sq == L.s - 1;
-            bwd_square(lane, n, ns, od, V, F, dF, Fn, dFn, trimmed);
+            const bool lonly = taped && sq + 1 < dx_tape_levels(L.s);
+            if (lonly) tape_load(lane, n, ns, hp, tcell + (size_t)(sq + 1) * a.P, Fn);
+            bwd_square(lane, n, ns, od, V, F, dF, Fn, dFn, trimmed ? kSqTrimmed : (lonly ? kSqLOnly : kSqFull));
+            if (lonly) {
+                cp_async_wait_all();
+                __syncwarp();
+            }
             if (!trimmed) {
                 double *t1 = F; F = Fn; Fn = t1;
             }
@@ -369,6 +435,18 @@ dx_backward_wpc(BwdArgs a, DxConsts K) {
     }
 }
 
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
+dx_backward_wpc(BwdArgs a, DxConsts K) {
+    bwd_wpc_body<false>(a, K);
+}
+
+// The same adjoint, reading E_0 .. E_{s-2} from the forward's tape where the
+// cell's fingerprint matches.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
+dx_backward_wpc_taped(BwdArgs a, DxConsts K) {
+    bwd_wpc_body<true>(a, K);
+}
+
 bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
 
 size_t bwd_smem_bytes(int n) {
@@ -377,28 +455,59 @@ size_t bwd_smem_bytes(int n) {
 
 }  // namespace
 
-extern "C" int drag_expm_backward(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
-                                  const double *t_s, double dt, const double *v_in, const double *grad_v_out,
-                                  double *grad_v_in, double *grad_rho_g, double *grad_rho_d, double *grad_t_s,
-                                  cudaStream_t stream) {
+static int backward_impl(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                         const double *t_s, double dt, const double *v_in, const double *grad_v_out,
+                         double *grad_v_in, double *grad_rho_g, double *grad_rho_d, double *grad_t_s, int32_t levels,
+                         const void *tape, size_t tape_bytes, bool taped, cudaStream_t stream) {
     if (ncells < 0 || nspecies < 1 || nspecies > DRAG_EXPM_NMAX || !(dt >= 0.0) || !std::isfinite(dt))
         return DRAG_EINVAL_SIZE;
+    if (taped && (levels < 1 || levels > DRAG_TAPE_MAX_LEVELS)) return DRAG_EINVAL_SIZE;
     if (ncells == 0) return DRAG_OK;
     if (!rho_g || !rho_d || !t_s || !v_in || !grad_v_out) return DRAG_ENULL;
+    if (taped && !tape) return DRAG_ENULL;
     const void *ptrs[] = {rho_g, rho_d, t_s, v_in, grad_v_out, grad_v_in, grad_rho_g, grad_rho_d, grad_t_s};
     for (const void *p : ptrs)
         if (p && !aligned8(p)) return DRAG_EALIGN;
+    if (taped && (reinterpret_cast<uintptr_t>(tape) & 255) != 0) return DRAG_EALIGN;
+    if (taped && tape_bytes < drag_expm_tape_bytes(ncells, nspecies, levels)) return DRAG_EWORKSPACE;
     uint32_t *st = dx_status_ptr();
     if (!st) return DRAG_ECUDA;
     if (!dx_once_per_device(1, [] {
             return cudaFuncSetAttribute(dx_backward_wpc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)bwd_smem_bytes(DX_NMAXF)) == cudaSuccess &&
+                   cudaFuncSetAttribute(dx_backward_wpc_taped, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)bwd_smem_bytes(DX_NMAXF)) == cudaSuccess;
         }))
         return DRAG_ECUDA;
     const int n = nspecies + 1;
     BwdArgs a{ncells, nspecies, rho_g, rho_d, t_s, v_in, grad_v_out, grad_v_in, grad_rho_g, grad_rho_d, grad_t_s,
-              dt, st};
+              dt, st, nullptr, nullptr, 0, 0};
+    if (taped) {
+        a.thdr = static_cast<const long long *>(tape);
+        a.tm = reinterpret_cast<const double *>(static_cast<const char *>(tape) + dx_tape_hdr_bytes(ncells));
+        a.levels = levels;
+        a.P = dx_tape_slot(n);
+    }
     const long long grid = (ncells + kCellsPerBlock - 1) / kCellsPerBlock;
-    dx_backward_wpc<<<(unsigned)grid, kWarpsPerBlock * 32, bwd_smem_bytes(n), stream>>>(a, dx_consts());
+    if (taped)
+        dx_backward_wpc_taped<<<(unsigned)grid, kWarpsPerBlock * 32, bwd_smem_bytes(n), stream>>>(a, dx_consts());
+    else
+        dx_backward_wpc<<<(unsigned)grid, kWarpsPerBlock * 32, bwd_smem_bytes(n), stream>>>(a, dx_consts());
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
+}
+
+extern "C" int drag_expm_backward(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                                  const double *t_s, double dt, const double *v_in, const double *grad_v_out,
+                                  double *grad_v_in, double *grad_rho_g, double *grad_rho_d, double *grad_t_s,
+                                  cudaStream_t stream) {
+    return backward_impl(ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, grad_v_out, grad_v_in, grad_rho_g, grad_rho_d,
+                         grad_t_s, 0, nullptr, 0, false, stream);
+}
+
+extern "C" int drag_expm_backward_taped(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                                        const double *t_s, double dt, const double *v_in, const double *grad_v_out,
+                                        double *grad_v_in, double *grad_rho_g, double *grad_rho_d, double *grad_t_s,
+                                        int32_t levels, const void *tape, size_t tape_bytes, cudaStream_t stream) {
+    return backward_impl(ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, grad_v_out, grad_v_in, grad_rho_g, grad_rho_d,
+                         grad_t_s, levels, tape, tape_bytes, true, stream);
 }

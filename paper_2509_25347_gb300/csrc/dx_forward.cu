@@ -39,8 +39,16 @@ struct FwdArgs {
     double *heat;          // optional per-cell dissipated kinetic energy
 };
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 7)
-dx_forward_wpc(FwdArgs a, DxConsts K) {
+// Adjoint tape of a launch (hdr null: none): cell c's fingerprint at hdr[c],
+// its level t at m + (c * levels + t) * P.
+struct FwdTape {
+    long long *hdr;
+    double *m;
+    int levels, P;
+};
+
+template <bool TAPE>
+__device__ __forceinline__ void fwd_wpc_body(const FwdArgs &a, const DxConsts &K, const FwdTape &tp) {
     extern __shared__ double smem[];
     const int n = a.N + 1;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -64,9 +72,22 @@ dx_forward_wpc(FwdArgs a, DxConsts K) {
         k = __shfl_sync(DX_FULL, k, 0);
         const long long c = base + k;
         if (k >= kCellsPerBlock || c >= a.C) break;
+        DxTapeCell tc{nullptr, nullptr, 0, 0};
+        if (TAPE) tc = DxTapeCell{tp.hdr + c, tp.m + (size_t)c * tp.levels * tp.P, tp.levels, tp.P};
         dx_wpc_forward_cell(lane, a.N, a.rho_g + c, a.rho_d + c, a.t_s + c, a.v_in + c, a.v_out + c, a.C, a.dt, K, wsm,
-                            od, hp, a.status, a.heat ? a.heat + c : nullptr);
+                            od, hp, a.status, a.heat ? a.heat + c : nullptr, (double *)nullptr, tc);
     }
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 7)
+dx_forward_wpc(FwdArgs a, DxConsts K) {
+    fwd_wpc_body<false>(a, K, FwdTape{nullptr, nullptr, 0, 0});
+}
+
+// The same update, also recording each cell's adjoint tape.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 7)
+dx_forward_wpc_taped(FwdArgs a, DxConsts K, FwdTape tp) {
+    fwd_wpc_body<true>(a, K, tp);
 }
 
 // Mixed-precision forward: FP64 inputs, outputs, set-up and Algorithm 2 (on
@@ -190,6 +211,41 @@ extern "C" int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *r
                                const double *t_s, double dt, const double *v_in, double *v_out,
                                cudaStream_t stream) {
     return apply_impl(dx_consts(), ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, nullptr, stream);
+}
+
+extern "C" size_t drag_expm_tape_bytes(int64_t ncells, int32_t nspecies, int32_t levels) {
+    if (ncells < 0 || nspecies < 1 || nspecies > DRAG_EXPM_NMAX || levels < 1 || levels > DRAG_TAPE_MAX_LEVELS)
+        return 0;
+    return dx_tape_hdr_bytes(ncells) + sizeof(double) * (size_t)ncells * (size_t)levels * dx_tape_slot(nspecies + 1);
+}
+
+extern "C" int32_t drag_expm_tape_levels(int32_t sstar) { return sstar < 0 ? 0 : dx_tape_levels(sstar); }
+
+extern "C" int drag_expm_apply_taped(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
+                                     const double *t_s, double dt, const double *v_in, double *v_out, int32_t levels,
+                                     void *tape, size_t tape_bytes, cudaStream_t stream) {
+    int rc = check_common(ncells, nspecies, rho_g, rho_d, t_s, dt);
+    if (rc != DRAG_OK) return rc;
+    if (levels < 1 || levels > DRAG_TAPE_MAX_LEVELS) return DRAG_EINVAL_SIZE;
+    if (ncells == 0) return DRAG_OK;
+    if (!v_in || !v_out || !tape) return DRAG_ENULL;
+    if (!aligned8(v_in) || !aligned8(v_out) || (reinterpret_cast<uintptr_t>(tape) & 255) != 0) return DRAG_EALIGN;
+    if (tape_bytes < drag_expm_tape_bytes(ncells, nspecies, levels)) return DRAG_EWORKSPACE;
+    uint32_t *st = dx_status_ptr();
+    if (!st) return DRAG_ECUDA;
+    if (!dx_once_per_device(5, [] {
+            return cudaFuncSetAttribute(dx_forward_wpc_taped, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)dx_forward_smem_bytes(DX_NMAXF)) == cudaSuccess;
+        }))
+        return DRAG_ECUDA;
+    const int n = nspecies + 1;
+    FwdArgs a{ncells, nspecies, rho_g, rho_d, t_s, v_in, v_out, dt, st, nullptr};
+    FwdTape tp{static_cast<long long *>(tape),
+               reinterpret_cast<double *>(static_cast<char *>(tape) + dx_tape_hdr_bytes(ncells)), levels,
+               dx_tape_slot(n)};
+    const long long grid = (ncells + kCellsPerBlock - 1) / kCellsPerBlock;
+    dx_forward_wpc_taped<<<(unsigned)grid, kWarpsPerBlock * 32, dx_forward_smem_bytes(n), stream>>>(a, dx_consts(), tp);
+    return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }
 
 int dx_launch_forward_f32(const DxConsts &K, long long ncells, int nspecies, const double *rho_g,

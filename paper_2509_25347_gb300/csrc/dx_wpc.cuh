@@ -238,6 +238,62 @@ __device__ __forceinline__ void dx_wpc_restore(int lane, int n, int ns, const Dx
     }
 }
 
+// The last squarings are replaced by repeated applications: P^(2^q) v is
+// computed as P (P (... P v)) with q = min(s*, DX_APPLY_Q). One squaring costs
+// n(n+1)/2 tasks of n FP64 operations, one application 3n tasks of n + 2, so
+// for n = 17 two squarings and one application (~206 warp-level FP64
+// instructions) become four applications (~152).
+#define DX_APPLY_Q 2
+
+// ------------------------------------------------------------ adjoint tape
+// The forward can record the restored symmetric iterates E_0 .. E_{s-q} it
+// forms (q = min(s, DX_APPLY_Q); E_t = exp(2^(t-s) S) up to rounding), so the
+// adjoint, which needs every E_t of the squaring phase, reads them instead of
+// recomputing the Taylor step and the squarings. Level t of a cell is its
+// upper triangle, row major with the diagonal, in a slot of dx_tape_slot(n)
+// doubles; entry (i, j), i <= j, at dx_tape_index(n, i, j).
+__host__ __device__ __forceinline__ int dx_tape_index(int n, int i, int j) { return i * (2 * n - i + 1) / 2 + j - i; }
+__host__ __device__ __forceinline__ int dx_tape_slot(int n) { return (n * (n + 1) / 2 + 15) & ~15; }   // 128-byte slots
+// Levels a cell with s* = s stores: E_0 .. E_{s-q}.
+__host__ __device__ __forceinline__ int dx_tape_levels(int s) { return s - (s < DX_APPLY_Q ? s : DX_APPLY_Q) + 1; }
+// Bytes of the fingerprint words that open a tape of C cells (256-byte multiple).
+__host__ __device__ __forceinline__ size_t dx_tape_hdr_bytes(long long C) {
+    return ((size_t)C * sizeof(long long) + 255) & ~(size_t)255;
+}
+
+// splitmix64 finaliser (Steele, Lea and Flood, OOPSLA 2014).
+__device__ __forceinline__ unsigned long long dx_mix64(unsigned long long x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ULL;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebULL;
+    x ^= x >> 31;
+    return x;
+}
+
+// Fingerprint of a cell's inputs (rho_g, dt, and rho_d, t_s of species f on
+// lane f), salted with the tape geometry; warp collective, same value on every
+// lane. A tape entry is used only where the adjoint's inputs reproduce the
+// fingerprint the forward stored, so a stale tape costs time, not accuracy.
+__device__ __forceinline__ long long dx_cell_fingerprint(int lane, int N, double rg, double rd, double ts, double dt,
+                                                         unsigned long long salt) {
+    unsigned long long h = 0;
+    if (lane >= 1 && lane <= N)
+        h = dx_mix64((unsigned long long)dx_bits(rd) + 0x9e3779b97f4a7c15ULL * (unsigned long long)lane) ^
+            dx_mix64((unsigned long long)dx_bits(ts) ^ (0xd1b54a32d192ed03ULL * (unsigned long long)lane));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h ^= __shfl_xor_sync(DX_FULL, h, o);
+    h = dx_mix64(h ^ dx_mix64((unsigned long long)dx_bits(rg) ^ dx_mix64((unsigned long long)dx_bits(dt) ^ salt)));
+    return (long long)h;
+}
+
+// One cell's view of a tape (pointers already offset to the cell; m null: no tape).
+struct DxTapeCell {
+    long long *hdr;   // fingerprint word
+    double *m;        // level 0; level t at m + t * P
+    int levels, P;
+};
+
 // Row-sum restoration of the starting matrix (t = 0) and s squarings with
 // restoration (t = 1..s), run on the round schedule generated by sched.py:
 // each round gives every lane one task of n FP64 operations, either an
@@ -252,14 +308,19 @@ __device__ __forceinline__ void dx_wpc_restore(int lane, int n, int ns, const Dx
 // product (the stale diagonal of the destination is multiplied by an exact 0),
 // which costs one more FMA per round but drops the per-term index select that
 // dominates instruction issue once the arithmetic is FP32.
+// tape (FP64 only, may be null): the lane that computes an entry of E_t also
+// stores it at tape[t * tP + dx_tape_index(n, i, j)] (entries of E_0 other than
+// its diagonal are the caller's to store).
 template <typename T>
 __device__ __forceinline__ int dx_wpc_square_chain(int lane, int n, int ns, int s, T *B0, T *B1, int p0,
-                                                   const DxVecsT<T> &V, const T *wz = nullptr) {
+                                                   const DxVecsT<T> &V, const T *wz = nullptr,
+                                                   double *tape = nullptr, int tP = 0) {
     const unsigned short *tab = dx_sched_task + (size_t)dx_sched_off[n] * 32;
     const unsigned short *endr = dx_sched_end + n * (DX_SCHED_H + 1);
     int remaining = s, parity = p0;
     do {
         const int h = remaining < DX_SCHED_H ? remaining : DX_SCHED_H;
+        const int lvl0 = s - remaining;   // level of this chunk's starting matrix
         const int nr = endr[h];
         for (int r = 0; r < nr; r++) {
             const unsigned int code = tab[r * 32 + lane];
@@ -295,6 +356,8 @@ __device__ __forceinline__ int dx_wpc_square_chain(int lane, int n, int ns, int 
                     dst[i * ns + j] = res;
                     dst[j * ns + i] = res;
                 }
+                if (sizeof(T) == sizeof(double) && tape)
+                    tape[(size_t)(lvl0 + t) * tP + dx_tape_index(n, i, j)] = (double)res;
             }
             __syncwarp();
         }
@@ -325,12 +388,6 @@ __device__ __forceinline__ void dx_build_pairs_warp(int lane, int n, unsigned sh
 // them) and two buffers of (v, sigma o v) for the repeated apply (2 x 2 x 3).
 __host__ __device__ __forceinline__ int dx_wpc_fwd_warp_doubles(int n) { return 2 * n * dx_stride(n) + 19 * n; }
 
-// The last squarings are replaced by repeated applications: P^(2^q) v is
-// computed as P (P (... P v)) with q = min(s*, DX_APPLY_Q). One squaring costs
-// n(n+1)/2 tasks of n FP64 operations, one application 3n tasks of n + 2, so
-// for n = 17 two squarings and one application (~206 warp-level FP64
-// instructions) become four applications (~152).
-#define DX_APPLY_Q 2
 
 // Per-cell vectors of the forward routines, laid out from vbase: sigma, tau,
 // X_0f, X_ff (4 n), the input velocities (3 n) and two buffers of
@@ -483,13 +540,15 @@ __device__ __forceinline__ void dx_wpc_apply_tail(int lane, int n, int ns, const
 // Forward update of one cell by one warp (warp-uniform arguments). Element i
 // of a per-species array is at p[i * stride]; velocity (d, f) at
 // p[(d * n + f) * stride]. od/hp: pair tables for this n. v_out may alias v_in.
-// heat: see dx_wpc_apply_tail.
+// heat: see dx_wpc_apply_tail. tp (FP64 only; tp.hdr null: none): the cell's
+// adjoint tape, written when its levels fit (the fingerprint word always).
 template <typename T>
 __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const double *rgp, const double *rdp,
                                                     const double *tsp, const double *vip, double *vop,
                                                     long long stride, double dt, const DxConsts &K, T *wsm,
                                                     const unsigned short *od, const unsigned short *hp,
-                                                    uint32_t *status, double *heat = nullptr, T *wz = nullptr) {
+                                                    uint32_t *status, double *heat = nullptr, T *wz = nullptr,
+                                                    DxTapeCell tp = DxTapeCell{nullptr, nullptr, 0, 0}) {
     const int n = N + 1, ns = dx_stride(n);
     const int n_hp = n * (n + 1) / 2 - 1;
     T *E0 = wsm;
@@ -497,7 +556,6 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
     DxVecsT<T> V;
     DxFwdBufsT<T> B;
     dx_wpc_fwd_layout(E1 + n * ns, n, V, B);
-    (void)od;
 
     DxCellIn c;
     dx_wpc_load_cell(lane, N, rgp, rdp, tsp, vip, stride, c);
@@ -507,6 +565,14 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
         return;
     }
     const int m = K.mk[L.k];
+    double *tape = nullptr;
+    if (sizeof(T) == sizeof(double) && tp.hdr) {
+        const long long h = dx_cell_fingerprint(lane, N, c.rg, c.rd, c.ts, dt,
+                                                ((unsigned long long)tp.levels << 8) | (unsigned long long)n);
+        const bool fits = dx_tape_levels(L.s) <= tp.levels;
+        if (lane == 0) *tp.hdr = fits ? h : ~h;
+        if (fits) tape = tp.m;
+    }
 
     // Taylor polynomial T_m(X) by Horner's rule in X
     T *F = E0, *G = E1;
@@ -515,6 +581,14 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
         dx_wpc_horner_step(lane, n, ns, n_hp, hp, V, (T)K.b[j], F, G);
         __syncwarp();
         T *tmp = F; F = G; G = tmp;
+    }
+
+    if (tape) {
+        // level 0 off the diagonal (the chain's first restoration stores the diagonal)
+        for (int t = lane; t < n * (n - 1) / 2; t += 32) {
+            const int p = od[t], i = p >> 8, j = p & 255;
+            tape[dx_tape_index(n, i, j)] = (double)F[i * ns + j];
+        }
     }
 
     // row-sum restoration, then s - q squarings (Eq. ExpEq1 with n = 2^s), each
@@ -528,6 +602,6 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
         }
         __syncwarp();
     }
-    F = dx_wpc_square_chain(lane, n, ns, L.s - q, E0, E1, F == E1 ? 1 : 0, V, wz) ? E1 : E0;
+    F = dx_wpc_square_chain(lane, n, ns, L.s - q, E0, E1, F == E1 ? 1 : 0, V, wz, tape, tp.P) ? E1 : E0;
     dx_wpc_apply_tail(lane, n, ns, V, B, F, q, c, L.sg, vop, stride, heat);
 }

@@ -155,6 +155,31 @@ def test_host_argument_errors(lib):
     assert bwd(10, 4, good, good, good, 1.0, good, null, null, null, null, null, s) == -2
     assert bwd(10, 4, good, good, good, 1.0, good, good, bad_align, null, null, null, s) == -3
     assert bwd(0, 4, null, null, null, 1.0, null, null, null, null, null, null, s) == 0
+    # adjoint tape: geometry, then argument errors of the taped forward and adjoint
+    tb = lib.drag_expm_tape_bytes
+    assert tb(-1, 4, 3) == 0 and tb(10, 0, 3) == 0 and tb(10, 4, 0) == 0 and tb(10, 4, 2049) == 0
+    assert tb(10, 16, 3) == 256 + 8 * 10 * 3 * 160          # 153 packed entries in 160-double slots
+    assert tb(100, 1, 1) == 1024 + 8 * 100 * 16
+    assert lib.drag_expm_tape_levels(-1) == 0
+    assert [lib.drag_expm_tape_levels(k) for k in range(6)] == [1, 1, 1, 2, 3, 4]
+    tape, big = ctypes.c_void_p(1 << 20), 1 << 40
+    at = lib.drag_expm_apply_taped
+    assert at(10, 4, good, good, good, 1.0, good, good, 0, tape, big, s) == -1
+    assert at(10, 4, good, good, good, 1.0, good, good, 2049, tape, big, s) == -1
+    assert at(10, 4, good, good, good, float("nan"), good, good, 3, tape, big, s) == -1
+    assert at(10, 4, good, good, good, 1.0, good, good, 3, null, big, s) == -2
+    assert at(10, 4, good, good, good, 1.0, null, good, 3, tape, big, s) == -2
+    assert at(10, 4, good, good, good, 1.0, good, good, 3, ctypes.c_void_p((1 << 20) + 128), big, s) == -3
+    assert at(10, 4, good, good, good, 1.0, good, bad_align, 3, tape, big, s) == -3
+    assert at(10, 4, good, good, good, 1.0, good, good, 3, tape, tb(10, 4, 3) - 8, s) == -5
+    assert at(0, 4, null, null, null, 1.0, null, null, 3, null, 0, s) == 0
+    bt = lib.drag_expm_backward_taped
+    assert bt(10, 4, good, good, good, 1.0, good, good, null, null, null, null, 0, tape, big, s) == -1
+    assert bt(10, 4, good, good, good, 1.0, good, good, null, null, null, null, 3, null, big, s) == -2
+    assert bt(10, 4, good, good, good, 1.0, good, good, null, null, null, null, 3, ctypes.c_void_p(4104), big,
+              s) == -3
+    assert bt(10, 4, good, good, good, 1.0, good, good, null, null, null, null, 3, tape, 64, s) == -5
+    assert bt(0, 4, null, null, null, 1.0, null, null, null, null, null, null, 3, null, 0, s) == 0
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
