@@ -48,10 +48,10 @@ KERNEL_SOURCES = {
 }
 MEASURED_TRAFFIC = {
     ("mrn_n16_128cube", "dx_forward_wpc"): {
-        "sources_sha256": "8d8f9e4a2bf43d8a3d3cb7ca289ec2df92bea32f1495dcbc96d50c6e05c36df0",
-        "bytes_per_cell": (187.130624e6 + 80.892416e6) / 262144,
+        "sources_sha256": "a2dd9024b1839328c5ac6a243bbb422ab1c89b0949c93d183d8017874761bc49",
+        "bytes_per_cell": (186.905856e6 + 81.047552e6) / 262144,
         # FP64 FLOPs the kernel executes: thread-level (2 DFMA + DADD + DMUL) per cycle x elapsed cycles
-        "executed_flop_per_cell": (2 * 233.436163 + 16.006212 + 3.464271) * 48791449.513 / 262144,
+        "executed_flop_per_cell": (2 * 233.345985 + 16.000029 + 3.640165) * 48810305.395 / 262144,
         "capture": "profiles/dx_forward_wpc_mrn_n16.md",
     },
 }
