@@ -379,15 +379,17 @@ int drag_expm_apply_batched_noalloc(int64_t nblocks, const drag_block_t *blocks,
                                     cudaStream_t stream);
 
 /*
- * Execution modes. Each matrix size n = N + 1 runs in one of three kernel
- * families (all compute the same update, Eq. ExacSolEqu by Algorithm 6):
- * one lane per cell with the matrix in registers (n <= 6), one lane per cell
- * with it in shared memory (n <= 12), or one warp per cell (any n). Defaults:
- * registers up to n = 6, shared memory up to n = 12, warp above.
+ * Execution modes. Each matrix size n = N + 1 runs in one of the kernel
+ * families below (all compute the same update, Eq. ExacSolEqu by Algorithm 6):
+ * one lane per cell with its matrices in registers (n <= 6), in shared memory
+ * (n <= 12), or the current one in registers and the next in shared memory
+ * (n = 7..12); or one warp per cell (any n). Defaults: registers up to n = 6,
+ * hybrid up to n = 12, warp above.
  */
 #define DRAG_MODE_WARP_PER_CELL 0
 #define DRAG_MODE_LANE_REGISTERS 1
 #define DRAG_MODE_LANE_SHARED 2
+#define DRAG_MODE_LANE_HYBRID 3   /* lane per cell, current matrix in registers, next in shared memory (n = 7..12) */
 
 /* drag_expm_set_mode / drag_expm_get_mode — mode for nspecies on the current
  * device (host only). set returns DRAG_EINVAL_SIZE for an invalid pair. */

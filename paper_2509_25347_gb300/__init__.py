@@ -503,6 +503,7 @@ def select(rho_g, rho_d, t_s, dt: float, stream=None, ubits: int = 53):
 MODE_WARP_PER_CELL = 0
 MODE_LANE_REGISTERS = 1
 MODE_LANE_SHARED = 2
+MODE_LANE_HYBRID = 3
 
 
 def set_mode(nspecies: int, mode: int) -> None:

@@ -227,27 +227,31 @@ struct MainArgs {
     int warp_doubles;   // per-warp shared-memory slice (doubles)
 };
 
-template <int NF, bool SMEM>
+template <int NF, int ST>
 __device__ __forceinline__ void lpc_item(int lane, const MainArgs &a, const Desc &d, long long c, const DxConsts &K,
                                          const double *bsh, double *wsm) {
     const long long C = d.ncells;
-    dx_lpc_forward_cell<NF, SMEM>(lane, a.rho_g + d.cell_offset + c, a.rho_d + d.dust_offset + c,
+    dx_lpc_forward_cell<NF, ST>(lane, a.rho_g + d.cell_offset + c, a.rho_d + d.dust_offset + c,
                                   a.t_s + d.dust_offset + c, a.v_in + d.vel_offset + c, a.v_out + d.vel_offset + c, C,
                                   d.dt, K, bsh, wsm, a.status);
 }
 
 __device__ __forceinline__ void lpc_dispatch(int n, int mode, int lane, const MainArgs &a, const Desc &d, long long c,
                                              const DxConsts &K, const double *bsh, double *wsm) {
-    const bool reg = mode == DX_MODE_LPC_REG;
+    // the batched modes are fixed (dx_batch_modes): registers up to n = 6, hybrid above
+    (void)mode;
     switch (n) {
-        case 2: reg ? lpc_item<2, false>(lane, a, d, c, K, bsh, wsm) : lpc_item<2, true>(lane, a, d, c, K, bsh, wsm); break;
-        case 3: reg ? lpc_item<3, false>(lane, a, d, c, K, bsh, wsm) : lpc_item<3, true>(lane, a, d, c, K, bsh, wsm); break;
-        case 4: reg ? lpc_item<4, false>(lane, a, d, c, K, bsh, wsm) : lpc_item<4, true>(lane, a, d, c, K, bsh, wsm); break;
-        case 5: reg ? lpc_item<5, false>(lane, a, d, c, K, bsh, wsm) : lpc_item<5, true>(lane, a, d, c, K, bsh, wsm); break;
-        case 6: reg ? lpc_item<6, false>(lane, a, d, c, K, bsh, wsm) : lpc_item<6, true>(lane, a, d, c, K, bsh, wsm); break;
-        case 7: lpc_item<7, true>(lane, a, d, c, K, bsh, wsm); break;
-        case 8: lpc_item<8, true>(lane, a, d, c, K, bsh, wsm); break;
-        case 9: lpc_item<9, true>(lane, a, d, c, K, bsh, wsm); break;
+#define DX_ITEM(NF, ST) \
+    case NF: lpc_item<NF, ST>(lane, a, d, c, K, bsh, wsm); break;
+        DX_ITEM(2, DX_LPC_REGS)
+        DX_ITEM(3, DX_LPC_REGS)
+        DX_ITEM(4, DX_LPC_REGS)
+        DX_ITEM(5, DX_LPC_REGS)
+        DX_ITEM(6, DX_LPC_REGS)
+        DX_ITEM(7, DX_LPC_HYBRID)
+        DX_ITEM(8, DX_LPC_HYBRID)
+        DX_ITEM(9, DX_LPC_HYBRID)
+#undef DX_ITEM
         default: break;
     }
 }
@@ -358,16 +362,20 @@ void warp_doubles_for(const Modes &M, int n_max, int *wpc, int *lpc, bool *has_w
             continue;
         }
         *has_lpc = true;
-        if (M.m[n] == DX_MODE_LPC_SMEM) {
+        const bool hyb = M.m[n] == DX_MODE_LPC_HYB;
+        if (M.m[n] == DX_MODE_LPC_SMEM || hyb) {
             switch (n) {
-                case 2: need = dx_lpc_warp_smem_doubles<2>(); break;
-                case 3: need = dx_lpc_warp_smem_doubles<3>(); break;
-                case 4: need = dx_lpc_warp_smem_doubles<4>(); break;
-                case 5: need = dx_lpc_warp_smem_doubles<5>(); break;
-                case 6: need = dx_lpc_warp_smem_doubles<6>(); break;
-                case 7: need = dx_lpc_warp_smem_doubles<7>(); break;
-                case 8: need = dx_lpc_warp_smem_doubles<8>(); break;
-                case 9: need = dx_lpc_warp_smem_doubles<9>(); break;
+#define DX_NEED(NF) \
+    case NF: need = hyb ? dx_lpc_warp_smem_doubles<NF, DX_LPC_HYBRID>() : dx_lpc_warp_smem_doubles<NF, DX_LPC_SHARED>(); break;
+                DX_NEED(2)
+                DX_NEED(3)
+                DX_NEED(4)
+                DX_NEED(5)
+                DX_NEED(6)
+                DX_NEED(7)
+                DX_NEED(8)
+                DX_NEED(9)
+#undef DX_NEED
                 default: break;
             }
         }
@@ -383,13 +391,13 @@ bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0;
 // so the 32 lanes of a lane-per-cell item run exactly their own Taylor order
 // and squaring count; the standalone kernels' mode table (measured on
 // unsorted cells, whose warps run the largest s* of 32 cells) does not
-// carry over. Lane per cell up to n = kBatchLpcNMax (matrix in registers up to
-// DX_LPC_REG_NMAX), warp per cell above.
+// carry over. Lane per cell up to n = kBatchLpcNMax (matrices in registers up
+// to DX_LPC_REG_NMAX, the hybrid storage above), warp per cell above.
 Modes dx_batch_modes() {
     Modes M;
     for (int n = 0; n <= DX_NMAXF; n++)
         M.m[n] = (n < 2 || n > kBatchLpcNMax) ? DX_MODE_WPC
-                                               : (n <= DX_LPC_REG_NMAX ? DX_MODE_LPC_REG : DX_MODE_LPC_SMEM);
+                                               : (n <= DX_LPC_REG_NMAX ? DX_MODE_LPC_REG : DX_MODE_LPC_HYB);
     return M;
 }
 

@@ -193,7 +193,7 @@ static int apply_impl(const DxConsts &K, int64_t ncells, int32_t nspecies, const
     const int n = nspecies + 1;
     const int mode = dx_mode_for(n);
     if (mode != DX_MODE_WPC)
-        return dx_launch_forward_lpc(K, n, mode == DX_MODE_LPC_SMEM, ncells, rho_g, rho_d, t_s, v_in, v_out, dt, st, heat,
+        return dx_launch_forward_lpc(K, n, dx_lpc_store(mode), ncells, rho_g, rho_d, t_s, v_in, v_out, dt, st, heat,
                                      stream);
     const size_t smem = dx_forward_smem_bytes(n);
     if (!dx_once_per_device(0, [] {

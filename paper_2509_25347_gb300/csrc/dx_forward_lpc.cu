@@ -9,12 +9,13 @@ namespace {
 
 constexpr int kTile = 512;   // largest tile of cells a block sorts and runs
 
-// Threads per block: 4 warps, or 2 warps when the matrix lives in shared
-// memory and n >= 9: there the slices (32 doubles per packed entry, 32 KB per
-// warp at n = 9) set the residency and smaller blocks pack more warps onto an
-// SM (measured: 1.3x at n = 9; 4-warp blocks stay faster up to n = 8).
-template <int NF, bool SMEM>
-__host__ __device__ constexpr int lpc_threads() { return (SMEM && NF >= 9) ? 64 : 128; }
+// Threads per block: 4 warps, or 2 warps when shared memory holds part of the
+// matrices and n >= 9: there the slices (32 doubles per packed entry, 32 KB per
+// warp at n = 9 with both buffers shared) set the residency and smaller blocks
+// pack more warps onto an SM (measured: 1.3x at n = 9; 4-warp blocks stay
+// faster up to n = 8).
+template <int NF, int ST>
+__host__ __device__ constexpr int lpc_threads() { return (ST != DX_LPC_REGS && NF >= 9) ? 64 : 128; }
 
 // A warp runs the largest Taylor order and squaring count of its 32 cells, so
 // each block first orders a tile of rounds x threads consecutive cells (the
@@ -39,8 +40,12 @@ __device__ __forceinline__ unsigned int cost_proxy(const double *rgp, const doub
     return (nrm >= 0.0f && b < 0x7f800000u) ? b : 0x7f800000u;   // non-finite and NaN last among valid cells
 }
 
-template <int NF, bool SMEM>
-__global__ void __launch_bounds__(lpc_threads<NF, SMEM>())
+// Register ceiling per thread.
+template <int NF, int ST>
+__host__ __device__ constexpr int lpc_max_regs() { return (ST == DX_LPC_HYBRID && NF == 9) ? 200 : 255; }
+
+template <int NF, int ST>
+__global__ void __launch_bounds__(lpc_threads<NF, ST>()) __maxnreg__((lpc_max_regs<NF, ST>()))
 dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d, const double *t_s,
                const double *v_in, double *v_out, double dt, uint32_t *status, double *heat, DxConsts K) {
     extern __shared__ double smem[];
@@ -48,7 +53,7 @@ dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d
     __shared__ unsigned short order[kTile];       // sorted position -> tile index
     double *bsh = smem;
     for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
-    constexpr int kThreads = lpc_threads<NF, SMEM>();
+    constexpr int kThreads = lpc_threads<NF, ST>();
     const int tile = rounds * kThreads;
     const long long base = (long long)blockIdx.x * tile;
     if (rounds > 1) {
@@ -72,56 +77,72 @@ dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    double *wsm = SMEM ? smem + 32 + (threadIdx.x >> 5) * dx_lpc_warp_smem_doubles<NF>() : nullptr;
+    double *wsm = ST != DX_LPC_REGS ? smem + 32 + (threadIdx.x >> 5) * dx_lpc_warp_smem_doubles<NF, ST>() : nullptr;
     for (int r = 0; r < rounds; r++) {
         const long long c = base + order[r * kThreads + threadIdx.x];
         if (c < C)
-            dx_lpc_forward_cell<NF, SMEM>(lane, rho_g + c, rho_d + c, t_s + c, v_in + c, v_out + c, C, dt, K, bsh,
+            dx_lpc_forward_cell<NF, ST>(lane, rho_g + c, rho_d + c, t_s + c, v_in + c, v_out + c, C, dt, K, bsh,
                                           wsm, status, heat ? heat + c : nullptr);
     }
 }
 
-template <int NF, bool SMEM>
+template <int NF, int ST>
 int launch_one(const DxConsts &K, long long C, const double *rho_g, const double *rho_d, const double *t_s,
                const double *v_in, double *v_out, double dt, uint32_t *status, double *heat, cudaStream_t stream) {
-    constexpr int kThreads = lpc_threads<NF, SMEM>();
-    const size_t smem = sizeof(double) * (32 + (SMEM ? (kThreads / 32) * dx_lpc_warp_smem_doubles<NF>() : 0));
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(dx_forward_lpc<NF, SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    constexpr int kThreads = lpc_threads<NF, ST>();
+    const size_t smem = sizeof(double) * (32 + (size_t)(kThreads / 32) * dx_lpc_warp_smem_doubles<NF, ST>());
+    // the opt-in covers dynamic + static shared memory (the sort keys and order, 5 KB) above 48 KB
+    constexpr size_t kStatic = kTile * (sizeof(unsigned long long) + sizeof(unsigned short));
+    if (smem + kStatic > 48 * 1024 &&
+        cudaFuncSetAttribute(dx_forward_lpc<NF, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
         return DRAG_ECUDA;
     int rounds = kTile / kThreads;
     while (rounds > 1 && (C + rounds * kThreads - 1) / (rounds * kThreads) < 4LL * dx_sm_count()) rounds >>= 1;
     const long long blocks = (C + rounds * kThreads - 1) / (rounds * kThreads);
-    dx_forward_lpc<NF, SMEM><<<(unsigned)blocks, kThreads, smem, stream>>>(C, rounds, rho_g, rho_d, t_s, v_in, v_out,
+    dx_forward_lpc<NF, ST><<<(unsigned)blocks, kThreads, smem, stream>>>(C, rounds, rho_g, rho_d, t_s, v_in, v_out,
                                                                           dt, status, heat, K);
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }
 
+// Storage modes built per n: registers or shared memory up to DX_LPC_REG_NMAX,
+// shared memory or hybrid above.
+template <int NF>
+int launch_store(int store, const DxConsts &K, long long C, const double *rho_g, const double *rho_d,
+                 const double *t_s, const double *v_in, double *v_out, double dt, uint32_t *status, double *heat,
+                 cudaStream_t stream) {
+    if constexpr (NF <= DX_LPC_REG_NMAX) {
+        if (store == DX_LPC_REGS)
+            return launch_one<NF, DX_LPC_REGS>(K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream);
+    } else {
+        if (store == DX_LPC_HYBRID)
+            return launch_one<NF, DX_LPC_HYBRID>(K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream);
+    }
+    if (store == DX_LPC_SHARED)
+        return launch_one<NF, DX_LPC_SHARED>(K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream);
+    return DRAG_EINVAL_SIZE;
+}
+
 }  // namespace
 
-int dx_launch_forward_lpc(const DxConsts &K, int n, bool smem, long long C, const double *rho_g,
+int dx_launch_forward_lpc(const DxConsts &K, int n, int store, long long C, const double *rho_g,
                           const double *rho_d, const double *t_s, const double *v_in, double *v_out, double dt,
                           uint32_t *status, double *heat, cudaStream_t stream) {
-#define DX_CASE_REG(NF) \
-    case NF: return smem ? launch_one<NF, true>(K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream) \
-                         : launch_one<NF, false>(K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream);
-#define DX_CASE_SMEM(NF) \
-    case NF: return launch_one<NF, true>(K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream);
     switch (n) {
-        DX_CASE_REG(2)
-        DX_CASE_REG(3)
-        DX_CASE_REG(4)
-        DX_CASE_REG(5)
-        DX_CASE_REG(6)
-        DX_CASE_SMEM(7)
-        DX_CASE_SMEM(8)
-        DX_CASE_SMEM(9)
-        DX_CASE_SMEM(10)
-        DX_CASE_SMEM(11)
-        DX_CASE_SMEM(12)
+#define DX_CASE(NF) \
+    case NF: return launch_store<NF>(store, K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, heat, stream);
+        DX_CASE(2)
+        DX_CASE(3)
+        DX_CASE(4)
+        DX_CASE(5)
+        DX_CASE(6)
+        DX_CASE(7)
+        DX_CASE(8)
+        DX_CASE(9)
+        DX_CASE(10)
+        DX_CASE(11)
+        DX_CASE(12)
+#undef DX_CASE
         default: return DRAG_EINVAL_SIZE;
     }
-#undef DX_CASE_REG
-#undef DX_CASE_SMEM
 }

@@ -177,15 +177,15 @@ bool g_once[64][16];
 int g_mode[64][DX_NMAXF + 1];
 bool g_mode_init[64];
 
-// Measured on GB300 (stiff MRN-like cells, cost-sorted lane-per-cell tiles):
-// lane per cell with the matrix in registers is fastest up to n = 6, in
-// shared memory up to n = 11 (its shared memory per warp grows as
-// 32 n(n+1) doubles and limits residency), warp per cell above.
-constexpr int kDefaultLpcSmemNMax = 11;
-
+// Measured on GB300 (stiff MRN-like cells, cost-sorted lane-per-cell tiles,
+// 1,048,576 cells): lane per cell with both matrices in registers is fastest
+// up to n = 6; from n = 7 to 12 the hybrid storage (current matrix in
+// registers, next one in shared memory) beats both all-shared storage (4 % at
+// n = 7, 9 % at n = 9, 26 % at n = 10: half the shared memory per warp, twice
+// the resident warps) and warp per cell (15 % at n = 12); warp per cell above.
 int default_mode(int n) {
     if (n <= DX_LPC_REG_NMAX) return DX_MODE_LPC_REG;
-    if (n <= kDefaultLpcSmemNMax) return DX_MODE_LPC_SMEM;
+    if (n <= DX_LPC_NMAX) return DX_MODE_LPC_HYB;
     return DX_MODE_WPC;
 }
 
@@ -250,6 +250,7 @@ bool dx_mode_valid(int n, int mode) {
     if (mode == DX_MODE_WPC) return true;
     if (mode == DX_MODE_LPC_REG) return n <= DX_LPC_REG_NMAX;
     if (mode == DX_MODE_LPC_SMEM) return n <= DX_LPC_NMAX;
+    if (mode == DX_MODE_LPC_HYB) return n > DX_LPC_REG_NMAX && n <= DX_LPC_NMAX;
     return false;
 }
 

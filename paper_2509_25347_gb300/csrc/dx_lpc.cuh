@@ -10,12 +10,19 @@
 // lanes of a warp agree.
 //
 // The symmetric matrix is stored packed (upper triangle, NT = n(n+1)/2
-// doubles) either in registers (SMEM = false, fully unrolled, n <= 6) or in
-// shared memory with a stride of 32 doubles between entries so that the 32
-// lanes of a warp hit 32 different banks (SMEM = true).
+// doubles), double-buffered as F (the current matrix) and G (the next one):
+//   DX_LPC_REGS   : F, G and the n-vectors in registers (fully unrolled, n <= 6);
+//   DX_LPC_SHARED : all in shared memory, a stride of 32 doubles between
+//                   entries so that the 32 lanes of a warp hit 32 banks;
+//   DX_LPC_HYBRID : F in registers, G and the n-vectors in shared memory. Half
+//                   the shared memory of DX_LPC_SHARED (more warps per SM to
+//                   cover FP64 latency) and register operands for every product;
+//                   each step ends by copying G back into F.
 #pragma once
 
 #include "dx_common.cuh"
+
+enum : int { DX_LPC_REGS = 0, DX_LPC_SHARED = 1, DX_LPC_HYBRID = 2 };
 
 template <int NF>
 struct DxPacked {
@@ -43,11 +50,11 @@ struct DxLaneArr<NT, true> {
     __device__ __forceinline__ double &operator[](int e) { return p[e * 32]; }
 };
 
-// F <- G after a step: registers are copied, shared-memory slices swapped.
-template <int NT>
-__device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, false> &F, DxLaneArr<NT, false> &G) {
+// F <- G after a step: copied into registers, or shared-memory slices swapped.
+template <int NT, bool GS>
+__device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, false> &F, DxLaneArr<NT, GS> &G) {
 #pragma unroll
-    for (int e = 0; e < NT; e++) F.v[e] = G.v[e];
+    for (int e = 0; e < NT; e++) F.v[e] = G[e];
 }
 template <int NT>
 __device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, true> &F, DxLaneArr<NT, true> &G) {
@@ -56,16 +63,17 @@ __device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, true> &F, DxLaneArr<N
     G.p = t;
 }
 
-// Shared-memory doubles one warp needs for the SMEM variant.
-template <int NF>
+// Shared-memory doubles one warp needs for storage mode ST.
+template <int NF, int ST>
 __host__ __device__ constexpr int dx_lpc_warp_smem_doubles() {
-    return 32 * (2 * DxPacked<NF>::NT + 4 * NF);
+    return ST == DX_LPC_SHARED ? 32 * (2 * DxPacked<NF>::NT + 4 * NF)
+                               : (ST == DX_LPC_HYBRID ? 32 * (DxPacked<NF>::NT + 4 * NF) : 0);
 }
 
 // One cell per lane. Pointers address this cell; element (i) of a per-species
 // array is at p[i * stride]; velocity (d, f) at p[(d * NF + f) * stride].
-// smem_warp: this warp's slice (SMEM = true only); bsh: b_i = 1/i! in shared memory.
-template <int NF, bool SMEM>
+// smem_warp: this warp's slice (ST != DX_LPC_REGS); bsh: b_i = 1/i! in shared memory.
+template <int NF, int ST>
 __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp, const double *rdp, const double *tsp,
                                                     const double *vip, double *vop, long long stride, double dt,
                                                     const DxConsts &K, const double *bsh, double *smem_warp,
@@ -123,15 +131,18 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
     const int m = K.mk[kk];
 
     // ---------------- symmetric arrowhead X = 2^-s D_sigma A D_sigma^-1
-    DxLaneArr<NF, SMEM> sig, tau, xs, ds;
-    DxLaneArr<NT, SMEM> Fm, Gm;
-    if constexpr (SMEM) {
-        Fm.bind(smem_warp, lane);
-        Gm.bind(smem_warp + 32 * NT, lane);
-        sig.bind(smem_warp + 64 * NT, lane);
-        tau.bind(smem_warp + 64 * NT + 32 * NF, lane);
-        xs.bind(smem_warp + 64 * NT + 64 * NF, lane);
-        ds.bind(smem_warp + 64 * NT + 96 * NF, lane);
+    constexpr bool kSharedF = ST == DX_LPC_SHARED, kSharedG = ST != DX_LPC_REGS;
+    DxLaneArr<NF, kSharedG> sig, tau, xs, ds;
+    DxLaneArr<NT, kSharedF> Fm;
+    DxLaneArr<NT, kSharedG> Gm;
+    if constexpr (kSharedG) {
+        constexpr int f = kSharedF ? 32 * NT : 0;   // F's slice, then G's, then the vectors
+        if constexpr (kSharedF) Fm.bind(smem_warp, lane);
+        Gm.bind(smem_warp + f, lane);
+        sig.bind(smem_warp + f + 32 * NT, lane);
+        tau.bind(smem_warp + f + 32 * NT + 32 * NF, lane);
+        xs.bind(smem_warp + f + 32 * NT + 64 * NF, lane);
+        ds.bind(smem_warp + f + 32 * NT + 96 * NF, lane);
     }
     sig[0] = 1.0;
     tau[0] = 1.0;

@@ -1,26 +1,34 @@
 // Execution-mode table shared by the host-side dispatchers: for each matrix
 // size n = N + 1 which kernel family runs a cell (lane per cell with the
-// matrix in registers or shared memory, or warp per cell). Defaults are set at
-// load time; drag_expm_autotune() overwrites them from measurements.
+// matrices in registers, in shared memory, or the current one in registers and
+// the next in shared memory; or warp per cell). Defaults are set at load time;
+// drag_expm_autotune() overwrites them from measurements.
 #pragma once
 
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "dx_common.cuh"
+#include "dx_lpc.cuh"
 
-enum DxMode : int { DX_MODE_WPC = 0, DX_MODE_LPC_REG = 1, DX_MODE_LPC_SMEM = 2 };
+enum DxMode : int { DX_MODE_WPC = 0, DX_MODE_LPC_REG = 1, DX_MODE_LPC_SMEM = 2, DX_MODE_LPC_HYB = 3 };
+#define DX_NMODES 4
 
 #define DX_LPC_NMAX 12   // largest n with a lane-per-cell kernel
 #define DX_LPC_REG_NMAX 6
 
 int dx_mode_for(int n);            // current mode for matrix size n (current device)
+// Lane-per-cell storage of a lane-per-cell mode.
+inline int dx_lpc_store(int mode) {
+    return mode == DX_MODE_LPC_REG ? DX_LPC_REGS : (mode == DX_MODE_LPC_HYB ? DX_LPC_HYBRID : DX_LPC_SHARED);
+}
 void dx_set_mode(int n, int mode);  // used by the autotuner
 bool dx_mode_valid(int n, int mode);
 
 int dx_launch_forward_f32(const DxConsts &K, long long ncells, int nspecies, const double *rho_g,
                           const double *rho_d, const double *t_s, double dt, const double *v_in, double *v_out,
                           cudaStream_t stream);
-int dx_launch_forward_lpc(const DxConsts &K, int n, bool smem, long long C, const double *rho_g,
+// store: DX_LPC_REGS / DX_LPC_SHARED / DX_LPC_HYBRID (dx_lpc.cuh) for the lane-per-cell modes.
+int dx_launch_forward_lpc(const DxConsts &K, int n, int store, long long C, const double *rho_g,
                           const double *rho_d, const double *t_s, const double *v_in, double *v_out, double dt,
                           uint32_t *status, double *heat, cudaStream_t stream);

@@ -124,7 +124,7 @@ extern "C" int drag_expm_autotune(int32_t nspecies_max, const char *cache_path, 
         const int prev = dx_mode_for(n);
         float best = 1e30f;
         int best_mode = prev;
-        for (int mode = 0; mode <= 2; mode++) {
+        for (int mode = 0; mode < DX_NMODES; mode++) {
             if (!dx_mode_valid(n, mode)) continue;
             dx_set_mode(n, mode);
             if ((rc = drag_expm_apply(C, N, rg, rd, ts, 1.0, v, vo, stream)) != DRAG_OK) break;   // warm-up

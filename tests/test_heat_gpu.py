@@ -33,7 +33,7 @@ def krel(cells):
 
 
 @pytest.mark.parametrize("N,mode", [(1, None), (4, None), (8, None), (16, None), (31, None),
-                                    (4, 0), (4, 2), (8, 0), (10, 2)])
+                                    (4, 0), (4, 2), (8, 0), (8, 3), (10, 2), (10, 3), (11, 3)])
 def test_heat_parity(dx, N, mode):
     cells = W.mrn(777, N, seed=40 + N, stiff_lo=-4.0, stiff_hi=8.0)
     cells.v += 3.0                                     # common motion must not matter

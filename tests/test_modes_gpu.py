@@ -1,6 +1,6 @@
 """Every kernel family for every size it supports (lane per cell in registers,
-lane per cell in shared memory, warp per cell) against the oracle, and the
-autotuner: valid choices, cache round trip, parity after tuning."""
+lane per cell in shared memory, lane per cell hybrid, warp per cell) against the
+oracle, and the autotuner: valid choices, cache round trip, parity after tuning."""
 import numpy as np
 import pytest
 
@@ -34,6 +34,8 @@ def valid_modes(N):
         modes.append(1)
     if n <= 12:
         modes.append(2)
+    if 7 <= n <= 12:
+        modes.append(3)
     return modes
 
 
@@ -43,20 +45,37 @@ def test_every_mode_parity(dx, N):
     ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v)
     sc = np.abs(cells.v).max(axis=1, keepdims=True)
     old = dx.get_mode(N)
+    outs = {}
     try:
         for mode in valid_modes(N):
             dx.set_mode(N, mode)
             assert dx.get_mode(N) == mode
-            out = dx.apply(t(cells.rho_g), t(cells.rho_d), t(cells.t_s), cells.dt, t(cells.v)).cpu().numpy()
+            outs[mode] = dx.apply(t(cells.rho_g), t(cells.rho_d), t(cells.t_s), cells.dt, t(cells.v))
+            out = outs[mode].cpu().numpy()
             assert np.max(np.abs(out - ref) / sc) <= TOL, (N, mode)
-        with pytest.raises(dx.DragExpmError):
-            dx.set_mode(N, 3)
-        if N + 1 > 12:
+        for bad in (4, -1) + ((3,) if not 7 <= N + 1 <= 12 else ()) + ((2,) if N + 1 > 12 else ()):
             with pytest.raises(dx.DragExpmError):
-                dx.set_mode(N, 2)
+                dx.set_mode(N, bad)
     finally:
         dx.set_mode(N, old)
+    if 3 in outs:
+        # the hybrid storage runs the shared-memory variant's FP64 operations in the same order
+        assert torch_equal(outs[2], outs[3])
     assert dx.get_status() == 0
+
+
+def torch_equal(a, b):
+    import torch
+    return torch.equal(a, b)
+
+
+def test_default_modes(dx):
+    """Built-in table (every test here restores what it changes): lane per cell in
+    registers up to n = 6, hybrid up to n = 12, warp per cell above."""
+    for N in range(1, dx.NMAX + 1):
+        n = N + 1
+        assert dx.get_mode(N) == (dx.MODE_LANE_REGISTERS if n <= 6 else
+                                  dx.MODE_LANE_HYBRID if n <= 12 else dx.MODE_WARP_PER_CELL), N
 
 
 def test_autotune_and_cache(dx, tmp_path):
