@@ -78,8 +78,9 @@ __device__ __forceinline__ void tape_load(int lane, int n, int ns, const unsigne
 }
 
 // Per-warp shared memory (doubles): E0, E1, L0, L1, then n-vectors: sigma,
-// tau, X_0f, X_ff, a_d and b_d (4 each), two buffers of y_d (3 each) and g_d (3).
-__host__ __device__ __forceinline__ int bwd_warp_smem_doubles(int n) { return 4 * n * dx_stride(n) + 21 * n; }
+// tau, X_0f, X_ff, a_d and b_d (4 each), two buffers of y_d (3 each), g_d (3)
+// and w = b_{j+1} a_3 of the current Taylor step.
+__host__ __device__ __forceinline__ int bwd_warp_smem_doubles(int n) { return 4 * n * dx_stride(n) + 22 * n; }
 
 constexpr int kRank = 4;   // rank of the Frechet direction H
 
@@ -108,6 +109,82 @@ __device__ __forceinline__ void bwd_xvec(int lane, int n, const DxVecs &V, doubl
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(DX_FULL, acc, o);
     if (on && phi == 0) yo[d * n] = fma(c1, acc, c0 * a[d * n]);
+}
+
+// Lanes of the fused round below: n for column 0, 3 for y'_d[0], nx for the
+// entries f >= 1 of the three y'_d, q entries each (3 FMAs per entry), all
+// within the round's n + 4 FMA steps. False when n is too large for that.
+__host__ __device__ __forceinline__ bool bwd_fold_fits(int n, int &nx, int &q) {
+    nx = 32 - n - 3;
+    if (nx < 1) return false;
+    q = (3 * (n - 1) + nx - 1) / nx;
+    return 3 * q <= n + 4;
+}
+
+// One Taylor step's column 0 of dF' = dF X + F H and the next y'_d = X y_d +
+// c0 a_d (d = 0, 1, 2), as one round of n + 4 FMA steps issued uniformly by all
+// lanes (each lane's operands depend on its role; absent terms are 0 * 0):
+//   lane i < n       : dF'_i0 = sum_{d<3} y_d,i b_d,0 + w_i b_3,0 + sum_k dF_ik X_k0;
+//   lane n + d (d<3) : y'_d,0 = c0 a_d,0 + sum_k X_0k y_d,k;
+//   lanes n + 3 + r  : y'_d,f = c0 a_d,f + X_ff y_d,f + X_f0 y_d,0 for the entries
+//                      (d, f) = r, r + nx, ... of the 3(n - 1) with f >= 1.
+// Requires bwd_fold_fits(n).
+__device__ __forceinline__ void bwd_col0_and_y(int lane, int n, int ns, int nx, int q, const DxVecs &V, double c0,
+                                               const double *a, const double *b, const double *w, const double *y,
+                                               const double *dF, double *dFn, double *yn) {
+    const int K = n + 4;
+    const int role = lane < n ? 0 : (lane < n + 3 ? 1 : (lane < n + 3 + nx ? 2 : 3));
+    const int d1 = lane - n;          // role 1: component d
+    const int r = lane - n - 3;       // role 2: first entry index
+    double acc = 0.0;
+    for (int st = 0; st < K; st++) {
+        double x = 0.0, z = 0.0;
+        double *dst = nullptr;
+        if (role == 0) {
+            if (st < 3) {
+                x = y[st * n + lane];
+                z = b[st * n];
+            } else if (st == 3) {
+                x = w[lane];
+                z = b[3 * n];
+            } else {
+                x = dF[lane * ns + st - 4];
+                z = V.xs[st - 4];
+            }
+            if (st == K - 1) dst = dFn + lane * ns;
+        } else if (role == 1) {
+            if (st == 0) {
+                x = c0;
+                z = a[d1 * n];
+            } else if (st <= n) {
+                x = V.xs[st - 1];
+                z = y[d1 * n + st - 1];
+            }
+            if (st == n) dst = yn + d1 * n;
+        } else if (role == 2) {
+            const int e = st / 3, ph = st - 3 * e;
+            const int t = r + nx * e;
+            if (e < q && t < 3 * (n - 1)) {
+                const int d = t / (n - 1), f = t - d * (n - 1) + 1;
+                if (ph == 0) {
+                    x = c0;
+                    z = a[d * n + f];
+                } else if (ph == 1) {
+                    x = V.ds[f];
+                    z = y[d * n + f];
+                } else {
+                    x = V.xs[f];
+                    z = y[d * n];
+                    dst = yn + d * n + f;
+                }
+            }
+        }
+        acc = fma(x, z, acc);
+        if (dst) {
+            *dst = acc;
+            acc = 0.0;
+        }
+    }
 }
 
 // One squaring of (E, L): (E, L) <- (E^2, E L + L E), E^2 restored, as tasks
@@ -220,6 +297,9 @@ __device__ __forceinline__ void bwd_wpc_body(const BwdArgs &a, const DxConsts &K
     double *yv0 = bv + 4 * n;    // y_d = F a_d (d < 3), two buffers          [3][n] x 2
     double *yv1 = yv0 + 3 * n;
     double *gg = yv1 + 3 * n;    // g_d                                       [3][n]
+    double *wv = gg + 3 * n;     // b_{j+1} a_3 of the current Taylor step    [n]
+    int fold_nx = 0, fold_q = 0;
+    const bool fold = bwd_fold_fits(n, fold_nx, fold_q);
 
     const long long C = a.C;
     // Each block owns kCellsPerBlock consecutive cells, taken one at a time by
@@ -330,29 +410,34 @@ __device__ __forceinline__ void bwd_wpc_body(const BwdArgs &a, const DxConsts &K
             // F a_3 = b_{jb+1} a_3. Finally y_d <- F_jb a_d = X y_d + b_jb a_d
             // (F_jb = X F + b_jb I: polynomials in X commute with X).
             if (!taped) dx_wpc_horner_step(lane, n, ns, n_hp, hp, V, K.b[jb], F, Fn);
-            const double b3 = K.b[jb + 1];
-            // columns j >= 1 (6 FMAs each: X has two nonzeros per column there)
-            // and column 0 (n + 4 FMAs) are dealt in separate rounds
+            if (lane < n) wv[lane] = K.b[jb + 1] * av[3 * n + lane];   // F a_3 = b_{jb+1} a_3
+            __syncwarp();
+            // columns j >= 1 (6 FMAs each: X has two nonzeros per column there),
+            // then column 0 (n + 4 FMAs) together with y' = X y + b_jb a
             for (int t = lane; t < n * (n - 1); t += 32) {
                 const int i = t / (n - 1), j = t - i * (n - 1) + 1;
                 double acc = y[i] * bv[j];
                 acc = fma(y[n + i], bv[n + j], acc);
                 acc = fma(y[2 * n + i], bv[2 * n + j], acc);
-                acc = fma(b3 * av[3 * n + i], bv[3 * n + j], acc);
+                acc = fma(wv[i], bv[3 * n + j], acc);
                 acc = fma(dF[i * ns], V.xs[j], acc);
                 acc = fma(dF[i * ns + j], V.ds[j], acc);
                 dFn[i * ns + j] = acc;
             }
-            for (int i = lane; i < n; i += 32) {
-                double acc = y[i] * bv[0];
-                acc = fma(y[n + i], bv[n], acc);
-                acc = fma(y[2 * n + i], bv[2 * n], acc);
-                acc = fma(b3 * av[3 * n + i], bv[3 * n], acc);
-                const double *ri = dF + i * ns;
-                for (int k = 0; k < n; k++) acc = fma(ri[k], V.xs[k], acc);
-                dFn[i * ns] = acc;
+            if (fold) {
+                bwd_col0_and_y(lane, n, ns, fold_nx, fold_q, V, K.b[jb], av, bv, wv, y, dF, dFn, yn);
+            } else {
+                for (int i = lane; i < n; i += 32) {
+                    double acc = y[i] * bv[0];
+                    acc = fma(y[n + i], bv[n], acc);
+                    acc = fma(y[2 * n + i], bv[2 * n], acc);
+                    acc = fma(wv[i], bv[3 * n], acc);
+                    const double *ri = dF + i * ns;
+                    for (int k = 0; k < n; k++) acc = fma(ri[k], V.xs[k], acc);
+                    dFn[i * ns] = acc;
+                }
+                bwd_xvec(lane, n, V, 1.0, K.b[jb], av, y, yn);
             }
-            bwd_xvec(lane, n, V, 1.0, K.b[jb], av, y, yn);
             __syncwarp();
             double *t1 = F; F = Fn; Fn = t1;
             double *t2 = dF; dF = dFn; dFn = t2;
