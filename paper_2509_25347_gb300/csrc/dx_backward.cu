@@ -195,16 +195,14 @@ __device__ __forceinline__ void bwd_col0_and_y(int lane, int n, int ns, int nx, 
 //   R (i)    : En_ii = 1 - tau_i sum_{k != i} En_ik sigma_k  (after every O).
 // mode kSqFull: all of the above. kSqTrimmed: only the entries of E L + L E in
 // row 0, column 0 and on the diagonal, and no E^2 (the gradients read only
-// those entries of the last L). kSqLOnly: E L + L E, and no E^2 (read from the
-// tape instead).
-constexpr int kSqFull = 0, kSqTrimmed = 1, kSqLOnly = 2;
+// those entries of the last L).
+constexpr int kSqFull = 0, kSqTrimmed = 1;
 __device__ __forceinline__ void bwd_square(int lane, int n, int ns, const unsigned short *od, const DxVecs &V,
                                            const double *E, const double *L, double *En, double *Ln, int mode) {
     const bool trimmed = mode == kSqTrimmed;
-    const bool noE2 = mode != kSqFull;
-    const int nO = noE2 ? 0 : n * (n - 1) / 2;
+    const int nO = trimmed ? 0 : n * (n - 1) / 2;
     const int nL = trimmed ? 3 * n - 2 : n * n;
-    const int nR = noE2 ? 0 : n;
+    const int nR = trimmed ? 0 : n;
     const int a0 = nO;
     const int b0 = nL >= 32 ? nO + nL : ((nO + nL + 31) & ~31);
     const int r0 = b0 + nL;
@@ -266,6 +264,94 @@ __device__ __forceinline__ void bwd_square(int lane, int n, int ns, const unsign
         } else if (kind == 3) {
             En[i * ns + i] = res;
         }
+        __syncwarp();
+    }
+}
+
+// A-task order of an L-only squaring whose first tasks ran in the previous
+// squaring's last round next to r of that squaring's B tasks (entries of row
+// n - 1, columns n - r .. n - 1, when 0 < r < n): first the entries with
+// i <= n - 2 and j <= n - 1 - r (safe to run in that round: their column of
+// L is complete and their slot of the old L is read by no pending B task),
+// then i <= n - 2 with j >= n - r, then row n - 1. r = 0: row major.
+__device__ __forceinline__ void lonly_a_entry(int n, int r, int e, int &i, int &j) {
+    if (r == 0) {
+        i = e / n;
+        j = e - i * n;
+    } else if (e < (n - 1) * (n - r)) {
+        i = e / (n - r);
+        j = e - i * (n - r);
+    } else if (e < (n - 1) * n) {
+        const int e2 = e - (n - 1) * (n - r);
+        i = e2 / r;
+        j = n - r + (e2 - i * r);
+    } else {
+        i = n - 1;
+        j = e - (n - 1) * n;
+    }
+}
+
+// One squaring L' = E L + L E without E^2 (E and the next E from the tape), as
+// A tasks (Ln_ij = sum_k E_ik L_kj) then B tasks (Ln_ij += sum_k L_ik E_jk),
+// n-FMA tasks dealt 32 per round. kin of its A tasks (order lonly_a_entry with
+// rin) already ran in the previous squaring's last round. When carry is set and
+// the last round holds r < n B tasks, its other lanes run the first 32 - r A
+// tasks of the next squaring (reading En, the next E, and Ln, whose columns
+// they need are complete; writing L, whose slots they overwrite are no longer
+// read); kout / rout describe them (0 / 0 otherwise). The tape copies into En
+// are waited for before the last round. Per entry the arithmetic is that of
+// bwd_square (same two n-FMA chains, in order), so results match it bit for bit.
+__device__ __forceinline__ void bwd_square_lonly(int lane, int n, int ns, const double *E, double *L, const double *En,
+                                                 double *Ln, int kin, int rin, bool carry, int &kout, int &rout) {
+    const int nn = n * n;
+    const int nA = nn - kin;
+    const int b0 = nA;                                 // B tasks follow the A tasks directly (nn >= 32) ...
+    const int b0p = nn >= 32 ? b0 : ((b0 + 31) & ~31); // ... or from the next round (B after its A)
+    const int ntask = b0p + nn;
+    const int rounds = (ntask + 31) >> 5;
+    const int rem = ntask & 31;
+    const int inv = (65536 + n - 1) / n;
+    // fill: enough safe A tasks for the idle lanes, and in the next squaring every
+    // B task at least a round after its A task (for the entries reordered behind
+    // the safe ones the two lie nn - (n - rem)(n - 2) tasks apart)
+    const bool fill = carry && nn >= 32 && rem > 0 && rem < n && (n - 1) * (n - rem) >= 32 - rem &&
+                      nn - (n - rem) * (n - 2) >= 32;
+    kout = fill ? 32 - rem : 0;
+    rout = fill ? rem : 0;
+    for (int rd = 0; rd < rounds; rd++) {
+        if (rd == rounds - 1) {
+            cp_async_wait_all();   // the next E (tape) before the round that may read it
+            __syncwarp();
+        }
+        const int t = rd * 32 + lane;
+        const double *pa = E, *pb = E;
+        int sb = 1, i = 0, j = 0;
+        double acc = 0.0;
+        double *dst = nullptr;
+        if (t < nA) {
+            lonly_a_entry(n, rin, kin + t, i, j);
+            pa = E + i * ns;
+            pb = L + j;
+            sb = ns;
+            dst = Ln + i * ns + j;
+        } else if (t >= b0p && t < ntask) {
+            const int e = t - b0p;
+            i = (e * inv) >> 16;
+            j = e - i * n;
+            pa = L + i * ns;
+            pb = E + j * ns;
+            acc = Ln[i * ns + j];
+            dst = Ln + i * ns + j;
+        } else if (fill && t >= ntask) {
+            lonly_a_entry(n, rem, t - ntask, i, j);    // next squaring's A task
+            pa = En + i * ns;
+            pb = Ln + j;
+            sb = ns;
+            dst = L + i * ns + j;
+        }
+        for (int q = 0; q < n - 1; q++) acc = fma(pa[q], pb[q * sb], acc);
+        const double res = fma(pa[n - 1], pb[(n - 1) * sb], acc);
+        if (dst) *dst = res;
         __syncwarp();
     }
 }
@@ -455,14 +541,17 @@ __device__ __forceinline__ void bwd_wpc_body(const BwdArgs &a, const DxConsts &K
         // ---- squarings: (E, L) <- (E^2, E L + L E); the last one only forms
         // the entries of L the gradients read and leaves E at E_{s-1}. Taped,
         // E_{sq+1} is loaded while the squaring forms L whenever the tape holds it.
+        int ka = 0, ra = 0;   // A tasks of the next L-only squaring already run, and their order
         for (int sq = 0; sq < L.s; sq++) {
             const bool trimmed = sq == L.s - 1;
             const bool lonly = taped && sq + 1 < dx_tape_levels(L.s);
-            if (lonly) tape_load(lane, n, ns, hp, tcell + (size_t)(sq + 1) * a.P, Fn);
-            bwd_square(lane, n, ns, od, V, F, dF, Fn, dFn, trimmed ? kSqTrimmed : (lonly ? kSqLOnly : kSqFull));
             if (lonly) {
-                cp_async_wait_all();
-                __syncwarp();
+                tape_load(lane, n, ns, hp, tcell + (size_t)(sq + 1) * a.P, Fn);
+                const bool carry = sq + 2 < dx_tape_levels(L.s);   // the next squaring is L-only too
+                bwd_square_lonly(lane, n, ns, F, dF, Fn, dFn, ka, ra, carry, ka, ra);
+            } else {
+                bwd_square(lane, n, ns, od, V, F, dF, Fn, dFn, trimmed ? kSqTrimmed : kSqFull);
+                ka = ra = 0;
             }
             if (!trimmed) {
                 double *t1 = F; F = Fn; Fn = t1;
