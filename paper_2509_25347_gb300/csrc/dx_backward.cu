@@ -250,12 +250,19 @@ __device__ __forceinline__ void bwd_square(int lane, int n, int ns, const unsign
             skip = i;
             kind = 3;
         }
-        for (int q = 0; q < n - 1; q++) {
-            const int k = q + (q >= skip);
-            acc = fma(pa[k], pb[k * sb], acc);
+        double res;
+        if (base + 32 <= r0) {
+            // no restoration in this round (warp uniform): plain n-term dot products
+            for (int q = 0; q < n - 1; q++) acc = fma(pa[q], pb[q * sb], acc);
+            res = fma(pa[n - 1], pb[(n - 1) * sb], acc);
+        } else {
+            for (int q = 0; q < n - 1; q++) {
+                const int k = q + (q >= skip);
+                acc = fma(pa[k], pb[k * sb], acc);
+            }
+            const bool isR = kind == 3;
+            res = fma(isR ? -V.tau[i] : pa[n - 1], isR ? acc : pb[(n - 1) * sb], isR ? 1.0 : acc);
         }
-        const bool isR = kind == 3;
-        const double res = fma(isR ? -V.tau[i] : pa[n - 1], isR ? acc : pb[(n - 1) * sb], isR ? 1.0 : acc);
         if (kind == 1) {
             En[i * ns + j] = res;
             En[j * ns + i] = res;
