@@ -566,7 +566,7 @@ def run_ours(args, rank, world):
             **{name: {"value": whole_job_rate(C, world, variant_ms[name]), "unit": UNIT,
                       "ms_per_step": variant_ms[name], "mean_degree": variant_deg[name]}
                for name in ("taylor_bound_test", "pade", "mixed_fp32_u24")}},
-        "gpu_launches": args.steps,
+        "gpu_launches": dx.apply_launches(C, N) * args.steps,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -80,11 +80,22 @@ extern "C" {
  *   v_in     : DEVICE, 3*(N+1)*ncells doubles, read only.
  *   v_out    : DEVICE, 3*(N+1)*ncells doubles, written. v_out == v_in (in
  *              place) is allowed; other overlaps are not.
- *   stream   : CUDA stream for the launch.
+ *   stream   : CUDA stream for the launches.
  * Returns DRAG_OK or a DRAG_E* code (nothing launched on error).
+ * Lane-per-cell sizes (N <= 8 with the default modes) on 262,144 cells or more
+ * run the batched pipeline over one block: the cells are binned by (k*, s*)
+ * first, so each warp runs 32 cells of equal cost. Its scratch (12 bytes per
+ * cell) is taken stream-ordered from a memory pool private to the library,
+ * which keeps what it once allocated; the launches stay capturable in a CUDA
+ * graph. If no scratch can be had, the single tile-sorted kernel runs instead.
+ * The results are the same either way.
  */
 int drag_expm_apply(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d, const double *t_s,
                     double dt, const double *v_in, double *v_out, cudaStream_t stream);
+
+/* drag_expm_apply_launches — number of kernels drag_expm_apply launches for
+ * (ncells, nspecies) with the current device's mode table (0 for bad sizes). */
+int32_t drag_expm_apply_launches(int64_t ncells, int32_t nspecies);
 
 /*
  * drag_expm_apply_target — drag_expm_apply for a lower accuracy target.
@@ -154,7 +165,8 @@ int drag_expm_apply_opts(int64_t ncells, int32_t nspecies, const double *rho_g, 
 
 /*
  * drag_expm_apply_host — drag_expm_apply on HOST arrays (same SoA layout,
- * stride ncells): the cells are processed in chunks of chunk_cells (0: 131072)
+ * stride ncells): the cells are processed in chunks of chunk_cells (0: 262,144
+ * where drag_expm_apply bins that many cells, see there, else 131,072)
  * through a two-stream pipeline, so the host-to-device copies of one chunk
  * and the device-to-host copy of another overlap the update of a third. The
  * copies are asynchronous only from page-locked (pinned) host memory; with

@@ -16,7 +16,7 @@ import os
 __all__ = [
     "load_library", "apply", "apply_heat", "backward", "rk1_apply", "apply_batched", "batched_workspace_bytes",
     "select", "get_status", "theta", "DragExpm", "DragExpmError", "apply_opts", "pade_theta", "apply_host",
-    "host_workspace_bytes", "apply_taped", "Tape", "tape_bytes", "tape_levels", "tape_levels_needed",
+    "host_workspace_bytes", "apply_launches", "apply_taped", "Tape", "tape_bytes", "tape_levels", "tape_levels_needed",
     "DragExpmTaped", "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"
 ]
 
@@ -94,6 +94,8 @@ def load_library(path: str | None = None):
     lib.drag_expm_backward_taped.restype = ctypes.c_int
     lib.drag_expm_backward_taped.argtypes = [i64, i32, vp, vp, vp, dbl, vp, vp, vp, vp, vp, vp, i32, vp,
                                              ctypes.c_size_t, vp]
+    lib.drag_expm_apply_launches.restype = ctypes.c_int32
+    lib.drag_expm_apply_launches.argtypes = [i64, i32]
     lib.drag_expm_strerror.restype = ctypes.c_char_p
     lib.drag_expm_strerror.argtypes = [ctypes.c_int]
     lib.drag_expm_version.restype = ctypes.c_int
@@ -174,6 +176,11 @@ def _f64_host(name, t, shape):
     if not t.is_contiguous():
         raise DragExpmError(f"{name} must be contiguous")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def apply_launches(ncells: int, nspecies: int) -> int:
+    """Kernels :func:`apply` launches for this size (the binned path launches 6)."""
+    return int(load_library().drag_expm_apply_launches(int(ncells), int(nspecies)))
 
 
 def host_workspace_bytes(nspecies: int, chunk_cells: int = 0) -> int:

@@ -10,15 +10,20 @@
 //   5. main     (persistent grids) : warps pull work items from atomic counters.
 //      An item is 32 cells of one bin run lane-per-cell (small n, the lanes
 //      of a warp share m* and s*, so no lane idles) or one cell run
-//      warp-per-cell (large n). The per-n choice comes from the mode table
-//      (drag_expm_autotune() measures it). The two kinds of item run in two
-//      kernels, each with its own queue, so that the register-heavy
-//      lane-per-cell code does not set the occupancy of the warp-per-cell
-//      work.
+//      warp-per-cell (large n), by the fixed per-n rule of dx_batch_modes().
+//      The two kinds of item run in two kernels, each with its own queue, so
+//      that the register-heavy lane-per-cell code does not set the occupancy
+//      of the warp-per-cell work.
 //
 // Every launch goes to the caller's stream; there is no host synchronisation
 // and no allocation (scratch is the caller's workspace), so the whole call can
 // be captured in a CUDA graph and replayed.
+//
+// The same pipeline also serves drag_expm_apply for lane-per-cell sizes on
+// large inputs (dx_binned_forward): one block, scratch from a library-private
+// stream-ordered memory pool. Binning by (k*, s*) over the whole input gives
+// every warp 32 cells of one Taylor order and squaring count, where the plain
+// lane-per-cell kernel can only sort within a tile of 512 cells.
 #include <cmath>
 #include <mutex>
 
@@ -401,30 +406,11 @@ Modes dx_batch_modes() {
     return M;
 }
 
-extern "C" size_t drag_expm_batched_workspace_bytes(int64_t nblocks, int64_t total_cells) {
-    if (nblocks < 0 || total_cells < 0) return 0;
-    return layout(nblocks, total_cells).total;
-}
-
-extern "C" int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *blocks, int64_t total_cells, int64_t rho_d_len,
-                                       int64_t v_len, int32_t nspecies_max, const double *rho_g, const double *rho_d,
-                                       const double *t_s, const double *v_in, double *v_out, void *workspace,
-                                       size_t workspace_bytes, cudaStream_t stream) {
-    if (nblocks < 0 || nblocks > (1LL << 31) - 1) return DRAG_EBLOCKS;
-    if (total_cells < 0 || total_cells > (1LL << 32) - 1 || rho_d_len < 0 || v_len < 0) return DRAG_EINVAL_SIZE;
-    if (nspecies_max < 1 || nspecies_max > DRAG_EXPM_NMAX) return DRAG_EINVAL_SIZE;
-    if (nblocks == 0 || total_cells == 0) return DRAG_OK;
-    if (!blocks || !rho_g || !rho_d || !t_s || !v_in || !v_out) return DRAG_ENULL;
-    if (!aligned8(blocks) || !aligned8(rho_g) || !aligned8(rho_d) || !aligned8(t_s) || !aligned8(v_in) ||
-        !aligned8(v_out))
-        return DRAG_EALIGN;
-    const Layout L = layout(nblocks, total_cells);
-    if (!workspace || workspace_bytes < L.total) return DRAG_EWORKSPACE;
-    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return DRAG_EALIGN;
-    uint32_t *st = dx_status_ptr();
-    if (!st) return DRAG_ECUDA;
-
-    char *ws = static_cast<char *>(workspace);
+// The five-kernel pipeline on a checked workspace ws with layout L.
+static int batched_run(const DxConsts &K, long long nblocks, const Desc *D, long long total_cells, long long rho_d_len,
+                       long long v_len, int nspecies_max, const double *rho_g, const double *rho_d,
+                       const double *t_s, const double *v_in, double *v_out, char *ws, const Layout &L,
+                       uint32_t *st, cudaStream_t stream) {
     Work W;
     W.perm = reinterpret_cast<unsigned long long *>(ws + L.perm);
     W.key = reinterpret_cast<unsigned int *>(ws + L.key);
@@ -437,8 +423,6 @@ extern "C" int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *bloc
     W.ctr = reinterpret_cast<unsigned int *>(ws + L.ctr);
 
     const Modes M = dx_batch_modes();
-    const DxConsts &K = dx_consts();
-    const Desc *D = reinterpret_cast<const Desc *>(blocks);
     const int sms = dx_sm_count();
     const long long cgrid_want = (total_cells + 255) / 256;
     const int cgrid = (int)(cgrid_want < (long long)sms * 16 ? cgrid_want : (long long)sms * 16);
@@ -477,6 +461,33 @@ extern "C" int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *bloc
         dx_batch_main_wpc<<<sms * per_sm, kWpcWarps * 32, smem, stream>>>(a, W, K);
     }
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
+}
+
+extern "C" size_t drag_expm_batched_workspace_bytes(int64_t nblocks, int64_t total_cells) {
+    if (nblocks < 0 || total_cells < 0) return 0;
+    return layout(nblocks, total_cells).total;
+}
+
+extern "C" int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *blocks, int64_t total_cells, int64_t rho_d_len,
+                                       int64_t v_len, int32_t nspecies_max, const double *rho_g, const double *rho_d,
+                                       const double *t_s, const double *v_in, double *v_out, void *workspace,
+                                       size_t workspace_bytes, cudaStream_t stream) {
+    if (nblocks < 0 || nblocks > (1LL << 31) - 1) return DRAG_EBLOCKS;
+    if (total_cells < 0 || total_cells > (1LL << 32) - 1 || rho_d_len < 0 || v_len < 0) return DRAG_EINVAL_SIZE;
+    if (nspecies_max < 1 || nspecies_max > DRAG_EXPM_NMAX) return DRAG_EINVAL_SIZE;
+    if (nblocks == 0 || total_cells == 0) return DRAG_OK;
+    if (!blocks || !rho_g || !rho_d || !t_s || !v_in || !v_out) return DRAG_ENULL;
+    if (!aligned8(blocks) || !aligned8(rho_g) || !aligned8(rho_d) || !aligned8(t_s) || !aligned8(v_in) ||
+        !aligned8(v_out))
+        return DRAG_EALIGN;
+    const Layout L = layout(nblocks, total_cells);
+    if (!workspace || workspace_bytes < L.total) return DRAG_EWORKSPACE;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return DRAG_EALIGN;
+    uint32_t *st = dx_status_ptr();
+    if (!st) return DRAG_ECUDA;
+
+    return batched_run(dx_consts(), nblocks, reinterpret_cast<const Desc *>(blocks), total_cells, rho_d_len, v_len,
+                       nspecies_max, rho_g, rho_d, t_s, v_in, v_out, static_cast<char *>(workspace), L, st, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -538,4 +549,87 @@ extern "C" int drag_expm_apply_batched_noalloc(int64_t nblocks, const drag_block
     }
     return drag_expm_apply_batched(nblocks, blocks, total_cells, rho_d_len, v_len, nspecies_max, rho_g, rho_d, t_s,
                                    v_in, v_out, scratch, kNoAllocBytes, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Binned forward: drag_expm_apply for lane-per-cell sizes on large inputs runs
+// the pipeline above with one block. Its scratch (12 bytes per cell) comes
+// from a library-private, stream-ordered memory pool that keeps what it has
+// once allocated (release threshold: never), so calls on different streams
+// never share scratch, repeated calls do not reallocate, and stream capture
+// records the allocation as graph nodes.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr long long kBinnedMinCells = 262144;   // below: the tile-sorted kernel (one launch) is as fast
+
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64];
+
+cudaMemPool_t scratch_pool() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+        uint64_t keep = ~0ull;
+        if (cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return nullptr;
+        }
+        g_pool[dev] = p;
+    }
+    return g_pool[dev];
+}
+
+__global__ void dx_batch_single_desc(Desc *d, long long C, int N, double dt) {
+    d->cell_offset = 0;
+    d->dust_offset = 0;
+    d->vel_offset = 0;
+    d->ncells = (int)C;
+    d->nspecies = N;
+    d->dt = dt;
+}
+
+}  // namespace
+
+bool dx_binned_eligible(int n, int mode, long long C) {
+    return n >= 2 && n <= kBatchLpcNMax && mode == dx_batch_modes().m[n] && C >= kBinnedMinCells &&
+           C <= 0x7fffffffLL;
+}
+
+int dx_binned_forward(const DxConsts &K, long long C, int N, const double *rho_g, const double *rho_d,
+                      const double *t_s, double dt, const double *v_in, double *v_out, uint32_t *status,
+                      cudaStream_t stream) {
+    cudaMemPool_t pool = scratch_pool();
+    if (!pool) return DX_BINNED_UNAVAILABLE;
+    const Layout L = layout(1, C);
+    void *p = nullptr;
+    if (cudaMallocFromPoolAsync(&p, L.total + 256, pool, stream) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return DX_BINNED_UNAVAILABLE;
+    }
+    int rc = DRAG_OK;
+    if ((reinterpret_cast<uintptr_t>(p) & 255) != 0) {
+        rc = DX_BINNED_UNAVAILABLE;
+    } else {
+        Desc *D = reinterpret_cast<Desc *>(static_cast<char *>(p) + L.total);
+        dx_batch_single_desc<<<1, 1, 0, stream>>>(D, C, N, dt);
+        rc = batched_run(K, 1, D, C, (long long)N * C, 3LL * (N + 1) * C, N, rho_g, rho_d, t_s, v_in, v_out,
+                         static_cast<char *>(p), L, status, stream);
+    }
+    if (cudaFreeAsync(p, stream) != cudaSuccess && rc == DRAG_OK) rc = DRAG_ECUDA;
+    return rc;
+}
+
+extern "C" int32_t drag_expm_apply_launches(int64_t ncells, int32_t nspecies) {
+    if (ncells <= 0 || nspecies < 1 || nspecies > DRAG_EXPM_NMAX) return 0;
+    const int n = nspecies + 1;
+    return dx_binned_eligible(n, dx_mode_for(n), ncells) ? 6 : 1;
 }

@@ -192,9 +192,14 @@ static int apply_impl(const DxConsts &K, int64_t ncells, int32_t nspecies, const
     if (!st) return DRAG_ECUDA;
     const int n = nspecies + 1;
     const int mode = dx_mode_for(n);
-    if (mode != DX_MODE_WPC)
+    if (mode != DX_MODE_WPC) {
+        if (!heat && dx_binned_eligible(n, mode, ncells)) {
+            const int rc = dx_binned_forward(K, ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, st, stream);
+            if (rc != DX_BINNED_UNAVAILABLE) return rc;
+        }
         return dx_launch_forward_lpc(K, n, dx_lpc_store(mode), ncells, rho_g, rho_d, t_s, v_in, v_out, dt, st, heat,
                                      stream);
+    }
     const size_t smem = dx_forward_smem_bytes(n);
     if (!dx_once_per_device(0, [] {
             return cudaFuncSetAttribute(dx_forward_wpc, cudaFuncAttributeMaxDynamicSharedMemorySize,

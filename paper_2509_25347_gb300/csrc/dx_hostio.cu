@@ -14,6 +14,7 @@
 namespace {
 
 constexpr long long kDefaultChunk = 131072;
+constexpr long long kBinnedChunk = 262144;   // chunks of lane-per-cell sizes take the binned forward
 
 struct Pipe {
     std::mutex mu;   // held while a call enqueues its work (the fork / join events are shared)
@@ -43,13 +44,19 @@ Pipe *pipe_for_device() {
 // Doubles of one chunk slab: rho_g, rho_d (N), t_s (N), v (3n).
 size_t slab_doubles(int N, long long chunk) { return (size_t)chunk * (1 + 2 * (size_t)N + 3 * (size_t)(N + 1)); }
 
-long long chunk_of(long long chunk_cells) { return chunk_cells > 0 ? chunk_cells : kDefaultChunk; }
+// Default chunk: the binned forward's threshold where that path applies, else
+// smaller chunks (less copy time exposed at the ends of the pipeline).
+long long chunk_of(long long chunk_cells, int nspecies) {
+    if (chunk_cells > 0) return chunk_cells;
+    const int n = nspecies + 1;
+    return dx_binned_eligible(n, dx_mode_for(n), kBinnedChunk) ? kBinnedChunk : kDefaultChunk;
+}
 
 }  // namespace
 
 extern "C" size_t drag_expm_host_workspace_bytes(int32_t nspecies, int64_t chunk_cells) {
     if (nspecies < 1 || nspecies > DRAG_EXPM_NMAX || chunk_cells < 0) return 0;
-    return 2 * sizeof(double) * slab_doubles(nspecies, chunk_of(chunk_cells));
+    return 2 * sizeof(double) * slab_doubles(nspecies, chunk_of(chunk_cells, nspecies));
 }
 
 extern "C" int drag_expm_apply_host(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
@@ -61,7 +68,7 @@ extern "C" int drag_expm_apply_host(int64_t ncells, int32_t nspecies, const doub
         return DRAG_EINVAL_SIZE;
     if (ncells == 0) return DRAG_OK;
     if (!rho_g || !rho_d || !t_s || !v_in || !v_out || !workspace) return DRAG_ENULL;
-    const long long chunk = chunk_of(chunk_cells);
+    const long long chunk = chunk_of(chunk_cells, nspecies);
     const int N = nspecies, n = N + 1;
     if (workspace_bytes < drag_expm_host_workspace_bytes(nspecies, chunk)) return DRAG_EWORKSPACE;
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return DRAG_EALIGN;

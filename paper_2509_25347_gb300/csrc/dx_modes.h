@@ -32,3 +32,13 @@ int dx_launch_forward_f32(const DxConsts &K, long long ncells, int nspecies, con
 int dx_launch_forward_lpc(const DxConsts &K, int n, int store, long long C, const double *rho_g,
                           const double *rho_d, const double *t_s, const double *v_in, double *v_out, double dt,
                           uint32_t *status, double *heat, cudaStream_t stream);
+
+// Binned lane-per-cell forward (dx_batched.cu): the batched pipeline with one
+// block over the whole input, for sizes whose batched mode is the current mode
+// (n <= 9) and at least 262,144 cells. DX_BINNED_UNAVAILABLE: no scratch could
+// be had; the caller runs the tile-sorted kernel instead.
+#define DX_BINNED_UNAVAILABLE 1
+bool dx_binned_eligible(int n, int mode, long long C);
+int dx_binned_forward(const DxConsts &K, long long C, int N, const double *rho_g, const double *rho_d,
+                      const double *t_s, double dt, const double *v_in, double *v_out, uint32_t *status,
+                      cudaStream_t stream);

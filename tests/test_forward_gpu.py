@@ -145,7 +145,7 @@ def test_matches_eigen_truth(dx):
     assert_parity(out, ref, cells.v, tol=4e-15)
 
 
-@pytest.mark.parametrize("name", ["mrn_n16_128cube", "mrn_n4_128cube", "dustybox_n1_32k"])
+@pytest.mark.parametrize("name", ["mrn_n16_128cube", "mrn_n4_128cube", "mrn_n8_128cube_adjoint", "dustybox_n1_32k"])
 def test_full_size_sampled(dx, name):
     """Full-size workload in the benchmark's launch configuration: 256 sampled
     cells against the oracle, conservation and convexity on every cell."""
@@ -172,14 +172,54 @@ def test_full_size_sampled(dx, name):
 
 @pytest.mark.parametrize("N", [1, 4, 7, 9])
 def test_sorted_tiles_parity(dx, N):
-    """Lane-per-cell kernels sort each tile of cells by a cost proxy before
-    running them; at 320,077 cells the tile is 4 rounds of 128 cells (the
-    largest) with a ragged last tile. Every cell against the oracle."""
+    """320,077 cells, every cell against the oracle, through both lane-per-cell
+    paths: the binned pipeline (the default at this size for N <= 8) and the
+    tile-sorted kernel (each tile of up to 512 cells sorted by a cost proxy,
+    ragged last tile; forced here by the all-shared storage mode)."""
     cells = W.mrn(320077, N, seed=900 + N, stiff_lo=-4.0, stiff_hi=8.0)
-    out = gpu_apply(dx, cells)
     ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v)
+    out = gpu_apply(dx, cells)
+    assert_parity(out, ref, cells.v)
+    old = dx.get_mode(N)
+    try:
+        dx.set_mode(N, dx.MODE_LANE_SHARED)
+        assert dx.apply_launches(cells.ncells, N) == 1
+        out = gpu_apply(dx, cells)
+    finally:
+        dx.set_mode(N, old)
     assert_parity(out, ref, cells.v)
     assert dx.get_status() == 0
+
+
+@pytest.mark.parametrize("N", [1, 4, 6, 8])
+def test_binned_forward(dx, N):
+    """From 262,144 cells the default lane-per-cell sizes run the batched
+    pipeline over one block (6 launches). The per-cell arithmetic is that of
+    the tile-sorted kernel, which drag_expm_apply_heat always uses: identical
+    v_out. In place, invalid cells (NaN and the status bit) and dt = 0 too."""
+    import torch
+    C = 300001
+    cells = W.mrn(C, N, seed=40 + N, stiff_lo=-4.0, stiff_hi=8.0)
+    cells.rho_d[0, 11] = np.nan
+    cells.t_s[-1, 222222] = 0.0
+    rg, rd, ts, v = dev(cells)
+    assert dx.apply_launches(C, N) == 6 and dx.apply_launches(262143, N) == 1
+    out = dx.apply(rg, rd, ts, cells.dt, v)
+    assert dx.get_status() & dx.STATUS_BAD_CELL
+    heat_out, _ = dx.apply_heat(rg, rd, ts, cells.dt, v)
+    dx.get_status()
+    assert torch.equal(torch.nan_to_num(out, nan=3.0), torch.nan_to_num(heat_out, nan=3.0))
+    assert bool(torch.isnan(out[:, :, 11]).all()) and bool(torch.isnan(out[:, :, 222222]).all())
+    ok = torch.ones(C, dtype=torch.bool, device=out.device)
+    ok[[11, 222222]] = False
+    assert bool(torch.isfinite(out[:, :, ok]).all())
+    vin = v.clone()
+    dx.apply(rg, rd, ts, cells.dt, vin, vin)                        # in place
+    dx.get_status()
+    assert torch.equal(torch.nan_to_num(vin, nan=3.0), torch.nan_to_num(out, nan=3.0))
+    zero = dx.apply(rg, rd, ts, 0.0, v)
+    dx.get_status()
+    assert torch.equal(zero[:, :, ok], v[:, :, ok])
 
 
 def extreme_cells(N, norms, seed=3):
