@@ -48,10 +48,10 @@ KERNEL_SOURCES = {
 }
 MEASURED_TRAFFIC = {
     ("mrn_n16_128cube", "dx_forward_wpc"): {
-        "sources_sha256": "a2dd9024b1839328c5ac6a243bbb422ab1c89b0949c93d183d8017874761bc49",
-        "bytes_per_cell": (186.905856e6 + 81.047552e6) / 262144,
+        "sources_sha256": "c3a540fcc231e8da1f662d6dd1f9cfe5ea9e7437f89e5f4b9e683b0a16691022",
+        "bytes_per_cell": (186.784768e6 + 80.873472e6) / 262144,
         # FP64 FLOPs the kernel executes: thread-level (2 DFMA + DADD + DMUL) per cycle x elapsed cycles
-        "executed_flop_per_cell": (2 * 233.345985 + 16.000029 + 3.640165) * 48810305.395 / 262144,
+        "executed_flop_per_cell": (2 * 232.563561 + 15.946380 + 3.627959) * 48974520.105 / 262144,
         "capture": "profiles/dx_forward_wpc_mrn_n16.md",
     },
 }

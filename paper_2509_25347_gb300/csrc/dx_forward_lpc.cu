@@ -40,9 +40,13 @@ __device__ __forceinline__ unsigned int cost_proxy(const double *rgp, const doub
     return (nrm >= 0.0f && b < 0x7f800000u) ? b : 0x7f800000u;   // non-finite and NaN last among valid cells
 }
 
-// Register ceiling per thread.
+// Register ceiling per thread. The register file is split among the four SM
+// sub-partitions (16K registers each): at 168 registers three warps fit on a
+// sub-partition instead of two, which at n = 9 (hybrid storage) pays for the
+// spills it causes (measured 5.31 against 5.57 ms on 240,000 cells; other n
+// gain nothing from a ceiling).
 template <int NF, int ST>
-__host__ __device__ constexpr int lpc_max_regs() { return (ST == DX_LPC_HYBRID && NF == 9) ? 200 : 255; }
+__host__ __device__ constexpr int lpc_max_regs() { return (ST == DX_LPC_HYBRID && NF == 9) ? 168 : 255; }
 
 template <int NF, int ST>
 __global__ void __launch_bounds__(lpc_threads<NF, ST>()) __maxnreg__((lpc_max_regs<NF, ST>()))
