@@ -10,7 +10,7 @@ Tolerances:
   block of the Frechet direction (it cancels in every parameter gradient) and
   then sit within ~5e-15 S of a 50-digit truth even at dt/t_s = 1e8 (the
   oracle's pins), so 1e-13 S bounds their difference with margin;
-* finite differences: the spec bar, 1e-6 relative (see
+* finite differences: 1e-6 relative (see
   tests/test_oracle_adjoint_pins.py for the exact criterion and its noise floor).
 """
 import numpy as np
