@@ -101,6 +101,10 @@ int launch_one(const DxConsts &K, long long C, const double *rho_g, const double
         cudaFuncSetAttribute(dx_forward_lpc<NF, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
         return DRAG_ECUDA;
+    // shared memory sets the residency of these kernels: ask for the largest carveout (a hint)
+    if (ST != DX_LPC_REGS)
+        cudaFuncSetAttribute(dx_forward_lpc<NF, ST>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
     int rounds = kTile / kThreads;
     while (rounds > 1 && (C + rounds * kThreads - 1) / (rounds * kThreads) < 4LL * dx_sm_count()) rounds >>= 1;
     const long long blocks = (C + rounds * kThreads - 1) / (rounds * kThreads);
