@@ -8,6 +8,11 @@
 namespace {
 
 constexpr int kTile = 512;   // largest tile of cells a block sorts and runs
+// Tiles of fewer rounds than this run unsorted (the launcher uses one round,
+// tiles of one block's threads, on inputs too small to fill the GPU otherwise).
+#ifndef DX_LPC_SORT_MIN_ROUNDS
+#define DX_LPC_SORT_MIN_ROUNDS 1
+#endif
 
 // Threads per block: 4 warps, or 2 warps when shared memory holds part of the
 // matrices and n >= 9: there the slices (32 doubles per packed entry, 32 KB per
@@ -53,14 +58,23 @@ __global__ void __launch_bounds__(lpc_threads<NF, ST>()) __maxnreg__((lpc_max_re
 dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d, const double *t_s,
                const double *v_in, double *v_out, double dt, uint32_t *status, double *heat, DxConsts K) {
     extern __shared__ double smem[];
-    __shared__ unsigned long long key[kTile];     // (proxy << 32) | tile index, unique
+    // Sort keys ((proxy << 32) | tile index, unique) live only until the tile is
+    // sorted: with shared-memory storage they overlay the warps' matrix slices,
+    // which are first written after that (5 KB less per CTA, one more CTA per SM
+    // at n = 9).
+    constexpr bool kOverlay = ST != DX_LPC_REGS && (kTile / lpc_threads<NF, ST>()) * lpc_threads<NF, ST>() *
+                                                       sizeof(unsigned long long) <=
+                                                   sizeof(double) * (lpc_threads<NF, ST>() / 32) *
+                                                       dx_lpc_warp_smem_doubles<NF, ST>();
+    __shared__ unsigned long long key_static[kOverlay ? 1 : kTile];
+    unsigned long long *key = kOverlay ? reinterpret_cast<unsigned long long *>(smem + 32) : key_static;
     __shared__ unsigned short order[kTile];       // sorted position -> tile index
     double *bsh = smem;
     for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
     constexpr int kThreads = lpc_threads<NF, ST>();
     const int tile = rounds * kThreads;
     const long long base = (long long)blockIdx.x * tile;
-    if (rounds > 1) {
+    if (rounds >= DX_LPC_SORT_MIN_ROUNDS) {
         for (int r = 0; r < rounds; r++) {
             const int e = r * kThreads + threadIdx.x;
             const long long c = base + e;
@@ -77,7 +91,7 @@ dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d
             order[rank] = (unsigned short)e;
         }
     } else {
-        order[threadIdx.x] = (unsigned short)threadIdx.x;   // one round: grid-sized for small inputs, no sort
+        order[threadIdx.x] = (unsigned short)threadIdx.x;   // unsorted
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -95,7 +109,8 @@ int launch_one(const DxConsts &K, long long C, const double *rho_g, const double
                const double *v_in, double *v_out, double dt, uint32_t *status, double *heat, cudaStream_t stream) {
     constexpr int kThreads = lpc_threads<NF, ST>();
     const size_t smem = sizeof(double) * (32 + (size_t)(kThreads / 32) * dx_lpc_warp_smem_doubles<NF, ST>());
-    // the opt-in covers dynamic + static shared memory (the sort keys and order, 5 KB) above 48 KB
+    // the opt-in covers dynamic + static shared memory (the sort order and, unless they
+    // overlay the dynamic region, the keys) above 48 KB
     constexpr size_t kStatic = kTile * (sizeof(unsigned long long) + sizeof(unsigned short));
     if (smem + kStatic > 48 * 1024 &&
         cudaFuncSetAttribute(dx_forward_lpc<NF, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
