@@ -252,8 +252,12 @@ int drag_expm_backward(int64_t ncells, int32_t nspecies, const double *rho_g, co
  * drag_expm_backward recomputes them. drag_expm_apply_taped stores the ones
  * the forward forms, E_0 .. E_{s*-2} (E_0 alone for s* <= 1), in a tape, and
  * drag_expm_backward_taped reads them instead: it then forms neither the
- * Taylor polynomial nor those products, and its gradients are identical to
- * drag_expm_backward's. The tape trades HBM for FP64 work:
+ * Taylor polynomial nor those products. Where the forward runs one warp per
+ * cell (N >= 9, or any N whose mode is warp per cell) it forms each E_t by
+ * the adjoint's own FP64 operations, and the gradients are identical to
+ * drag_expm_backward's. For N <= 8 with the default modes the lane-per-cell
+ * forward writes the tape, and the gradients agree with drag_expm_backward's to
+ * rounding. The tape trades HBM for FP64 work:
  *   drag_expm_tape_bytes(ncells, nspecies, levels) bytes, about
  *   ncells * levels * 8 * (N+1)(N+2)/2 (rounded up to 128-byte slots),
  * where `levels` is the capacity per cell; a cell needs
@@ -273,8 +277,10 @@ size_t drag_expm_tape_bytes(int64_t ncells, int32_t nspecies, int32_t levels);
 int32_t drag_expm_tape_levels(int32_t sstar);
 
 /*
- * drag_expm_apply_taped — drag_expm_apply (bit-identical v_out), run one warp
- * per cell for every nspecies, that also writes the adjoint tape.
+ * drag_expm_apply_taped — drag_expm_apply that also writes the adjoint tape.
+ * v_out is bit-identical to drag_expm_apply's under the same mode table. N <= 8
+ * with the default modes run lane per cell (tile-sorted, one launch); other
+ * sizes run one warp per cell.
  *   levels : tape capacity per cell, 1 .. DRAG_TAPE_MAX_LEVELS.
  *   tape   : DEVICE, 256-byte aligned, >= drag_expm_tape_bytes(ncells,
  *            nspecies, levels) bytes, owned by the caller, written; must not

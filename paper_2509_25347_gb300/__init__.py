@@ -310,7 +310,7 @@ def tape_levels_needed(rho_g, rho_d, t_s, dt: float, stream=None) -> int:
 
 def apply_taped(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, levels: int | None = None, tape=None,
                 stream=None):
-    """:func:`apply` (bit-identical v_out, one warp per cell) that also records
+    """:func:`apply` (bit-identical v_out) that also records
     the adjoint tape; returns (v_out, Tape). ``levels`` is the tape capacity per
     cell (default: :func:`tape_levels_needed`); ``tape`` may pass a Tape to reuse
     (its buffer must be large enough)."""
@@ -396,7 +396,8 @@ def _autograd_function():
 
     class _DragExpmTaped(torch.autograd.Function):
         """DragExpm whose forward records the adjoint tape (apply_taped) and whose
-        backward reads it: identical values and gradients, less FP64 work in the
+        backward reads it: identical values, gradients identical from N = 9 on (to
+        rounding below, where the lane-per-cell forward writes the tape), less FP64 work in the
         backward for a tape of about ncells * levels * 4 (N+1)(N+2) bytes.
 
         forward(rho_g, rho_d, t_s, dt, v_in, levels=None)."""

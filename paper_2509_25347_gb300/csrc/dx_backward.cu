@@ -441,8 +441,7 @@ __device__ __forceinline__ void bwd_wpc_body(const BwdArgs &a, const DxConsts &K
         bool taped = false;
         const double *tcell = nullptr;
         if (TAPE) {
-            const long long h = dx_cell_fingerprint(lane, N, rg, rd, ts, a.dt,
-                                                    ((unsigned long long)a.levels << 8) | (unsigned long long)n);
+            const long long h = dx_cell_fingerprint(lane, N, rg, rd, ts, a.dt, dx_tape_salt(a.levels, n));
             long long stored = 0;
             if (lane == 0) stored = a.thdr[c];
             stored = __shfl_sync(DX_FULL, stored, 0);

@@ -248,6 +248,13 @@ extern "C" int drag_expm_apply_taped(int64_t ncells, int32_t nspecies, const dou
     FwdTape tp{static_cast<long long *>(tape),
                reinterpret_cast<double *>(static_cast<char *>(tape) + dx_tape_hdr_bytes(ncells)), levels,
                dx_tape_slot(n)};
+    // small n: the lane-per-cell forward writes the tape (when the mode table has
+    // its default storage there), far cheaper than warp per cell at these sizes
+    const int mode = dx_mode_for(n);
+    if (n <= DX_LPC_TAPE_NMAX &&
+        mode == (n <= DX_LPC_REG_NMAX ? DX_MODE_LPC_REG : DX_MODE_LPC_HYB))
+        return dx_launch_forward_lpc_taped(dx_consts(), n, ncells, rho_g, rho_d, t_s, v_in, v_out, dt, st, tp.hdr,
+                                           tp.m, levels, tp.P, stream);
     const long long grid = (ncells + kCellsPerBlock - 1) / kCellsPerBlock;
     dx_forward_wpc_taped<<<(unsigned)grid, kWarpsPerBlock * 32, dx_forward_smem_bytes(n), stream>>>(a, dx_consts(), tp);
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;

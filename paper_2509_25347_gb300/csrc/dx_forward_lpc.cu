@@ -46,17 +46,26 @@ __device__ __forceinline__ unsigned int cost_proxy(const double *rgp, const doub
 }
 
 // Register ceiling per thread. The register file is split among the four SM
-// sub-partitions (16K registers each): at 168 registers three warps fit on a
-// sub-partition instead of two, which at n = 9 (hybrid storage) pays for the
-// spills it causes (measured 5.31 against 5.57 ms on 240,000 cells; other n
-// gain nothing from a ceiling).
+// sub-partitions (16K registers each): at 168 registers a sub-partition can
+// hold three warps instead of two, which at n = 9 (hybrid storage) paid for the
+// spills it causes (5.31 against 5.57 ms on 240,000 cells; other n gained
+// nothing from a ceiling).
 template <int NF, int ST>
 __host__ __device__ constexpr int lpc_max_regs() { return (ST == DX_LPC_HYBRID && NF == 9) ? 168 : 255; }
 
-template <int NF, int ST>
+// Adjoint tape of a launch (TAPE kernels): cell c's fingerprint at hdr[c], its
+// level t at m + (c * levels + t) * P.
+struct LpcTape {
+    long long *hdr;
+    double *m;
+    int levels, P;
+};
+
+template <int NF, int ST, bool TAPE>
 __global__ void __launch_bounds__(lpc_threads<NF, ST>()) __maxnreg__((lpc_max_regs<NF, ST>()))
 dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d, const double *t_s,
-               const double *v_in, double *v_out, double dt, uint32_t *status, double *heat, DxConsts K) {
+               const double *v_in, double *v_out, double dt, uint32_t *status, double *heat, DxConsts K,
+               LpcTape tp) {
     extern __shared__ double smem[];
     // Sort keys ((proxy << 32) | tile index, unique) live only until the tile is
     // sorted: with shared-memory storage they overlay the warps' matrix slices,
@@ -98,33 +107,37 @@ dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d
     double *wsm = ST != DX_LPC_REGS ? smem + 32 + (threadIdx.x >> 5) * dx_lpc_warp_smem_doubles<NF, ST>() : nullptr;
     for (int r = 0; r < rounds; r++) {
         const long long c = base + order[r * kThreads + threadIdx.x];
-        if (c < C)
+        if (c < C) {
+            DxTapeCell tc{nullptr, nullptr, 0, 0};
+            if (TAPE) tc = DxTapeCell{tp.hdr + c, tp.m + (size_t)c * tp.levels * tp.P, tp.levels, tp.P};
             dx_lpc_forward_cell<NF, ST>(lane, rho_g + c, rho_d + c, t_s + c, v_in + c, v_out + c, C, dt, K, bsh,
-                                          wsm, status, heat ? heat + c : nullptr);
+                                        wsm, status, heat ? heat + c : nullptr, tc);
+        }
     }
 }
 
-template <int NF, int ST>
+template <int NF, int ST, bool TAPE = false>
 int launch_one(const DxConsts &K, long long C, const double *rho_g, const double *rho_d, const double *t_s,
-               const double *v_in, double *v_out, double dt, uint32_t *status, double *heat, cudaStream_t stream) {
+               const double *v_in, double *v_out, double dt, uint32_t *status, double *heat, cudaStream_t stream,
+               LpcTape tp = LpcTape{nullptr, nullptr, 0, 0}) {
     constexpr int kThreads = lpc_threads<NF, ST>();
     const size_t smem = sizeof(double) * (32 + (size_t)(kThreads / 32) * dx_lpc_warp_smem_doubles<NF, ST>());
     // the opt-in covers dynamic + static shared memory (the sort order and, unless they
     // overlay the dynamic region, the keys) above 48 KB
     constexpr size_t kStatic = kTile * (sizeof(unsigned long long) + sizeof(unsigned short));
     if (smem + kStatic > 48 * 1024 &&
-        cudaFuncSetAttribute(dx_forward_lpc<NF, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaFuncSetAttribute(dx_forward_lpc<NF, ST, TAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
         return DRAG_ECUDA;
     // shared memory sets the residency of these kernels: ask for the largest carveout (a hint)
     if (ST != DX_LPC_REGS)
-        cudaFuncSetAttribute(dx_forward_lpc<NF, ST>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(dx_forward_lpc<NF, ST, TAPE>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     int rounds = kTile / kThreads;
     while (rounds > 1 && (C + rounds * kThreads - 1) / (rounds * kThreads) < 4LL * dx_sm_count()) rounds >>= 1;
     const long long blocks = (C + rounds * kThreads - 1) / (rounds * kThreads);
-    dx_forward_lpc<NF, ST><<<(unsigned)blocks, kThreads, smem, stream>>>(C, rounds, rho_g, rho_d, t_s, v_in, v_out,
-                                                                          dt, status, heat, K);
+    dx_forward_lpc<NF, ST, TAPE><<<(unsigned)blocks, kThreads, smem, stream>>>(C, rounds, rho_g, rho_d, t_s, v_in,
+                                                                                v_out, dt, status, heat, K, tp);
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }
 
@@ -165,6 +178,26 @@ int dx_launch_forward_lpc(const DxConsts &K, int n, int store, long long C, cons
         DX_CASE(10)
         DX_CASE(11)
         DX_CASE(12)
+#undef DX_CASE
+        default: return DRAG_EINVAL_SIZE;
+    }
+}
+
+int dx_launch_forward_lpc_taped(const DxConsts &K, int n, long long C, const double *rho_g, const double *rho_d,
+                                const double *t_s, const double *v_in, double *v_out, double dt, uint32_t *status,
+                                long long *hdr, double *m, int levels, int P, cudaStream_t stream) {
+    const LpcTape tp{hdr, m, levels, P};
+    switch (n) {
+#define DX_CASE(NF, ST) \
+    case NF: return launch_one<NF, ST, true>(K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, nullptr, stream, tp);
+        DX_CASE(2, DX_LPC_REGS)
+        DX_CASE(3, DX_LPC_REGS)
+        DX_CASE(4, DX_LPC_REGS)
+        DX_CASE(5, DX_LPC_REGS)
+        DX_CASE(6, DX_LPC_REGS)
+        DX_CASE(7, DX_LPC_HYBRID)
+        DX_CASE(8, DX_LPC_HYBRID)
+        DX_CASE(9, DX_LPC_HYBRID)
 #undef DX_CASE
         default: return DRAG_EINVAL_SIZE;
     }

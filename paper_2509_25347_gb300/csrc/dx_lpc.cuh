@@ -21,6 +21,7 @@
 #pragma once
 
 #include "dx_common.cuh"
+#include "dx_tape.cuh"
 
 enum : int { DX_LPC_REGS = 0, DX_LPC_SHARED = 1, DX_LPC_HYBRID = 2 };
 
@@ -73,11 +74,15 @@ __host__ __device__ constexpr int dx_lpc_warp_smem_doubles() {
 // One cell per lane. Pointers address this cell; element (i) of a per-species
 // array is at p[i * stride]; velocity (d, f) at p[(d * NF + f) * stride].
 // smem_warp: this warp's slice (ST != DX_LPC_REGS); bsh: b_i = 1/i! in shared memory.
+// tp (tp.hdr null: none): the cell's adjoint tape, written as by the warp-per-cell
+// forward (the packed order here is the tape's): E_0 .. E_{s-2} when they fit,
+// the fingerprint word always.
 template <int NF, int ST>
 __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp, const double *rdp, const double *tsp,
                                                     const double *vip, double *vop, long long stride, double dt,
                                                     const DxConsts &K, const double *bsh, double *smem_warp,
-                                                    uint32_t *status, double *heat = nullptr) {
+                                                    uint32_t *status, double *heat = nullptr,
+                                                    DxTapeCell tp = DxTapeCell{nullptr, nullptr, 0, 0}) {
     constexpr int N = NF - 1;
     constexpr int NT = DxPacked<NF>::NT;
     using P = DxPacked<NF>;
@@ -99,6 +104,12 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
         if (heat) *heat = NAN;
         atomicOr(status, DRAG_STATUS_BAD_CELL);
         return;
+    }
+
+    unsigned long long fph = 0;   // fingerprint of the raw inputs (rho_d, t_s still unconverted here)
+    if (tp.hdr) {
+#pragma unroll
+        for (int i = 0; i < N; i++) fph ^= dx_fingerprint_term(i + 1, eps[i], alpha[i]);
     }
 
     // ---------------- A = dt Omega_v entries and the 1-norm (ascending species order)
@@ -129,6 +140,14 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
     int kk, s;
     dx_select(__longlong_as_double(nb), K, kk, s);
     const int m = K.mk[kk];
+    double *tape = nullptr;
+    const int tlev = dx_tape_levels(s);
+    if (tp.hdr) {
+        const long long h = dx_fingerprint_final(fph, rg, dt, dx_tape_salt(tp.levels, NF));
+        const bool fits = tlev <= tp.levels;
+        *tp.hdr = fits ? h : ~h;
+        if (fits) tape = tp.m;
+    }
 
     // ---------------- symmetric arrowhead X = 2^-s D_sigma A D_sigma^-1
     constexpr bool kSharedF = ST == DX_LPC_SHARED, kSharedG = ST != DX_LPC_REGS;
@@ -196,6 +215,10 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
             if (k != i) acc = fma(Fm[P::at(i, k)], sig[k], acc);
         Fm[P::at(i, i)] = fma(-tau[i], acc, 1.0);
     }
+    if (tape) {
+#pragma unroll
+        for (int e = 0; e < NT; e++) tape[e] = Fm[e];
+    }
     for (int it = 0; it < s; it++) {
 #pragma unroll
         for (int i = 0; i < NF; i++) {
@@ -214,6 +237,11 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
             for (int k = 0; k < NF; k++)
                 if (k != i) acc = fma(Gm[P::at(i, k)], sig[k], acc);
             Gm[P::at(i, i)] = fma(-tau[i], acc, 1.0);
+        }
+        if (tape && it + 1 < tlev) {
+            double *lv = tape + (size_t)(it + 1) * tp.P;
+#pragma unroll
+            for (int e = 0; e < NT; e++) lv[e] = Gm[e];
         }
         dx_lane_take(Fm, Gm);
     }
