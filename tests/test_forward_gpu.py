@@ -255,3 +255,33 @@ def test_extreme_norms(dx, N):
     assert st == 1 and np.all(np.isnan(ref[:, :, 1]))
     assert np.all(np.isnan(out[:, :, 1])) and np.all(np.isfinite(out[:, :, 0]))
     assert dx.get_status() & dx.STATUS_BAD_CELL
+
+
+def test_binned_forward_in_cuda_graph(dx):
+    """The binned forward (scratch taken stream-ordered from the library's pool)
+    is captured in a CUDA graph and replayed: same outputs as eager calls, also
+    after the inputs change in place between replays."""
+    import torch
+    N, C = 4, 262147
+    cells = W.mrn(C, N, seed=77, stiff_lo=-4.0, stiff_hi=8.0)
+    rg, rd, ts, v = dev(cells)
+    assert dx.apply_launches(C, N) == 6
+    out = torch.empty_like(v)
+    eager = dx.apply(rg, rd, ts, cells.dt, v)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        dx.apply(rg, rd, ts, cells.dt, v, out)          # warm-up outside capture (pool, attributes)
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        dx.apply(rg, rd, ts, cells.dt, v, out)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, eager)
+    v.mul_(-0.5)
+    ts.mul_(3.0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, dx.apply(rg, rd, ts, cells.dt, v))
+    assert dx.get_status() == 0
