@@ -10,7 +10,7 @@
 //   5. main     (persistent grids) : warps pull work items from atomic counters.
 //      An item is 32 cells of one bin run lane-per-cell (small n, the lanes
 //      of a warp share m* and s*, so no lane idles) or one cell run
-//      warp-per-cell (large n), by the fixed per-n rule of dx_batch_modes().
+//      warp-per-cell (large n), per n as dx_batch_modes() reads the mode table.
 //      The two kinds of item run in two kernels, each with its own queue, so
 //      that the register-heavy lane-per-cell code does not set the occupancy
 //      of the warp-per-cell work.
@@ -392,17 +392,21 @@ bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0;
 
 }  // namespace
 
-// Kernel family per n for the batched path. Items are binned by (n, k*, s*),
-// so the 32 lanes of a lane-per-cell item run exactly their own Taylor order
-// and squaring count; the standalone kernels' mode table (measured on
-// unsorted cells, whose warps run the largest s* of 32 cells) does not
-// carry over. Lane per cell up to n = kBatchLpcNMax (matrices in registers up
-// to DX_LPC_REG_NMAX, the hybrid storage above), warp per cell above.
+// Kernel family per n for the batched path: 32 cells per warp (lane per cell)
+// or one (warp per cell) as the device's mode table says (drag_expm_autotune
+// sets it from measurements), for n <= kBatchLpcNMax; warp per cell above.
+// The lane-per-cell storage here is the one compiled into dx_batch_main_lpc:
+// registers up to DX_LPC_REG_NMAX, the hybrid storage above. Items are binned
+// by (n, k*, s*), so the 32 lanes of a lane-per-cell item run exactly their
+// own Taylor order and squaring count.
 Modes dx_batch_modes() {
     Modes M;
-    for (int n = 0; n <= DX_NMAXF; n++)
-        M.m[n] = (n < 2 || n > kBatchLpcNMax) ? DX_MODE_WPC
-                                               : (n <= DX_LPC_REG_NMAX ? DX_MODE_LPC_REG : DX_MODE_LPC_HYB);
+    for (int n = 0; n <= DX_NMAXF; n++) {
+        if (n < 2 || n > kBatchLpcNMax || dx_mode_for(n) == DX_MODE_WPC)
+            M.m[n] = DX_MODE_WPC;
+        else
+            M.m[n] = n <= DX_LPC_REG_NMAX ? DX_MODE_LPC_REG : DX_MODE_LPC_HYB;
+    }
     return M;
 }
 

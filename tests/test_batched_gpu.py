@@ -65,6 +65,25 @@ def test_batched_parity_mixed(dx):
     assert_block_parity(desc, v, out, ref)
 
 
+def test_batched_follows_mode_table(dx):
+    """The batched path takes lane- or warp-per-cell per n from the mode table:
+    with N = 4 and N = 8 set to warp per cell, those blocks run warp per cell
+    and still match the oracle."""
+    batch = mixed_batch(seed=3)
+    desc, rg, rd, ts, v = batch.pack()
+    ref, st = oracle.drag_apply_batched(desc, rg, rd, ts, v)
+    old = {N: dx.get_mode(N) for N in (4, 8)}
+    try:
+        for N in old:
+            dx.set_mode(N, dx.MODE_WARP_PER_CELL)
+        out = dx.apply_batched(desc, t(rg), t(rd), t(ts), t(v)).cpu().numpy()
+    finally:
+        for N, m in old.items():
+            dx.set_mode(N, m)
+    assert dx.get_status() == 0 and st == 0
+    assert_block_parity(desc, v, out, ref)
+
+
 def test_batched_matches_plain_entry_point(dx):
     """Per block, the batched result equals drag_expm_apply on the same cells to 1e-13
     (bit-identical where both take the same kernel family)."""
