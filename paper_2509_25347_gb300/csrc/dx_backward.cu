@@ -26,6 +26,9 @@
 //   dL/dalpha_i = dt [eps_i (Z_0i - Z_00) + (Z_i0 - Z_ii)],
 //   dL/drho_d,i = dL/deps_i / rho_g,  dL/dt_s,i = -alpha_i^2 dL/dalpha_i,
 //   dL/drho_g = -sum_i eps_i dL/deps_i / rho_g.
+// The taped kernel reads E_0 .. E_{s-2} from the adjoint tape the forward wrote
+// (dx_tape.cuh) wherever the cell's fingerprint matches, so it forms neither F
+// nor those E^2; its squarings before the last two carry only E L + L E.
 #include <cmath>
 
 #include "dx_wpc.cuh"
