@@ -114,6 +114,13 @@ __device__ __forceinline__ void bwd_xvec(int lane, int n, const DxVecs &V, doubl
     if (on && phi == 0) yo[d * n] = fma(c1, acc, c0 * a[d * n]);
 }
 
+// Smallest n whose Taylor steps use the fused round below. Below it the
+// round's per-step role selection costs more than the rounds it saves
+// (measured: n = 4, 5, 6 slower by 5-7 %; n = 7, 8, 9, 17 faster by 1-3 %).
+#ifndef DX_BWD_FOLD_NMIN
+#define DX_BWD_FOLD_NMIN 7
+#endif
+
 // Lanes of the fused round below: n for column 0, 3 for y'_d[0], nx for the
 // entries f >= 1 of the three y'_d, q entries each (3 FMAs per entry), all
 // within the round's n + 4 FMA steps. False when n is too large for that.
@@ -395,7 +402,7 @@ __device__ __forceinline__ void bwd_wpc_body(const BwdArgs &a, const DxConsts &K
     double *gg = yv1 + 3 * n;    // g_d                                       [3][n]
     double *wv = gg + 3 * n;     // b_{j+1} a_3 of the current Taylor step    [n]
     int fold_nx = 0, fold_q = 0;
-    const bool fold = bwd_fold_fits(n, fold_nx, fold_q);
+    const bool fold = n >= DX_BWD_FOLD_NMIN && bwd_fold_fits(n, fold_nx, fold_q);
 
     const long long C = a.C;
     // Each block owns kCellsPerBlock consecutive cells, taken one at a time by
