@@ -21,6 +21,7 @@ import pytest
 import oracle
 from paper_2509_25347_gb300 import workloads as W
 from tests.test_backward_gpu import assert_adjoint_parity
+from tests.test_oracle_adjoint_pins import assert_fd_agreement, finite_difference_gradients
 
 pytestmark = pytest.mark.gpu
 
@@ -266,3 +267,26 @@ def test_lane_per_cell_tape(dx, N):
     for a, b in zip(stale, fresh):
         assert torch.equal(a, b)
     assert dx.get_status() == 0
+
+
+def test_taped_finite_differences_64_cells(dx):
+    """The N = 8 differentiation workload through the tape (written there by the
+    lane-per-cell forward): loss 0.5 ||v_out - v_target||^2, gradients with
+    respect to v_in, rho_d, t_s on 64 random cells against central differences
+    of the GPU forward (1e-6 relative, as for the recomputing adjoint)."""
+    cells = W.workload("mrn_n8_128cube_adjoint", ncells=8192)
+    target = W.adjoint_target(cells.ncells, cells.nspecies)
+    idx = np.sort(np.random.default_rng(4321).choice(cells.ncells, 64, replace=False))
+    sub = cells.subset(idx)
+    vt = target[:, :, idx]
+
+    def fwd(c):
+        return dx.apply(t(c.rho_g), t(c.rho_d), t(c.t_s), c.dt, t(c.v)).cpu().numpy()
+
+    rg, rd, ts = dev_args(sub)
+    out, tape = dx.apply_taped(rg, rd, ts, sub.dt, t(sub.v))
+    g = out.cpu().numpy() - vt
+    gv, _, grd, gts = [x.cpu().numpy() for x in dx.backward(rg, rd, ts, sub.dt, t(sub.v), t(g), tape=tape)]
+    gv_fd, grd_fd, gts_fd = finite_difference_gradients(fwd, sub, vt)
+    assert_fd_agreement(sub, g, gv, grd, gts, gv_fd, grd_fd, gts_fd)
+
