@@ -279,8 +279,8 @@ int32_t drag_expm_tape_levels(int32_t sstar);
 /*
  * drag_expm_apply_taped — drag_expm_apply that also writes the adjoint tape.
  * v_out is bit-identical to drag_expm_apply's under the same mode table. N <= 8
- * with the default modes run lane per cell (tile-sorted, one launch); other
- * sizes run one warp per cell.
+ * with the default modes run lane per cell, like drag_expm_apply (binned from
+ * 262,144 cells, tile-sorted below); other sizes run one warp per cell.
  *   levels : tape capacity per cell, 1 .. DRAG_TAPE_MAX_LEVELS.
  *   tape   : DEVICE, 256-byte aligned, >= drag_expm_tape_bytes(ncells,
  *            nspecies, levels) bytes, owned by the caller, written; must not

@@ -230,24 +230,35 @@ struct MainArgs {
     double *v_out;
     uint32_t *status;
     int warp_doubles;   // per-warp shared-memory slice (doubles)
+    // adjoint tape (taped lane-per-cell kernel only): the cell at cell_offset +
+    // c of its block has its fingerprint at thdr[cell], its level t at
+    // tm + (cell * tlevels + t) * tP
+    long long *thdr;
+    double *tm;
+    int tlevels, tP;
 };
 
-template <int NF, int ST>
+template <int NF, int ST, bool TAPE>
 __device__ __forceinline__ void lpc_item(int lane, const MainArgs &a, const Desc &d, long long c, const DxConsts &K,
                                          const double *bsh, double *wsm) {
     const long long C = d.ncells;
+    DxTapeCell tc{nullptr, nullptr, 0, 0};
+    if (TAPE) {
+        const long long cell = d.cell_offset + c;
+        tc = DxTapeCell{a.thdr + cell, a.tm + (size_t)cell * a.tlevels * a.tP, a.tlevels, a.tP};
+    }
     dx_lpc_forward_cell<NF, ST>(lane, a.rho_g + d.cell_offset + c, a.rho_d + d.dust_offset + c,
                                   a.t_s + d.dust_offset + c, a.v_in + d.vel_offset + c, a.v_out + d.vel_offset + c, C,
-                                  d.dt, K, bsh, wsm, a.status);
+                                  d.dt, K, bsh, wsm, a.status, nullptr, tc);
 }
 
-__device__ __forceinline__ void lpc_dispatch(int n, int mode, int lane, const MainArgs &a, const Desc &d, long long c,
+template <bool TAPE>
+__device__ __forceinline__ void lpc_dispatch(int n, int lane, const MainArgs &a, const Desc &d, long long c,
                                              const DxConsts &K, const double *bsh, double *wsm) {
-    // the batched modes are fixed (dx_batch_modes): registers up to n = 6, hybrid above
-    (void)mode;
+    // the storage per n is compiled in: registers up to n = 6, hybrid above
     switch (n) {
 #define DX_ITEM(NF, ST) \
-    case NF: lpc_item<NF, ST>(lane, a, d, c, K, bsh, wsm); break;
+    case NF: lpc_item<NF, ST, TAPE>(lane, a, d, c, K, bsh, wsm); break;
         DX_ITEM(2, DX_LPC_REGS)
         DX_ITEM(3, DX_LPC_REGS)
         DX_ITEM(4, DX_LPC_REGS)
@@ -311,8 +322,10 @@ dx_batch_main_wpc(MainArgs a, Work W, DxConsts K) {
     });
 }
 
+template <bool TAPE>
 __global__ void __launch_bounds__(kLpcWarps * 32)
 dx_batch_main_lpc(MainArgs a, Work W, Modes M, DxConsts K) {
+    (void)M;   // lane-per-cell items only (the bins already carry the mode)
     extern __shared__ double smem[];
     double *bsh = smem;
     for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
@@ -325,7 +338,7 @@ dx_batch_main_lpc(MainArgs a, Work W, Modes M, DxConsts K) {
         if (pos < W.offs[bin + 1]) {
             const unsigned long long p = W.perm[pos];
             const Desc d = a.blocks[p >> 32];
-            lpc_dispatch(n, M.m[n], lane, a, d, (long long)(p & 0xffffffffull), K, bsh, wsm);
+            lpc_dispatch<TAPE>(n, lane, a, d, (long long)(p & 0xffffffffull), K, bsh, wsm);
         }
         __syncwarp();
     });
@@ -410,11 +423,13 @@ Modes dx_batch_modes() {
     return M;
 }
 
-// The five-kernel pipeline on a checked workspace ws with layout L.
+// The five-kernel pipeline on a checked workspace ws with layout L. thdr
+// (null: none): adjoint tape written by the lane-per-cell items (see MainArgs).
 static int batched_run(const DxConsts &K, long long nblocks, const Desc *D, long long total_cells, long long rho_d_len,
                        long long v_len, int nspecies_max, const double *rho_g, const double *rho_d,
                        const double *t_s, const double *v_in, double *v_out, char *ws, const Layout &L,
-                       uint32_t *st, cudaStream_t stream) {
+                       uint32_t *st, cudaStream_t stream, long long *thdr = nullptr, double *tm = nullptr,
+                       int tlevels = 0, int tP = 0) {
     Work W;
     W.perm = reinterpret_cast<unsigned long long *>(ws + L.perm);
     W.key = reinterpret_cast<unsigned int *>(ws + L.key);
@@ -440,20 +455,21 @@ static int batched_run(const DxConsts &K, long long nblocks, const Desc *D, long
     bool has_wpc = false, has_lpc = false;
     warp_doubles_for(M, nspecies_max + 1, &wd_wpc, &wd_lpc, &has_wpc, &has_lpc);
     if (has_lpc) {
-        MainArgs a{D, rho_g, rho_d, t_s, v_in, v_out, st, wd_lpc};
+        MainArgs a{D, rho_g, rho_d, t_s, v_in, v_out, st, wd_lpc, thdr, tm, tlevels, tP};
+        void (*kern)(MainArgs, Work, Modes, DxConsts) = thdr ? dx_batch_main_lpc<true> : dx_batch_main_lpc<false>;
         const size_t smem = sizeof(double) * (32 + (size_t)kLpcWarps * wd_lpc);
         if (smem > 48 * 1024 &&
-            cudaFuncSetAttribute(dx_batch_main_lpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return DRAG_ECUDA;
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dx_batch_main_lpc, kLpcWarps * 32, smem) !=
-                cudaSuccess || per_sm < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLpcWarps * 32, smem) != cudaSuccess ||
+            per_sm < 1)
             per_sm = 1;
-        dx_batch_main_lpc<<<sms * per_sm, kLpcWarps * 32, smem, stream>>>(a, W, M, K);
+        kern<<<sms * per_sm, kLpcWarps * 32, smem, stream>>>(a, W, M, K);
         if (cudaGetLastError() != cudaSuccess) return DRAG_ECUDA;
     }
     if (has_wpc) {
-        MainArgs a{D, rho_g, rho_d, t_s, v_in, v_out, st, wd_wpc};
+        MainArgs a{D, rho_g, rho_d, t_s, v_in, v_out, st, wd_wpc, nullptr, nullptr, 0, 0};
         const size_t smem = sizeof(double) * (size_t)kWpcWarps * (wd_wpc + 2 * kPairSlots / 4);
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(dx_batch_main_wpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -610,7 +626,7 @@ bool dx_binned_eligible(int n, int mode, long long C) {
 
 int dx_binned_forward(const DxConsts &K, long long C, int N, const double *rho_g, const double *rho_d,
                       const double *t_s, double dt, const double *v_in, double *v_out, uint32_t *status,
-                      cudaStream_t stream) {
+                      cudaStream_t stream, long long *thdr, double *tm, int tlevels, int tP) {
     cudaMemPool_t pool = scratch_pool();
     if (!pool) return DX_BINNED_UNAVAILABLE;
     const Layout L = layout(1, C);
@@ -626,7 +642,7 @@ int dx_binned_forward(const DxConsts &K, long long C, int N, const double *rho_g
         Desc *D = reinterpret_cast<Desc *>(static_cast<char *>(p) + L.total);
         dx_batch_single_desc<<<1, 1, 0, stream>>>(D, C, N, dt);
         rc = batched_run(K, 1, D, C, (long long)N * C, 3LL * (N + 1) * C, N, rho_g, rho_d, t_s, v_in, v_out,
-                         static_cast<char *>(p), L, status, stream);
+                         static_cast<char *>(p), L, status, stream, thdr, tm, tlevels, tP);
     }
     if (cudaFreeAsync(p, stream) != cudaSuccess && rc == DRAG_OK) rc = DRAG_ECUDA;
     return rc;

@@ -252,9 +252,15 @@ extern "C" int drag_expm_apply_taped(int64_t ncells, int32_t nspecies, const dou
     // its default storage there), far cheaper than warp per cell at these sizes
     const int mode = dx_mode_for(n);
     if (n <= DX_LPC_TAPE_NMAX &&
-        mode == (n <= DX_LPC_REG_NMAX ? DX_MODE_LPC_REG : DX_MODE_LPC_HYB))
+        mode == (n <= DX_LPC_REG_NMAX ? DX_MODE_LPC_REG : DX_MODE_LPC_HYB)) {
+        if (dx_binned_eligible(n, mode, ncells)) {   // large inputs: binned, as drag_expm_apply
+            const int rc2 = dx_binned_forward(dx_consts(), ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, st,
+                                              stream, tp.hdr, tp.m, levels, tp.P);
+            if (rc2 != DX_BINNED_UNAVAILABLE) return rc2;
+        }
         return dx_launch_forward_lpc_taped(dx_consts(), n, ncells, rho_g, rho_d, t_s, v_in, v_out, dt, st, tp.hdr,
                                            tp.m, levels, tp.P, stream);
+    }
     const long long grid = (ncells + kCellsPerBlock - 1) / kCellsPerBlock;
     dx_forward_wpc_taped<<<(unsigned)grid, kWarpsPerBlock * 32, dx_forward_smem_bytes(n), stream>>>(a, dx_consts(), tp);
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;

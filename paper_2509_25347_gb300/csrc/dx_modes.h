@@ -39,9 +39,11 @@ int dx_launch_forward_lpc(const DxConsts &K, int n, int store, long long C, cons
 // be had; the caller runs the tile-sorted kernel instead.
 #define DX_BINNED_UNAVAILABLE 1
 bool dx_binned_eligible(int n, int mode, long long C);
+// thdr (null: none): also writes the adjoint tape (geometry as in drag_expm_apply_taped).
 int dx_binned_forward(const DxConsts &K, long long C, int N, const double *rho_g, const double *rho_d,
                       const double *t_s, double dt, const double *v_in, double *v_out, uint32_t *status,
-                      cudaStream_t stream);
+                      cudaStream_t stream, long long *thdr = nullptr, double *tm = nullptr, int tlevels = 0,
+                      int tP = 0);
 
 // Lane-per-cell forward that also writes the adjoint tape (dx_tape.cuh), for
 // n <= DX_LPC_TAPE_NMAX with the default storage of each n (registers up to
