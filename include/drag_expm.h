@@ -253,9 +253,9 @@ int drag_expm_backward(int64_t ncells, int32_t nspecies, const double *rho_g, co
  * the forward forms, E_0 .. E_{s*-2} (E_0 alone for s* <= 1), in a tape, and
  * drag_expm_backward_taped reads them instead: it then forms neither the
  * Taylor polynomial nor those products. Where the forward runs one warp per
- * cell (N >= 9, or any N whose mode is warp per cell) it forms each E_t by
+ * cell (N >= 12, or any N whose mode is warp per cell) it forms each E_t by
  * the adjoint's own FP64 operations, and the gradients are identical to
- * drag_expm_backward's. For N <= 8 with the default modes the lane-per-cell
+ * drag_expm_backward's. For N <= 11 with the default modes the lane-per-cell
  * forward writes the tape, and the gradients agree with drag_expm_backward's to
  * rounding. The tape trades HBM for FP64 work:
  *   drag_expm_tape_bytes(ncells, nspecies, levels) bytes, about
@@ -278,9 +278,10 @@ int32_t drag_expm_tape_levels(int32_t sstar);
 
 /*
  * drag_expm_apply_taped — drag_expm_apply that also writes the adjoint tape.
- * v_out is bit-identical to drag_expm_apply's under the same mode table. N <= 8
- * with the default modes run lane per cell, like drag_expm_apply (binned from
- * 262,144 cells, tile-sorted below); other sizes run one warp per cell.
+ * v_out is bit-identical to drag_expm_apply's under the same mode table: the
+ * taped forward runs the same kernel family, lane per cell for N <= 11 with the
+ * default modes (binned from 262,144 cells up to N = 8, tile-sorted otherwise),
+ * one warp per cell for other sizes.
  *   levels : tape capacity per cell, 1 .. DRAG_TAPE_MAX_LEVELS.
  *   tape   : DEVICE, 256-byte aligned, >= drag_expm_tape_bytes(ncells,
  *            nspecies, levels) bytes, owned by the caller, written; must not

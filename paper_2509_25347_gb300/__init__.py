@@ -396,7 +396,7 @@ def _autograd_function():
 
     class _DragExpmTaped(torch.autograd.Function):
         """DragExpm whose forward records the adjoint tape (apply_taped) and whose
-        backward reads it: identical values, gradients identical from N = 9 on (to
+        backward reads it: identical values, gradients identical from N = 12 on (to
         rounding below, where the lane-per-cell forward writes the tape), less FP64 work in the
         backward for a tape of about ncells * levels * 4 (N+1)(N+2) bytes.
 

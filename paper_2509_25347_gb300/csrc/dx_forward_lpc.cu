@@ -198,6 +198,9 @@ int dx_launch_forward_lpc_taped(const DxConsts &K, int n, long long C, const dou
         DX_CASE(7, DX_LPC_HYBRID)
         DX_CASE(8, DX_LPC_HYBRID)
         DX_CASE(9, DX_LPC_HYBRID)
+        DX_CASE(10, DX_LPC_HYBRID)
+        DX_CASE(11, DX_LPC_HYBRID)
+        DX_CASE(12, DX_LPC_HYBRID)
 #undef DX_CASE
         default: return DRAG_EINVAL_SIZE;
     }

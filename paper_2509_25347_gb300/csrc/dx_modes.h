@@ -48,7 +48,7 @@ int dx_binned_forward(const DxConsts &K, long long C, int N, const double *rho_g
 // Lane-per-cell forward that also writes the adjoint tape (dx_tape.cuh), for
 // n <= DX_LPC_TAPE_NMAX with the default storage of each n (registers up to
 // DX_LPC_REG_NMAX, hybrid above); the tape geometry as in drag_expm_apply_taped.
-#define DX_LPC_TAPE_NMAX 9
+#define DX_LPC_TAPE_NMAX 12
 int dx_launch_forward_lpc_taped(const DxConsts &K, int n, long long C, const double *rho_g, const double *rho_d,
                                 const double *t_s, const double *v_in, double *v_out, double dt, uint32_t *status,
                                 long long *hdr, double *m, int levels, int P, cudaStream_t stream);

@@ -2,14 +2,14 @@
 
 The taped forward stores the restored iterates E_0 .. E_{s*-2} it forms; the
 taped adjoint reads them instead of recomputing the Taylor step and those
-squarings. From n = 10 (and for any n whose mode is warp per cell) the forward
+squarings. From n = 13 (and for any n whose mode is warp per cell) the forward
 runs warp per cell, and both sides form each E_t by the same FP64 operations in
 the same order, so:
 * the taped forward's v_out equals the warp-per-cell drag_expm_apply's bit for bit;
 * the taped adjoint's four gradients equal drag_expm_backward's bit for bit,
   for recorded cells, for cells past the tape's capacity (recomputed) and for
   cells whose inputs no longer match the tape's fingerprint (recomputed).
-For n <= 9 with the default modes the lane-per-cell forward writes the tape: its
+For n <= 12 with the default modes the lane-per-cell forward writes the tape: its
 v_out equals drag_expm_apply's bit for bit, and the E_t it stores differ from
 the adjoint's own recomputation by rounding (its Taylor step sums G_00 in
 another order), so there the taped gradients are checked against the oracle's
@@ -182,7 +182,7 @@ def test_tape_invalid_cells(dx, N):
     assert dx.get_status() & dx.STATUS_BAD_CELL
     for a, b in zip(plain, taped):
         assert torch.isnan(b[..., 7]).all()
-    if N + 1 > 9:
+    if N + 1 > 12:
         for a, b in zip(plain, taped):
             assert torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0))
     else:
@@ -242,9 +242,9 @@ def test_autograd_taped(dx):
         assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("N", [1, 4, 5, 8])
+@pytest.mark.parametrize("N", [1, 4, 5, 8, 9, 11])
 def test_lane_per_cell_tape(dx, N):
-    """n <= 9, default modes: the lane-per-cell forward writes the tape. Its v_out
+    """n <= 12, default modes: the lane-per-cell forward writes the tape. Its v_out
     is drag_expm_apply's bit for bit; the taped gradients match the oracle's
     adjoint (and the recomputing adjoint) at the adjoint tolerances; a tape whose
     fingerprints do not match (another dt) gives the recomputed gradients exactly."""
