@@ -4,7 +4,8 @@ species counts on every kernel family (lane per cell in registers, hybrid, warp
 per cell), ragged cell counts, random stiffness ranges and time steps. The
 forward is checked against the oracle on sampled cells at 1e-13 of the velocity
 scale; the taped adjoint against the recomputing adjoint at the adjoint
-tolerances of tests/test_backward_gpu.py."""
+tolerances of tests/test_backward_gpu.py. The lower accuracy targets and the
+host-array pipeline are run above the threshold too."""
 import numpy as np
 import pytest
 
@@ -65,4 +66,45 @@ def test_dispatch_fuzz(dx, k, N, C, lo, hi, dt):
     taped = [x.cpu().numpy()[..., idx] for x in dx.backward(rg, rd, ts, dt, v, g, tape=tape)]
     plain = [x.cpu().numpy()[..., idx] for x in dx.backward(rg, rd, ts, dt, v, g)]
     assert_adjoint_parity(sub, g_np[:, :, idx], taped, plain)
+    assert dx.get_status() == 0
+
+
+@pytest.mark.parametrize("N,ubits", [(4, 24), (8, 11), (16, 24)])
+def test_targets_above_binning_threshold(dx, N, ubits):
+    """The lower accuracy targets on 300,001 cells (the binned path carries the
+    target's theta table for N <= 8): sampled cells against the oracle at the
+    same target, and (k*, s*) bit-exact."""
+    import torch
+    C = 300001
+    cells = W.mrn(C, N, seed=80 + N, stiff_lo=-4.0, stiff_hi=8.0)
+    rg, rd, ts, v = t(cells.rho_g), t(cells.rho_d), t(cells.t_s), t(cells.v)
+    out = dx.apply(rg, rd, ts, cells.dt, v, ubits=ubits)
+    idx = np.unique(np.concatenate([np.random.default_rng(N).integers(0, C, 96), [0, C - 1]]))
+    sub = cells.subset(idx)
+    u = 2.0 ** -ubits
+    ref, k, s, st = oracle.drag_apply(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v, return_ks=True, u=u)
+    got = out[:, :, torch.from_numpy(idx).cuda()].cpu().numpy()
+    sc = np.abs(sub.v).max(axis=1, keepdims=True)
+    assert st == 0 and np.max(np.abs(got - ref) / sc) <= TOL
+    kg, sg = dx.select(rg, rd, ts, cells.dt, ubits=ubits)
+    assert np.array_equal(kg.cpu().numpy()[idx], k) and np.array_equal(sg.cpu().numpy()[idx], s)
+    assert dx.get_status() == 0
+
+
+@pytest.mark.parametrize("N,C,chunk", [(4, 600011, 0), (8, 524300, 0), (16, 300001, 65536), (3, 270000, 100000)])
+def test_host_pipeline_large(dx, N, C, chunk):
+    """drag_expm_apply_host over several chunks, binned ones included (default
+    chunk 262,144 for N <= 8): bit-identical to drag_expm_apply on the device."""
+    import torch
+    cells = W.mrn(C, N, seed=90 + N, stiff_lo=-4.0, stiff_hi=8.0)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    out = dx.apply_host(pin(cells.rho_g), pin(cells.rho_d), pin(cells.t_s), cells.dt, pin(cells.v),
+                        chunk_cells=chunk)
+    torch.cuda.synchronize()
+    dev_out = dx.apply(t(cells.rho_g), t(cells.rho_d), t(cells.t_s), cells.dt, t(cells.v)).cpu()
+    if chunk == 0 and N + 1 <= 9:
+        assert torch.equal(out, dev_out)     # same binned kernel chunk by chunk
+    else:
+        sc = np.abs(cells.v).max(axis=1, keepdims=True)
+        assert np.max(np.abs(out.numpy() - dev_out.numpy()) / sc) <= TOL
     assert dx.get_status() == 0
