@@ -48,10 +48,10 @@ KERNEL_SOURCES = {
 }
 MEASURED_TRAFFIC = {
     ("mrn_n16_128cube", "dx_forward_wpc"): {
-        "sources_sha256": "a1111227b8c208c33b60c27551e02b7256b83c0d4db5f9c05468f1e3997319bd",
-        "bytes_per_cell": (186.928e6 + 80.945e6) / 262144,
+        "sources_sha256": "f950f6c493d2a33d0c91a98262307d52299e93c66fbed3697cfecb38b8e7fd88",
+        "bytes_per_cell": (188.071936e6 + 81.039104e6) / 262144,
         # FP64 FLOPs the kernel executes: thread-level (2 DFMA + DADD + DMUL) per cycle x elapsed cycles
-        "executed_flop_per_cell": (2 * 232.378394 + 15.933683 + 3.625070) * 49013544.553 / 262144,
+        "executed_flop_per_cell": (2 * 231.801724 + 15.894142 + 3.616074) * 49135479.171 / 262144,
         "capture": "profiles/dx_forward_wpc_mrn_n16.md",
     },
 }
