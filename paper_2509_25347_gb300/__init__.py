@@ -114,13 +114,33 @@ def _check(rc: int):
 def _stream_handle(stream):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
+    if s.device.index != torch.cuda.current_device():
+        raise DragExpmError(f"stream is on {s.device}, the library launches on the current device "
+                            f"cuda:{torch.cuda.current_device()}")
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def _on_current_device(name, t):
+    """The library launches on the current CUDA device; every buffer it is given must live there."""
+    import torch
+    if t.device.index != torch.cuda.current_device():
+        raise DragExpmError(f"{name} is on {t.device}, not on the current device cuda:{torch.cuda.current_device()}")
+
+
+def _bytes_cuda(name, t):
+    """(pointer, size in bytes) of a contiguous CUDA scratch tensor (workspace, tape) on the current device."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise DragExpmError(f"{name} must be a contiguous CUDA tensor")
+    _on_current_device(name, t)
+    return ctypes.c_void_p(t.data_ptr()), t.numel() * t.element_size()
 
 
 def _f64_cuda(name, t, shape):
     import torch
     if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
         raise DragExpmError(f"{name} must be a float64 CUDA tensor")
+    _on_current_device(name, t)
     if tuple(t.shape) != tuple(shape):
         raise DragExpmError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
     if not t.is_contiguous():
@@ -198,10 +218,12 @@ def apply_host(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, chunk_cells: int 
     vi = _f64_host("v_in", v_in, (3, N + 1, C))
     vo = _f64_host("v_out", v_out, (3, N + 1, C))
     nbytes = host_workspace_bytes(N, chunk_cells)
-    if workspace is None or workspace.numel() < nbytes:
+    if workspace is None:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    _check(load_library().drag_expm_apply_host(C, N, *args, float(dt), vi, vo, int(chunk_cells),
-                                               ctypes.c_void_p(workspace.data_ptr()), nbytes,
+    wp, wbytes = _bytes_cuda("workspace", workspace)
+    if wbytes < nbytes:
+        raise DragExpmError(f"workspace holds {wbytes} bytes, drag_expm_apply_host needs {nbytes}")
+    _check(load_library().drag_expm_apply_host(C, N, *args, float(dt), vi, vo, int(chunk_cells), wp, nbytes,
                                                _stream_handle(stream)))
     return v_out
 
@@ -285,7 +307,7 @@ class Tape:
 
     @property
     def nbytes(self) -> int:
-        return int(self.buf.numel())
+        return int(self.buf.numel() * self.buf.element_size())
 
 
 def tape_bytes(ncells: int, nspecies: int, levels: int) -> int:
@@ -325,12 +347,12 @@ def apply_taped(rho_g, rho_d, t_s, dt: float, v_in, v_out=None, levels: int | No
         tape = Tape(torch.empty((max(nbytes, 1),), dtype=torch.uint8, device=rho_g.device), C, N, levels)
     else:
         tape = Tape(tape.buf, C, N, levels)
+    tp, tbytes = _bytes_cuda("tape", tape.buf)
     if v_out is None:
         v_out = torch.empty_like(v_in)
     args = [_f64_cuda("rho_g", rho_g, (C,)), _f64_cuda("rho_d", rho_d, (N, C)), _f64_cuda("t_s", t_s, (N, C))]
     _check(load_library().drag_expm_apply_taped(C, N, *args, float(dt), _f64_cuda("v_in", v_in, (3, N + 1, C)),
-                                                _f64_cuda("v_out", v_out, (3, N + 1, C)), int(levels),
-                                                ctypes.c_void_p(tape.buf.data_ptr()), tape.nbytes,
+                                                _f64_cuda("v_out", v_out, (3, N + 1, C)), int(levels), tp, tbytes,
                                                 _stream_handle(stream)))
     return v_out, tape
 
@@ -363,9 +385,9 @@ def backward(rho_g, rho_d, t_s, dt: float, v_in, grad_v_out, need_v_in=True, nee
         if (tape.ncells, tape.nspecies) != (C, N):
             raise DragExpmError(f"tape written for ncells={tape.ncells} nspecies={tape.nspecies}, "
                                 f"called with ncells={C} nspecies={N}")
-        _check(load_library().drag_expm_backward_taped(C, N, *args, float(dt), vi, go, *outs, tape.levels,
-                                                       ctypes.c_void_p(tape.buf.data_ptr()), tape.nbytes,
-                                                       _stream_handle(stream)))
+        tp, tbytes = _bytes_cuda("tape", tape.buf)
+        _check(load_library().drag_expm_backward_taped(C, N, *args, float(dt), vi, go, *outs, tape.levels, tp,
+                                                       tbytes, _stream_handle(stream)))
     return gvi, grg, grd, gts
 
 
@@ -452,6 +474,7 @@ def _flat_f64(name, t):
     import torch
     if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
         raise DragExpmError(f"{name} must be a contiguous float64 CUDA tensor")
+    _on_current_device(name, t)
     return ctypes.c_void_p(t.data_ptr()), t.numel()
 
 
@@ -473,8 +496,9 @@ def apply_batched(blocks, rho_g, rho_d, t_s, v_in, v_out=None, nspecies_max=None
     if nspecies_max is None:
         raise DragExpmError("nspecies_max is required when blocks are already on the device")
     if not isinstance(blocks, torch.Tensor) or blocks.dtype != torch.uint8 or not blocks.is_cuda or \
-            blocks.numel() % BLOCK_BYTES:
-        raise DragExpmError("blocks must be a CUDA uint8 tensor of drag_block_t records")
+            not blocks.is_contiguous() or blocks.numel() % BLOCK_BYTES:
+        raise DragExpmError("blocks must be a contiguous CUDA uint8 tensor of drag_block_t records")
+    _on_current_device("blocks", blocks)
     nblocks = blocks.numel() // BLOCK_BYTES
     if v_out is None:
         v_out = torch.empty_like(v_in)
@@ -488,9 +512,9 @@ def apply_batched(blocks, rho_g, rho_d, t_s, v_in, v_out=None, nspecies_max=None
     need = batched_workspace_bytes(nblocks, C)
     if workspace is None:
         workspace = torch.empty(need, dtype=torch.uint8, device=rho_g.device)
+    wp, wbytes = _bytes_cuda("workspace", workspace)
     _check(load_library().drag_expm_apply_batched(nblocks, ctypes.c_void_p(blocks.data_ptr()), C, nd, nv,
-                                                  int(nspecies_max), prg, prd, pts, pvi, pvo,
-                                                  ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                                  int(nspecies_max), prg, prd, pts, pvi, pvo, wp, wbytes,
                                                   _stream_handle(stream)))
     return v_out
 

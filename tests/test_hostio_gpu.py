@@ -69,3 +69,24 @@ def test_host_pipeline_errors(dx):
                                   dx.host_workspace_bytes(4, 512), ctypes.c_void_p(0))
     assert rc == -3                                         # misaligned workspace
     assert dx.host_workspace_bytes(0, 512) == 0 and dx.host_workspace_bytes(4, -1) == 0
+
+
+def test_binding_rejects_misplaced_scratch(dx):
+    """The binding hands the library device pointers only: a host tensor or an
+    undersized tensor as the pipeline's workspace is refused before any call."""
+    import torch
+    cells = W.workload("mrn_n4_128cube", ncells=1000)
+    hrg, hrd, hts, hv = host(cells, True)
+    need = dx.host_workspace_bytes(4, 512)
+    with pytest.raises(dx.DragExpmError, match="CUDA tensor"):
+        dx.apply_host(hrg, hrd, hts, cells.dt, hv, chunk_cells=512, workspace=torch.empty(need, dtype=torch.uint8))
+    with pytest.raises(dx.DragExpmError, match="needs"):
+        dx.apply_host(hrg, hrd, hts, cells.dt, hv, chunk_cells=512,
+                      workspace=torch.empty(need - 1, dtype=torch.uint8, device="cuda"))
+    # a float64 workspace counts in bytes
+    out = dx.apply_host(hrg, hrd, hts, cells.dt, hv, chunk_cells=512,
+                        workspace=torch.empty((need + 7) // 8, dtype=torch.float64, device="cuda"))
+    torch.cuda.current_stream().synchronize()
+    rg, rd, ts, v = dev(cells)
+    assert np.array_equal(out.numpy(), dx.apply(rg, rd, ts, cells.dt, v).cpu().numpy())
+    assert dx.get_status() == 0

@@ -157,6 +157,20 @@ def test_stale_and_foreign_tapes(dx):
         assert torch.equal(a, b)
 
 
+def test_tape_on_host_is_refused(dx):
+    """A Tape whose buffer is not a CUDA tensor never reaches the library."""
+    import torch
+    cells = spread_cells(4, 64, seed=3)
+    rg, rd, ts = dev_args(cells)
+    v = t(cells.v)
+    _, tape = dx.apply_taped(rg, rd, ts, cells.dt, v)
+    host_tape = dx.Tape(tape.buf.cpu(), tape.ncells, tape.nspecies, tape.levels)
+    with pytest.raises(dx.DragExpmError, match="CUDA tensor"):
+        dx.backward(rg, rd, ts, cells.dt, v, torch.ones_like(v), tape=host_tape)
+    with pytest.raises(dx.DragExpmError, match="CUDA tensor"):
+        dx.apply_taped(rg, rd, ts, cells.dt, v, tape=host_tape)
+
+
 @pytest.mark.parametrize("N", [4, 12])
 def test_tape_invalid_cells(dx, N):
     """Invalid cells: NaN outputs and gradients and the status bit, as untaped;
