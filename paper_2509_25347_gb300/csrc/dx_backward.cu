@@ -31,6 +31,7 @@
 // nor those E^2; its squarings before the last two carry only E L + L E.
 #include <cmath>
 
+#include "dx_modes.h"
 #include "dx_wpc.cuh"
 
 namespace {
@@ -678,6 +679,9 @@ static int backward_impl(int64_t ncells, int32_t nspecies, const double *rho_g, 
         a.levels = levels;
         a.P = dx_tape_slot(n);
     }
+    if (n <= DX_BWD_LPC_NMAX && dx_mode_for(n) != DX_MODE_WPC)
+        return dx_launch_backward_lpc(n, ncells, rho_g, rho_d, t_s, dt, v_in, grad_v_out, grad_v_in, grad_rho_g,
+                                      grad_rho_d, grad_t_s, st, a.thdr, a.tm, a.levels, a.P, stream);
     const long long grid = (ncells + kCellsPerBlock - 1) / kCellsPerBlock;
     if (taped)
         dx_backward_wpc_taped<<<(unsigned)grid, kWarpsPerBlock * 32, bwd_smem_bytes(n), stream>>>(a, dx_consts());

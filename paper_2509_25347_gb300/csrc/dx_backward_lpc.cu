@@ -1,0 +1,394 @@
+// Adjoint of the EXP drag update, lane-per-cell kernels for small matrices
+// (n = N + 1 <= DX_BWD_LPC_NMAX).
+//
+// Same mathematics as the warp-per-cell adjoint (dx_backward.cu): with g_d =
+// dL/dv_out,d, the forward-mode Frechet derivative L(S, H) of the symmetric
+// similarity form is carried through the scaling and squaring beside E,
+//   Taylor:   F <- F X + b_j I,   dF <- dF X + F H   (F H = sum_d (F a_d) b_d^T),
+//   squaring: (E, L) <- (E^2, E L + L E),
+// with the rank-4 direction H = 2^-s (sum_d a_d b_d^T - kappa sigma sigma^T),
+// a_d = g_d / sigma, b_d = sigma o v_in,d, and the gradients read from row 0,
+// column 0 and the diagonal of the last L (Eqs. DragEqVar2/3, jacobian).
+//
+// Here one lane owns one cell and runs all of it serially, so every FP64
+// instruction of a warp works on 32 cells; at n <= 6 a warp-per-cell round keeps
+// only a fraction of its lanes busy (n(n-1)/2 upper-triangle entries, n-term
+// reductions through shuffles). E is formed with the lane-per-cell forward's
+// own steps (dx_lpc.cuh), so the taped variant, which reads E_0 .. E_{s-2} from
+// the forward's tape instead, gives bit-identical gradients.
+#include <cmath>
+
+#include "dx_lpc.cuh"
+#include "dx_modes.h"
+
+namespace {
+
+constexpr int kThreads = 64;   // 2 warps per block: shared memory per warp sets the residency
+constexpr int kTile = 512;     // largest tile of cells a block sorts
+
+struct BwdLpcArgs {
+    long long C;
+    const double *rho_g, *rho_d, *t_s, *v_in, *g_out;
+    double *g_vin, *g_rho_g, *g_rho_d, *g_ts;
+    double dt;
+    uint32_t *status;
+    const long long *thdr;   // tape (TAPE kernels): fingerprints, then levels
+    const double *tm;
+    int levels, P;
+};
+
+// Storage per n: E (packed, double-buffered) and L (full, double-buffered) in
+// registers; the n-vectors (sigma, tau, X_0f, X_ff, a_d, -kappa sigma, b_d, y_d:
+// 14 n doubles) in registers up to n = 3 and in shared memory above.
+template <int NF>
+struct BwdLpcStore {
+    static constexpr bool kVecShared = NF >= 4;
+    static constexpr int kVec = 14 * NF;
+    static constexpr int kWarpDoubles = kVecShared ? 32 * kVec : 0;
+};
+
+template <int NF>
+__device__ __forceinline__ void bwd_lpc_fail(long long c, const BwdLpcArgs &a) {
+    const long long C = a.C;
+    if (a.g_vin)
+        for (int e = 0; e < 3 * NF; e++) a.g_vin[e * C + c] = NAN;
+    for (int i = 0; i < NF - 1; i++) {
+        if (a.g_rho_d) a.g_rho_d[i * C + c] = NAN;
+        if (a.g_ts) a.g_ts[i * C + c] = NAN;
+    }
+    if (a.g_rho_g) a.g_rho_g[c] = NAN;
+    atomicOr(a.status, DRAG_STATUS_BAD_CELL);
+}
+
+template <int NF, bool TAPE>
+__device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpcArgs &a, const DxConsts &K,
+                                             const double *bsh, double *wsm) {
+    constexpr int N = NF - 1;
+    constexpr int NT = DxPacked<NF>::NT;
+    constexpr bool SV = BwdLpcStore<NF>::kVecShared;
+    using P = DxPacked<NF>;
+    const long long C = a.C;
+    const double dt = a.dt;
+
+    // ---------------- load and validate (as the lane-per-cell forward)
+    const double rg = a.rho_g[c];
+    bool ok = dx_pos_finite(rg);
+    double eps[N], alpha[N];
+    unsigned long long fph = 0;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const double rd = a.rho_d[i * C + c], ts = a.t_s[i * C + c];
+        ok = ok && dx_nonneg_finite(rd) && dx_pos_or_inf(ts);
+        if (TAPE) fph ^= dx_fingerprint_term(i + 1, rd, ts);
+        eps[i] = rd;
+        alpha[i] = ts;
+    }
+    if (!ok) {
+        bwd_lpc_fail<NF>(c, a);
+        return;
+    }
+    double s1 = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        eps[i] = __ddiv_rn(eps[i], rg);      // Eq. DragEqVar2
+        alpha[i] = __ddiv_rn(1.0, alpha[i]); // Eq. DragEqVar3
+        s1 = __dadd_rn(s1, __dmul_rn(__dmul_rn(eps[i], alpha[i]), dt));
+    }
+    double col0 = s1;
+    long long cmax = 0;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const double ai0 = __dmul_rn(alpha[i], dt);
+        col0 = __dadd_rn(col0, ai0);
+        const long long cb = dx_bits(__dadd_rn(__dmul_rn(__dmul_rn(eps[i], alpha[i]), dt), ai0));
+        cmax = cb > cmax ? cb : cmax;
+    }
+    const long long nb = dx_bits(col0) > cmax ? dx_bits(col0) : cmax;
+    if (!dx_norm_ok(nb)) {
+        bwd_lpc_fail<NF>(c, a);
+        return;
+    }
+    int kk, s;
+    dx_select(__longlong_as_double(nb), K, kk, s);
+    const int m = K.mk[kk];
+    const int tlev = dx_tape_levels(s);
+    bool taped = false;
+    const double *tcell = nullptr;
+    if (TAPE) {
+        const long long h = dx_fingerprint_final(fph, rg, dt, dx_tape_salt(a.levels, NF));
+        taped = a.thdr[c] == h && tlev <= a.levels;
+        tcell = a.tm + (size_t)c * a.levels * a.P;
+    }
+
+    // ---------------- symmetric arrowhead X = 2^-s D_sigma A D_sigma^-1 and the direction
+    DxLaneArr<NF, SV> sig, tau, xs, ds, a3;
+    DxLaneArr<3 * NF, SV> av, bv, yv;
+    if constexpr (SV) {
+        sig.bind(wsm, lane);
+        tau.bind(wsm + 32 * NF, lane);
+        xs.bind(wsm + 64 * NF, lane);
+        ds.bind(wsm + 96 * NF, lane);
+        a3.bind(wsm + 128 * NF, lane);
+        av.bind(wsm + 160 * NF, lane);
+        bv.bind(wsm + 256 * NF, lane);
+        yv.bind(wsm + 352 * NF, lane);
+    }
+    sig[0] = 1.0;
+    tau[0] = 1.0;
+    xs[0] = dx_scale2(-s1, s);
+    ds[0] = 0.0;
+#pragma unroll
+    for (int i = 1; i < NF; i++) {
+        const double e = dx_bits(eps[i - 1]) < dx_bits(DX_EPS_FLOOR) ? DX_EPS_FLOOR : eps[i - 1];
+        const double sg = __dsqrt_rn(e);
+        sig[i] = sg;
+        tau[i] = __ddiv_rn(1.0, sg);
+        xs[i] = __dmul_rn(__dmul_rn(sg, alpha[i - 1]), dx_scale2(dt, s));
+        ds[i] = -dx_scale2(__dmul_rn(alpha[i - 1], dt), s);
+    }
+    {
+        // a_d = g_d / sigma, b_d = 2^-s sigma o v_d, and the stationary block kappa
+        double sa[3] = {0.0, 0.0, 0.0}, sb[3] = {0.0, 0.0, 0.0}, ss = 0.0;
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            const double sg = sig[f], tu = tau[f];
+            ss = fma(sg, sg, ss);
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const double ad = a.g_out[(d * NF + f) * C + c] * tu;
+                const double bd = dx_scale2(sg * a.v_in[(d * NF + f) * C + c], s);
+                av[d * NF + f] = ad;
+                bv[d * NF + f] = bd;
+                sa[d] = fma(sg, ad, sa[d]);
+                sb[d] = fma(sg, bd, sb[d]);
+            }
+        }
+        const double kappa = __ddiv_rn(fma(sa[2], sb[2], fma(sa[1], sb[1], sa[0] * sb[0])), ss * ss);
+#pragma unroll
+        for (int f = 0; f < NF; f++) a3[f] = -kappa * sig[f];
+    }
+
+    // ---------------- Taylor and its derivative: F = b_m X + b_{m-1} I, dF = b_m H, y_d = F a_d
+    DxLaneArr<NT, false> Fm, Gm;
+    DxLaneArr<NF * NF, false> Lm, Ln;
+    const double bm = bsh[m], bm1 = bsh[m - 1];
+    if (!taped) dx_lpc_taylor_init<NF>(Fm, xs, ds, bm, bm1);
+#pragma unroll
+    for (int i = 0; i < NF; i++) {
+#pragma unroll
+        for (int j = 0; j < NF; j++) {
+            double acc = av[i] * bv[j];
+            acc = fma(av[NF + i], bv[NF + j], acc);
+            acc = fma(av[2 * NF + i], bv[2 * NF + j], acc);
+            acc = fma(a3[i], sig[j], acc);
+            Lm[i * NF + j] = bm * acc;
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < NF; k++) acc = fma(xs[k], av[d * NF + k], acc);
+        yv[d * NF] = fma(bm, acc, bm1 * av[d * NF]);
+#pragma unroll
+        for (int f = 1; f < NF; f++)
+            yv[d * NF + f] = fma(bm, fma(xs[f], av[d * NF], ds[f] * av[d * NF + f]), bm1 * av[d * NF + f]);
+    }
+    for (int jb = m - 2; jb >= 0; jb--) {
+        // F_jb = F X + b_jb I; dF_jb = dF X + F H, where F a_d = y_d (d < 3) and
+        // F a_3 = b_{jb+1} a_3 (X sigma = 0); then y_d <- X y_d + b_jb a_d.
+        if (!taped) {
+            dx_lpc_horner_step<NF>(Fm, Gm, xs, ds, bsh[jb]);
+            dx_lane_take(Fm, Gm);
+        }
+        const double bj1 = bsh[jb + 1], bj = bsh[jb];
+#pragma unroll
+        for (int i = 0; i < NF; i++) {
+            const double y0 = yv[i], y1 = yv[NF + i], y2 = yv[2 * NF + i], w = bj1 * a3[i];
+            double acc = y0 * bv[0];
+            acc = fma(y1, bv[NF], acc);
+            acc = fma(y2, bv[2 * NF], acc);
+            acc = fma(w, sig[0], acc);
+#pragma unroll
+            for (int k = 0; k < NF; k++) acc = fma(Lm[i * NF + k], xs[k], acc);
+            Ln[i * NF] = acc;
+#pragma unroll
+            for (int j = 1; j < NF; j++) {
+                double t = y0 * bv[j];
+                t = fma(y1, bv[NF + j], t);
+                t = fma(y2, bv[2 * NF + j], t);
+                t = fma(w, sig[j], t);
+                t = fma(Lm[i * NF], xs[j], t);
+                Ln[i * NF + j] = fma(Lm[i * NF + j], ds[j], t);
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double y0 = yv[d * NF];
+            double acc = bj * av[d * NF];
+#pragma unroll
+            for (int k = 0; k < NF; k++) acc = fma(xs[k], yv[d * NF + k], acc);
+#pragma unroll
+            for (int f = 1; f < NF; f++)
+                yv[d * NF + f] = fma(xs[f], y0, fma(ds[f], yv[d * NF + f], bj * av[d * NF + f]));
+            yv[d * NF] = acc;
+        }
+        dx_lane_take(Lm, Ln);
+    }
+    if (taped) {
+#pragma unroll
+        for (int e = 0; e < NT; e++) Fm[e] = tcell[e];
+    } else {
+        dx_lpc_restore<NF>(Fm, sig, tau);
+    }
+
+    // ---------------- squarings: (E, L) <- (E^2, E L + L E); the last one forms only
+    // row 0, column 0 and the diagonal of L (all the gradients read) and leaves E at E_{s-1}
+    for (int sq = 0; sq < s; sq++) {
+        const bool last = sq == s - 1;
+#pragma unroll
+        for (int i = 0; i < NF; i++) {
+#pragma unroll
+            for (int j = 0; j < NF; j++) {
+                if (last && i != 0 && j != 0 && i != j) continue;
+                double acc = 0.0;
+#pragma unroll
+                for (int k = 0; k < NF; k++) acc = fma(Fm[P::at(i, k)], Lm[k * NF + j], acc);
+#pragma unroll
+                for (int k = 0; k < NF; k++) acc = fma(Lm[i * NF + k], Fm[P::at(j, k)], acc);
+                Ln[i * NF + j] = acc;
+            }
+        }
+        if (!last) {
+            if (taped && sq + 1 < tlev) {
+                const double *lv = tcell + (size_t)(sq + 1) * a.P;
+#pragma unroll
+                for (int e = 0; e < NT; e++) Gm[e] = lv[e];
+            } else {
+                dx_lpc_square_offdiag<NF>(Fm, Gm);
+                dx_lpc_restore<NF>(Gm, sig, tau);
+            }
+            dx_lane_take(Fm, Gm);
+        }
+        dx_lane_take(Lm, Ln);
+    }
+
+    // ---------------- outputs
+    if (a.g_vin) {
+        // P^T g with P^T = D_sigma E D_sigma^-1: (P^T g)_i = E_ii g_i + sigma_i
+        // sum_{k != i} E_ik a_k, a = g / sigma. After s >= 1 squarings E holds
+        // E_{s-1} and P^T = (D_sigma E D_sigma^-1)^2: two applications, the first
+        // into (y_d, a_d) = (g', g' / sigma).
+        if (s >= 1) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+#pragma unroll
+                for (int i = 0; i < NF; i++) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int k = 0; k < NF; k++)
+                        if (k != i) acc = fma(Fm[P::at(i, k)], av[d * NF + k], acc);
+                    yv[d * NF + i] = fma(sig[i], acc, Fm[P::at(i, i)] * a.g_out[(d * NF + i) * C + c]);
+                }
+#pragma unroll
+                for (int i = 0; i < NF; i++) av[d * NF + i] = tau[i] * yv[d * NF + i];
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+#pragma unroll
+            for (int i = 0; i < NF; i++) {
+                double acc = 0.0;
+#pragma unroll
+                for (int k = 0; k < NF; k++)
+                    if (k != i) acc = fma(Fm[P::at(i, k)], av[d * NF + k], acc);
+                const double gi = s >= 1 ? yv[d * NF + i] : a.g_out[(d * NF + i) * C + c];
+                a.g_vin[(d * NF + i) * C + c] = fma(sig[i], acc, Fm[P::at(i, i)] * gi);
+            }
+        }
+    }
+    double part = 0.0;
+#pragma unroll
+    for (int i = 1; i < NF; i++) {
+        const double z00 = Lm[0], z0i = Lm[i] * tau[i], zi0 = sig[i] * Lm[i * NF], zii = Lm[i * NF + i];
+        const double d0 = z0i - z00;
+        const double geps = alpha[i - 1] * dt * d0;
+        const double galpha = dt * fma(eps[i - 1], d0, zi0 - zii);
+        if (a.g_rho_d) a.g_rho_d[(i - 1) * C + c] = __ddiv_rn(geps, rg);
+        if (a.g_ts) a.g_ts[(i - 1) * C + c] = -galpha * (alpha[i - 1] * alpha[i - 1]);
+        part = fma(eps[i - 1], geps, part);
+    }
+    if (a.g_rho_g) a.g_rho_g[c] = -__ddiv_rn(part, rg);
+}
+
+template <int NF, bool TAPE>
+__global__ void __launch_bounds__(kThreads) dx_backward_lpc(BwdLpcArgs a, DxConsts K, int rounds) {
+    extern __shared__ double smem[];
+    __shared__ unsigned long long key[kTile];
+    __shared__ unsigned short order[kTile];
+    double *bsh = smem;
+    for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
+    const long long C = a.C;
+    const int tile = rounds * kThreads;
+    const long long base = (long long)blockIdx.x * tile;
+    // order the tile's cells by the cost proxy so that a warp's 32 cells share (k*, s*)
+    for (int r = 0; r < rounds; r++) {
+        const int e = r * kThreads + threadIdx.x;
+        const long long c = base + e;
+        const unsigned int p =
+            c < C ? dx_lpc_cost_proxy<NF - 1>(a.rho_g + c, a.rho_d + c, a.t_s + c, C, a.dt) : 0xffffffffu;
+        key[e] = ((unsigned long long)p << 32) | (unsigned int)e;
+    }
+    __syncthreads();
+    for (int r = 0; r < rounds; r++) {
+        const int e = r * kThreads + threadIdx.x;
+        const unsigned long long me = key[e];
+        int rank = 0;
+        for (int j = 0; j < tile; j++) rank += key[j] < me;
+        order[rank] = (unsigned short)e;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    double *wsm = smem + 32 + (threadIdx.x >> 5) * BwdLpcStore<NF>::kWarpDoubles;
+    for (int r = 0; r < rounds; r++) {
+        const long long c = base + order[r * kThreads + threadIdx.x];
+        if (c < C) bwd_lpc_cell<NF, TAPE>(lane, c, a, K, bsh, wsm);
+    }
+}
+
+template <int NF, bool TAPE>
+int launch(const BwdLpcArgs &a, cudaStream_t stream) {
+    const size_t smem = sizeof(double) * (32 + (size_t)(kThreads / 32) * BwdLpcStore<NF>::kWarpDoubles);
+    constexpr size_t kStatic = kTile * (sizeof(unsigned long long) + sizeof(unsigned short));
+    if (smem + kStatic > 48 * 1024 &&
+        cudaFuncSetAttribute(dx_backward_lpc<NF, TAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return DRAG_ECUDA;
+    int rounds = kTile / kThreads;
+    while (rounds > 1 && (a.C + rounds * kThreads - 1) / (rounds * kThreads) < 4LL * dx_sm_count()) rounds >>= 1;
+    const long long blocks = (a.C + rounds * kThreads - 1) / (rounds * kThreads);
+    dx_backward_lpc<NF, TAPE><<<(unsigned)blocks, kThreads, smem, stream>>>(a, dx_consts(), rounds);
+    return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
+}
+
+}  // namespace
+
+int dx_launch_backward_lpc(int n, long long C, const double *rho_g, const double *rho_d, const double *t_s,
+                           double dt, const double *v_in, const double *grad_v_out, double *grad_v_in,
+                           double *grad_rho_g, double *grad_rho_d, double *grad_t_s, uint32_t *status,
+                           const long long *thdr, const double *tm, int levels, int P, cudaStream_t stream) {
+    const BwdLpcArgs a{C,         rho_g,      rho_d,     t_s,    v_in, grad_v_out, grad_v_in, grad_rho_g,
+                       grad_rho_d, grad_t_s, dt,         status, thdr, tm,         levels,    P};
+    const bool tape = thdr != nullptr;
+    switch (n) {
+#define DX_CASE(NF) \
+    case NF: return tape ? launch<NF, true>(a, stream) : launch<NF, false>(a, stream);
+        DX_CASE(2)
+        DX_CASE(3)
+        DX_CASE(4)
+        DX_CASE(5)
+        DX_CASE(6)
+#undef DX_CASE
+        default: return DRAG_EINVAL_SIZE;
+    }
+}

@@ -25,25 +25,8 @@ __host__ __device__ constexpr int lpc_threads() { return (ST != DX_LPC_REGS && N
 // A warp runs the largest Taylor order and squaring count of its 32 cells, so
 // each block first orders a tile of rounds x threads consecutive cells (the
 // launcher shrinks the tile when the grid would leave SMs idle) by a cost proxy
-// (the 1-norm of A = dt Omega_v in FP32, whose binary exponent tracks s*) and
-// hands every warp 32 cells of similar cost. The proxy only groups cells; the
-// cell routine still selects (k*, s*) from the FP64 norm.
-template <int N>
-__device__ __forceinline__ unsigned int cost_proxy(const double *rgp, const double *rdp, const double *tsp,
-                                                   long long stride, double dt) {
-    const float rg = (float)*rgp, fdt = (float)dt;
-    float col0 = 0.0f, cmax = 0.0f;
-#pragma unroll
-    for (int i = 0; i < N; i++) {
-        const float a = fdt / (float)tsp[i * stride];
-        const float ea = a * ((float)rdp[i * stride] / rg);
-        col0 += ea + a;
-        cmax = fmaxf(cmax, ea + a);
-    }
-    const float nrm = fmaxf(col0, cmax);
-    const unsigned int b = __float_as_uint(nrm);
-    return (nrm >= 0.0f && b < 0x7f800000u) ? b : 0x7f800000u;   // non-finite and NaN last among valid cells
-}
+// (dx_lpc_cost_proxy) and hands every warp 32 cells of similar cost. The proxy
+// only groups cells; the cell routine still selects (k*, s*) from the FP64 norm.
 
 // Register ceiling per thread. The register file is split among the four SM
 // sub-partitions (16K registers each): at 168 registers a sub-partition can
@@ -87,7 +70,7 @@ dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d
         for (int r = 0; r < rounds; r++) {
             const int e = r * kThreads + threadIdx.x;
             const long long c = base + e;
-            const unsigned int p = c < C ? cost_proxy<NF - 1>(rho_g + c, rho_d + c, t_s + c, C, dt) : 0xffffffffu;
+            const unsigned int p = c < C ? dx_lpc_cost_proxy<NF - 1>(rho_g + c, rho_d + c, t_s + c, C, dt) : 0xffffffffu;
             key[e] = ((unsigned long long)p << 32) | (unsigned int)e;
         }
         __syncthreads();

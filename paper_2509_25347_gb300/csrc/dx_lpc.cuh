@@ -64,6 +64,94 @@ __device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, true> &F, DxLaneArr<N
     G.p = t;
 }
 
+// ---- per-lane steps shared by the forward and the adjoint (one cell, packed
+// symmetric n x n matrices; FA, GA, VA are DxLaneArr types). Both sides form
+// the iterates E_t with exactly these operations, so a lane-per-cell adjoint
+// that recomputes them gets the values the forward's tape holds.
+
+// F = b_m X + b_{m-1} I for the arrowhead X (xs: row 0, ds: diagonal).
+template <int NF, class FA, class VA>
+__device__ __forceinline__ void dx_lpc_taylor_init(FA &Fm, VA &xs, VA &ds, double bm, double bm1) {
+    using P = DxPacked<NF>;
+#pragma unroll
+    for (int e = 0; e < P::NT; e++) Fm[e] = 0.0;
+    Fm[0] = fma(bm, xs[0], bm1);
+#pragma unroll
+    for (int i = 1; i < NF; i++) {
+        Fm[P::at(0, i)] = bm * xs[i];
+        Fm[P::at(i, i)] = fma(bm, ds[i], bm1);
+    }
+}
+
+// One Horner step in X: G = F X + b_j I (F is a polynomial in X, so F X is
+// symmetric; entry (i, j), j >= 1, needs F_i0 X_0j + F_ij X_jj).
+template <int NF, class FA, class GA, class VA>
+__device__ __forceinline__ void dx_lpc_horner_step(FA &Fm, GA &Gm, VA &xs, VA &ds, double bj) {
+    using P = DxPacked<NF>;
+    double g00 = fma(Fm[0], xs[0], bj);
+#pragma unroll
+    for (int k = 1; k < NF; k++) g00 = fma(Fm[P::at(0, k)], xs[k], g00);
+#pragma unroll
+    for (int jj = 1; jj < NF; jj++) {
+#pragma unroll
+        for (int i = 0; i <= jj; i++) {
+            double acc = fma(Fm[P::at(i, 0)], xs[jj], i == jj ? bj : 0.0);
+            Gm[P::at(i, jj)] = fma(Fm[P::at(i, jj)], ds[jj], acc);
+        }
+    }
+    Gm[0] = g00;
+}
+
+// Row-sum restoration E_ii = 1 - tau_i sum_{k != i} E_ik sigma_k.
+template <int NF, class MA, class VA>
+__device__ __forceinline__ void dx_lpc_restore(MA &M, VA &sig, VA &tau) {
+    using P = DxPacked<NF>;
+#pragma unroll
+    for (int i = 0; i < NF; i++) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < NF; k++)
+            if (k != i) acc = fma(M[P::at(i, k)], sig[k], acc);
+        M[P::at(i, i)] = fma(-tau[i], acc, 1.0);
+    }
+}
+
+// Off-diagonal entries of G = F^2 (F symmetric); the diagonal comes from dx_lpc_restore.
+template <int NF, class FA, class GA>
+__device__ __forceinline__ void dx_lpc_square_offdiag(FA &Fm, GA &Gm) {
+    using P = DxPacked<NF>;
+#pragma unroll
+    for (int i = 0; i < NF; i++) {
+#pragma unroll
+        for (int jj = i + 1; jj < NF; jj++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < NF; k++) acc = fma(Fm[P::at(i, k)], Fm[P::at(jj, k)], acc);
+            Gm[P::at(i, jj)] = acc;
+        }
+    }
+}
+
+// FP32 cost proxy of a cell for grouping cells of similar (k*, s*) into warps:
+// the 1-norm of A = dt Omega_v in FP32 (its binary exponent tracks s*), as an
+// order-preserving bit pattern; non-finite and NaN norms sort last among valid cells.
+template <int N>
+__device__ __forceinline__ unsigned int dx_lpc_cost_proxy(const double *rgp, const double *rdp, const double *tsp,
+                                                          long long stride, double dt) {
+    const float rg = (float)*rgp, fdt = (float)dt;
+    float col0 = 0.0f, cmax = 0.0f;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const float a = fdt / (float)tsp[i * stride];
+        const float ea = a * ((float)rdp[i * stride] / rg);
+        col0 += ea + a;
+        cmax = fmaxf(cmax, ea + a);
+    }
+    const float nrm = fmaxf(col0, cmax);
+    const unsigned int b = __float_as_uint(nrm);
+    return (nrm >= 0.0f && b < 0x7f800000u) ? b : 0x7f800000u;
+}
+
 // Shared-memory doubles one warp needs for storage mode ST.
 template <int NF, int ST>
 __host__ __device__ constexpr int dx_lpc_warp_smem_doubles() {
@@ -178,66 +266,21 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
     }
 
     // ---------------- Taylor: F = b_m X + b_{m-1} I, then F <- F X + b_j I (Horner in X)
-    {
-        const double bm = bsh[m], bm1 = bsh[m - 1];
-#pragma unroll
-        for (int e = 0; e < NT; e++) Fm[e] = 0.0;
-        Fm[0] = fma(bm, xs[0], bm1);
-#pragma unroll
-        for (int i = 1; i < NF; i++) {
-            Fm[P::at(0, i)] = bm * xs[i];
-            Fm[P::at(i, i)] = fma(bm, ds[i], bm1);
-        }
-    }
+    dx_lpc_taylor_init<NF>(Fm, xs, ds, bsh[m], bsh[m - 1]);
     for (int j = m - 2; j >= 0; j--) {
-        const double bj = bsh[j];
-        double g00 = fma(Fm[0], xs[0], bj);
-#pragma unroll
-        for (int k = 1; k < NF; k++) g00 = fma(Fm[P::at(0, k)], xs[k], g00);
-#pragma unroll
-        for (int jj = 1; jj < NF; jj++) {
-#pragma unroll
-            for (int i = 0; i <= jj; i++) {
-                double acc = fma(Fm[P::at(i, 0)], xs[jj], i == jj ? bj : 0.0);
-                Gm[P::at(i, jj)] = fma(Fm[P::at(i, jj)], ds[jj], acc);
-            }
-        }
-        Gm[0] = g00;
+        dx_lpc_horner_step<NF>(Fm, Gm, xs, ds, bsh[j]);
         dx_lane_take(Fm, Gm);
     }
 
     // ---------------- restore E_ii = 1 - tau_i sum_{k != i} E_ik sigma_k, then s squarings
-#pragma unroll
-    for (int i = 0; i < NF; i++) {
-        double acc = 0.0;
-#pragma unroll
-        for (int k = 0; k < NF; k++)
-            if (k != i) acc = fma(Fm[P::at(i, k)], sig[k], acc);
-        Fm[P::at(i, i)] = fma(-tau[i], acc, 1.0);
-    }
+    dx_lpc_restore<NF>(Fm, sig, tau);
     if (tape) {
 #pragma unroll
         for (int e = 0; e < NT; e++) tape[e] = Fm[e];
     }
     for (int it = 0; it < s; it++) {
-#pragma unroll
-        for (int i = 0; i < NF; i++) {
-#pragma unroll
-            for (int jj = i + 1; jj < NF; jj++) {
-                double acc = 0.0;
-#pragma unroll
-                for (int k = 0; k < NF; k++) acc = fma(Fm[P::at(i, k)], Fm[P::at(jj, k)], acc);
-                Gm[P::at(i, jj)] = acc;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < NF; i++) {
-            double acc = 0.0;
-#pragma unroll
-            for (int k = 0; k < NF; k++)
-                if (k != i) acc = fma(Gm[P::at(i, k)], sig[k], acc);
-            Gm[P::at(i, i)] = fma(-tau[i], acc, 1.0);
-        }
+        dx_lpc_square_offdiag<NF>(Fm, Gm);
+        dx_lpc_restore<NF>(Gm, sig, tau);
         if (tape && it + 1 < tlev) {
             double *lv = tape + (size_t)(it + 1) * tp.P;
 #pragma unroll

@@ -52,3 +52,13 @@ int dx_binned_forward(const DxConsts &K, long long C, int N, const double *rho_g
 int dx_launch_forward_lpc_taped(const DxConsts &K, int n, long long C, const double *rho_g, const double *rho_d,
                                 const double *t_s, const double *v_in, double *v_out, double dt, uint32_t *status,
                                 long long *hdr, double *m, int levels, int P, cudaStream_t stream);
+
+// Lane-per-cell adjoint (dx_backward_lpc.cu) for n <= DX_BWD_LPC_NMAX, run by
+// drag_expm_backward(_taped) when the mode of n is a lane-per-cell one. thdr
+// (null: none) is the tape the forward wrote (geometry as in
+// drag_expm_backward_taped; tm its first level).
+#define DX_BWD_LPC_NMAX 6
+int dx_launch_backward_lpc(int n, long long C, const double *rho_g, const double *rho_d, const double *t_s,
+                           double dt, const double *v_in, const double *grad_v_out, double *grad_v_in,
+                           double *grad_rho_g, double *grad_rho_d, double *grad_t_s, uint32_t *status,
+                           const long long *thdr, const double *tm, int levels, int P, cudaStream_t stream);

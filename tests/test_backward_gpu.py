@@ -203,3 +203,68 @@ def test_backward_extreme_norms(dx):
     ref = oracle.drag_backward(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, g)[:4]
     assert_adjoint_parity(cells, g, got, ref)
     assert dx.get_status() == 0
+
+
+# ---- lane-per-cell adjoint (n = N + 1 <= 6 under a lane-per-cell mode, the default there)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
+def test_backward_both_kernel_families(dx, N):
+    """Under the default (lane-per-cell) mode the adjoint runs one lane per cell;
+    under the warp-per-cell mode one warp per cell. Both match the oracle's
+    adjoint on a ragged count of cells spread over ten decades of stiffness."""
+    cells = W.mrn(677 + 3 * N, N, seed=500 + N, stiff_lo=-5.0, stiff_hi=8.0)
+    g = np.random.default_rng(50 + N).standard_normal(cells.v.shape)
+    ref = oracle.drag_backward(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, g)[:4]
+    assert dx.get_mode(N) != dx.MODE_WARP_PER_CELL
+    assert_adjoint_parity(cells, g, gpu_backward(dx, cells, g), ref)
+    saved = dx.get_mode(N)
+    dx.set_mode(N, dx.MODE_WARP_PER_CELL)
+    try:
+        wpc = gpu_backward(dx, cells, g)
+    finally:
+        dx.set_mode(N, saved)
+    assert_adjoint_parity(cells, g, wpc, ref)
+    assert dx.get_status() == 0
+
+
+@pytest.mark.parametrize("N", [1, 4])
+def test_lane_per_cell_backward_extreme_norms(dx, N):
+    """The lane-per-cell adjoint at norms up to 1.5e308 (s* ~ 1023; dL/dv_in
+    checked) and up to 1e14 (all gradients), as for the warp-per-cell one."""
+    from tests.test_forward_gpu import extreme_cells
+    cells = extreme_cells(N, [1e250, 1e300, 1.5e308])
+    g = np.random.default_rng(8).standard_normal(cells.v.shape)
+    gv = gpu_backward(dx, cells, g)[0]
+    rv = oracle.drag_backward(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, g)[0]
+    assert np.all(np.isfinite(gv))
+    assert np.max(np.abs(gv - rv) / np.abs(g).sum(axis=1, keepdims=True)) <= TOL_V
+    cells = extreme_cells(N, [1e8, 1e11, 1e14])
+    g = np.random.default_rng(9).standard_normal(cells.v.shape)
+    ref = oracle.drag_backward(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, g)[:4]
+    assert_adjoint_parity(cells, g, gpu_backward(dx, cells, g), ref)
+    assert dx.get_status() == 0
+
+
+def test_lane_per_cell_backward_finite_differences(dx):
+    """The N = 4 workload through the lane-per-cell adjoint: 64 random cells
+    against central differences of the GPU forward (1e-6 relative)."""
+    cells = W.workload("mrn_n4_128cube", ncells=8192)
+    target = W.adjoint_target(cells.ncells, cells.nspecies)
+    idx = np.sort(np.random.default_rng(99).choice(cells.ncells, 64, replace=False))
+    sub = cells.subset(idx)
+    vt = target[:, :, idx]
+
+    def fwd(c):
+        return dx.apply(t(c.rho_g), t(c.rho_d), t(c.t_s), c.dt, t(c.v)).cpu().numpy()
+
+    g = fwd(sub) - vt
+    gv, _, grd, gts = gpu_backward(dx, sub, g)
+    gv_fd, grd_fd, gts_fd = finite_difference_gradients(fwd, sub, vt)
+    assert_fd_agreement(sub, g, gv, grd, gts, gv_fd, grd_fd, gts_fd)
+
+
+def test_lane_per_cell_backward_full_size_sampled(dx):
+    """The N = 4 workload at full size (2,097,152 cells: tiles of 512 sorted
+    cells): 128 sampled cells against the oracle's adjoint."""
+    test_backward_full_size_sampled(dx, "mrn_n4_128cube")

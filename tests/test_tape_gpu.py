@@ -260,7 +260,8 @@ def test_autograd_taped(dx):
 def test_lane_per_cell_tape(dx, N):
     """n <= 12, default modes: the lane-per-cell forward writes the tape. Its v_out
     is drag_expm_apply's bit for bit; the taped gradients match the oracle's
-    adjoint (and the recomputing adjoint) at the adjoint tolerances; a tape whose
+    adjoint (and the recomputing adjoint) at the adjoint tolerances, bit for bit
+    for n <= 6 where the adjoint runs lane per cell too; a tape whose
     fingerprints do not match (another dt) gives the recomputed gradients exactly."""
     import torch
     cells = spread_cells(N, 211, seed=170 + N)
@@ -275,6 +276,11 @@ def test_lane_per_cell_tape(dx, N):
     assert_adjoint_parity(cells, g_np, taped, (rv, rrg, rrd, rts))
     plain = [x.cpu().numpy() for x in dx.backward(rg, rd, ts, cells.dt, v, g)]
     assert_adjoint_parity(cells, g_np, taped, plain)
+    if N + 1 <= 6:
+        # the lane-per-cell adjoint forms E as the lane-per-cell forward does: the
+        # tape changes the work, not one bit of the gradients
+        for a, b in zip(taped, plain):
+            assert np.array_equal(a, b)
     dt2 = float(np.nextafter(cells.dt, 2.0))
     stale = dx.backward(rg, rd, ts, dt2, v, g, tape=tape)
     fresh = dx.backward(rg, rd, ts, dt2, v, g)
