@@ -310,10 +310,12 @@ __device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpc
     double part = 0.0;
 #pragma unroll
     for (int i = 1; i < NF; i++) {
-        const double z00 = Lm[0], z0i = Lm[i] * tau[i], zi0 = sig[i] * Lm[i * NF], zii = Lm[i * NF + i];
-        const double d0 = z0i - z00;
-        const double geps = alpha[i - 1] * dt * d0;
-        const double galpha = dt * fma(eps[i - 1], d0, zi0 - zii);
+        // explicit roundings (no contraction), so every instantiation gives the same bits
+        const double z00 = Lm[0], zii = Lm[i * NF + i];
+        const double z0i = __dmul_rn(Lm[i], tau[i]), zi0 = __dmul_rn(sig[i], Lm[i * NF]);
+        const double d0 = __dsub_rn(z0i, z00);
+        const double geps = __dmul_rn(__dmul_rn(alpha[i - 1], dt), d0);
+        const double galpha = __dmul_rn(dt, fma(eps[i - 1], d0, __dsub_rn(zi0, zii)));
         if (a.g_rho_d) a.g_rho_d[(i - 1) * C + c] = __ddiv_rn(geps, rg);
         if (a.g_ts) a.g_ts[(i - 1) * C + c] = -galpha * (alpha[i - 1] * alpha[i - 1]);
         part = fma(eps[i - 1], geps, part);
@@ -356,14 +358,46 @@ __global__ void __launch_bounds__(kThreads) dx_backward_lpc(BwdLpcArgs a, DxCons
     }
 }
 
+// The same adjoint over the cells of the whole input binned by (k*, s*)
+// (perm: cell indices bin by bin), so that a warp's 32 cells share their
+// Taylor order and squaring count except where a warp straddles two bins.
+// Blocks take the permutation from its end, so the costliest bins start first
+// and the cheap ones fill the tail.
+template <int NF, bool TAPE>
+__global__ void __launch_bounds__(kThreads)
+dx_backward_lpc_binned(BwdLpcArgs a, DxConsts K, const unsigned long long *perm) {
+    extern __shared__ double smem[];
+    double *bsh = smem;
+    for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
+    __syncthreads();
+    const long long pos = a.C - 1 - ((long long)blockIdx.x * kThreads + threadIdx.x);
+    double *wsm = smem + 32 + (threadIdx.x >> 5) * BwdLpcStore<NF>::kWarpDoubles;
+    if (pos >= 0) bwd_lpc_cell<NF, TAPE>(threadIdx.x & 31, (long long)(perm[pos] & 0xffffffffull), a, K, bsh, wsm);
+}
+
 template <int NF, bool TAPE>
 int launch(const BwdLpcArgs &a, cudaStream_t stream) {
     const size_t smem = sizeof(double) * (32 + (size_t)(kThreads / 32) * BwdLpcStore<NF>::kWarpDoubles);
     constexpr size_t kStatic = kTile * (sizeof(unsigned long long) + sizeof(unsigned short));
-    if (smem + kStatic > 48 * 1024 &&
-        cudaFuncSetAttribute(dx_backward_lpc<NF, TAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-        return DRAG_ECUDA;
+    if (a.C >= DX_BINNED_MIN_CELLS) {
+        const unsigned long long *perm = nullptr;
+        void *scratch = dx_binned_perm(dx_consts(), a.C, NF - 1, a.rho_g, a.rho_d, a.t_s, a.dt, a.status, stream, &perm);
+        if (scratch) {
+            int rc = DRAG_OK;
+            if (smem > 48 * 1024 && cudaFuncSetAttribute(dx_backward_lpc_binned<NF, TAPE>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)smem) != cudaSuccess)
+                rc = DRAG_ECUDA;
+            if (rc == DRAG_OK) {
+                const long long blocks = (a.C + kThreads - 1) / kThreads;
+                dx_backward_lpc_binned<NF, TAPE><<<(unsigned)blocks, kThreads, smem, stream>>>(a, dx_consts(), perm);
+                if (cudaGetLastError() != cudaSuccess) rc = DRAG_ECUDA;
+            }
+            const int rr = dx_binned_release(scratch, stream);
+            return rc != DRAG_OK ? rc : rr;
+        }
+        // no scratch: the tile-sorted kernel below
+    }
     int rounds = kTile / kThreads;
     while (rounds > 1 && (a.C + rounds * kThreads - 1) / (rounds * kThreads) < 4LL * dx_sm_count()) rounds >>= 1;
     const long long blocks = (a.C + rounds * kThreads - 1) / (rounds * kThreads);

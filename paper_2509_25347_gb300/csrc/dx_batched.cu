@@ -423,13 +423,7 @@ Modes dx_batch_modes() {
     return M;
 }
 
-// The five-kernel pipeline on a checked workspace ws with layout L. thdr
-// (null: none): adjoint tape written by the lane-per-cell items (see MainArgs).
-static int batched_run(const DxConsts &K, long long nblocks, const Desc *D, long long total_cells, long long rho_d_len,
-                       long long v_len, int nspecies_max, const double *rho_g, const double *rho_d,
-                       const double *t_s, const double *v_in, double *v_out, char *ws, const Layout &L,
-                       uint32_t *st, cudaStream_t stream, long long *thdr = nullptr, double *tm = nullptr,
-                       int tlevels = 0, int tP = 0) {
+Work work_at(char *ws, const Layout &L) {
     Work W;
     W.perm = reinterpret_cast<unsigned long long *>(ws + L.perm);
     W.key = reinterpret_cast<unsigned int *>(ws + L.key);
@@ -440,16 +434,34 @@ static int batched_run(const DxConsts &K, long long nblocks, const Desc *D, long
     W.item_w = reinterpret_cast<unsigned int *>(ws + L.item_w);
     W.item_l = reinterpret_cast<unsigned int *>(ws + L.item_l);
     W.ctr = reinterpret_cast<unsigned int *>(ws + L.ctr);
+    return W;
+}
 
-    const Modes M = dx_batch_modes();
+// The binning stages of the pipeline: block offsets, (k*, s*) of every cell,
+// bin offsets and item tables, then the bin-sorted permutation W.perm.
+void launch_binning(const DxConsts &K, long long nblocks, const Desc *D, long long total_cells, long long rho_d_len,
+                    long long v_len, const double *rho_g, const double *rho_d, const double *t_s, const Work &W,
+                    const Modes &M, uint32_t *st, cudaStream_t stream) {
     const int sms = dx_sm_count();
     const long long cgrid_want = (total_cells + 255) / 256;
     const int cgrid = (int)(cgrid_want < (long long)sms * 16 ? cgrid_want : (long long)sms * 16);
-
     dx_batch_prepare<<<1, kScanThreads, 0, stream>>>(nblocks, D, total_cells, rho_d_len, v_len, W, st);
     dx_batch_count<<<cgrid, 256, 0, stream>>>(nblocks, D, rho_g, rho_d, t_s, W, K);
     dx_batch_bins<<<1, kScanThreads, 0, stream>>>(W, M);
     dx_batch_scatter<<<cgrid, 256, 0, stream>>>(nblocks, W);
+}
+
+// The five-kernel pipeline on a checked workspace ws with layout L. thdr
+// (null: none): adjoint tape written by the lane-per-cell items (see MainArgs).
+static int batched_run(const DxConsts &K, long long nblocks, const Desc *D, long long total_cells, long long rho_d_len,
+                       long long v_len, int nspecies_max, const double *rho_g, const double *rho_d,
+                       const double *t_s, const double *v_in, double *v_out, char *ws, const Layout &L,
+                       uint32_t *st, cudaStream_t stream, long long *thdr = nullptr, double *tm = nullptr,
+                       int tlevels = 0, int tP = 0) {
+    const Work W = work_at(ws, L);
+    const Modes M = dx_batch_modes();
+    const int sms = dx_sm_count();
+    launch_binning(K, nblocks, D, total_cells, rho_d_len, v_len, rho_g, rho_d, t_s, W, M, st, stream);
 
     int wd_wpc = 0, wd_lpc = 0;
     bool has_wpc = false, has_lpc = false;
@@ -582,7 +594,7 @@ extern "C" int drag_expm_apply_batched_noalloc(int64_t nblocks, const drag_block
 
 namespace {
 
-constexpr long long kBinnedMinCells = 262144;   // below: the tile-sorted kernel (one launch) is as fast
+constexpr long long kBinnedMinCells = DX_BINNED_MIN_CELLS;
 
 std::mutex g_pool_mu;
 cudaMemPool_t g_pool[64];
@@ -646,6 +658,39 @@ int dx_binned_forward(const DxConsts &K, long long C, int N, const double *rho_g
     }
     if (cudaFreeAsync(p, stream) != cudaSuccess && rc == DRAG_OK) rc = DRAG_ECUDA;
     return rc;
+}
+
+void *dx_binned_perm(const DxConsts &K, long long C, int N, const double *rho_g, const double *rho_d,
+                     const double *t_s, double dt, uint32_t *status, cudaStream_t stream,
+                     const unsigned long long **perm) {
+    cudaMemPool_t pool = scratch_pool();
+    if (!pool || C < 1 || C > 0x7fffffffLL) return nullptr;
+    const Layout L = layout(1, C);
+    void *p = nullptr;
+    if (cudaMallocFromPoolAsync(&p, L.total + 256, pool, stream) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if ((reinterpret_cast<uintptr_t>(p) & 255) != 0) {
+        cudaFreeAsync(p, stream);
+        return nullptr;
+    }
+    char *ws = static_cast<char *>(p);
+    Desc *D = reinterpret_cast<Desc *>(ws + L.total);
+    const Work W = work_at(ws, L);
+    dx_batch_single_desc<<<1, 1, 0, stream>>>(D, C, N, dt);
+    launch_binning(K, 1, D, C, (long long)N * C, 3LL * (N + 1) * C, rho_g, rho_d, t_s, W, dx_batch_modes(), status,
+                   stream);
+    if (cudaGetLastError() != cudaSuccess) {
+        cudaFreeAsync(p, stream);
+        return nullptr;
+    }
+    *perm = W.perm;
+    return p;
+}
+
+int dx_binned_release(void *scratch, cudaStream_t stream) {
+    return cudaFreeAsync(scratch, stream) == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }
 
 extern "C" int32_t drag_expm_apply_launches(int64_t ncells, int32_t nspecies) {

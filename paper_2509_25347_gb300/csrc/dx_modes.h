@@ -38,6 +38,7 @@ int dx_launch_forward_lpc(const DxConsts &K, int n, int store, long long C, cons
 // (n <= 9) and at least 262,144 cells. DX_BINNED_UNAVAILABLE: no scratch could
 // be had; the caller runs the tile-sorted kernel instead.
 #define DX_BINNED_UNAVAILABLE 1
+#define DX_BINNED_MIN_CELLS 262144   // below: the tile-sorted kernels (one launch) are as fast
 bool dx_binned_eligible(int n, int mode, long long C);
 // thdr (null: none): also writes the adjoint tape (geometry as in drag_expm_apply_taped).
 int dx_binned_forward(const DxConsts &K, long long C, int N, const double *rho_g, const double *rho_d,
@@ -53,8 +54,21 @@ int dx_launch_forward_lpc_taped(const DxConsts &K, int n, long long C, const dou
                                 const double *t_s, const double *v_in, double *v_out, double dt, uint32_t *status,
                                 long long *hdr, double *m, int levels, int P, cudaStream_t stream);
 
+// The cells of one input (C cells, N species, one dt) in bin order, binned by
+// (k*, s*) as the binned forward bins them: *perm (device, C entries) holds
+// each cell's index in its low 32 bits, bins in ascending (k*, s*). Scratch
+// comes from the library's stream-ordered pool; the return value (null: no
+// scratch could be had, nothing launched) is released with dx_binned_release
+// on the same stream after the kernels that read *perm. 5 launches.
+void *dx_binned_perm(const DxConsts &K, long long C, int N, const double *rho_g, const double *rho_d,
+                     const double *t_s, double dt, uint32_t *status, cudaStream_t stream,
+                     const unsigned long long **perm);
+int dx_binned_release(void *scratch, cudaStream_t stream);
+
 // Lane-per-cell adjoint (dx_backward_lpc.cu) for n <= DX_BWD_LPC_NMAX, run by
-// drag_expm_backward(_taped) when the mode of n is a lane-per-cell one. thdr
+// drag_expm_backward(_taped) when the mode of n is a lane-per-cell one: cells
+// binned by (k*, s*) over the whole input from DX_BINNED_MIN_CELLS cells on
+// (6 launches), tile-sorted below (1 launch). thdr
 // (null: none) is the tape the forward wrote (geometry as in
 // drag_expm_backward_taped; tm its first level).
 #define DX_BWD_LPC_NMAX 6

@@ -268,3 +268,61 @@ def test_lane_per_cell_backward_full_size_sampled(dx):
     """The N = 4 workload at full size (2,097,152 cells: tiles of 512 sorted
     cells): 128 sampled cells against the oracle's adjoint."""
     test_backward_full_size_sampled(dx, "mrn_n4_128cube")
+
+
+@pytest.mark.parametrize("N", [1, 4, 5])
+def test_lane_per_cell_backward_binned(dx, N):
+    """From 262,144 cells the lane-per-cell adjoint bins the cells by (k*, s*)
+    over the whole input before running them: its gradients equal, bit for bit,
+    those of the tile-sorted kernel that runs on fewer cells (the per-cell
+    arithmetic does not depend on the grouping), and sampled cells match the
+    oracle's adjoint; through the tape they are unchanged."""
+    import torch
+    C = 300007
+    cells = W.mrn(C, N, seed=410 + N, stiff_lo=-5.0, stiff_hi=8.0)
+    g_np = np.random.default_rng(41 + N).standard_normal(cells.v.shape)
+    rg, rd, ts, v, g = t(cells.rho_g), t(cells.rho_d), t(cells.t_s), t(cells.v), t(g_np)
+    binned = [x.cpu().numpy() for x in dx.backward(rg, rd, ts, cells.dt, v, g)]
+    head = np.arange(200003)
+    sub = cells.subset(head)
+    tiled = gpu_backward(dx, sub, g_np[:, :, head])
+    for a, b in zip(binned, tiled):
+        assert np.array_equal(a[..., head], b)
+    idx = np.unique(np.concatenate([np.random.default_rng(N).integers(0, C, 160), [0, C - 1]]))
+    sub = cells.subset(idx)
+    ref = oracle.drag_backward(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v, g_np[:, :, idx])[:4]
+    assert_adjoint_parity(sub, g_np[:, :, idx], [x[..., idx] for x in binned], ref)
+    _, tape = dx.apply_taped(rg, rd, ts, cells.dt, v)
+    taped = [x.cpu().numpy() for x in dx.backward(rg, rd, ts, cells.dt, v, g, tape=tape)]
+    for a, b in zip(binned, taped):
+        assert np.array_equal(a, b)
+    assert dx.get_status() == 0
+    torch.cuda.synchronize()
+
+
+def test_lane_per_cell_backward_in_cuda_graph(dx):
+    """The binned adjoint (scratch from the library's stream-ordered pool) can
+    be captured in a CUDA graph and replayed with the same results."""
+    import torch
+    C, N = 270001, 4
+    cells = W.mrn(C, N, seed=77, stiff_lo=-4.0, stiff_hi=8.0)
+    rg, rd, ts, v = t(cells.rho_g), t(cells.rho_d), t(cells.t_s), t(cells.v)
+    g = t(np.random.default_rng(7).standard_normal(cells.v.shape))
+    ref = dx.backward(rg, rd, ts, cells.dt, v, g)
+    out = tuple(torch.empty_like(x) for x in ref)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        dx.backward(rg, rd, ts, cells.dt, v, g, out=out)   # warm-up outside the capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        dx.backward(rg, rd, ts, cells.dt, v, g, out=out)
+    for x in out:
+        x.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(ref, out):
+        assert torch.equal(a, b)
+    assert dx.get_status() == 0

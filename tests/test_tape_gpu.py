@@ -333,4 +333,7 @@ def test_binned_tape(dx, N):
     idx = np.sort(np.random.default_rng(9).choice(C, 1500, replace=False))
     sub = cells.subset(idx)
     assert_adjoint_parity(sub, g_np[:, :, idx], [x[..., idx] for x in taped], [x[..., idx] for x in plain])
+    if N + 1 <= 6:   # lane-per-cell adjoint (binned too): bit for bit
+        for a, b in zip(taped, plain):
+            assert np.array_equal(a, b)
     assert dx.get_status() == 0
