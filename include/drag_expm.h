@@ -232,6 +232,11 @@ int drag_expm_select_target(int64_t ncells, int32_t nspecies, const double *rho_
  * DragEqVar3, jacobian). The Frechet derivative is carried through the same
  * Algorithm 2 / Taylor / squaring steps as the forward (block-triangular
  * form [[A, E], [0, A]]), recomputing the forward on the fly (no storage).
+ * Kernel family: one warp per cell, or, for N <= 5 under a lane-per-cell mode
+ * (the default there), one lane per cell. The lane-per-cell adjoint bins the
+ * cells by (k*, s*) over the whole input from 262,144 cells on, with scratch
+ * from the library's private stream-ordered pool (graph-capturable, 6 launches),
+ * and sorts them by cost within tiles below (1 launch); both give the same bits.
  *   rho_g, rho_d, t_s, v_in : DEVICE inputs of the forward call (read only).
  *   grad_v_out : DEVICE, 3*(N+1)*ncells doubles, layout of v (read only).
  *   grad_v_in  : DEVICE, layout of v, written (may be NULL).
@@ -252,12 +257,13 @@ int drag_expm_backward(int64_t ncells, int32_t nspecies, const double *rho_g, co
  * drag_expm_backward recomputes them. drag_expm_apply_taped stores the ones
  * the forward forms, E_0 .. E_{s*-2} (E_0 alone for s* <= 1), in a tape, and
  * drag_expm_backward_taped reads them instead: it then forms neither the
- * Taylor polynomial nor those products. Where the forward runs one warp per
- * cell (N >= 12, or any N whose mode is warp per cell) it forms each E_t by
- * the adjoint's own FP64 operations, and the gradients are identical to
- * drag_expm_backward's. For N <= 11 with the default modes the lane-per-cell
- * forward writes the tape, and the gradients agree with drag_expm_backward's to
- * rounding. The tape trades HBM for FP64 work:
+ * Taylor polynomial nor those products. Where forward and adjoint run the same
+ * kernel family (N >= 12, any N whose mode is warp per cell, and N <= 5 under
+ * a lane-per-cell mode) the forward forms each E_t by the adjoint's own FP64
+ * operations, and the gradients are identical to drag_expm_backward's. For
+ * 6 <= N <= 11 with the default modes the lane-per-cell forward writes the
+ * tape that the warp-per-cell adjoint reads, and the gradients agree with
+ * drag_expm_backward's to rounding. The tape trades HBM for FP64 work:
  *   drag_expm_tape_bytes(ncells, nspecies, levels) bytes, about
  *   ncells * levels * 8 * (N+1)(N+2)/2 (rounded up to 128-byte slots),
  * where `levels` is the capacity per cell; a cell needs

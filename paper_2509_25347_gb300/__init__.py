@@ -418,9 +418,10 @@ def _autograd_function():
 
     class _DragExpmTaped(torch.autograd.Function):
         """DragExpm whose forward records the adjoint tape (apply_taped) and whose
-        backward reads it: identical values, gradients identical from N = 12 on (to
-        rounding below, where the lane-per-cell forward writes the tape), less FP64 work in the
-        backward for a tape of about ncells * levels * 4 (N+1)(N+2) bytes.
+        backward reads it: identical values; gradients identical for N <= 5 and from
+        N = 12 on under the default modes (to rounding for 6 <= N <= 11, where the
+        lane-per-cell forward writes a tape the warp-per-cell adjoint reads); less FP64
+        work in the backward for a tape of about ncells * levels * 4 (N+1)(N+2) bytes.
 
         forward(rho_g, rho_d, t_s, dt, v_in, levels=None)."""
 
