@@ -70,57 +70,7 @@ __device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpc
     const long long C = a.C;
     const double dt = a.dt;
 
-    // ---------------- load and validate (as the lane-per-cell forward)
-    const double rg = a.rho_g[c];
-    bool ok = dx_pos_finite(rg);
-    double eps[N], alpha[N];
-    unsigned long long fph = 0;
-#pragma unroll
-    for (int i = 0; i < N; i++) {
-        const double rd = a.rho_d[i * C + c], ts = a.t_s[i * C + c];
-        ok = ok && dx_nonneg_finite(rd) && dx_pos_or_inf(ts);
-        if (TAPE) fph ^= dx_fingerprint_term(i + 1, rd, ts);
-        eps[i] = rd;
-        alpha[i] = ts;
-    }
-    if (!ok) {
-        bwd_lpc_fail<NF>(c, a);
-        return;
-    }
-    double s1 = 0.0;
-#pragma unroll
-    for (int i = 0; i < N; i++) {
-        eps[i] = __ddiv_rn(eps[i], rg);      // Eq. DragEqVar2
-        alpha[i] = __ddiv_rn(1.0, alpha[i]); // Eq. DragEqVar3
-        s1 = __dadd_rn(s1, __dmul_rn(__dmul_rn(eps[i], alpha[i]), dt));
-    }
-    double col0 = s1;
-    long long cmax = 0;
-#pragma unroll
-    for (int i = 0; i < N; i++) {
-        const double ai0 = __dmul_rn(alpha[i], dt);
-        col0 = __dadd_rn(col0, ai0);
-        const long long cb = dx_bits(__dadd_rn(__dmul_rn(__dmul_rn(eps[i], alpha[i]), dt), ai0));
-        cmax = cb > cmax ? cb : cmax;
-    }
-    const long long nb = dx_bits(col0) > cmax ? dx_bits(col0) : cmax;
-    if (!dx_norm_ok(nb)) {
-        bwd_lpc_fail<NF>(c, a);
-        return;
-    }
-    int kk, s;
-    dx_select(__longlong_as_double(nb), K, kk, s);
-    const int m = K.mk[kk];
-    const int tlev = dx_tape_levels(s);
-    bool taped = false;
-    const double *tcell = nullptr;
-    if (TAPE) {
-        const long long h = dx_fingerprint_final(fph, rg, dt, dx_tape_salt(a.levels, NF));
-        taped = a.thdr[c] == h && tlev <= a.levels;
-        tcell = a.tm + (size_t)c * a.levels * a.P;
-    }
-
-    // ---------------- symmetric arrowhead X = 2^-s D_sigma A D_sigma^-1 and the direction
+    // ---------------- set-up, Algorithm 2 and X, as the lane-per-cell forward (dx_lpc_setup)
     DxLaneArr<NF, SV> sig, tau, xs, ds, a3;
     DxLaneArr<3 * NF, SV> av, bv, yv;
     if constexpr (SV) {
@@ -133,18 +83,22 @@ __device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpc
         bv.bind(wsm + 256 * NF, lane);
         yv.bind(wsm + 352 * NF, lane);
     }
-    sig[0] = 1.0;
-    tau[0] = 1.0;
-    xs[0] = dx_scale2(-s1, s);
-    ds[0] = 0.0;
-#pragma unroll
-    for (int i = 1; i < NF; i++) {
-        const double e = dx_bits(eps[i - 1]) < dx_bits(DX_EPS_FLOOR) ? DX_EPS_FLOOR : eps[i - 1];
-        const double sg = __dsqrt_rn(e);
-        sig[i] = sg;
-        tau[i] = __ddiv_rn(1.0, sg);
-        xs[i] = __dmul_rn(__dmul_rn(sg, alpha[i - 1]), dx_scale2(dt, s));
-        ds[i] = -dx_scale2(__dmul_rn(alpha[i - 1], dt), s);
+    double rg, eps[N], alpha[N];
+    int kk, s;
+    unsigned long long fph;
+    if (!dx_lpc_setup<NF>(a.rho_g + c, a.rho_d + c, a.t_s + c, C, dt, K, TAPE, rg, eps, alpha, kk, s, fph, sig, tau,
+                          xs, ds)) {
+        bwd_lpc_fail<NF>(c, a);
+        return;
+    }
+    const int m = K.mk[kk];
+    const int tlev = dx_tape_levels(s);
+    bool taped = false;
+    const double *tcell = nullptr;
+    if (TAPE) {
+        const long long h = dx_fingerprint_final(fph, rg, dt, dx_tape_salt(a.levels, NF));
+        taped = a.thdr[c] == h && tlev <= a.levels;
+        tcell = a.tm + (size_t)c * a.levels * a.P;
     }
     {
         // a_d = g_d / sigma, b_d = 2^-s sigma o v_d, and the stationary block kappa
@@ -331,25 +285,9 @@ __global__ void __launch_bounds__(kThreads) dx_backward_lpc(BwdLpcArgs a, DxCons
     double *bsh = smem;
     for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
     const long long C = a.C;
-    const int tile = rounds * kThreads;
-    const long long base = (long long)blockIdx.x * tile;
+    const long long base = (long long)blockIdx.x * rounds * kThreads;
     // order the tile's cells by the cost proxy so that a warp's 32 cells share (k*, s*)
-    for (int r = 0; r < rounds; r++) {
-        const int e = r * kThreads + threadIdx.x;
-        const long long c = base + e;
-        const unsigned int p =
-            c < C ? dx_lpc_cost_proxy<NF - 1>(a.rho_g + c, a.rho_d + c, a.t_s + c, C, a.dt) : 0xffffffffu;
-        key[e] = ((unsigned long long)p << 32) | (unsigned int)e;
-    }
-    __syncthreads();
-    for (int r = 0; r < rounds; r++) {
-        const int e = r * kThreads + threadIdx.x;
-        const unsigned long long me = key[e];
-        int rank = 0;
-        for (int j = 0; j < tile; j++) rank += key[j] < me;
-        order[rank] = (unsigned short)e;
-    }
-    __syncthreads();
+    dx_lpc_tile_order<NF - 1>(base, rounds, kThreads, C, a.rho_g, a.rho_d, a.t_s, a.dt, key, order);
     const int lane = threadIdx.x & 31;
     double *wsm = smem + 32 + (threadIdx.x >> 5) * BwdLpcStore<NF>::kWarpDoubles;
     for (int r = 0; r < rounds; r++) {

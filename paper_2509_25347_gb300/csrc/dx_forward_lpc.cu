@@ -64,28 +64,13 @@ dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d
     double *bsh = smem;
     for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
     constexpr int kThreads = lpc_threads<NF, ST>();
-    const int tile = rounds * kThreads;
-    const long long base = (long long)blockIdx.x * tile;
+    const long long base = (long long)blockIdx.x * rounds * kThreads;
     if (rounds >= DX_LPC_SORT_MIN_ROUNDS) {
-        for (int r = 0; r < rounds; r++) {
-            const int e = r * kThreads + threadIdx.x;
-            const long long c = base + e;
-            const unsigned int p = c < C ? dx_lpc_cost_proxy<NF - 1>(rho_g + c, rho_d + c, t_s + c, C, dt) : 0xffffffffu;
-            key[e] = ((unsigned long long)p << 32) | (unsigned int)e;
-        }
-        __syncthreads();
-        // rank sort: position of each key among the tile's distinct keys
-        for (int r = 0; r < rounds; r++) {
-            const int e = r * kThreads + threadIdx.x;
-            const unsigned long long me = key[e];
-            int rank = 0;
-            for (int j = 0; j < tile; j++) rank += key[j] < me;
-            order[rank] = (unsigned short)e;
-        }
+        dx_lpc_tile_order<NF - 1>(base, rounds, kThreads, C, rho_g, rho_d, t_s, dt, key, order);
     } else {
         order[threadIdx.x] = (unsigned short)threadIdx.x;   // unsorted
+        __syncthreads();
     }
-    __syncthreads();
     const int lane = threadIdx.x & 31;
     double *wsm = ST != DX_LPC_REGS ? smem + 32 + (threadIdx.x >> 5) * dx_lpc_warp_smem_doubles<NF, ST>() : nullptr;
     for (int r = 0; r < rounds; r++) {

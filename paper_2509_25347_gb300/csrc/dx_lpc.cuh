@@ -152,6 +152,93 @@ __device__ __forceinline__ unsigned int dx_lpc_cost_proxy(const double *rgp, con
     return (nrm >= 0.0f && b < 0x7f800000u) ? b : 0x7f800000u;
 }
 
+// Orders a tile of rounds x threads consecutive cells starting at base by the
+// cost proxy (ties by position): order[rank] = tile index, key: the tile's
+// scratch. Block-wide; ends with a barrier.
+template <int N>
+__device__ __forceinline__ void dx_lpc_tile_order(long long base, int rounds, int threads, long long C,
+                                                  const double *rho_g, const double *rho_d, const double *t_s,
+                                                  double dt, unsigned long long *key, unsigned short *order) {
+    const int tile = rounds * threads;
+    for (int r = 0; r < rounds; r++) {
+        const int e = r * threads + threadIdx.x;
+        const long long c = base + e;
+        const unsigned int p = c < C ? dx_lpc_cost_proxy<N>(rho_g + c, rho_d + c, t_s + c, C, dt) : 0xffffffffu;
+        key[e] = ((unsigned long long)p << 32) | (unsigned int)e;
+    }
+    __syncthreads();
+    // rank sort: position of each key among the tile's distinct keys
+    for (int r = 0; r < rounds; r++) {
+        const int e = r * threads + threadIdx.x;
+        const unsigned long long me = key[e];
+        int rank = 0;
+        for (int j = 0; j < tile; j++) rank += key[j] < me;
+        order[rank] = (unsigned short)e;
+    }
+    __syncthreads();
+}
+
+// Per-lane set-up of one cell. Loads and validates rho_g, rho_d, t_s (integer
+// checks on bit patterns); forms eps_i = rho_d,i / rho_g and alpha_i = 1 / t_s,i
+// (Eqs. DragEqVar2, DragEqVar3) and the 1-norm of A = dt Omega_v summed in
+// ascending species order (as the oracle sums it, so (k*, s*) are reproducible);
+// runs Algorithm 2; and writes the scaled symmetric arrowhead X = 2^-s*
+// D_sigma A D_sigma^-1 (sig, tau: sigma and 1 / sigma; xs: row 0; ds: the
+// diagonal). With want_fp, fph is the XOR of the species' fingerprint terms over
+// the raw inputs. Returns false for an invalid cell, before writing the vectors.
+template <int NF, class VA>
+__device__ __forceinline__ bool dx_lpc_setup(const double *rgp, const double *rdp, const double *tsp, long long stride,
+                                             double dt, const DxConsts &K, bool want_fp, double &rg,
+                                             double (&eps)[NF - 1], double (&alpha)[NF - 1], int &kk, int &s,
+                                             unsigned long long &fph, VA &sig, VA &tau, VA &xs, VA &ds) {
+    constexpr int N = NF - 1;
+    rg = *rgp;
+    bool ok = dx_pos_finite(rg);
+    fph = 0;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const double rd = rdp[i * stride], ts = tsp[i * stride];
+        ok = ok && dx_nonneg_finite(rd) && dx_pos_or_inf(ts);
+        if (want_fp) fph ^= dx_fingerprint_term(i + 1, rd, ts);
+        eps[i] = rd;
+        alpha[i] = ts;
+    }
+    if (!ok) return false;
+    double s1 = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        eps[i] = __ddiv_rn(eps[i], rg);      // Eq. DragEqVar2
+        alpha[i] = __ddiv_rn(1.0, alpha[i]); // Eq. DragEqVar3
+        s1 = __dadd_rn(s1, __dmul_rn(__dmul_rn(eps[i], alpha[i]), dt));
+    }
+    double col0 = s1;
+    long long cmax = 0;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const double ai0 = __dmul_rn(alpha[i], dt);
+        col0 = __dadd_rn(col0, ai0);
+        const long long cb = dx_bits(__dadd_rn(__dmul_rn(__dmul_rn(eps[i], alpha[i]), dt), ai0));
+        cmax = cb > cmax ? cb : cmax;
+    }
+    const long long nb = dx_bits(col0) > cmax ? dx_bits(col0) : cmax;
+    if (!dx_norm_ok(nb)) return false;
+    dx_select(__longlong_as_double(nb), K, kk, s);
+    sig[0] = 1.0;
+    tau[0] = 1.0;
+    xs[0] = dx_scale2(-s1, s);
+    ds[0] = 0.0;
+#pragma unroll
+    for (int i = 1; i < NF; i++) {
+        const double e = dx_bits(eps[i - 1]) < dx_bits(DX_EPS_FLOOR) ? DX_EPS_FLOOR : eps[i - 1];
+        const double sg = __dsqrt_rn(e);
+        sig[i] = sg;
+        tau[i] = __ddiv_rn(1.0, sg);
+        xs[i] = __dmul_rn(__dmul_rn(sg, alpha[i - 1]), dx_scale2(dt, s));
+        ds[i] = -dx_scale2(__dmul_rn(alpha[i - 1], dt), s);
+    }
+    return true;
+}
+
 // Shared-memory doubles one warp needs for storage mode ST.
 template <int NF, int ST>
 __host__ __device__ constexpr int dx_lpc_warp_smem_doubles() {
@@ -175,69 +262,7 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
     constexpr int NT = DxPacked<NF>::NT;
     using P = DxPacked<NF>;
 
-    // ---------------- load and validate (integer checks on bit patterns)
-    const double rg = *rgp;
-    bool ok = dx_pos_finite(rg);
-    double eps[N > 0 ? N : 1], alpha[N > 0 ? N : 1];
-#pragma unroll
-    for (int i = 0; i < N; i++) {
-        const double rd = rdp[i * stride], ts = tsp[i * stride];
-        ok = ok && dx_nonneg_finite(rd) && dx_pos_or_inf(ts);
-        eps[i] = rd;
-        alpha[i] = ts;
-    }
-    if (!ok) {
-#pragma unroll
-        for (int e = 0; e < 3 * NF; e++) vop[e * stride] = NAN;
-        if (heat) *heat = NAN;
-        atomicOr(status, DRAG_STATUS_BAD_CELL);
-        return;
-    }
-
-    unsigned long long fph = 0;   // fingerprint of the raw inputs (rho_d, t_s still unconverted here)
-    if (tp.hdr) {
-#pragma unroll
-        for (int i = 0; i < N; i++) fph ^= dx_fingerprint_term(i + 1, eps[i], alpha[i]);
-    }
-
-    // ---------------- A = dt Omega_v entries and the 1-norm (ascending species order)
-    double s1 = 0.0;
-#pragma unroll
-    for (int i = 0; i < N; i++) {
-        eps[i] = __ddiv_rn(eps[i], rg);      // Eq. DragEqVar2
-        alpha[i] = __ddiv_rn(1.0, alpha[i]); // Eq. DragEqVar3
-        s1 = __dadd_rn(s1, __dmul_rn(__dmul_rn(eps[i], alpha[i]), dt));
-    }
-    double col0 = s1;
-    long long cmax = 0;
-#pragma unroll
-    for (int i = 0; i < N; i++) {
-        const double ai0 = __dmul_rn(alpha[i], dt);
-        col0 = __dadd_rn(col0, ai0);
-        const long long cb = dx_bits(__dadd_rn(__dmul_rn(__dmul_rn(eps[i], alpha[i]), dt), ai0));
-        cmax = cb > cmax ? cb : cmax;
-    }
-    const long long nb = dx_bits(col0) > cmax ? dx_bits(col0) : cmax;
-    if (!dx_norm_ok(nb)) {
-#pragma unroll
-        for (int e = 0; e < 3 * NF; e++) vop[e * stride] = NAN;
-        if (heat) *heat = NAN;
-        atomicOr(status, DRAG_STATUS_BAD_CELL);
-        return;
-    }
-    int kk, s;
-    dx_select(__longlong_as_double(nb), K, kk, s);
-    const int m = K.mk[kk];
-    double *tape = nullptr;
-    const int tlev = dx_tape_levels(s);
-    if (tp.hdr) {
-        const long long h = dx_fingerprint_final(fph, rg, dt, dx_tape_salt(tp.levels, NF));
-        const bool fits = tlev <= tp.levels;
-        *tp.hdr = fits ? h : ~h;
-        if (fits) tape = tp.m;
-    }
-
-    // ---------------- symmetric arrowhead X = 2^-s D_sigma A D_sigma^-1
+    // ---------------- set-up, Algorithm 2 and the scaled symmetric arrowhead X
     constexpr bool kSharedF = ST == DX_LPC_SHARED, kSharedG = ST != DX_LPC_REGS;
     DxLaneArr<NF, kSharedG> sig, tau, xs, ds;
     DxLaneArr<NT, kSharedF> Fm;
@@ -251,18 +276,25 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
         xs.bind(smem_warp + f + 32 * NT + 64 * NF, lane);
         ds.bind(smem_warp + f + 32 * NT + 96 * NF, lane);
     }
-    sig[0] = 1.0;
-    tau[0] = 1.0;
-    xs[0] = dx_scale2(-s1, s);
-    ds[0] = 0.0;
+    double rg, eps[N], alpha[N];
+    int kk, s;
+    unsigned long long fph;   // fingerprint of the raw inputs (tape)
+    if (!dx_lpc_setup<NF>(rgp, rdp, tsp, stride, dt, K, tp.hdr != nullptr, rg, eps, alpha, kk, s, fph, sig, tau, xs,
+                          ds)) {
 #pragma unroll
-    for (int i = 1; i < NF; i++) {
-        const double e = dx_bits(eps[i - 1]) < dx_bits(DX_EPS_FLOOR) ? DX_EPS_FLOOR : eps[i - 1];
-        const double sg = __dsqrt_rn(e);
-        sig[i] = sg;
-        tau[i] = __ddiv_rn(1.0, sg);
-        xs[i] = __dmul_rn(__dmul_rn(sg, alpha[i - 1]), dx_scale2(dt, s));
-        ds[i] = -dx_scale2(__dmul_rn(alpha[i - 1], dt), s);
+        for (int e = 0; e < 3 * NF; e++) vop[e * stride] = NAN;
+        if (heat) *heat = NAN;
+        atomicOr(status, DRAG_STATUS_BAD_CELL);
+        return;
+    }
+    const int m = K.mk[kk];
+    double *tape = nullptr;
+    const int tlev = dx_tape_levels(s);
+    if (tp.hdr) {
+        const long long h = dx_fingerprint_final(fph, rg, dt, dx_tape_salt(tp.levels, NF));
+        const bool fits = tlev <= tp.levels;
+        *tp.hdr = fits ? h : ~h;
+        if (fits) tape = tp.m;
     }
 
     // ---------------- Taylor: F = b_m X + b_{m-1} I, then F <- F X + b_j I (Horner in X)
