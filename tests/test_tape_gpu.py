@@ -337,3 +337,34 @@ def test_binned_tape(dx, N):
         for a, b in zip(taped, plain):
             assert np.array_equal(a, b)
     assert dx.get_status() == 0
+
+
+@pytest.mark.parametrize("N", [2, 5])
+def test_tape_across_kernel_families(dx, N):
+    """One tape format for both kernel families: a tape the warp-per-cell
+    forward wrote, read by the lane-per-cell adjoint, and one the lane-per-cell
+    forward wrote, read by the warp-per-cell adjoint, both give the oracle's
+    gradients at the adjoint tolerances."""
+    cells = spread_cells(N, 223, seed=260 + N)
+    rg, rd, ts = dev_args(cells)
+    v = t(cells.v)
+    g_np = np.random.default_rng(26 + N).standard_normal(cells.v.shape)
+    g = t(g_np)
+    ref = oracle.drag_backward(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, g_np)[:4]
+    saved = dx.get_mode(N)
+    assert saved != dx.MODE_WARP_PER_CELL
+    dx.set_mode(N, dx.MODE_WARP_PER_CELL)
+    try:
+        _, tape_w = dx.apply_taped(rg, rd, ts, cells.dt, v)
+    finally:
+        dx.set_mode(N, saved)
+    got = [x.cpu().numpy() for x in dx.backward(rg, rd, ts, cells.dt, v, g, tape=tape_w)]
+    assert_adjoint_parity(cells, g_np, got, ref)
+    _, tape_l = dx.apply_taped(rg, rd, ts, cells.dt, v)
+    dx.set_mode(N, dx.MODE_WARP_PER_CELL)
+    try:
+        got = [x.cpu().numpy() for x in dx.backward(rg, rd, ts, cells.dt, v, g, tape=tape_l)]
+    finally:
+        dx.set_mode(N, saved)
+    assert_adjoint_parity(cells, g_np, got, ref)
+    assert dx.get_status() == 0
