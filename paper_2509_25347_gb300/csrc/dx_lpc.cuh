@@ -20,6 +20,9 @@
 //                   each step ends by copying G back into F.
 #pragma once
 
+#include <type_traits>
+#include <utility>
+
 #include "dx_common.cuh"
 #include "dx_tape.cuh"
 
@@ -33,48 +36,56 @@ struct DxPacked {
     }
 };
 
-// Storage of NT doubles per lane: registers or a strided shared-memory slice.
-template <int NT, bool SMEM>
+// Storage of NT values (double, or float on the mixed-precision path) per
+// lane: registers or a strided shared-memory slice.
+template <int NT, bool SMEM, typename V = double>
 struct DxLaneArr;
 
-template <int NT>
-struct DxLaneArr<NT, false> {
-    double v[NT];
-    __device__ __forceinline__ void bind(double *, int) {}
-    __device__ __forceinline__ double &operator[](int e) { return v[e]; }
+template <int NT, typename V>
+struct DxLaneArr<NT, false, V> {
+    V v[NT];
+    __device__ __forceinline__ void bind(V *, int) {}
+    __device__ __forceinline__ V &operator[](int e) { return v[e]; }
 };
 
-template <int NT>
-struct DxLaneArr<NT, true> {
-    double *p;
-    __device__ __forceinline__ void bind(double *base, int lane) { p = base + lane; }
-    __device__ __forceinline__ double &operator[](int e) { return p[e * 32]; }
+template <int NT, typename V>
+struct DxLaneArr<NT, true, V> {
+    V *p;
+    __device__ __forceinline__ void bind(V *base, int lane) { p = base + lane; }
+    __device__ __forceinline__ V &operator[](int e) { return p[e * 32]; }
 };
 
 // F <- G after a step: copied into registers, or shared-memory slices swapped.
-template <int NT, bool GS>
-__device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, false> &F, DxLaneArr<NT, GS> &G) {
+template <int NT, bool GS, typename V>
+__device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, false, V> &F, DxLaneArr<NT, GS, V> &G) {
 #pragma unroll
     for (int e = 0; e < NT; e++) F.v[e] = G[e];
 }
-template <int NT>
-__device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, true> &F, DxLaneArr<NT, true> &G) {
-    double *t = F.p;
+template <int NT, typename V>
+__device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, true, V> &F, DxLaneArr<NT, true, V> &G) {
+    V *t = F.p;
     F.p = G.p;
     G.p = t;
 }
 
+// Element type of a DxLaneArr.
+template <class A>
+using DxElem = typename std::remove_reference<decltype(std::declval<A &>()[0])>::type;
+
 // ---- per-lane steps shared by the forward and the adjoint (one cell, packed
-// symmetric n x n matrices; FA, GA, VA are DxLaneArr types). Both sides form
-// the iterates E_t with exactly these operations, so a lane-per-cell adjoint
-// that recomputes them gets the values the forward's tape holds.
+// symmetric n x n matrices; FA, GA, VA are DxLaneArr types, all of one element
+// type T, in which the arithmetic runs). Both sides form the iterates E_t with
+// exactly these operations, so a lane-per-cell adjoint that recomputes them
+// gets the values the forward's tape holds.
 
 // F = b_m X + b_{m-1} I for the arrowhead X (xs: row 0, ds: diagonal).
 template <int NF, class FA, class VA>
-__device__ __forceinline__ void dx_lpc_taylor_init(FA &Fm, VA &xs, VA &ds, double bm, double bm1) {
+__device__ __forceinline__ void dx_lpc_taylor_init(FA &Fm, VA &xs, VA &ds, double bm_, double bm1_) {
     using P = DxPacked<NF>;
+    using T = DxElem<FA>;
+    const T bm = (T)bm_, bm1 = (T)bm1_;
 #pragma unroll
-    for (int e = 0; e < P::NT; e++) Fm[e] = 0.0;
+    for (int e = 0; e < P::NT; e++) Fm[e] = T(0);
     Fm[0] = fma(bm, xs[0], bm1);
 #pragma unroll
     for (int i = 1; i < NF; i++) {
@@ -86,16 +97,18 @@ __device__ __forceinline__ void dx_lpc_taylor_init(FA &Fm, VA &xs, VA &ds, doubl
 // One Horner step in X: G = F X + b_j I (F is a polynomial in X, so F X is
 // symmetric; entry (i, j), j >= 1, needs F_i0 X_0j + F_ij X_jj).
 template <int NF, class FA, class GA, class VA>
-__device__ __forceinline__ void dx_lpc_horner_step(FA &Fm, GA &Gm, VA &xs, VA &ds, double bj) {
+__device__ __forceinline__ void dx_lpc_horner_step(FA &Fm, GA &Gm, VA &xs, VA &ds, double bj_) {
     using P = DxPacked<NF>;
-    double g00 = fma(Fm[0], xs[0], bj);
+    using T = DxElem<FA>;
+    const T bj = (T)bj_;
+    T g00 = fma(Fm[0], xs[0], bj);
 #pragma unroll
     for (int k = 1; k < NF; k++) g00 = fma(Fm[P::at(0, k)], xs[k], g00);
 #pragma unroll
     for (int jj = 1; jj < NF; jj++) {
 #pragma unroll
         for (int i = 0; i <= jj; i++) {
-            double acc = fma(Fm[P::at(i, 0)], xs[jj], i == jj ? bj : 0.0);
+            T acc = fma(Fm[P::at(i, 0)], xs[jj], i == jj ? bj : T(0));
             Gm[P::at(i, jj)] = fma(Fm[P::at(i, jj)], ds[jj], acc);
         }
     }
@@ -106,13 +119,14 @@ __device__ __forceinline__ void dx_lpc_horner_step(FA &Fm, GA &Gm, VA &xs, VA &d
 template <int NF, class MA, class VA>
 __device__ __forceinline__ void dx_lpc_restore(MA &M, VA &sig, VA &tau) {
     using P = DxPacked<NF>;
+    using T = DxElem<MA>;
 #pragma unroll
     for (int i = 0; i < NF; i++) {
-        double acc = 0.0;
+        T acc = T(0);
 #pragma unroll
         for (int k = 0; k < NF; k++)
             if (k != i) acc = fma(M[P::at(i, k)], sig[k], acc);
-        M[P::at(i, i)] = fma(-tau[i], acc, 1.0);
+        M[P::at(i, i)] = fma(-tau[i], acc, T(1));
     }
 }
 
@@ -124,7 +138,7 @@ __device__ __forceinline__ void dx_lpc_square_offdiag(FA &Fm, GA &Gm) {
     for (int i = 0; i < NF; i++) {
 #pragma unroll
         for (int jj = i + 1; jj < NF; jj++) {
-            double acc = 0.0;
+            DxElem<FA> acc = 0;
 #pragma unroll
             for (int k = 0; k < NF; k++) acc = fma(Fm[P::at(i, k)], Fm[P::at(jj, k)], acc);
             Gm[P::at(i, jj)] = acc;
@@ -185,12 +199,14 @@ __device__ __forceinline__ void dx_lpc_tile_order(long long base, int rounds, in
 // runs Algorithm 2; and writes the scaled symmetric arrowhead X = 2^-s*
 // D_sigma A D_sigma^-1 (sig, tau: sigma and 1 / sigma; xs: row 0; ds: the
 // diagonal). With want_fp, fph is the XOR of the species' fingerprint terms over
-// the raw inputs. Returns false for an invalid cell, before writing the vectors.
+// the raw inputs. Dust-to-gas ratios below eps_floor are raised to it in the
+// symmetric form. Returns false for an invalid cell, before writing the vectors.
 template <int NF, class VA>
 __device__ __forceinline__ bool dx_lpc_setup(const double *rgp, const double *rdp, const double *tsp, long long stride,
                                              double dt, const DxConsts &K, bool want_fp, double &rg,
                                              double (&eps)[NF - 1], double (&alpha)[NF - 1], int &kk, int &s,
-                                             unsigned long long &fph, VA &sig, VA &tau, VA &xs, VA &ds) {
+                                             unsigned long long &fph, VA &sig, VA &tau, VA &xs, VA &ds,
+                                             double eps_floor = DX_EPS_FLOOR) {
     constexpr int N = NF - 1;
     rg = *rgp;
     bool ok = dx_pos_finite(rg);
@@ -229,7 +245,7 @@ __device__ __forceinline__ bool dx_lpc_setup(const double *rgp, const double *rd
     ds[0] = 0.0;
 #pragma unroll
     for (int i = 1; i < NF; i++) {
-        const double e = dx_bits(eps[i - 1]) < dx_bits(DX_EPS_FLOOR) ? DX_EPS_FLOOR : eps[i - 1];
+        const double e = dx_bits(eps[i - 1]) < dx_bits(eps_floor) ? eps_floor : eps[i - 1];
         const double sg = __dsqrt_rn(e);
         sig[i] = sg;
         tau[i] = __ddiv_rn(1.0, sg);

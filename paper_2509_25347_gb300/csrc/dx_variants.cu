@@ -287,6 +287,19 @@ extern "C" int drag_expm_apply_opts(int64_t ncells, int32_t nspecies, const doub
         // precision; at 2^-11, theta reaches ~8 and the Taylor sum's cancellation costs up to e^theta FP32 ulps)
         if (opts->method != DRAG_METHOD_TAYLOR || opts->bound_test || opts->ubits != 24 || m_out || s_out)
             return DRAG_EINVAL_OPTION;
+        const int n = nspecies + 1;
+        if (nspecies >= 1 && n <= DX_LPC_NMAX && dx_mode_for(n) != DX_MODE_WPC) {
+            // lane per cell, as the FP64 forward runs these sizes
+            if (ncells < 0 || !(dt >= 0.0) || !std::isfinite(dt)) return DRAG_EINVAL_SIZE;
+            if (ncells == 0) return DRAG_OK;
+            if (!rho_g || !rho_d || !t_s || !v_in || !v_out) return DRAG_ENULL;
+            const void *ptrs[] = {rho_g, rho_d, t_s, v_in, v_out};
+            for (const void *p : ptrs)
+                if (!aligned8(p)) return DRAG_EALIGN;
+            uint32_t *st = dx_status_ptr();
+            if (!st) return DRAG_ECUDA;
+            return dx_launch_forward_lpc_f32(*K, n, ncells, rho_g, rho_d, t_s, v_in, v_out, dt, st, stream);
+        }
         return dx_launch_forward_f32(*K, ncells, nspecies, rho_g, rho_d, t_s, dt, v_in, v_out, stream);
     }
     const DxPade *P = opts->method == DRAG_METHOD_PADE ? dx_pade_for(opts->ubits) : dx_pade_for(53);

@@ -118,3 +118,38 @@ def test_mixed_full_size_sampled(dx):
     got = out[:, :, torch.from_numpy(idx).cuda()].cpu().numpy()
     assert_parity(got, ref, sub.v, tol=TOL)
     assert dx.get_status() == 0
+
+
+@pytest.mark.parametrize("N", [1, 4, 8, 11])
+def test_mixed_both_kernel_families(dx, N):
+    """Up to N = 11 the mixed-precision path runs lane per cell under the
+    default modes (FP32 registers, all s* squarings, one apply) and one warp
+    per cell under the warp-per-cell mode (the last two squarings as four
+    applications); both match the oracle at the 2^-24 target to 64 u32."""
+    cells = W.mrn(333 + N, N, seed=880 + N, stiff_lo=-4.0, stiff_hi=8.0)
+    ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, u=2.0 ** -24)
+    saved = dx.get_mode(N)
+    assert saved != dx.MODE_WARP_PER_CELL
+    assert_parity(mixed(dx, cells, 24), ref, cells.v, tol=TOL)
+    dx.set_mode(N, dx.MODE_WARP_PER_CELL)
+    try:
+        out = mixed(dx, cells, 24)
+    finally:
+        dx.set_mode(N, saved)
+    assert_parity(out, ref, cells.v, tol=TOL)
+    assert dx.get_status() == 0
+
+
+def test_mixed_full_size_lane_per_cell(dx):
+    """The N = 4 workload at full size (2,097,152 cells) through the
+    lane-per-cell mixed-precision kernel: 400 sampled cells against the oracle."""
+    import torch
+    cells = W.workload("mrn_n4_128cube")
+    rg, rd, ts, v = dev(cells)
+    out = dx.apply_opts(rg, rd, ts, cells.dt, v, ubits=24, arith="fp32")
+    idx = np.random.default_rng(31).choice(cells.ncells, 400, replace=False)
+    sub = cells.subset(idx)
+    ref = oracle.drag_apply(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v, u=2.0 ** -24)
+    got = out[:, :, torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert_parity(got, ref, sub.v, tol=TOL)
+    assert dx.get_status() == 0
