@@ -411,7 +411,10 @@ int drag_expm_apply_batched_noalloc(int64_t nblocks, const drag_block_t *blocks,
  * one lane per cell with its matrices in registers (n <= 6), in shared memory
  * (n <= 12), or the current one in registers and the next in shared memory
  * (n = 7..12); or one warp per cell (any n). Defaults: registers up to n = 6,
- * hybrid up to n = 12, warp above.
+ * hybrid up to n = 12, warp above. The mode of n also picks the family of the
+ * batched path (n <= 9), of the adjoint (lane per cell for n <= 6 under any
+ * lane-per-cell mode) and of the mixed-precision path (lane per cell for
+ * n <= 12 likewise); drag_expm_autotune times the forward only.
  */
 #define DRAG_MODE_WARP_PER_CELL 0
 #define DRAG_MODE_LANE_REGISTERS 1
