@@ -336,6 +336,11 @@ int launch(const BwdLpcArgs &a, cudaStream_t stream) {
         }
         // no scratch: the tile-sorted kernel below
     }
+    // the opt-in covers dynamic + static shared memory (the sort keys and order) above 48 KB
+    if (smem + kStatic > 48 * 1024 &&
+        cudaFuncSetAttribute(dx_backward_lpc<NF, TAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return DRAG_ECUDA;
     int rounds = kTile / kThreads;
     while (rounds > 1 && (a.C + rounds * kThreads - 1) / (rounds * kThreads) < 4LL * dx_sm_count()) rounds >>= 1;
     const long long blocks = (a.C + rounds * kThreads - 1) / (rounds * kThreads);
