@@ -326,3 +326,26 @@ def test_lane_per_cell_backward_in_cuda_graph(dx):
     for a, b in zip(ref, out):
         assert torch.equal(a, b)
     assert dx.get_status() == 0
+
+
+def test_lane_per_cell_backward_binned_invalid_cells(dx):
+    """Invalid cells inside a binned lane-per-cell adjoint (270,001 cells):
+    NaN gradients and the status bit there, oracle gradients elsewhere."""
+    import torch
+    C, N = 270001, 4
+    cells = W.mrn(C, N, seed=91, stiff_lo=-4.0, stiff_hi=8.0)
+    bad = [5, 123456, C - 1]
+    cells.t_s[1, bad[0]] = -1.0
+    cells.rho_d[3, bad[1]] = np.nan
+    cells.t_s[0, bad[2]] = 0.0
+    g_np = np.random.default_rng(91).standard_normal(cells.v.shape)
+    out = [x.cpu().numpy() for x in dx.backward(t(cells.rho_g), t(cells.rho_d), t(cells.t_s), cells.dt, t(cells.v),
+                                                 t(g_np))]
+    torch.cuda.synchronize()
+    for x in out:
+        assert np.all(np.isnan(x[..., bad]))
+    assert dx.get_status() & dx.STATUS_BAD_CELL
+    idx = np.setdiff1d(np.unique(np.random.default_rng(5).integers(0, C, 120)), bad)
+    sub = cells.subset(idx)
+    ref = oracle.drag_backward(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v, g_np[:, :, idx])[:4]
+    assert_adjoint_parity(sub, g_np[:, :, idx], [x[..., idx] for x in out], ref)

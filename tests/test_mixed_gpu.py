@@ -153,3 +153,17 @@ def test_mixed_full_size_lane_per_cell(dx):
     got = out[:, :, torch.from_numpy(idx).cuda()].cpu().numpy()
     assert_parity(got, ref, sub.v, tol=TOL)
     assert dx.get_status() == 0
+
+
+@pytest.mark.parametrize("N", [4, 16])
+def test_mixed_extreme_norms(dx, N):
+    """Norms up to 1.5e308 (s* ~ 1023) on the mixed-precision path, lane per
+    cell (N = 4) and warp per cell (N = 16): every cell has relaxed to V_CM and
+    matches the oracle at the 2^-24 target to 64 u32."""
+    from tests.test_forward_gpu import extreme_cells
+    cells = extreme_cells(N, [1e8, 1e14, 1e250, 1e300, 1.5e308])
+    out = mixed(dx, cells, 24)
+    ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, u=2.0 ** -24)
+    assert np.all(np.isfinite(out))
+    assert_parity(out, ref, cells.v, tol=TOL)
+    assert dx.get_status() == 0
