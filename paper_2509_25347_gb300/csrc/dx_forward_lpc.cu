@@ -127,100 +127,7 @@ int launch_store(int store, const DxConsts &K, long long C, const double *rho_g,
     return DRAG_EINVAL_SIZE;
 }
 
-// Mixed-precision lane-per-cell forward: FP64 loads, set-up and Algorithm 2
-// (dx_lpc_setup on the caller's theta table, dust-to-gas ratios floored at
-// 1e-30 so that sigma and 1/sigma stay inside the FP32 range), then the Taylor
-// step, the restorations, all s* squarings and the apply in FP32 registers.
-// The FP32 pipe issues 64x faster than the FP64 one on this part, so the FP64
-// set-up is most of the cost. The apply uses the plain form
-// v_i' = tau_i sum_j E_ij sigma_j v_j (its j = i term is E_ii v_i).
-template <int NF>
-__global__ void __launch_bounds__(128)
-dx_forward_lpc_f32(long long C, const double *rho_g, const double *rho_d, const double *t_s, const double *v_in,
-                   double *v_out, double dt, uint32_t *status, DxConsts K) {
-    constexpr int N = NF - 1;
-    constexpr int NT = DxPacked<NF>::NT;
-    using P = DxPacked<NF>;
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    DxLaneArr<NF, false> sgd, tud, xsd, dsd;
-    double rg, eps[N], alpha[N];
-    int kk, s;
-    unsigned long long fph;
-    if (!dx_lpc_setup<NF>(rho_g + c, rho_d + c, t_s + c, C, dt, K, false, rg, eps, alpha, kk, s, fph, sgd, tud, xsd,
-                          dsd, 1e-30)) {
-#pragma unroll
-        for (int e = 0; e < 3 * NF; e++) v_out[e * C + c] = NAN;
-        atomicOr(status, DRAG_STATUS_BAD_CELL);
-        return;
-    }
-    DxLaneArr<NF, false, float> sig, tau, xs, ds;
-#pragma unroll
-    for (int i = 0; i < NF; i++) {
-        sig[i] = (float)sgd[i];
-        tau[i] = (float)tud[i];
-        xs[i] = (float)xsd[i];
-        ds[i] = (float)dsd[i];
-    }
-    const int m = K.mk[kk];
-    DxLaneArr<NT, false, float> Fm, Gm;
-    dx_lpc_taylor_init<NF>(Fm, xs, ds, K.b[m], K.b[m - 1]);
-    for (int j = m - 2; j >= 0; j--) {
-        dx_lpc_horner_step<NF>(Fm, Gm, xs, ds, K.b[j]);
-        dx_lane_take(Fm, Gm);
-    }
-    dx_lpc_restore<NF>(Fm, sig, tau);
-    for (int it = 0; it < s; it++) {
-        dx_lpc_square_offdiag<NF>(Fm, Gm);
-        dx_lpc_restore<NF>(Gm, sig, tau);
-        dx_lane_take(Fm, Gm);
-    }
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        float y[NF];
-#pragma unroll
-        for (int f = 0; f < NF; f++) y[f] = sig[f] * (float)v_in[(d * NF + f) * C + c];
-#pragma unroll
-        for (int i = 0; i < NF; i++) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int k = 0; k < NF; k++) acc = fmaf(Fm[P::at(i, k)], y[k], acc);
-            v_out[(d * NF + i) * C + c] = (double)(tau[i] * acc);
-        }
-    }
-}
-
-template <int NF>
-int launch_f32(const DxConsts &K, long long C, const double *rho_g, const double *rho_d, const double *t_s,
-               const double *v_in, double *v_out, double dt, uint32_t *status, cudaStream_t stream) {
-    const long long blocks = (C + 127) / 128;
-    dx_forward_lpc_f32<NF><<<(unsigned)blocks, 128, 0, stream>>>(C, rho_g, rho_d, t_s, v_in, v_out, dt, status, K);
-    return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
-}
-
 }  // namespace
-
-int dx_launch_forward_lpc_f32(const DxConsts &K, int n, long long C, const double *rho_g, const double *rho_d,
-                              const double *t_s, const double *v_in, double *v_out, double dt, uint32_t *status,
-                              cudaStream_t stream) {
-    switch (n) {
-#define DX_CASE(NF) \
-    case NF: return launch_f32<NF>(K, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, stream);
-        DX_CASE(2)
-        DX_CASE(3)
-        DX_CASE(4)
-        DX_CASE(5)
-        DX_CASE(6)
-        DX_CASE(7)
-        DX_CASE(8)
-        DX_CASE(9)
-        DX_CASE(10)
-        DX_CASE(11)
-        DX_CASE(12)
-#undef DX_CASE
-        default: return DRAG_EINVAL_SIZE;
-    }
-}
 
 int dx_launch_forward_lpc(const DxConsts &K, int n, int store, long long C, const double *rho_g,
                           const double *rho_d, const double *t_s, const double *v_in, double *v_out, double dt,

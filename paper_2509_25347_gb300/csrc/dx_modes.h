@@ -33,8 +33,9 @@ int dx_launch_forward_lpc(const DxConsts &K, int n, int store, long long C, cons
                           const double *rho_d, const double *t_s, const double *v_in, double *v_out, double dt,
                           uint32_t *status, double *heat, cudaStream_t stream);
 
-// Mixed-precision (FP32 matrix work) lane-per-cell forward for n <= DX_LPC_NMAX
+// Mixed-precision (FP32 matrix work) lane-per-cell forward for n <= DX_LPC_F32_NMAX
 // (dx_forward_lpc.cu); arguments already checked by the caller.
+#define DX_LPC_F32_NMAX 17
 int dx_launch_forward_lpc_f32(const DxConsts &K, int n, long long C, const double *rho_g, const double *rho_d,
                               const double *t_s, const double *v_in, double *v_out, double dt, uint32_t *status,
                               cudaStream_t stream);

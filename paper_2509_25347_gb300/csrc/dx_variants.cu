@@ -288,8 +288,10 @@ extern "C" int drag_expm_apply_opts(int64_t ncells, int32_t nspecies, const doub
         if (opts->method != DRAG_METHOD_TAYLOR || opts->bound_test || opts->ubits != 24 || m_out || s_out)
             return DRAG_EINVAL_OPTION;
         const int n = nspecies + 1;
-        if (nspecies >= 1 && n <= DX_LPC_NMAX && dx_mode_for(n) != DX_MODE_WPC) {
-            // lane per cell, as the FP64 forward runs these sizes
+        if (nspecies >= 1 && ((n <= DX_LPC_NMAX && dx_mode_for(n) != DX_MODE_WPC) ||
+                              (n > DX_LPC_NMAX && n <= DX_LPC_F32_NMAX))) {
+            // lane per cell: as the FP64 forward runs these sizes up to n = 12, and up to n = 17
+            // whatever the mode (FP32 work in registers beats the warp-per-cell rounds there)
             if (ncells < 0 || !(dt >= 0.0) || !std::isfinite(dt)) return DRAG_EINVAL_SIZE;
             if (ncells == 0) return DRAG_OK;
             if (!rho_g || !rho_d || !t_s || !v_in || !v_out) return DRAG_ENULL;

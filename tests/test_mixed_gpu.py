@@ -140,6 +140,18 @@ def test_mixed_both_kernel_families(dx, N):
     assert dx.get_status() == 0
 
 
+def test_mixed_sizes_past_the_fp64_lane_range(dx):
+    """n = 13..17 run lane per cell on the mixed-precision path whatever the
+    mode (F in FP32 registers, G in shared memory, tile-sorted), also under the
+    warp-per-cell mode; ragged counts spanning several tiles."""
+    for N in (12, 14, 16):
+        cells = W.mrn(1111 + N, N, seed=890 + N, stiff_lo=-4.0, stiff_hi=8.0)
+        ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, u=2.0 ** -24)
+        assert dx.get_mode(N) == dx.MODE_WARP_PER_CELL
+        assert_parity(mixed(dx, cells, 24), ref, cells.v, tol=TOL)
+    assert dx.get_status() == 0
+
+
 def test_mixed_full_size_lane_per_cell(dx):
     """The N = 4 workload at full size (2,097,152 cells) through the
     lane-per-cell mixed-precision kernel: 400 sampled cells against the oracle."""
@@ -155,11 +167,12 @@ def test_mixed_full_size_lane_per_cell(dx):
     assert dx.get_status() == 0
 
 
-@pytest.mark.parametrize("N", [4, 16])
+@pytest.mark.parametrize("N", [4, 16, 24])
 def test_mixed_extreme_norms(dx, N):
     """Norms up to 1.5e308 (s* ~ 1023) on the mixed-precision path, lane per
-    cell (N = 4) and warp per cell (N = 16): every cell has relaxed to V_CM and
-    matches the oracle at the 2^-24 target to 64 u32."""
+    cell in registers (N = 4) and hybrid (N = 16), and warp per cell (N = 24):
+    every cell has relaxed to V_CM and matches the oracle at the 2^-24 target
+    to 64 u32."""
     from tests.test_forward_gpu import extreme_cells
     cells = extreme_cells(N, [1e8, 1e14, 1e250, 1e300, 1.5e308])
     out = mixed(dx, cells, 24)
