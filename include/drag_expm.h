@@ -157,7 +157,8 @@ typedef struct {
  *   s_out : DEVICE int16[ncells] or NULL, receives s* (-1 for invalid cells).
  * The bound-test and Pade variants run one warp per cell whatever the mode
  * table says; the mixed-precision path runs one lane per cell for N <= 11 under
- * a lane-per-cell mode (the default there), one warp per cell otherwise.
+ * a lane-per-cell mode (the default there) and for N = 12..16 always, one warp
+ * per cell otherwise.
  * Returns DRAG_ENULL (opts NULL), DRAG_EINVAL_OPTION, DRAG_EINVAL_TARGET, or as
  * drag_expm_apply.
  */
@@ -414,7 +415,8 @@ int drag_expm_apply_batched_noalloc(int64_t nblocks, const drag_block_t *blocks,
  * hybrid up to n = 12, warp above. The mode of n also picks the family of the
  * batched path (n <= 9), of the adjoint (lane per cell for n <= 6 under any
  * lane-per-cell mode) and of the mixed-precision path (lane per cell for
- * n <= 12 likewise); drag_expm_autotune times the forward only.
+ * n <= 12 likewise, and for n = 13..17 always); drag_expm_autotune times the
+ * forward only.
  */
 #define DRAG_MODE_WARP_PER_CELL 0
 #define DRAG_MODE_LANE_REGISTERS 1
