@@ -361,14 +361,15 @@ size_t drag_expm_batched_workspace_bytes(int64_t nblocks, int64_t total_cells);
  *   total_cells, rho_d_len, v_len : lengths (in doubles) of rho_g, of rho_d
  *                 and t_s, and of v_in/v_out; blocks outside them are skipped
  *                 and set DRAG_STATUS_BAD_BLOCK, as are blocks with bad N or dt.
- *   nspecies_max: upper bound on the blocks' N (sizes the shared memory).
+ *   nspecies_max: upper bound on the blocks' N (sizes the shared memory); a
+ *                 block with N > nspecies_max is skipped (its v_out slice is
+ *                 left untouched) and sets DRAG_STATUS_BAD_BLOCK.
  *   rho_g, rho_d, t_s, v_in : DEVICE inputs; v_out : DEVICE output (may equal v_in).
  *   workspace   : DEVICE scratch of at least drag_expm_batched_workspace_bytes()
  *                 bytes, 256-byte aligned, caller-owned; contents are
  *                 overwritten. Must not be shared by calls in flight at once.
  * All work is queued on `stream` with no host synchronisation and no
- * allocation, so the call can be captured in a CUDA graph. Blocks with N
- * above nspecies_max are processed with too little shared memory: don't.
+ * allocation, so the call can be captured in a CUDA graph.
  * Returns DRAG_OK or DRAG_EBLOCKS / DRAG_EINVAL_SIZE / DRAG_ENULL /
  * DRAG_EALIGN / DRAG_EWORKSPACE / DRAG_ECUDA (nothing launched on error).
  */
@@ -393,8 +394,11 @@ int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *blocks, int64_t
  *   DRAG_NOALLOC_MAX_CELLS; larger batches return DRAG_ENOALLOC_LIMIT and
  *   launch nothing. All other arguments and errors are those of
  *   drag_expm_apply_batched.
- *   The first call on each device looks up the array's device address (with
- *   that device current); make that first call before any stream capture.
+ *   A call looks up the array's device address on the current device
+ *   (cudaGetSymbolAddress, which allocates nothing) whenever `stream` is not
+ *   capturing, so the address follows a device reset; a call made while
+ *   `stream` captures reuses the address of the last call on that device, so
+ *   make one call on each device before any stream capture.
  *   Calls share the array: each call clears what must start at zero, but two
  *   calls whose work overlaps on the GPU race on it, so order them (same
  *   stream, or an event between streams).

@@ -170,3 +170,26 @@ def drag_truth_grad_cell(rho_g, rho_d, t_s, dt, v, g, dps: int = 50, rel_h: floa
     P = propagator_truth(rho_g, rho_d, t_s, dt, dps=dps)
     gv = np.einsum("ji,dj->di", P, np.asarray(g, dtype=np.float64))
     return gv, float(g_rg), np.array([float(x) for x in g_rd]), np.array([float(x) for x in g_ts])
+
+
+def collisions_exact(rho_g, rho_d, t_s, v0, times) -> np.ndarray:
+    """Exact velocities of the Collisions tests (Sec. 3.1, Eq. V_analytic:
+    V(t) = V_CM + sum_j c_j exp(lambda_j t)) for every time (rows) and fluid
+    (columns, gas first), from the eigenpairs of the symmetric form
+    S = D^(1/2) Omega_v D^(-1/2) of the drag matrix (Eq. eigen_problem), in FP64
+    through numpy's symmetric eigensolver. rho_d, t_s: the N species; v0: the
+    N+1 initial velocities. Pinned by Table 1's printed modes."""
+    rho_d = np.asarray(rho_d, dtype=np.float64)
+    t_s = np.asarray(t_s, dtype=np.float64)
+    eps = rho_d / float(rho_g)
+    alpha = 1.0 / t_s
+    n = eps.size + 1
+    sig = np.concatenate([[1.0], np.sqrt(eps)])
+    S = np.zeros((n, n))
+    S[0, 0] = -np.sum(eps * alpha)
+    S[0, 1:] = S[1:, 0] = sig[1:] * alpha
+    S[1:, 1:] = np.diag(-alpha)
+    lam, Q = np.linalg.eigh(S)
+    y0 = Q.T @ (sig * np.asarray(v0, dtype=np.float64))
+    out = np.exp(np.outer(np.asarray(times, dtype=np.float64), lam)) * y0[None, :] @ Q.T
+    return out / sig[None, :]

@@ -67,8 +67,12 @@ __device__ __forceinline__ int bin_of(int n, int k, int s) {
     return ((n - 2) * DX_K + (k - 1)) * kSBins + (s < kSBins - 1 ? s : kSBins - 1);
 }
 
-__device__ __forceinline__ bool desc_valid(const Desc &d, long long total_cells, long long rho_d_len, long long v_len) {
-    if (d.ncells < 0 || d.nspecies < 1 || d.nspecies > DRAG_EXPM_NMAX) return false;
+// A block is run only if its record is in range. N above nspecies_max is
+// rejected too: the main kernels' per-warp shared-memory slices are sized for
+// matrices up to nspecies_max + 1.
+__device__ __forceinline__ bool desc_valid(const Desc &d, int nspecies_max, long long total_cells, long long rho_d_len,
+                                           long long v_len) {
+    if (d.ncells < 0 || d.nspecies < 1 || d.nspecies > nspecies_max || d.nspecies > DRAG_EXPM_NMAX) return false;
     const long long b = __double_as_longlong(d.dt);
     if (!((b & 0x7fffffffffffffffLL) == 0 || (b > 0 && b < 0x7ff0000000000000LL))) return false;   // dt >= 0 finite
     const long long C = d.ncells, N = d.nspecies;
@@ -97,8 +101,8 @@ __device__ T block_exclusive_scan(T v, T *sh, T &total) {
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-dx_batch_prepare(long long nblocks, const Desc *blocks, long long total_cells, long long rho_d_len, long long v_len,
-                 Work W, uint32_t *status) {
+dx_batch_prepare(long long nblocks, const Desc *blocks, int nspecies_max, long long total_cells, long long rho_d_len,
+                 long long v_len, Work W, uint32_t *status) {
     __shared__ long long sh[kScanThreads];
     const int t = threadIdx.x;
     for (int i = t; i < kNBins; i += kScanThreads) W.hist[i] = 0;
@@ -109,7 +113,7 @@ dx_batch_prepare(long long nblocks, const Desc *blocks, long long total_cells, l
     bool bad = false;
     for (long long b = b0; b < b1; b++) {
         const Desc d = blocks[b];
-        const bool ok = desc_valid(d, total_cells, rho_d_len, v_len);
+        const bool ok = desc_valid(d, nspecies_max, total_cells, rho_d_len, v_len);
         bad |= !ok;
         sum += ok ? d.ncells : 0;
     }
@@ -118,7 +122,7 @@ dx_batch_prepare(long long nblocks, const Desc *blocks, long long total_cells, l
     for (long long b = b0; b < b1; b++) {
         W.blk_start[b] = run;
         const Desc d = blocks[b];
-        run += desc_valid(d, total_cells, rho_d_len, v_len) ? d.ncells : 0;
+        run += desc_valid(d, nspecies_max, total_cells, rho_d_len, v_len) ? d.ncells : 0;
     }
     if (t == 0) {
         W.blk_start[nblocks] = total;
@@ -439,13 +443,13 @@ Work work_at(char *ws, const Layout &L) {
 
 // The binning stages of the pipeline: block offsets, (k*, s*) of every cell,
 // bin offsets and item tables, then the bin-sorted permutation W.perm.
-void launch_binning(const DxConsts &K, long long nblocks, const Desc *D, long long total_cells, long long rho_d_len,
-                    long long v_len, const double *rho_g, const double *rho_d, const double *t_s, const Work &W,
+void launch_binning(const DxConsts &K, long long nblocks, const Desc *D, int nspecies_max, long long total_cells,
+                    long long rho_d_len, long long v_len, const double *rho_g, const double *rho_d, const double *t_s, const Work &W,
                     const Modes &M, uint32_t *st, cudaStream_t stream) {
     const int sms = dx_sm_count();
     const long long cgrid_want = (total_cells + 255) / 256;
     const int cgrid = (int)(cgrid_want < (long long)sms * 16 ? cgrid_want : (long long)sms * 16);
-    dx_batch_prepare<<<1, kScanThreads, 0, stream>>>(nblocks, D, total_cells, rho_d_len, v_len, W, st);
+    dx_batch_prepare<<<1, kScanThreads, 0, stream>>>(nblocks, D, nspecies_max, total_cells, rho_d_len, v_len, W, st);
     dx_batch_count<<<cgrid, 256, 0, stream>>>(nblocks, D, rho_g, rho_d, t_s, W, K);
     dx_batch_bins<<<1, kScanThreads, 0, stream>>>(W, M);
     dx_batch_scatter<<<cgrid, 256, 0, stream>>>(nblocks, W);
@@ -461,7 +465,7 @@ static int batched_run(const DxConsts &K, long long nblocks, const Desc *D, long
     const Work W = work_at(ws, L);
     const Modes M = dx_batch_modes();
     const int sms = dx_sm_count();
-    launch_binning(K, nblocks, D, total_cells, rho_d_len, v_len, rho_g, rho_d, t_s, W, M, st, stream);
+    launch_binning(K, nblocks, D, nspecies_max, total_cells, rho_d_len, v_len, rho_g, rho_d, t_s, W, M, st, stream);
 
     int wd_wpc = 0, wd_lpc = 0;
     bool has_wpc = false, has_lpc = false;
@@ -536,8 +540,9 @@ extern "C" int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *bloc
 //
 // The array lives in device global memory of every GPU that loads the library
 // and stays there until the process exits. In host code its name only stands
-// in for it, so its device address is looked up once per device (first call on
-// that device, with that device current) and passed to the kernels. Every call
+// in for it, so its device address is looked up on the current device (every
+// call outside stream capture; a capture reuses the last address) and passed
+// to the kernels. Every call
 // uses the same array: the first kernel of the pipeline clears the histogram
 // and the counters, and every other part is written before it is read, so no
 // stale contents leak from one call to the next; but two calls whose work
@@ -569,10 +574,14 @@ extern "C" int drag_expm_apply_batched_noalloc(int64_t nblocks, const drag_block
         return DRAG_ENOALLOC_LIMIT;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DRAG_ECUDA;
+    // The address is taken again outside stream capture, so that it follows a
+    // new context after a device reset; a capture reuses the last one.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return DRAG_ECUDA;
     void *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
+        if (!g_noalloc_addr[dev] || cap == cudaStreamCaptureStatusNone) {
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DRAG_ECUDA;
             g_noalloc_addr[dev] = p;
@@ -679,7 +688,7 @@ void *dx_binned_perm(const DxConsts &K, long long C, int N, const double *rho_g,
     Desc *D = reinterpret_cast<Desc *>(ws + L.total);
     const Work W = work_at(ws, L);
     dx_batch_single_desc<<<1, 1, 0, stream>>>(D, C, N, dt);
-    launch_binning(K, 1, D, C, (long long)N * C, 3LL * (N + 1) * C, rho_g, rho_d, t_s, W, dx_batch_modes(), status,
+    launch_binning(K, 1, D, N, C, (long long)N * C, 3LL * (N + 1) * C, rho_g, rho_d, t_s, W, dx_batch_modes(), status,
                    stream);
     if (cudaGetLastError() != cudaSuccess) {
         cudaFreeAsync(p, stream);

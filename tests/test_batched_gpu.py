@@ -164,6 +164,30 @@ def test_batched_bad_blocks_and_cells(dx):
     assert np.all(np.isnan(o[:, :, 0])) and np.all(np.isfinite(o[:, :, 1:]))
 
 
+@pytest.mark.parametrize("nmax", [8, 15])
+def test_batched_rejects_blocks_above_nspecies_max(dx, nmax):
+    """A block whose N exceeds the nspecies_max argument (which sizes the main
+    kernels' shared memory) is a bad block: it sets DRAG_STATUS_BAD_BLOCK and
+    its v_out slice is left untouched; every other block matches the oracle.
+    nmax = 8: the N = 9 blocks are one species over (n = 10 would run lane per
+    cell); nmax = 15: the warp-per-cell sizes N = 16, 20, 31 are over."""
+    batch = mixed_batch(seed=5)
+    desc, rg, rd, ts, v = batch.pack()
+    over = [b for b in range(len(desc)) if desc[b]["nspecies"] > nmax and desc[b]["ncells"] > 0]
+    assert any(desc[b]["nspecies"] == nmax + 1 for b in over)
+    sentinel = np.full_like(v, 7.0)
+    dx.get_status()
+    out = dx.apply_batched(desc, t(rg), t(rd), t(ts), t(v), t(sentinel), nspecies_max=nmax).cpu().numpy()
+    assert dx.get_status() & dx.STATUS_BAD_BLOCK
+    ok = np.array([b not in over for b in range(len(desc))])
+    ref, st = oracle.drag_apply_batched(desc[ok], rg, rd, ts, v)
+    assert st == 0
+    for b in over:
+        N, C, vo = int(desc[b]["nspecies"]), int(desc[b]["ncells"]), int(desc[b]["vel_offset"])
+        assert np.all(out[vo:vo + 3 * (N + 1) * C] == 7.0), (b, N)
+    assert_block_parity(desc[ok], v, out, ref)
+
+
 def test_batched_workspace_and_argument_errors(dx):
     import torch
     batch = mixed_batch(seed=4)
