@@ -469,6 +469,41 @@ int drag_expm_theta_target(int32_t k, int32_t ubits, double *theta_out);
  */
 int drag_expm_pade_theta(int32_t m, int32_t ubits, double *theta_out);
 
+/*
+ * Measurement probes. Not part of the drag update: they measure the resource
+ * that bounds it, the FP64 rate of the GPU (App. B, "Numerical cost", counts
+ * the update's work as n x n matrix products), for the roofline's peak and for
+ * the choice between the FP64 pipe and the FP64 tensor cores.
+ *
+ * drag_expm_probe_fp64_rate — one launch of independent FP64 operation chains,
+ * one full wave (4 blocks of 256 threads per SM), `iters` steps per chain.
+ *   kind 0: DFMA (fma.rn.f64, the FP64 pipe); kind 1: DMMA (mma.sync
+ *   m8n8k4 f64, the tensor cores).
+ *   sink     : DEVICE, 1 double; written only by a result that never occurs.
+ *   flop_out : HOST, receives the launch's FP64 FLOPs (an FMA is 2).
+ * Time the launch with CUDA events on `stream`. Returns DRAG_OK, or
+ * DRAG_EINVAL_SIZE (kind, iters outside 1..2^40) / DRAG_ENULL / DRAG_ECUDA.
+ */
+int drag_expm_probe_fp64_rate(int32_t kind, int64_t iters, double *sink, double *flop_out, cudaStream_t stream);
+
+/*
+ * drag_expm_probe_square — `reps` squarings, each followed by the row-sum
+ * restoration E_ii = 1 - (1/sigma_i) sum_{k != i} E_ik sigma_k, of nmat
+ * symmetric n x n matrices (the similarity form of the propagator, Eq. ExpEq1
+ * with the restoration of the structured method), one warp per matrix.
+ *   kind 0: the forward kernels' own routine (upper-triangle dot products and
+ *           restorations on the FP64 pipe, build-time round schedule);
+ *   kind 1: the products as 8x8x4 DMMA tiles (E padded to a multiple of 8,
+ *           tiles on and above the diagonal), the restorations on the FP64 pipe.
+ *   E_in  : DEVICE, nmat x n x n doubles, row major (read only).
+ *   sig   : DEVICE, nmat x n doubles, sigma > 0 (read only).
+ *   E_out : DEVICE, nmat x n x n doubles, the result (must not alias E_in).
+ * n in 2..32, reps in 0..4096. Returns DRAG_OK or DRAG_EINVAL_SIZE /
+ * DRAG_ENULL / DRAG_EALIGN / DRAG_ECUDA.
+ */
+int drag_expm_probe_square(int32_t kind, int32_t n, int64_t nmat, int32_t reps, const double *E_in,
+                           const double *sig, double *E_out, cudaStream_t stream);
+
 /* drag_expm_strerror — static text for a DRAG_E* code. */
 const char *drag_expm_strerror(int code);
 

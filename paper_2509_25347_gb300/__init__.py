@@ -17,7 +17,7 @@ __all__ = [
     "load_library", "apply", "apply_heat", "backward", "rk1_apply", "apply_batched", "batched_workspace_bytes",
     "select", "get_status", "theta", "DragExpm", "DragExpmError", "apply_opts", "pade_theta", "apply_host",
     "host_workspace_bytes", "apply_launches", "apply_taped", "Tape", "tape_bytes", "tape_levels", "tape_levels_needed",
-    "DragExpmTaped", "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"
+    "DragExpmTaped", "probe_fp64_rate", "probe_square", "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -96,6 +96,10 @@ def load_library(path: str | None = None):
                                              ctypes.c_size_t, vp]
     lib.drag_expm_apply_launches.restype = ctypes.c_int32
     lib.drag_expm_apply_launches.argtypes = [i64, i32]
+    lib.drag_expm_probe_fp64_rate.restype = ctypes.c_int
+    lib.drag_expm_probe_fp64_rate.argtypes = [i32, i64, vp, ctypes.POINTER(ctypes.c_double), vp]
+    lib.drag_expm_probe_square.restype = ctypes.c_int
+    lib.drag_expm_probe_square.argtypes = [i32, i32, i64, i32, vp, vp, vp, vp]
     lib.drag_expm_strerror.restype = ctypes.c_char_p
     lib.drag_expm_strerror.argtypes = [ctypes.c_int]
     lib.drag_expm_version.restype = ctypes.c_int
@@ -555,6 +559,40 @@ def autotune(nspecies_max: int, cache_path: str | None = None, stream=None) -> d
     p = cache_path.encode() if cache_path else None
     _check(load_library().drag_expm_autotune(int(nspecies_max), p, _stream_handle(stream)))
     return {N: get_mode(N) for N in range(1, int(nspecies_max) + 1)}
+
+
+def probe_fp64_rate(kind: str = "dfma", iters: int = 20000, sink=None, stream=None) -> float:
+    """Launch the FP64 throughput probe (kind "dfma": the FP64 pipe; "dmma":
+    the FP64 tensor cores) on the stream; returns the launch's FP64 FLOPs.
+    Time it with CUDA events around the call."""
+    import torch
+    if sink is None:
+        sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _on_current_device("sink", sink)
+    flop = ctypes.c_double(0.0)
+    _check(load_library().drag_expm_probe_fp64_rate({"dfma": 0, "dmma": 1}[kind], int(iters),
+                                                    ctypes.c_void_p(sink.data_ptr()), ctypes.byref(flop),
+                                                    _stream_handle(stream)))
+    return flop.value
+
+
+def probe_square(E, sig, reps: int, kind: str = "dfma", out=None, stream=None):
+    """`reps` restored squarings of each symmetric matrix E[m] (float64 CUDA,
+    (nmat, n, n)) with sigma sig[m] ((nmat, n)): kind "dfma" is the forward
+    kernels' routine, "dmma" the FP64 tensor-core tiles. Returns the result."""
+    import torch
+    if E.dim() != 3 or E.shape[1] != E.shape[2] or sig.shape != E.shape[:2]:
+        raise DragExpmError("E must be (nmat, n, n) and sig (nmat, n)")
+    for nm, x in (("E", E), ("sig", sig)):
+        if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+            raise DragExpmError(f"{nm} must be a contiguous float64 CUDA tensor")
+        _on_current_device(nm, x)
+    if out is None:
+        out = torch.empty_like(E)
+    _check(load_library().drag_expm_probe_square({"dfma": 0, "dmma": 1}[kind], E.shape[1], E.shape[0], int(reps),
+                                                 ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(sig.data_ptr()),
+                                                 ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out
 
 
 def get_status(stream=None) -> int:

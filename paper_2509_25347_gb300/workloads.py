@@ -105,9 +105,16 @@ WORKLOADS = {
 }
 
 
-def workload(name: str, ncells: int | None = None) -> Cells:
-    """Cells of one plain (single-N) workload; ``ncells`` truncates the draw size."""
+def replica_seed(seed: int, replica: int) -> int:
+    """Seed of an independent copy of a workload (replica 0 is the workload itself)."""
+    return seed if replica == 0 else seed + 1_000_003 * replica
+
+
+def workload(name: str, ncells: int | None = None, replica: int = 0) -> Cells:
+    """Cells of one plain (single-N) workload; ``ncells`` truncates the draw size;
+    ``replica`` > 0 draws an independent copy with the same recipe."""
     desc, C, N, seed = WORKLOADS[name]
+    seed = replica_seed(seed, replica)
     C = C if ncells is None else int(ncells)
     if name == "dustybox_n1_32k":
         return dustybox(C, seed=seed)
