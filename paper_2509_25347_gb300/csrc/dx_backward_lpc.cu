@@ -11,11 +11,24 @@
 // column 0 and the diagonal of the last L (Eqs. DragEqVar2/3, jacobian).
 //
 // Here one lane owns one cell and runs all of it serially, so every FP64
-// instruction of a warp works on 32 cells; at n <= 6 a warp-per-cell round keeps
-// only a fraction of its lanes busy (n(n-1)/2 upper-triangle entries, n-term
-// reductions through shuffles). E is formed with the lane-per-cell forward's
-// own steps (dx_lpc.cuh), so the taped variant, which reads E_0 .. E_{s-2} from
-// the forward's tape instead, gives bit-identical gradients.
+// instruction of a warp works on 32 cells, where a warp-per-cell round keeps
+// only part of its lanes busy (n(n-1)/2 upper-triangle entries, n-term
+// reductions through shuffles, set-up and Taylor phases on n lanes). E is
+// formed with the lane-per-cell forward's own steps (dx_lpc.cuh), so the taped
+// variant, which reads E_0 .. E_{s-2} from the forward's tape instead, gives
+// bit-identical gradients.
+//
+// Storage. Up to n = 6 E and L live in registers, double-buffered. For
+// n = 7..9 (the hybrid storage) the per-lane state no longer fits: L (n^2
+// doubles) stays in registers, E in shared memory, and the squaring's new L
+// goes to shared memory before it is copied back (it needs all of the old L).
+// E^2 forms in registers once the old L is dead, and the Horner chain of F
+// before the derivative chain starts (the latter carries y_d = F a_d by its
+// own recurrence). The Taylor derivative updates L in place (its row i needs
+// only the old row i), so the n^2 slice of the new L can share its shared
+// memory with the Taylor phase's vectors a_d, b_d, y_d (9n >= n^2 for n <= 9);
+// a_d is formed again for the outputs, and eps, alpha are divided again
+// there (the same roundings) instead of holding registers through the cell.
 #include <cmath>
 
 #include "dx_lpc.cuh"
@@ -23,8 +36,13 @@
 
 namespace {
 
-constexpr int kThreads = 64;   // 2 warps per block: shared memory per warp sets the residency
-constexpr int kTile = 512;     // largest tile of cells a block sorts
+// Threads per block: 2 warps, or one for the hybrid storage, whose 39-55 KB of
+// shared memory per warp would otherwise strand part of an SM; and the largest
+// tile of cells a block sorts.
+template <int NF>
+__host__ __device__ constexpr int bwd_threads() { return NF >= 7 ? 32 : 64; }
+template <int NF>
+__host__ __device__ constexpr int bwd_tile() { return NF >= 7 ? 128 : 512; }
 
 struct BwdLpcArgs {
     long long C;
@@ -39,12 +57,19 @@ struct BwdLpcArgs {
 
 // Storage per n: E (packed, double-buffered) and L (full, double-buffered) in
 // registers; the n-vectors (sigma, tau, X_0f, X_ff, a_d, -kappa sigma, b_d, y_d:
-// 14 n doubles) in registers up to n = 3 and in shared memory above.
+// 14 n doubles) in registers up to n = 3 and in shared memory above. Hybrid
+// (n >= 7): L in registers, E and the squaring's new L in shared memory, the
+// latter over the slices of a_d, b_d, y_d; the Horner chain and E^2 form in
+// registers while L is not live (171 doubles of shared memory per lane at
+// n = 9: five warps per SM).
 template <int NF>
 struct BwdLpcStore {
     static constexpr bool kVecShared = NF >= 4;
+    static constexpr bool kHybrid = NF >= 7;
     static constexpr int kVec = 14 * NF;
-    static constexpr int kWarpDoubles = kVecShared ? 32 * kVec : 0;
+    static constexpr int kNT = NF * (NF + 1) / 2;
+    static constexpr int kWarpDoubles = (kVecShared ? 32 * kVec : 0) + (kHybrid ? 32 * kNT : 0);
+    static_assert(!kHybrid || NF * NF <= 9 * NF, "the new L overlays a_d, b_d, y_d");
 };
 
 template <int NF>
@@ -60,12 +85,112 @@ __device__ __forceinline__ void bwd_lpc_fail(long long c, const BwdLpcArgs &a) {
     atomicOr(a.status, DRAG_STATUS_BAD_CELL);
 }
 
+// dF = b_m H for the rank-4 direction H = sum_d a_d b_d^T + a_3 sigma^T.
+template <int NF, class LA, class VA, class WA>
+__device__ __forceinline__ void bwd_lpc_dinit(LA &L, WA &av, WA &bv, VA &a3, VA &sig, double bm) {
+#pragma unroll
+    for (int i = 0; i < NF; i++) {
+#pragma unroll
+        for (int j = 0; j < NF; j++) {
+            double acc = av[i] * bv[j];
+            acc = fma(av[NF + i], bv[NF + j], acc);
+            acc = fma(av[2 * NF + i], bv[2 * NF + j], acc);
+            acc = fma(a3[i], sig[j], acc);
+            L[i * NF + j] = bm * acc;
+        }
+    }
+}
+
+// y_d = F a_d for F = b_m X + b_{m-1} I.
+template <int NF, class VA, class WA>
+__device__ __forceinline__ void bwd_lpc_yinit(WA &yv, VA &xs, VA &ds, WA &av, double bm, double bm1) {
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < NF; k++) acc = fma(xs[k], av[d * NF + k], acc);
+        yv[d * NF] = fma(bm, acc, bm1 * av[d * NF]);
+#pragma unroll
+        for (int f = 1; f < NF; f++)
+            yv[d * NF + f] = fma(bm, fma(xs[f], av[d * NF], ds[f] * av[d * NF + f]), bm1 * av[d * NF + f]);
+    }
+}
+
+// Row i of dF' = dF X + F H, with F H = sum_d y_d b_d^T + b_{j+1} a_3 sigma^T
+// (X the arrowhead): column 0 is a dot product over the row, the other
+// entries take two FMAs of dF X each. Reads row i of Lsrc before writing row
+// i of Ldst, so Lsrc and Ldst may be the same array.
+template <int NF, class LS, class LD, class VA, class WA>
+__device__ __forceinline__ void bwd_lpc_drow(LS &Lsrc, LD &Ldst, int i, WA &yv, WA &bv, VA &a3, VA &sig, VA &xs,
+                                             VA &ds, double bj1) {
+    double r[NF];
+#pragma unroll
+    for (int k = 0; k < NF; k++) r[k] = Lsrc[i * NF + k];
+    const double y0 = yv[i], y1 = yv[NF + i], y2 = yv[2 * NF + i], w = bj1 * a3[i];
+    double acc = y0 * bv[0];
+    acc = fma(y1, bv[NF], acc);
+    acc = fma(y2, bv[2 * NF], acc);
+    acc = fma(w, sig[0], acc);
+#pragma unroll
+    for (int k = 0; k < NF; k++) acc = fma(r[k], xs[k], acc);
+#pragma unroll
+    for (int j = 1; j < NF; j++) {
+        double t = y0 * bv[j];
+        t = fma(y1, bv[NF + j], t);
+        t = fma(y2, bv[2 * NF + j], t);
+        t = fma(w, sig[j], t);
+        t = fma(r[0], xs[j], t);
+        Ldst[i * NF + j] = fma(r[j], ds[j], t);
+    }
+    Ldst[i * NF] = acc;
+}
+
+// y_d <- X y_d + b_j a_d.
+template <int NF, class VA, class WA>
+__device__ __forceinline__ void bwd_lpc_ystep(WA &yv, VA &xs, VA &ds, WA &av, double bj) {
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const double y0 = yv[d * NF];
+        double acc = bj * av[d * NF];
+#pragma unroll
+        for (int k = 0; k < NF; k++) acc = fma(xs[k], yv[d * NF + k], acc);
+#pragma unroll
+        for (int f = 1; f < NF; f++)
+            yv[d * NF + f] = fma(xs[f], y0, fma(ds[f], yv[d * NF + f], bj * av[d * NF + f]));
+        yv[d * NF] = acc;
+    }
+}
+
+// L' = E L + L E (E symmetric, packed; L full), each entry's two sums in
+// ascending k. TRIM forms only row 0, column 0 and the diagonal (all the
+// gradients read, in the last squaring). The entries are chosen at compile
+// time, so the whole product is one straight block whose independent entries
+// the compiler interleaves.
+template <int NF, bool TRIM, class FA, class LA, class NA>
+__device__ __forceinline__ void bwd_lpc_el_le(FA &Fm, LA &Lm, NA &Ln) {
+    using P = DxPacked<NF>;
+#pragma unroll
+    for (int i = 0; i < NF; i++) {
+#pragma unroll
+        for (int j = 0; j < NF; j++) {
+            if (TRIM && i != 0 && j != 0 && i != j) continue;
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < NF; k++) acc = fma(dx_lane_ld(Fm, P::at(i, k)), Lm[k * NF + j], acc);
+#pragma unroll
+            for (int k = 0; k < NF; k++) acc = fma(Lm[i * NF + k], dx_lane_ld(Fm, P::at(j, k)), acc);
+            Ln[i * NF + j] = acc;
+        }
+    }
+}
+
 template <int NF, bool TAPE>
 __device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpcArgs &a, const DxConsts &K,
                                              const double *bsh, double *wsm) {
     constexpr int N = NF - 1;
     constexpr int NT = DxPacked<NF>::NT;
     constexpr bool SV = BwdLpcStore<NF>::kVecShared;
+    constexpr bool HY = BwdLpcStore<NF>::kHybrid;
     using P = DxPacked<NF>;
     const long long C = a.C;
     const double dt = a.dt;
@@ -123,97 +248,83 @@ __device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpc
     }
 
     // ---------------- Taylor and its derivative: F = b_m X + b_{m-1} I, dF = b_m H, y_d = F a_d
-    DxLaneArr<NT, false> Fm, Gm;
-    DxLaneArr<NF * NF, false> Lm, Ln;
+    DxLaneArr<NT, HY> Fm;                 // E (hybrid: shared memory)
+    DxLaneArr<NT, false> Gm;              // the next E, or the Horner step's next F
+    DxLaneArr<NF * NF, false> Lm, Lt;     // L, and the Taylor step's new L (in place for the compiler)
+    DxLaneArr<NF * NF, HY> Ln;            // the squaring's new L
+    if constexpr (HY) {
+        Fm.bind(wsm + 32 * BwdLpcStore<NF>::kVec, lane);
+        Ln.bind(wsm + 160 * NF, lane);   // over a_d, b_d, y_d, dead in the squarings
+    }
     const double bm = bsh[m], bm1 = bsh[m - 1];
-    if (!taped) dx_lpc_taylor_init<NF>(Fm, xs, ds, bm, bm1);
+    if constexpr (HY) {
+        // The Horner chain of F shares only X with the derivative chain (which
+        // carries y_d = F a_d by its own recurrence): it runs first, in
+        // registers, and leaves E_0 in shared memory; then the derivative
+        // chain runs with L in registers.
+        if (taped) {
 #pragma unroll
-    for (int i = 0; i < NF; i++) {
-#pragma unroll
-        for (int j = 0; j < NF; j++) {
-            double acc = av[i] * bv[j];
-            acc = fma(av[NF + i], bv[NF + j], acc);
-            acc = fma(av[2 * NF + i], bv[2 * NF + j], acc);
-            acc = fma(a3[i], sig[j], acc);
-            Lm[i * NF + j] = bm * acc;
-        }
-    }
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        double acc = 0.0;
-#pragma unroll
-        for (int k = 0; k < NF; k++) acc = fma(xs[k], av[d * NF + k], acc);
-        yv[d * NF] = fma(bm, acc, bm1 * av[d * NF]);
-#pragma unroll
-        for (int f = 1; f < NF; f++)
-            yv[d * NF + f] = fma(bm, fma(xs[f], av[d * NF], ds[f] * av[d * NF + f]), bm1 * av[d * NF + f]);
-    }
-    for (int jb = m - 2; jb >= 0; jb--) {
-        // F_jb = F X + b_jb I; dF_jb = dF X + F H, where F a_d = y_d (d < 3) and
-        // F a_3 = b_{jb+1} a_3 (X sigma = 0); then y_d <- X y_d + b_jb a_d.
-        if (!taped) {
-            dx_lpc_horner_step<NF>(Fm, Gm, xs, ds, bsh[jb]);
-            dx_lane_take(Fm, Gm);
-        }
-        const double bj1 = bsh[jb + 1], bj = bsh[jb];
-#pragma unroll
-        for (int i = 0; i < NF; i++) {
-            const double y0 = yv[i], y1 = yv[NF + i], y2 = yv[2 * NF + i], w = bj1 * a3[i];
-            double acc = y0 * bv[0];
-            acc = fma(y1, bv[NF], acc);
-            acc = fma(y2, bv[2 * NF], acc);
-            acc = fma(w, sig[0], acc);
-#pragma unroll
-            for (int k = 0; k < NF; k++) acc = fma(Lm[i * NF + k], xs[k], acc);
-            Ln[i * NF] = acc;
-#pragma unroll
-            for (int j = 1; j < NF; j++) {
-                double t = y0 * bv[j];
-                t = fma(y1, bv[NF + j], t);
-                t = fma(y2, bv[2 * NF + j], t);
-                t = fma(w, sig[j], t);
-                t = fma(Lm[i * NF], xs[j], t);
-                Ln[i * NF + j] = fma(Lm[i * NF + j], ds[j], t);
+            for (int e = 0; e < NT; e++) Fm[e] = tcell[e];
+        } else {
+            DxLaneArr<NT, false> Fr;
+            dx_lpc_taylor_init<NF>(Fr, xs, ds, bm, bm1);
+            for (int jb = m - 2; jb >= 0; jb--) {
+                dx_lpc_horner_step<NF>(Fr, Gm, xs, ds, bsh[jb]);
+                dx_lane_take(Fr, Gm);
             }
+            dx_lpc_restore<NF>(Fr, sig, tau);
+#pragma unroll
+            for (int e = 0; e < NT; e++) Fm[e] = Fr[e];
         }
+        bwd_lpc_dinit<NF>(Lm, av, bv, a3, sig, bm);
+        bwd_lpc_yinit<NF>(yv, xs, ds, av, bm, bm1);
+        for (int jb = m - 2; jb >= 0; jb--) {
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-            const double y0 = yv[d * NF];
-            double acc = bj * av[d * NF];
-#pragma unroll
-            for (int k = 0; k < NF; k++) acc = fma(xs[k], yv[d * NF + k], acc);
-#pragma unroll
-            for (int f = 1; f < NF; f++)
-                yv[d * NF + f] = fma(xs[f], y0, fma(ds[f], yv[d * NF + f], bj * av[d * NF + f]));
-            yv[d * NF] = acc;
+            for (int i = 0; i < NF; i++) {
+                bwd_lpc_drow<NF>(Lm, Lt, i, yv, bv, a3, sig, xs, ds, bsh[jb + 1]);
+                // one row at a time: overlapped, the rows' vector loads would
+                // outgrow the registers L leaves free
+                asm volatile("" ::: "memory");
+            }
+            bwd_lpc_ystep<NF>(yv, xs, ds, av, bsh[jb]);
+            dx_lane_take(Lm, Lt);
         }
-        dx_lane_take(Lm, Ln);
-    }
-    if (taped) {
-#pragma unroll
-        for (int e = 0; e < NT; e++) Fm[e] = tcell[e];
     } else {
-        dx_lpc_restore<NF>(Fm, sig, tau);
+        if (!taped) dx_lpc_taylor_init<NF>(Fm, xs, ds, bm, bm1);
+        bwd_lpc_dinit<NF>(Lm, av, bv, a3, sig, bm);
+        bwd_lpc_yinit<NF>(yv, xs, ds, av, bm, bm1);
+        for (int jb = m - 2; jb >= 0; jb--) {
+            // F_jb = F X + b_jb I; dF_jb = dF X + F H, where F a_d = y_d (d < 3) and
+            // F a_3 = b_{jb+1} a_3 (X sigma = 0); then y_d <- X y_d + b_jb a_d.
+            if (!taped) {
+                dx_lpc_horner_step<NF>(Fm, Gm, xs, ds, bsh[jb]);
+                dx_lane_take(Fm, Gm);
+            }
+#pragma unroll
+            for (int i = 0; i < NF; i++) bwd_lpc_drow<NF>(Lm, Lt, i, yv, bv, a3, sig, xs, ds, bsh[jb + 1]);
+            bwd_lpc_ystep<NF>(yv, xs, ds, av, bsh[jb]);
+            dx_lane_take(Lm, Lt);
+        }
+        if (taped) {
+#pragma unroll
+            for (int e = 0; e < NT; e++) Fm[e] = tcell[e];
+        } else {
+            dx_lpc_restore<NF>(Fm, sig, tau);
+        }
     }
 
     // ---------------- squarings: (E, L) <- (E^2, E L + L E); the last one forms only
     // row 0, column 0 and the diagonal of L (all the gradients read) and leaves E at E_{s-1}
     for (int sq = 0; sq < s; sq++) {
         const bool last = sq == s - 1;
-#pragma unroll
-        for (int i = 0; i < NF; i++) {
-#pragma unroll
-            for (int j = 0; j < NF; j++) {
-                if (last && i != 0 && j != 0 && i != j) continue;
-                double acc = 0.0;
-#pragma unroll
-                for (int k = 0; k < NF; k++) acc = fma(Fm[P::at(i, k)], Lm[k * NF + j], acc);
-#pragma unroll
-                for (int k = 0; k < NF; k++) acc = fma(Lm[i * NF + k], Fm[P::at(j, k)], acc);
-                Ln[i * NF + j] = acc;
-            }
-        }
+        if (last)
+            bwd_lpc_el_le<NF, true>(Fm, Lm, Ln);
+        else
+            bwd_lpc_el_le<NF, false>(Fm, Lm, Ln);
+
         if (!last) {
+            // hybrid: the old L is dead once the new one is stored, so E^2 forms
+            // in the registers it held and goes back over E
             if (taped && sq + 1 < tlev) {
                 const double *lv = tcell + (size_t)(sq + 1) * a.P;
 #pragma unroll
@@ -223,11 +334,26 @@ __device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpc
                 dx_lpc_restore<NF>(Gm, sig, tau);
             }
             dx_lane_take(Fm, Gm);
+            if constexpr (HY) asm volatile("" ::: "memory");   // the new L loads after E^2 is stored
         }
-        dx_lane_take(Lm, Ln);
+        dx_lane_take(Lm, Ln);   // after the trimmed last squaring only the slots the gradients read are fresh
     }
 
     // ---------------- outputs
+    if constexpr (HY) {
+        // a_d = g_d / sigma again (its slice held the new L), and eps, alpha
+        // divided again exactly as the set-up divided them
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) av[d * NF + f] = a.g_out[(d * NF + f) * C + c] * tau[f];
+        }
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+            eps[i] = __ddiv_rn(a.rho_d[i * C + c], rg);
+            alpha[i] = __ddiv_rn(1.0, a.t_s[i * C + c]);
+        }
+    }
     if (a.g_vin) {
         // P^T g with P^T = D_sigma E D_sigma^-1: (P^T g)_i = E_ii g_i + sigma_i
         // sum_{k != i} E_ik a_k, a = g / sigma. After s >= 1 squarings E holds
@@ -278,21 +404,41 @@ __device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpc
 }
 
 template <int NF, bool TAPE>
-__global__ void __launch_bounds__(kThreads) dx_backward_lpc(BwdLpcArgs a, DxConsts K, int rounds) {
+__global__ void __launch_bounds__(bwd_threads<NF>()) dx_backward_lpc(BwdLpcArgs a, DxConsts K, int rounds) {
+    constexpr int kThreads = bwd_threads<NF>(), kTile = bwd_tile<NF>();
+    constexpr bool HY = BwdLpcStore<NF>::kHybrid;
     extern __shared__ double smem[];
-    __shared__ unsigned long long key[kTile];
-    __shared__ unsigned short order[kTile];
+    // the hybrid storage sorts in the slices of the first cell's matrices and
+    // keeps its own positions in registers before any cell starts
+    __shared__ unsigned long long key_static[HY ? 1 : kTile];
+    __shared__ unsigned short order_static[HY ? 1 : kTile];
     double *bsh = smem;
     for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
+    double *wsm = smem + 32 + (threadIdx.x >> 5) * BwdLpcStore<NF>::kWarpDoubles;
+    unsigned long long *key = HY ? reinterpret_cast<unsigned long long *>(smem + 32 + 32 * BwdLpcStore<NF>::kVec)
+                                 : key_static;
+    unsigned short *order = HY ? reinterpret_cast<unsigned short *>(key + kTile) : order_static;
     const long long C = a.C;
     const long long base = (long long)blockIdx.x * rounds * kThreads;
     // order the tile's cells by the cost proxy so that a warp's 32 cells share (k*, s*)
     dx_lpc_tile_order<NF - 1>(base, rounds, kThreads, C, a.rho_g, a.rho_d, a.t_s, a.dt, key, order);
     const int lane = threadIdx.x & 31;
-    double *wsm = smem + 32 + (threadIdx.x >> 5) * BwdLpcStore<NF>::kWarpDoubles;
-    for (int r = 0; r < rounds; r++) {
-        const long long c = base + order[r * kThreads + threadIdx.x];
-        if (c < C) bwd_lpc_cell<NF, TAPE>(lane, c, a, K, bsh, wsm);
+    if constexpr (HY) {
+        // at most 4 rounds of 32 cells: the 7-bit tile positions packed in one word
+        static_assert(kTile / kThreads <= 4 && kTile <= 256, "positions packed 8 bits each");
+        unsigned int mine = 0;
+        for (int r = 0; r < rounds; r++) mine |= (unsigned int)order[r * kThreads + threadIdx.x] << (8 * r);
+        __syncthreads();
+#pragma unroll 1
+        for (int r = 0; r < rounds; r++) {
+            const long long c = base + ((mine >> (8 * r)) & 0xffu);
+            if (c < C) bwd_lpc_cell<NF, TAPE>(lane, c, a, K, bsh, wsm);
+        }
+    } else {
+        for (int r = 0; r < rounds; r++) {
+            const long long c = base + order[r * kThreads + threadIdx.x];
+            if (c < C) bwd_lpc_cell<NF, TAPE>(lane, c, a, K, bsh, wsm);
+        }
     }
 }
 
@@ -302,8 +448,9 @@ __global__ void __launch_bounds__(kThreads) dx_backward_lpc(BwdLpcArgs a, DxCons
 // Blocks take the permutation from its end, so the costliest bins start first
 // and the cheap ones fill the tail.
 template <int NF, bool TAPE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(bwd_threads<NF>())
 dx_backward_lpc_binned(BwdLpcArgs a, DxConsts K, const unsigned long long *perm) {
+    constexpr int kThreads = bwd_threads<NF>();
     extern __shared__ double smem[];
     double *bsh = smem;
     for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
@@ -315,8 +462,14 @@ dx_backward_lpc_binned(BwdLpcArgs a, DxConsts K, const unsigned long long *perm)
 
 template <int NF, bool TAPE>
 int launch(const BwdLpcArgs &a, cudaStream_t stream) {
+    constexpr int kThreads = bwd_threads<NF>(), kTile = bwd_tile<NF>();
+    static_assert(!BwdLpcStore<NF>::kHybrid ||
+                      kTile * (sizeof(unsigned long long) + sizeof(unsigned short)) <= 32 * sizeof(double) *
+                          BwdLpcStore<NF>::kNT,
+                  "the sort keys fit the first warp's matrix slices");
     const size_t smem = sizeof(double) * (32 + (size_t)(kThreads / 32) * BwdLpcStore<NF>::kWarpDoubles);
-    constexpr size_t kStatic = kTile * (sizeof(unsigned long long) + sizeof(unsigned short));
+    constexpr size_t kStatic =
+        BwdLpcStore<NF>::kHybrid ? 16 : kTile * (sizeof(unsigned long long) + sizeof(unsigned short));
     if (a.C >= DX_BINNED_MIN_CELLS) {
         const unsigned long long *perm = nullptr;
         void *scratch = dx_binned_perm(dx_consts(), a.C, NF - 1, a.rho_g, a.rho_d, a.t_s, a.dt, a.status, stream, &perm);
@@ -365,6 +518,9 @@ int dx_launch_backward_lpc(int n, long long C, const double *rho_g, const double
         DX_CASE(4)
         DX_CASE(5)
         DX_CASE(6)
+        DX_CASE(7)
+        DX_CASE(8)
+        DX_CASE(9)
 #undef DX_CASE
         default: return DRAG_EINVAL_SIZE;
     }

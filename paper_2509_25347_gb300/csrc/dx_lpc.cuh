@@ -55,11 +55,29 @@ struct DxLaneArr<NT, true, V> {
     __device__ __forceinline__ V &operator[](int e) { return p[e * 32]; }
 };
 
+// Entry e of a lane array read at its point of use: a register, or for a
+// shared-memory slice a load the compiler may not merge with another read of
+// the same entry (so it cannot hold a whole matrix in registers to reuse it).
+template <int NT, typename V>
+__device__ __forceinline__ V dx_lane_ld(DxLaneArr<NT, false, V> &a, int e) { return a.v[e]; }
+template <int NT>
+__device__ __forceinline__ double dx_lane_ld(DxLaneArr<NT, true, double> &a, int e) {
+    double v;
+    const unsigned addr = (unsigned)__cvta_generic_to_shared(a.p + e * 32);
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(addr));
+    return v;
+}
+
 // F <- G after a step: copied into registers, or shared-memory slices swapped.
 template <int NT, bool GS, typename V>
 __device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, false, V> &F, DxLaneArr<NT, GS, V> &G) {
 #pragma unroll
     for (int e = 0; e < NT; e++) F.v[e] = G[e];
+}
+template <int NT, typename V>
+__device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, true, V> &F, DxLaneArr<NT, false, V> &G) {
+#pragma unroll
+    for (int e = 0; e < NT; e++) F[e] = G.v[e];
 }
 template <int NT, typename V>
 __device__ __forceinline__ void dx_lane_take(DxLaneArr<NT, true, V> &F, DxLaneArr<NT, true, V> &G) {

@@ -78,7 +78,7 @@ int dx_binned_release(void *scratch, cudaStream_t stream);
 // (6 launches), tile-sorted below (1 launch). thdr
 // (null: none) is the tape the forward wrote (geometry as in
 // drag_expm_backward_taped; tm its first level).
-#define DX_BWD_LPC_NMAX 6
+#define DX_BWD_LPC_NMAX 9
 int dx_launch_backward_lpc(int n, long long C, const double *rho_g, const double *rho_d, const double *t_s,
                            double dt, const double *v_in, const double *grad_v_out, double *grad_v_in,
                            double *grad_rho_g, double *grad_rho_d, double *grad_t_s, uint32_t *status,

@@ -205,10 +205,11 @@ def test_backward_extreme_norms(dx):
     assert dx.get_status() == 0
 
 
-# ---- lane-per-cell adjoint (n = N + 1 <= 6 under a lane-per-cell mode, the default there)
+# ---- lane-per-cell adjoint (n = N + 1 <= 9 under a lane-per-cell mode, the default there;
+# n = 7..9 keep L in registers and E in shared memory)
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_backward_both_kernel_families(dx, N):
     """Under the default (lane-per-cell) mode the adjoint runs one lane per cell;
     under the warp-per-cell mode one warp per cell. Both match the oracle's
@@ -270,7 +271,7 @@ def test_lane_per_cell_backward_full_size_sampled(dx):
     test_backward_full_size_sampled(dx, "mrn_n4_128cube")
 
 
-@pytest.mark.parametrize("N", [1, 4, 5])
+@pytest.mark.parametrize("N", [1, 4, 5, 6, 8])
 def test_lane_per_cell_backward_binned(dx, N):
     """From 262,144 cells the lane-per-cell adjoint bins the cells by (k*, s*)
     over the whole input before running them: its gradients equal, bit for bit,
