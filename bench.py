@@ -565,7 +565,8 @@ def leg_single(dx, args, name, rank, world, stream, peak, hbm_peak, local, steps
     clocks = sampler.stop()
     if dx.get_status():
         raise RuntimeError(f"device status set after the {name} forward")
-    fb_ms = None
+    fb_ms = ft_ms = None
+    levels = tape_nbytes = 0
     if adjoint:
         vt = dev(W.adjoint_target(C, N))
         gvi, grg = torch.empty_like(v), torch.empty_like(rg)
@@ -584,8 +585,28 @@ def leg_single(dx, args, name, rank, world, stream, peak, hbm_peak, local, steps
         fb_ms = float(np.mean(fb))
         if dx.get_status():
             raise RuntimeError(f"device status set after the {name} forward + adjoint")
+        # the same step through the adjoint tape (the forward stores E_0 .. E_{s*-2})
+        levels = dx.tape_levels_needed(rg, rd, ts, cells.dt)
+        tape_nbytes = dx.tape_bytes(C, N, levels)
+        ft_ms = None
+        if tape_nbytes < 0.8 * torch.cuda.mem_get_info()[0]:
+            holder = [None]
+
+            def fwd_bwd_taped():
+                _, holder[0] = dx.apply_taped(rg, rd, ts, cells.dt, v, vout, levels=levels, tape=holder[0],
+                                              stream=stream)
+                torch.sub(vout, vt, out=gvi)
+                dx.backward(rg, rd, ts, cells.dt, v, gvi, out=(vout, grg, grd, gts), tape=holder[0], stream=stream)
+
+            with torch.cuda.stream(stream):
+                fwd_bwd_taped()
+                torch.cuda.synchronize()
+                ft_ms = float(np.mean(time_steps(fwd_bwd_taped, fb_steps, stream)))
+            holder[0] = None
+            if dx.get_status():
+                raise RuntimeError(f"device status set after the {name} taped forward + adjoint")
     mean_ms = float(np.mean(per))
-    vals = [float(np.sum(per)), mean_ms] + ([fb_ms] if adjoint else [])
+    vals = [float(np.sum(per)), mean_ms] + ([fb_ms, ft_ms or 0.0] if adjoint else [])
     red = max_over_ranks(vals, world, device="cuda")
     ms_step = red[0] / steps
     entry = {
@@ -605,6 +626,11 @@ def leg_single(dx, args, name, rank, world, stream, peak, hbm_peak, local, steps
         entry["fwd_adjoint"] = {"value": total / (red[2] * 1e-3), "unit": UNIT, "ms_per_step": red[2],
                                 "adjoint_over_forward_time": red[2] / ms_step,
                                 "note": "forward + dL/dv_out (torch sub) + drag_expm_backward, CUDA events"}
+        if ft_ms is not None:
+            entry["fwd_adjoint_taped"] = {
+                "value": total / (red[3] * 1e-3), "unit": UNIT, "ms_per_step": red[3],
+                "adjoint_over_forward_time": red[3] / ms_step, "tape_levels": levels, "tape_bytes": tape_nbytes,
+                "note": "drag_expm_apply_taped + dL/dv_out (torch sub) + drag_expm_backward_taped, CUDA events"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         entry["cpu_baseline"] = cpu_baseline_entry(cells, name, cpu_seconds, adjoint=adjoint)
     return entry, (cells, rg, rd, ts, v, vout, k, s, per, total)

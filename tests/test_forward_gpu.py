@@ -222,6 +222,31 @@ def test_binned_forward(dx, N):
     assert torch.equal(zero[:, :, ok], v[:, :, ok])
 
 
+@pytest.mark.parametrize("N", [1, 3, 5])
+def test_tile_sorted_forward_small_and_prefix(dx, N):
+    """Below 262,144 cells the register-storage sizes (n <= 6) run one tile-sorted
+    launch. Ragged sizes (part of a CTA, one cell) against the oracle; and, since
+    the per-cell routine is the binned pipeline's, the first 200,003 cells of a
+    300,001-cell input give the binned run's v_out bit for bit."""
+    import torch
+    for C in (1, 100, 1025, 32785):
+        cells = W.mrn(C, N, seed=70 + C % 97 + N, stiff_lo=-5.0, stiff_hi=8.0)
+        ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v)
+        assert dx.apply_launches(C, N) == 1
+        assert_parity(gpu_apply(dx, cells), ref, cells.v)
+    C = 300001
+    cells = W.mrn(C, N, seed=80 + N, stiff_lo=-4.0, stiff_hi=8.0)
+    rg, rd, ts, v = dev(cells)
+    binned = dx.apply(rg, rd, ts, cells.dt, v)
+    head = 200003
+    sub = cells.subset(np.arange(head))
+    srg, srd, sts, sv = dev(sub)
+    tiled = dx.apply(srg, srd, sts, cells.dt, sv)
+    assert dx.apply_launches(head, N) == 1 and dx.apply_launches(C, N) == 6
+    assert torch.equal(tiled, binned[:, :, :head])
+    assert dx.get_status() == 0
+
+
 def extreme_cells(N, norms, seed=3):
     """Cells whose 1-norm |A|_1 is about `norms[c]` (rho_d = rho_g = 1, dt = 1,
     stopping times spread over a factor 2): s* up to ~1023."""
