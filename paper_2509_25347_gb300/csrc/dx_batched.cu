@@ -41,6 +41,13 @@ constexpr int kWpcWarps = 4;                         // warps per CTA, warp-per-
 constexpr int kWpcMinBlocks = 6;                     // resident CTAs per SM the latter is compiled for
 constexpr int kScanThreads = 1024;
 constexpr int kBatchLpcNMax = 9;                     // largest n run lane-per-cell in the batched kernel
+// One n (the binned drag_expm_apply and adjoint): the bins are chunk-major,
+// (chunk of consecutive cells, k*, s*), so that the items run one chunk after
+// the other and a chunk's cells, scattered over its bins, are read from DRAM
+// once and then from L2 (65,536 cells of N = 8 hold 37 MB). At most
+// kMaxChunks chunks, so that the bin scans stay short.
+constexpr long long kChunkMin = 65536;
+constexpr long long kMaxChunks = 64;
 
 struct Desc {
     long long cell_offset, dust_offset, vel_offset;
@@ -53,10 +60,13 @@ struct Work {
     unsigned long long *perm;   // (block << 32) | local cell, bin-sorted
     unsigned int *key;          // bin of each enumerated cell
     long long *blk_start;       // exclusive prefix of valid block sizes [nblocks + 1]
-    unsigned int *hist, *offs, *cursor;               // [kNBins + 1]
-    unsigned int *item_w, *item_l;   // [kNBins + 1] first item of each bin among warp- / lane-per-cell items
+    unsigned int *hist, *offs, *cursor;               // [nbins + 1]
+    unsigned int *item_w, *item_l;   // [nbins + 1] first item of each bin among warp- / lane-per-cell items
     unsigned int *ctr;   // [0] / [1] warp-per-cell queue counter / items, [2] enumerated cells,
                          // [3] / [4] lane-per-cell queue counter / items
+    int nbins;           // kNBins (bins by n, k*, s*) or chunks x kBinsPerN (one n: chunk, k*, s*)
+    int n_fixed;         // 0, or the n of every cell (chunk-major bins)
+    long long chunk;     // cells per chunk (n_fixed only)
 };
 
 struct Modes {
@@ -66,6 +76,15 @@ struct Modes {
 __device__ __forceinline__ int bin_of(int n, int k, int s) {
     return ((n - 2) * DX_K + (k - 1)) * kSBins + (s < kSBins - 1 ? s : kSBins - 1);
 }
+
+// Bin of enumerated cell g with (n, k*, s*) under the work's binning.
+__device__ __forceinline__ unsigned int bin_of(const Work &W, long long g, int n, int k, int s) {
+    if (!W.n_fixed) return (unsigned int)bin_of(n, k, s);
+    return (unsigned int)((g / W.chunk) * kBinsPerN + (k - 1) * kSBins + (s < kSBins - 1 ? s : kSBins - 1));
+}
+
+// Matrix size of the cells in a bin.
+__device__ __forceinline__ int n_of_bin(const Work &W, int bin) { return W.n_fixed ? W.n_fixed : bin / kBinsPerN + 2; }
 
 // A block is run only if its record is in range. N above nspecies_max is
 // rejected too: the main kernels' per-warp shared-memory slices are sized for
@@ -105,7 +124,7 @@ dx_batch_prepare(long long nblocks, const Desc *blocks, int nspecies_max, long l
                  long long v_len, Work W, uint32_t *status) {
     __shared__ long long sh[kScanThreads];
     const int t = threadIdx.x;
-    for (int i = t; i < kNBins; i += kScanThreads) W.hist[i] = 0;
+    for (int i = t; i < W.nbins; i += kScanThreads) W.hist[i] = 0;
     if (t < 8) W.ctr[t] = 0;
     const long long per = (nblocks + kScanThreads - 1) / kScanThreads;
     const long long b0 = t * per, b1 = b0 + per < nblocks ? b0 + per : nblocks;
@@ -174,7 +193,7 @@ __global__ void dx_batch_count(long long nblocks, const Desc *blocks, const doub
             const long long nb = dx_bits(col0) > cmax ? dx_bits(col0) : cmax;
             if (dx_norm_ok(nb)) dx_select(__longlong_as_double(nb), K, kk, s);   // else the cell routine flags it
         }
-        const unsigned int key = (unsigned int)bin_of(N + 1, kk, s);
+        const unsigned int key = bin_of(W, g, N + 1, kk, s);
         W.key[g] = key;
         atomicAdd(&W.hist[key], 1u);
     }
@@ -183,12 +202,13 @@ __global__ void dx_batch_count(long long nblocks, const Desc *blocks, const doub
 __global__ void __launch_bounds__(kScanThreads) dx_batch_bins(Work W, Modes M) {
     __shared__ long long sh[kScanThreads];
     const int t = threadIdx.x;
-    constexpr int per = (kNBins + kScanThreads - 1) / kScanThreads;
-    const int i0 = t * per, i1 = i0 + per < kNBins ? i0 + per : kNBins;
+    const int nb = W.nbins;
+    const int per = (nb + kScanThreads - 1) / kScanThreads;
+    const int i0 = t * per < nb ? t * per : nb, i1 = i0 + per < nb ? i0 + per : nb;
     long long cs = 0, ws = 0, ls = 0;
     for (int i = i0; i < i1; i++) {
         const unsigned int c = W.hist[i];
-        const bool wpc = M.m[i / kBinsPerN + 2] == DX_MODE_WPC;
+        const bool wpc = M.m[n_of_bin(W, i)] == DX_MODE_WPC;
         cs += c;
         ws += wpc ? c : 0;
         ls += wpc ? 0 : (c + 31) / 32;
@@ -199,7 +219,7 @@ __global__ void __launch_bounds__(kScanThreads) dx_batch_bins(Work W, Modes M) {
     long long lrun = block_exclusive_scan(ls, sh, ltot);
     for (int i = i0; i < i1; i++) {
         const unsigned int c = W.hist[i];
-        const bool wpc = M.m[i / kBinsPerN + 2] == DX_MODE_WPC;
+        const bool wpc = M.m[n_of_bin(W, i)] == DX_MODE_WPC;
         W.offs[i] = (unsigned int)crun;
         W.cursor[i] = (unsigned int)crun;
         W.item_w[i] = (unsigned int)wrun;
@@ -209,9 +229,9 @@ __global__ void __launch_bounds__(kScanThreads) dx_batch_bins(Work W, Modes M) {
         lrun += wpc ? 0 : (c + 31) / 32;
     }
     if (t == 0) {
-        W.offs[kNBins] = (unsigned int)ctot;
-        W.item_w[kNBins] = (unsigned int)wtot;
-        W.item_l[kNBins] = (unsigned int)ltot;
+        W.offs[nb] = (unsigned int)ctot;
+        W.item_w[nb] = (unsigned int)wtot;
+        W.item_l[nb] = (unsigned int)ltot;
         W.ctr[1] = (unsigned int)wtot;
         W.ctr[4] = (unsigned int)ltot;
     }
@@ -282,7 +302,8 @@ __device__ __forceinline__ void lpc_dispatch(int n, int lane, const MainArgs &a,
 // of them.
 template <typename F>
 __device__ __forceinline__ void dx_batch_queue(unsigned int *counter, unsigned int nitems,
-                                               const unsigned int *item_offs, uint32_t *status, F &&run) {
+                                               const unsigned int *item_offs, int nbins, uint32_t *status,
+                                               F &&run) {
     const int lane = threadIdx.x & 31;
     for (unsigned int guard = 0;; guard++) {
         if (guard > nitems) {
@@ -294,7 +315,7 @@ __device__ __forceinline__ void dx_batch_queue(unsigned int *counter, unsigned i
         item = __shfl_sync(DX_FULL, item, 0);
         if (item >= nitems) break;
         // bin holding this item: last bin with item_offs[bin] <= item
-        int lo = 0, hi = kNBins;
+        int lo = 0, hi = nbins;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
             if (item_offs[mid] <= item) lo = mid; else hi = mid;
@@ -311,8 +332,8 @@ dx_batch_main_wpc(MainArgs a, Work W, DxConsts K) {
     unsigned short *od = reinterpret_cast<unsigned short *>(wsm + a.warp_doubles);
     unsigned short *hp = od + kPairSlots;
     int table_n = 0;
-    dx_batch_queue(&W.ctr[0], W.ctr[1], W.item_w, a.status, [&](int bin, unsigned int sub) {
-        const int n = bin / kBinsPerN + 2;
+    dx_batch_queue(&W.ctr[0], W.ctr[1], W.item_w, W.nbins, a.status, [&](int bin, unsigned int sub) {
+        const int n = n_of_bin(W, bin);
         const unsigned long long p = W.perm[W.offs[bin] + sub];
         const Desc d = a.blocks[p >> 32];
         const long long c = (long long)(p & 0xffffffffull);
@@ -336,8 +357,8 @@ dx_batch_main_lpc(MainArgs a, Work W, Modes M, DxConsts K) {
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     double *wsm = smem + 32 + wib * a.warp_doubles;
-    dx_batch_queue(&W.ctr[3], W.ctr[4], W.item_l, a.status, [&](int bin, unsigned int sub) {
-        const int n = bin / kBinsPerN + 2;
+    dx_batch_queue(&W.ctr[3], W.ctr[4], W.item_l, W.nbins, a.status, [&](int bin, unsigned int sub) {
+        const int n = n_of_bin(W, bin);
         const unsigned int pos = W.offs[bin] + 32 * sub + lane;
         if (pos < W.offs[bin + 1]) {
             const unsigned long long p = W.perm[pos];
@@ -354,17 +375,17 @@ struct Layout {
     size_t perm, key, blk_start, hist, offs, cursor, item_w, item_l, ctr, total;
 };
 
-Layout layout(long long nblocks, long long total_cells) {
+Layout layout(long long nblocks, long long total_cells, int nbins = kNBins) {
     Layout L;
     size_t o = 0;
     L.perm = o; o += align256(sizeof(unsigned long long) * (size_t)total_cells);
     L.key = o; o += align256(sizeof(unsigned int) * (size_t)total_cells);
     L.blk_start = o; o += align256(sizeof(long long) * (size_t)(nblocks + 1));
-    L.hist = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
-    L.offs = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
-    L.cursor = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
-    L.item_w = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
-    L.item_l = o; o += align256(sizeof(unsigned int) * (kNBins + 1));
+    L.hist = o; o += align256(sizeof(unsigned int) * ((size_t)nbins + 1));
+    L.offs = o; o += align256(sizeof(unsigned int) * ((size_t)nbins + 1));
+    L.cursor = o; o += align256(sizeof(unsigned int) * ((size_t)nbins + 1));
+    L.item_w = o; o += align256(sizeof(unsigned int) * ((size_t)nbins + 1));
+    L.item_l = o; o += align256(sizeof(unsigned int) * ((size_t)nbins + 1));
     L.ctr = o; o += align256(sizeof(unsigned int) * 8);
     L.total = o;
     return L;
@@ -427,8 +448,18 @@ Modes dx_batch_modes() {
     return M;
 }
 
-Work work_at(char *ws, const Layout &L) {
+// Chunk-major binning of C cells of one n: cells per chunk and bins.
+long long fixed_n_chunk(long long C) {
+    const long long by_count = (C + kMaxChunks - 1) / kMaxChunks;
+    return by_count > kChunkMin ? by_count : kChunkMin;
+}
+int fixed_n_bins(long long C) { return (int)((C + fixed_n_chunk(C) - 1) / fixed_n_chunk(C)) * kBinsPerN; }
+
+Work work_at(char *ws, const Layout &L, int nbins = kNBins, int n_fixed = 0, long long chunk = 0) {
     Work W;
+    W.nbins = nbins;
+    W.n_fixed = n_fixed;
+    W.chunk = chunk;
     W.perm = reinterpret_cast<unsigned long long *>(ws + L.perm);
     W.key = reinterpret_cast<unsigned int *>(ws + L.key);
     W.blk_start = reinterpret_cast<long long *>(ws + L.blk_start);
@@ -461,8 +492,9 @@ static int batched_run(const DxConsts &K, long long nblocks, const Desc *D, long
                        long long v_len, int nspecies_max, const double *rho_g, const double *rho_d,
                        const double *t_s, const double *v_in, double *v_out, char *ws, const Layout &L,
                        uint32_t *st, cudaStream_t stream, long long *thdr = nullptr, double *tm = nullptr,
-                       int tlevels = 0, int tP = 0) {
-    const Work W = work_at(ws, L);
+                       int tlevels = 0, int tP = 0, int n_fixed = 0) {
+    const Work W = n_fixed ? work_at(ws, L, fixed_n_bins(total_cells), n_fixed, fixed_n_chunk(total_cells))
+                           : work_at(ws, L);
     const Modes M = dx_batch_modes();
     const int sms = dx_sm_count();
     launch_binning(K, nblocks, D, nspecies_max, total_cells, rho_d_len, v_len, rho_g, rho_d, t_s, W, M, st, stream);
@@ -594,7 +626,7 @@ extern "C" int drag_expm_apply_batched_noalloc(int64_t nblocks, const drag_block
 
 // ---------------------------------------------------------------------------
 // Binned forward: drag_expm_apply for lane-per-cell sizes on large inputs runs
-// the pipeline above with one block. Its scratch (12 bytes per cell) comes
+// the pipeline above with one block, its bins chunk-major (chunk, k*, s*). Its scratch (12 bytes per cell) comes
 // from a library-private, stream-ordered memory pool that keeps what it has
 // once allocated (release threshold: never), so calls on different streams
 // never share scratch, repeated calls do not reallocate, and stream capture
@@ -650,7 +682,7 @@ int dx_binned_forward(const DxConsts &K, long long C, int N, const double *rho_g
                       cudaStream_t stream, long long *thdr, double *tm, int tlevels, int tP) {
     cudaMemPool_t pool = scratch_pool();
     if (!pool) return DX_BINNED_UNAVAILABLE;
-    const Layout L = layout(1, C);
+    const Layout L = layout(1, C, fixed_n_bins(C));
     void *p = nullptr;
     if (cudaMallocFromPoolAsync(&p, L.total + 256, pool, stream) != cudaSuccess || !p) {
         cudaGetLastError();
@@ -663,7 +695,7 @@ int dx_binned_forward(const DxConsts &K, long long C, int N, const double *rho_g
         Desc *D = reinterpret_cast<Desc *>(static_cast<char *>(p) + L.total);
         dx_batch_single_desc<<<1, 1, 0, stream>>>(D, C, N, dt);
         rc = batched_run(K, 1, D, C, (long long)N * C, 3LL * (N + 1) * C, N, rho_g, rho_d, t_s, v_in, v_out,
-                         static_cast<char *>(p), L, status, stream, thdr, tm, tlevels, tP);
+                         static_cast<char *>(p), L, status, stream, thdr, tm, tlevels, tP, N + 1);
     }
     if (cudaFreeAsync(p, stream) != cudaSuccess && rc == DRAG_OK) rc = DRAG_ECUDA;
     return rc;
@@ -674,7 +706,7 @@ void *dx_binned_perm(const DxConsts &K, long long C, int N, const double *rho_g,
                      const unsigned long long **perm) {
     cudaMemPool_t pool = scratch_pool();
     if (!pool || C < 1 || C > 0x7fffffffLL) return nullptr;
-    const Layout L = layout(1, C);
+    const Layout L = layout(1, C, fixed_n_bins(C));
     void *p = nullptr;
     if (cudaMallocFromPoolAsync(&p, L.total + 256, pool, stream) != cudaSuccess || !p) {
         cudaGetLastError();
@@ -686,7 +718,7 @@ void *dx_binned_perm(const DxConsts &K, long long C, int N, const double *rho_g,
     }
     char *ws = static_cast<char *>(p);
     Desc *D = reinterpret_cast<Desc *>(ws + L.total);
-    const Work W = work_at(ws, L);
+    const Work W = work_at(ws, L, fixed_n_bins(C), N + 1, fixed_n_chunk(C));
     dx_batch_single_desc<<<1, 1, 0, stream>>>(D, C, N, dt);
     launch_binning(K, 1, D, N, C, (long long)N * C, 3LL * (N + 1) * C, rho_g, rho_d, t_s, W, dx_batch_modes(), status,
                    stream);
