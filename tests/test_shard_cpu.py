@@ -156,3 +156,22 @@ def test_sharded_results_equal_single_rank_gloo():
             got = pout[int(pdesc[j]["vel_offset"]):int(pdesc[j]["vel_offset"]) + n_v]
             exp = ref[int(desc[b]["vel_offset"]):int(desc[b]["vel_offset"]) + n_v]
             assert np.array_equal(got, exp), (rank, b)
+
+
+def test_bench_cell_loading_partition_and_replicas():
+    """bench.py's per-rank cells: under --partition the ranks' contiguous shares of
+    one workload concatenate to the single-rank draw; otherwise each rank gets an
+    independent draw of the same size (rank 0's is the workload itself)."""
+    import bench
+    name, nc = "mrn_n4_128cube", 1001
+    full, total = bench.load_cells(name, 0, 1, True, ncells=nc)
+    assert total == nc
+    parts = [bench.load_cells(name, r, 3, True, ncells=nc) for r in range(3)]
+    assert all(t == nc for _, t in parts)
+    assert np.array_equal(np.concatenate([p.v for p, _ in parts], axis=2), full.v)
+    assert np.array_equal(np.concatenate([p.t_s for p, _ in parts], axis=1), full.t_s)
+    r0, tot0 = bench.load_cells(name, 0, 2, False, ncells=nc)
+    r1, tot1 = bench.load_cells(name, 1, 2, False, ncells=nc)
+    assert tot0 == tot1 == 2 * nc
+    assert np.array_equal(r0.v, full.v) and not np.array_equal(r1.v, full.v)
+    assert r1.ncells == nc and r1.rho_d.shape == full.rho_d.shape
