@@ -229,7 +229,7 @@ def test_backward_both_kernel_families(dx, N):
     assert dx.get_status() == 0
 
 
-@pytest.mark.parametrize("N", [1, 4])
+@pytest.mark.parametrize("N", [1, 4, 6, 8])
 def test_lane_per_cell_backward_extreme_norms(dx, N):
     """The lane-per-cell adjoint at norms up to 1.5e308 (s* ~ 1023; dL/dv_in
     checked) and up to 1e14 (all gradients), as for the warp-per-cell one."""
@@ -329,15 +329,17 @@ def test_lane_per_cell_backward_in_cuda_graph(dx):
     assert dx.get_status() == 0
 
 
-def test_lane_per_cell_backward_binned_invalid_cells(dx):
-    """Invalid cells inside a binned lane-per-cell adjoint (270,001 cells):
-    NaN gradients and the status bit there, oracle gradients elsewhere."""
+@pytest.mark.parametrize("N", [4, 8])
+def test_lane_per_cell_backward_binned_invalid_cells(dx, N):
+    """Invalid cells inside a binned lane-per-cell adjoint (270,001 cells; N = 8
+    with the hybrid storage): NaN gradients and the status bit there, oracle
+    gradients elsewhere."""
     import torch
-    C, N = 270001, 4
+    C = 270001
     cells = W.mrn(C, N, seed=91, stiff_lo=-4.0, stiff_hi=8.0)
     bad = [5, 123456, C - 1]
     cells.t_s[1, bad[0]] = -1.0
-    cells.rho_d[3, bad[1]] = np.nan
+    cells.rho_d[N - 1, bad[1]] = np.nan
     cells.t_s[0, bad[2]] = 0.0
     g_np = np.random.default_rng(91).standard_normal(cells.v.shape)
     out = [x.cpu().numpy() for x in dx.backward(t(cells.rho_g), t(cells.rho_d), t(cells.t_s), cells.dt, t(cells.v),

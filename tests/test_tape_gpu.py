@@ -109,11 +109,13 @@ def test_taped_backward_oracle_parity(dx):
     assert_adjoint_parity(cells, g, got, (rv, rrg, rrd, rts))
 
 
-def test_tape_capacity_short(dx):
+@pytest.mark.parametrize("N", [16, 8])
+def test_tape_capacity_short(dx, N):
     """Cells needing more levels than the capacity are not recorded; their
-    adjoint recomputes and the gradients stay identical."""
+    adjoint recomputes and the gradients stay identical (N = 16 warp per cell;
+    N = 8 lane per cell with the hybrid storage, tape written by the
+    lane-per-cell forward)."""
     import torch
-    N = 16
     cells = spread_cells(N, 150, seed=5)
     rg, rd, ts = dev_args(cells)
     v = t(cells.v)
@@ -129,12 +131,12 @@ def test_tape_capacity_short(dx):
         assert torch.equal(a, b)
 
 
-def test_stale_and_foreign_tapes(dx):
+@pytest.mark.parametrize("N", [12, 8])
+def test_stale_and_foreign_tapes(dx, N):
     """A tape is used only where the cell's inputs reproduce its fingerprint:
     changed inputs (by one ulp), another dt, or random bytes all give the
-    recomputed gradients exactly."""
+    recomputed gradients exactly (N = 8: lane per cell, hybrid storage)."""
     import torch
-    N = 12
     cells = spread_cells(N, 180, seed=9)
     rg, rd, ts = dev_args(cells)
     v = t(cells.v)
