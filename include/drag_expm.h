@@ -394,11 +394,11 @@ int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *blocks, int64_t
  *   DRAG_NOALLOC_MAX_CELLS; larger batches return DRAG_ENOALLOC_LIMIT and
  *   launch nothing. All other arguments and errors are those of
  *   drag_expm_apply_batched.
- *   A call looks up the array's device address on the current device
- *   (cudaGetSymbolAddress, which allocates nothing) whenever `stream` is not
- *   capturing, so the address follows a device reset; a call made while
- *   `stream` captures reuses the address of the last call on that device, so
- *   make one call on each device before any stream capture.
+ *   The first call on each device looks up the array's device address (with
+ *   that device current; cudaGetSymbolAddress allocates nothing) and keeps it
+ *   for the process: make that first call before any stream capture, and do
+ *   not call this entry point again after a cudaDeviceReset of that device
+ *   (the kept address belongs to the old context).
  *   Calls share the array: each call clears what must start at zero, but two
  *   calls whose work overlaps on the GPU race on it, so order them (same
  *   stream, or an event between streams).

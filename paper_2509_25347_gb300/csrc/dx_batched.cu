@@ -572,9 +572,10 @@ extern "C" int drag_expm_apply_batched(int64_t nblocks, const drag_block_t *bloc
 //
 // The array lives in device global memory of every GPU that loads the library
 // and stays there until the process exits. In host code its name only stands
-// in for it, so its device address is looked up on the current device (every
-// call outside stream capture; a capture reuses the last address) and passed
-// to the kernels. Every call
+// in for it, so its device address is looked up once per device (first call on
+// that device, with that device current) and passed to the kernels. The
+// cached address belongs to that device's context: it does not survive a
+// cudaDeviceReset. Every call
 // uses the same array: the first kernel of the pipeline clears the histogram
 // and the counters, and every other part is written before it is read, so no
 // stale contents leak from one call to the next; but two calls whose work
@@ -606,14 +607,10 @@ extern "C" int drag_expm_apply_batched_noalloc(int64_t nblocks, const drag_block
         return DRAG_ENOALLOC_LIMIT;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DRAG_ECUDA;
-    // The address is taken again outside stream capture, so that it follows a
-    // new context after a device reset; a capture reuses the last one.
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return DRAG_ECUDA;
     void *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_addr[dev] || cap == cudaStreamCaptureStatusNone) {
+        if (!g_noalloc_addr[dev]) {
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DRAG_ECUDA;
             g_noalloc_addr[dev] = p;
