@@ -247,6 +247,30 @@ def test_tile_sorted_forward_small_and_prefix(dx, N):
     assert dx.get_status() == 0
 
 
+def test_binned_forward_wide_chunks(dx):
+    """Above 64 chunks of 65,536 cells the binned forward widens its chunks
+    (here 4,500,001 cells of N = 1: 64 chunks of 70,313 cells, the last one
+    ragged). Sampled cells against the oracle, the first 200,003 cells bit for
+    bit against the tile-sorted kernel, and the status word clean."""
+    import torch
+    C, N = 4500001, 1
+    cells = W.mrn(C, N, seed=4242, stiff_lo=-4.0, stiff_hi=8.0)
+    rg, rd, ts, v = dev(cells)
+    assert dx.apply_launches(C, N) == 6
+    out = dx.apply(rg, rd, ts, cells.dt, v)
+    assert dx.get_status() == 0
+    idx = np.unique(np.concatenate([np.random.default_rng(1).integers(0, C, 400),
+                                    [0, 70312, 70313, C - 2, C - 1]]))
+    sub = cells.subset(idx)
+    ref = oracle.drag_apply(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v)
+    assert_parity(out[:, :, idx].cpu().numpy(), ref, sub.v)
+    head = 200003
+    hrg, hrd, hts, hv = dev(cells.subset(np.arange(head)))
+    tiled = dx.apply(hrg, hrd, hts, cells.dt, hv)
+    assert torch.equal(tiled, out[:, :, :head])
+    assert dx.get_status() == 0
+
+
 def extreme_cells(N, norms, seed=3):
     """Cells whose 1-norm |A|_1 is about `norms[c]` (rho_d = rho_g = 1, dt = 1,
     stopping times spread over a factor 2): s* up to ~1023."""
