@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(bwd_threads<NF>()) dx_backward_lpc(BwdLpcArgs 
     const long long C = a.C;
     const long long base = (long long)blockIdx.x * rounds * kThreads;
     // order the tile's cells by the cost proxy so that a warp's 32 cells share (k*, s*)
-    dx_lpc_tile_order<NF - 1>(base, rounds, kThreads, C, a.rho_g, a.rho_d, a.t_s, a.dt, key, order);
+    dx_lpc_tile_order<NF - 1>(base, rounds, kThreads, C, C, a.rho_g, a.rho_d, a.t_s, a.dt, key, order);
     const int lane = threadIdx.x & 31;
     if constexpr (HY) {
         // at most 4 rounds of 32 cells: the 7-bit tile positions packed in one word

@@ -66,7 +66,7 @@ dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d
     constexpr int kThreads = lpc_threads<NF, ST>();
     const long long base = (long long)blockIdx.x * rounds * kThreads;
     if (rounds >= DX_LPC_SORT_MIN_ROUNDS) {
-        dx_lpc_tile_order<NF - 1>(base, rounds, kThreads, C, rho_g, rho_d, t_s, dt, key, order);
+        dx_lpc_tile_order<NF - 1>(base, rounds, kThreads, C, C, rho_g, rho_d, t_s, dt, key, order);
     } else {
         order[threadIdx.x] = (unsigned short)threadIdx.x;   // unsorted
         __syncthreads();
@@ -84,11 +84,60 @@ dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d
     }
 }
 
+// Balanced blocks (register storage). With one round of 4-warp blocks, the
+// blocks that share an SM all hand their costliest 32 cells to the same warp
+// slot, so one SM sub-partition (warp w runs on sub-partition w % 4) gets the
+// costliest group of every block. Instead: blocks of up to 16 warps, as many
+// as a multiple of the SM count, each on a contiguous share of C / gridDim.x
+// cells sorted by the cost proxy, with the sorted groups of 32 dealt to the
+// warp slots in snake order over the four sub-partitions (costliest to 0, 1,
+// 2, 3, then 3, 2, 1, 0, ...), which pairs costly groups with cheap ones.
+// Groups are cut from the costly end, so the ragged one holds the cheapest
+// cells.
+template <int NF>
+__host__ __device__ constexpr int lpc_wave_warps() { return NF <= 5 ? 16 : 8; }   // 128 / 255 registers
+
+template <int NF>
+__global__ void __launch_bounds__(32 * lpc_wave_warps<NF>())
+dx_forward_lpc_wave(long long C, const double *rho_g, const double *rho_d, const double *t_s, const double *v_in,
+                    double *v_out, double dt, uint32_t *status, double *heat, DxConsts K) {
+    constexpr int kMax = 32 * lpc_wave_warps<NF>();
+    __shared__ double bsh[32];
+    __shared__ unsigned long long key[kMax];
+    __shared__ unsigned short order[kMax];
+    const long long c0 = (long long)blockIdx.x * C / gridDim.x;
+    const long long c1 = ((long long)blockIdx.x + 1) * C / gridDim.x;
+    for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
+    dx_lpc_tile_order<NF - 1>(c0, 1, blockDim.x, c1, C, rho_g, rho_d, t_s, dt, key, order);
+    const int T = (int)(c1 - c0);
+    const int q = threadIdx.x >> 5, row = q >> 2, sp = q & 3;
+    const int k = 4 * row + ((row & 1) ? 3 - sp : sp);   // this slot's rank, costliest group first
+    const int pos = T - 32 * (k + 1) + (threadIdx.x & 31);
+    if (pos >= 0) {
+        const long long c = c0 + order[pos];
+        dx_lpc_forward_cell<NF, DX_LPC_REGS>(threadIdx.x & 31, rho_g + c, rho_d + c, t_s + c, v_in + c, v_out + c, C,
+                                             dt, K, bsh, nullptr, status, heat ? heat + c : nullptr,
+                                             DxTapeCell{nullptr, nullptr, 0, 0});
+    }
+}
+
 template <int NF, int ST, bool TAPE = false>
 int launch_one(const DxConsts &K, long long C, const double *rho_g, const double *rho_d, const double *t_s,
                const double *v_in, double *v_out, double dt, uint32_t *status, double *heat, cudaStream_t stream,
                LpcTape tp = LpcTape{nullptr, nullptr, 0, 0}) {
     constexpr int kThreads = lpc_threads<NF, ST>();
+    if constexpr (ST == DX_LPC_REGS && !TAPE) {
+        const long long sms = dx_sm_count();
+        if (sms > 0 && C > (long long)kThreads * sms) {
+            const long long cap = 32LL * lpc_wave_warps<NF>();
+            const long long G = sms * ((C + sms * cap - 1) / (sms * cap));
+            const long long per = (C + G - 1) / G;
+            const int warps = (int)(((per + 31) / 32 + 3) / 4 * 4);
+            dx_forward_lpc_wave<NF><<<(unsigned)G, 32 * warps, 0, stream>>>(C, rho_g, rho_d, t_s, v_in, v_out, dt,
+                                                                           status, heat, K);
+            return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
+        }
+    }
     const size_t smem = sizeof(double) * (32 + (size_t)(kThreads / 32) * dx_lpc_warp_smem_doubles<NF, ST>());
     // the opt-in covers dynamic + static shared memory (the sort order and, unless they
     // overlay the dynamic region, the keys) above 48 KB

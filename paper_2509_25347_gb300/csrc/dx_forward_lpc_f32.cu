@@ -104,7 +104,7 @@ dx_forward_lpc_f32(long long C, const double *rho_g, const double *rho_d, const 
         __shared__ unsigned short order[S::kTile];
         unsigned long long *key = reinterpret_cast<unsigned long long *>(smf);
         const long long base = (long long)blockIdx.x * rounds * S::kThreads;
-        dx_lpc_tile_order<NF - 1>(base, rounds, S::kThreads, C, rho_g, rho_d, t_s, dt, key, order);
+        dx_lpc_tile_order<NF - 1>(base, rounds, S::kThreads, C, C, rho_g, rho_d, t_s, dt, key, order);
         for (int r = 0; r < rounds; r++) {
             const long long c = base + order[r * S::kThreads + threadIdx.x];
             if (c < C) f32_cell<NF>(threadIdx.x, c, C, rho_g, rho_d, t_s, v_in, v_out, dt, status, K, smf);

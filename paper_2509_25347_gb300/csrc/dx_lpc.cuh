@@ -186,16 +186,17 @@ __device__ __forceinline__ unsigned int dx_lpc_cost_proxy(const double *rgp, con
 
 // Orders a tile of rounds x threads consecutive cells starting at base by the
 // cost proxy (ties by position): order[rank] = tile index, key: the tile's
-// scratch. Block-wide; ends with a barrier.
+// scratch. Cells at or past `end` are padding and sort last; C is the SoA
+// stride. Block-wide; ends with a barrier.
 template <int N>
-__device__ __forceinline__ void dx_lpc_tile_order(long long base, int rounds, int threads, long long C,
+__device__ __forceinline__ void dx_lpc_tile_order(long long base, int rounds, int threads, long long end, long long C,
                                                   const double *rho_g, const double *rho_d, const double *t_s,
                                                   double dt, unsigned long long *key, unsigned short *order) {
     const int tile = rounds * threads;
     for (int r = 0; r < rounds; r++) {
         const int e = r * threads + threadIdx.x;
         const long long c = base + e;
-        const unsigned int p = c < C ? dx_lpc_cost_proxy<N>(rho_g + c, rho_d + c, t_s + c, C, dt) : 0xffffffffu;
+        const unsigned int p = c < end ? dx_lpc_cost_proxy<N>(rho_g + c, rho_d + c, t_s + c, C, dt) : 0xffffffffu;
         key[e] = ((unsigned long long)p << 32) | (unsigned int)e;
     }
     __syncthreads();

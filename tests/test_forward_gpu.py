@@ -247,6 +247,36 @@ def test_tile_sorted_forward_small_and_prefix(dx, N):
     assert dx.get_status() == 0
 
 
+@pytest.mark.parametrize("N", [1, 4, 5])
+def test_balanced_blocks_forward_edges(dx, N):
+    """Register-storage sizes with more than 128 cells per SM run blocks of up
+    to 16 warps (8 at n = 6), a multiple of the SM count of them, each sorting
+    a contiguous share and dealing its groups to the warp slots in snake order.
+    Against the oracle (every cell): just past 128 cells per SM, the most one
+    block per SM takes, and one cell more (two blocks per SM). The first 128 x SMs
+    cells bit for bit against a one-block-per-SM tile-sorted launch on them;
+    the energy epilogue through the same kernel."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    top = sms * (512 if N <= 4 else 256)
+    low = 128 * sms
+    for C in (low + 1, top, top + 1):
+        cells = W.mrn(C, N, seed=900 + C % 89 + N, stiff_lo=-4.0, stiff_hi=8.0)
+        rg, rd, ts, v = dev(cells)
+        out = dx.apply(rg, rd, ts, cells.dt, v)
+        assert dx.get_status() == 0
+        ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v)
+        assert_parity(out.cpu().numpy(), ref, cells.v)
+        prg, prd, pts, pv = dev(cells.subset(np.arange(low)))
+        tiled = dx.apply(prg, prd, pts, cells.dt, pv)
+        assert torch.equal(tiled, out[:, :, :low])
+        hout, heat = dx.apply_heat(rg, rd, ts, cells.dt, v)
+        _, pheat = dx.apply_heat(prg, prd, pts, cells.dt, pv)
+        assert torch.equal(hout, out) and torch.equal(pheat, heat[:low])
+        assert bool(torch.isfinite(heat).all())
+        assert dx.get_status() == 0
+
+
 def test_binned_forward_wide_chunks(dx):
     """Above 64 chunks of 65,536 cells the binned forward widens its chunks
     (here 4,500,001 cells of N = 1: 64 chunks of 70,313 cells, the last one
