@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(bwd_threads<NF>()) dx_backward_lpc(BwdLpcArgs 
         }
     } else {
         for (int r = 0; r < rounds; r++) {
-            const long long c = base + order[r * kThreads + threadIdx.x];
+            const long long c = base + order[dx_lpc_round_pos(r, kThreads)];
             if (c < C) bwd_lpc_cell<NF, TAPE>(lane, c, a, K, bsh, wsm);
         }
     }

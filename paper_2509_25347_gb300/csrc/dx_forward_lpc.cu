@@ -74,7 +74,7 @@ dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d
     const int lane = threadIdx.x & 31;
     double *wsm = ST != DX_LPC_REGS ? smem + 32 + (threadIdx.x >> 5) * dx_lpc_warp_smem_doubles<NF, ST>() : nullptr;
     for (int r = 0; r < rounds; r++) {
-        const long long c = base + order[r * kThreads + threadIdx.x];
+        const long long c = base + order[dx_lpc_round_pos(r, kThreads)];
         if (c < C) {
             DxTapeCell tc{nullptr, nullptr, 0, 0};
             if (TAPE) tc = DxTapeCell{tp.hdr + c, tp.m + (size_t)c * tp.levels * tp.P, tp.levels, tp.P};

@@ -211,6 +211,16 @@ __device__ __forceinline__ void dx_lpc_tile_order(long long base, int rounds, in
     __syncthreads();
 }
 
+// Tile position of this thread's cell in round r of a multi-round tile. The
+// rounds' groups of 32 sorted cells are dealt to the block's warps in snake
+// order, warp w taking group w of even rounds and group nw - 1 - w of odd
+// ones, so that no warp (and so no SM sub-partition) holds the costliest group
+// of every round.
+__device__ __forceinline__ int dx_lpc_round_pos(int r, int threads) {
+    const int nw = threads >> 5, w = threadIdx.x >> 5;
+    return r * threads + 32 * ((r & 1) ? nw - 1 - w : w) + (threadIdx.x & 31);
+}
+
 // Per-lane set-up of one cell. Loads and validates rho_g, rho_d, t_s (integer
 // checks on bit patterns); forms eps_i = rho_d,i / rho_g and alpha_i = 1 / t_s,i
 // (Eqs. DragEqVar2, DragEqVar3) and the 1-norm of A = dt Omega_v summed in
