@@ -82,9 +82,12 @@ extern "C" {
  *              place) is allowed; other overlaps are not.
  *   stream   : CUDA stream for the launches.
  * Returns DRAG_OK or a DRAG_E* code (nothing launched on error).
- * Lane-per-cell sizes (N <= 8 with the default modes) on 262,144 cells or more
- * run the batched pipeline over one block: the cells are binned by (k*, s*)
- * first, so each warp runs 32 cells of equal cost. Its scratch (12 bytes per
+ * Lane-per-cell sizes (N <= 8 with the default modes) on enough cells run the
+ * batched pipeline over one block: the cells are binned by (k*, s*) first, so
+ * each warp runs 32 cells of equal cost. "Enough" is where that measured
+ * faster than one tile-sorted launch on GB300: 655,360 cells at N = 1,
+ * 163,840 at N = 2, 131,072 at N = 3, 98,304 at N = 4 and 5, 40,960 at N = 6
+ * and 7, 28,672 at N = 8 (drag_expm_apply_launches reports the choice). Its scratch (12 bytes per
  * cell) is taken stream-ordered from a memory pool private to the library,
  * which keeps what it once allocated; the launches stay capturable in a CUDA
  * graph. If no scratch can be had, the single tile-sorted kernel runs instead.
@@ -169,7 +172,8 @@ int drag_expm_apply_opts(int64_t ncells, int32_t nspecies, const double *rho_g, 
 /*
  * drag_expm_apply_host — drag_expm_apply on HOST arrays (same SoA layout,
  * stride ncells): the cells are processed in chunks of chunk_cells (0: 262,144
- * where drag_expm_apply bins that many cells, see there, else 131,072)
+ * where drag_expm_apply bins that many cells, N = 2..8 with the default
+ * modes, see there, else 131,072)
  * through a two-stream pipeline, so the host-to-device copies of one chunk
  * and the device-to-host copy of another overlap the update of a third. The
  * copies are asynchronous only from page-locked (pinned) host memory; with
@@ -235,11 +239,13 @@ int drag_expm_select_target(int64_t ncells, int32_t nspecies, const double *rho_
  * DragEqVar3, jacobian). The Frechet derivative is carried through the same
  * Algorithm 2 / Taylor / squaring steps as the forward (block-triangular
  * form [[A, E], [0, A]]), recomputing the forward on the fly (no storage).
- * Kernel family: one warp per cell, or, for N <= 5 under a lane-per-cell mode
+ * Kernel family: one warp per cell, or, for N <= 8 under a lane-per-cell mode
  * (the default there), one lane per cell. The lane-per-cell adjoint bins the
- * cells by (k*, s*) over the whole input from 262,144 cells on, with scratch
- * from the library's private stream-ordered pool (graph-capturable, 6 launches),
- * and sorts them by cost within tiles below (1 launch); both give the same bits.
+ * cells by (k*, s*) over the whole input, with scratch from the library's
+ * private stream-ordered pool (graph-capturable, 6 launches), from 32,768
+ * cells at N = 1, 24,576 at N = 2 and 4,096 at N = 3..8, and sorts them by
+ * cost within tiles below (1 launch; drag_expm_backward_launches reports the
+ * choice); both give the same bits.
  *   rho_g, rho_d, t_s, v_in : DEVICE inputs of the forward call (read only).
  *   grad_v_out : DEVICE, 3*(N+1)*ncells doubles, layout of v (read only).
  *   grad_v_in  : DEVICE, layout of v, written (may be NULL).
@@ -252,6 +258,11 @@ int drag_expm_backward(int64_t ncells, int32_t nspecies, const double *rho_g, co
                        const double *t_s, double dt, const double *v_in, const double *grad_v_out,
                        double *grad_v_in, double *grad_rho_g, double *grad_rho_d, double *grad_t_s,
                        cudaStream_t stream);
+
+/* drag_expm_backward_launches — number of kernels drag_expm_backward (and
+ * drag_expm_backward_taped) launch for (ncells, nspecies) with the current
+ * device's mode table (0 for bad sizes). */
+int32_t drag_expm_backward_launches(int64_t ncells, int32_t nspecies);
 
 /*
  * Adjoint tape. The adjoint needs every restored iterate E_t = exp(2^(t-s*) S)
@@ -289,7 +300,8 @@ int32_t drag_expm_tape_levels(int32_t sstar);
  * drag_expm_apply_taped — drag_expm_apply that also writes the adjoint tape.
  * v_out is bit-identical to drag_expm_apply's under the same mode table: the
  * taped forward runs the same kernel family, lane per cell for N <= 11 with the
- * default modes (binned from 262,144 cells up to N = 8, tile-sorted otherwise),
+ * default modes (binned up to N = 8 from the sizes drag_expm_apply bins,
+ * tile-sorted otherwise),
  * one warp per cell for other sizes.
  *   levels : tape capacity per cell, 1 .. DRAG_TAPE_MAX_LEVELS.
  *   tape   : DEVICE, 256-byte aligned, >= drag_expm_tape_bytes(ncells,

@@ -16,7 +16,7 @@ import os
 __all__ = [
     "load_library", "apply", "apply_heat", "backward", "rk1_apply", "apply_batched", "batched_workspace_bytes",
     "select", "get_status", "theta", "DragExpm", "DragExpmError", "apply_opts", "pade_theta", "apply_host",
-    "host_workspace_bytes", "apply_launches", "apply_taped", "Tape", "tape_bytes", "tape_levels", "tape_levels_needed",
+    "host_workspace_bytes", "apply_launches", "backward_launches", "apply_taped", "Tape", "tape_bytes", "tape_levels", "tape_levels_needed",
     "DragExpmTaped", "probe_fp64_rate", "probe_square", "NMAX", "STATUS_BAD_CELL", "STATUS_BAD_BLOCK", "STATUS_QUEUE_GUARD"
 ]
 
@@ -96,6 +96,8 @@ def load_library(path: str | None = None):
                                              ctypes.c_size_t, vp]
     lib.drag_expm_apply_launches.restype = ctypes.c_int32
     lib.drag_expm_apply_launches.argtypes = [i64, i32]
+    lib.drag_expm_backward_launches.restype = ctypes.c_int32
+    lib.drag_expm_backward_launches.argtypes = [i64, i32]
     lib.drag_expm_probe_fp64_rate.restype = ctypes.c_int
     lib.drag_expm_probe_fp64_rate.argtypes = [i32, i64, vp, ctypes.POINTER(ctypes.c_double), vp]
     lib.drag_expm_probe_square.restype = ctypes.c_int
@@ -205,6 +207,11 @@ def _f64_host(name, t, shape):
 def apply_launches(ncells: int, nspecies: int) -> int:
     """Kernels :func:`apply` launches for this size (the binned path launches 6)."""
     return int(load_library().drag_expm_apply_launches(int(ncells), int(nspecies)))
+
+
+def backward_launches(ncells: int, nspecies: int) -> int:
+    """Kernels drag_expm_backward launches for this size (0: bad size)."""
+    return int(load_library().drag_expm_backward_launches(int(ncells), int(nspecies)))
 
 
 def host_workspace_bytes(nspecies: int, chunk_cells: int = 0) -> int:

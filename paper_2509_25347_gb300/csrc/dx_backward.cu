@@ -698,6 +698,14 @@ extern "C" int drag_expm_backward(int64_t ncells, int32_t nspecies, const double
                          grad_t_s, 0, nullptr, 0, false, stream);
 }
 
+extern "C" int32_t drag_expm_backward_launches(int64_t ncells, int32_t nspecies) {
+    if (ncells <= 0 || nspecies < 1 || nspecies > DRAG_EXPM_NMAX) return 0;
+    const int n = nspecies + 1;
+    const bool binned = n <= DX_BWD_LPC_NMAX && dx_mode_for(n) != DX_MODE_WPC &&
+                        ncells >= dx_binned_min_cells(n, true) && ncells <= 0x7fffffffLL;
+    return binned ? 6 : 1;
+}
+
 extern "C" int drag_expm_backward_taped(int64_t ncells, int32_t nspecies, const double *rho_g, const double *rho_d,
                                         const double *t_s, double dt, const double *v_in, const double *grad_v_out,
                                         double *grad_v_in, double *grad_rho_g, double *grad_rho_d, double *grad_t_s,

@@ -470,7 +470,7 @@ int launch(const BwdLpcArgs &a, cudaStream_t stream) {
     const size_t smem = sizeof(double) * (32 + (size_t)(kThreads / 32) * BwdLpcStore<NF>::kWarpDoubles);
     constexpr size_t kStatic =
         BwdLpcStore<NF>::kHybrid ? 16 : kTile * (sizeof(unsigned long long) + sizeof(unsigned short));
-    if (a.C >= DX_BINNED_MIN_CELLS) {
+    if (a.C >= dx_binned_min_cells(NF, true) && a.C <= 0x7fffffffLL) {
         const unsigned long long *perm = nullptr;
         void *scratch = dx_binned_perm(dx_consts(), a.C, NF - 1, a.rho_g, a.rho_d, a.t_s, a.dt, a.status, stream, &perm);
         if (scratch) {

@@ -24,6 +24,7 @@
 // stream-ordered memory pool. Binning by (k*, s*) over the whole input gives
 // every warp 32 cells of one Taylor order and squaring count, where the plain
 // lane-per-cell kernel can only sort within a tile of 512 cells.
+#include <climits>
 #include <cmath>
 #include <mutex>
 
@@ -632,7 +633,6 @@ extern "C" int drag_expm_apply_batched_noalloc(int64_t nblocks, const drag_block
 
 namespace {
 
-constexpr long long kBinnedMinCells = DX_BINNED_MIN_CELLS;
 
 std::mutex g_pool_mu;
 cudaMemPool_t g_pool[64];
@@ -669,8 +669,29 @@ __global__ void dx_batch_single_desc(Desc *d, long long C, int N, double dt) {
 
 }  // namespace
 
+// Smallest input from which binning the whole input by (chunk, k*, s*) beats
+// one tile-sorted launch: the crossovers measured on GB300 (CUDA events, cold
+// L2, the MRN-like workloads, n = 2..9). Binning pays earlier for larger n,
+// whose per-warp work varies more with (k*, s*), and much earlier for the
+// adjoint, whose squarings cost 5x the forward's; at n = 2 the forward's five
+// binning launches outweigh the gain up to ~600k cells. Building with
+// -DDX_BINNED_MIN_CELLS=<cells> sets one threshold for every n (measurements).
+long long dx_binned_min_cells(int n, bool adjoint) {
+#ifdef DX_BINNED_MIN_CELLS
+    (void)adjoint;
+    return n >= 2 && n <= kBatchLpcNMax ? (long long)(DX_BINNED_MIN_CELLS) : LLONG_MAX;
+#else
+    static constexpr long long kForward[kBatchLpcNMax + 1] = {0, 0, 655360, 163840, 131072, 98304, 98304,
+                                                              40960, 40960, 28672};
+    static constexpr long long kAdjoint[kBatchLpcNMax + 1] = {0, 0, 32768, 24576, 4096, 4096, 4096,
+                                                              4096, 4096, 4096};
+    if (n < 2 || n > kBatchLpcNMax) return LLONG_MAX;
+    return adjoint ? kAdjoint[n] : kForward[n];
+#endif
+}
+
 bool dx_binned_eligible(int n, int mode, long long C) {
-    return n >= 2 && n <= kBatchLpcNMax && mode == dx_batch_modes().m[n] && C >= kBinnedMinCells &&
+    return n >= 2 && n <= kBatchLpcNMax && mode == dx_batch_modes().m[n] && C >= dx_binned_min_cells(n, false) &&
            C <= 0x7fffffffLL;
 }
 

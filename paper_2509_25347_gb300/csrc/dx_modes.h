@@ -42,12 +42,11 @@ int dx_launch_forward_lpc_f32(const DxConsts &K, int n, long long C, const doubl
 
 // Binned lane-per-cell forward (dx_batched.cu): the batched pipeline with one
 // block over the whole input, for sizes whose batched mode is the current mode
-// (n <= 9) and at least 262,144 cells. DX_BINNED_UNAVAILABLE: no scratch could
-// be had; the caller runs the tile-sorted kernel instead.
+// (n <= 9) and at least dx_binned_min_cells(n, false) cells. The lane-per-cell
+// adjoint bins from dx_binned_min_cells(n, true) cells. DX_BINNED_UNAVAILABLE:
+// no scratch could be had; the caller runs the tile-sorted kernel instead.
 #define DX_BINNED_UNAVAILABLE 1
-#ifndef DX_BINNED_MIN_CELLS
-#define DX_BINNED_MIN_CELLS 262144   // below: the tile-sorted kernels (one launch) are as fast
-#endif
+long long dx_binned_min_cells(int n, bool adjoint);
 bool dx_binned_eligible(int n, int mode, long long C);
 // thdr (null: none): also writes the adjoint tape (geometry as in drag_expm_apply_taped).
 int dx_binned_forward(const DxConsts &K, long long C, int N, const double *rho_g, const double *rho_d,

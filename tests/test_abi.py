@@ -157,6 +157,8 @@ def test_host_argument_errors(lib):
     assert bwd(0, 4, null, null, null, 1.0, null, null, null, null, null, null, s) == 0
     assert lib.drag_expm_apply_launches(-1, 4) == 0 and lib.drag_expm_apply_launches(0, 4) == 0
     assert lib.drag_expm_apply_launches(10, 0) == 0 and lib.drag_expm_apply_launches(10, 32) == 0
+    assert lib.drag_expm_backward_launches(-1, 4) == 0 and lib.drag_expm_backward_launches(0, 4) == 0
+    assert lib.drag_expm_backward_launches(10, 0) == 0 and lib.drag_expm_backward_launches(10, 32) == 0
     # adjoint tape: geometry, then argument errors of the taped forward and adjoint
     tb = lib.drag_expm_tape_bytes
     assert tb(-1, 4, 3) == 0 and tb(10, 0, 3) == 0 and tb(10, 4, 0) == 0 and tb(10, 4, 2049) == 0

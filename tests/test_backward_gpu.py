@@ -18,6 +18,7 @@ import pytest
 
 import oracle
 from paper_2509_25347_gb300 import workloads as W
+from tests.dispatch_sizes import binned_threshold
 from tests.test_oracle_adjoint_pins import assert_fd_agreement, finite_difference_gradients, loss_scale
 
 pytestmark = pytest.mark.gpu
@@ -273,18 +274,21 @@ def test_lane_per_cell_backward_full_size_sampled(dx):
 
 @pytest.mark.parametrize("N", [1, 4, 5, 6, 8])
 def test_lane_per_cell_backward_binned(dx, N):
-    """From 262,144 cells the lane-per-cell adjoint bins the cells by (k*, s*)
-    over the whole input before running them: its gradients equal, bit for bit,
-    those of the tile-sorted kernel that runs on fewer cells (the per-cell
+    """From its binning size on (per N, as the library reports it) the
+    lane-per-cell adjoint bins the cells by (k*, s*) over the whole input
+    before running them: its gradients equal, bit for bit, those of the
+    tile-sorted kernel that runs on the cells below that size (the per-cell
     arithmetic does not depend on the grouping), and sampled cells match the
     oracle's adjoint; through the tape they are unchanged."""
     import torch
     C = 300007
+    thr = binned_threshold(dx, N, adjoint=True)
+    assert dx.backward_launches(C, N) == 6 and dx.backward_launches(thr - 1, N) == 1
     cells = W.mrn(C, N, seed=410 + N, stiff_lo=-5.0, stiff_hi=8.0)
     g_np = np.random.default_rng(41 + N).standard_normal(cells.v.shape)
     rg, rd, ts, v, g = t(cells.rho_g), t(cells.rho_d), t(cells.t_s), t(cells.v), t(g_np)
     binned = [x.cpu().numpy() for x in dx.backward(rg, rd, ts, cells.dt, v, g)]
-    head = np.arange(200003)
+    head = np.arange(thr - 1)
     sub = cells.subset(head)
     tiled = gpu_backward(dx, sub, g_np[:, :, head])
     for a, b in zip(binned, tiled):

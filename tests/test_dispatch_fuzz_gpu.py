@@ -1,5 +1,6 @@
 """Seeded random cases across the dispatch boundaries of drag_expm_apply and the
-adjoint tape: sizes below and above the binning threshold (262,144 cells),
+adjoint tape: sizes below, at and above the forward's and the adjoint's binning
+sizes (per N, as the library reports them),
 species counts on every kernel family (lane per cell in registers, hybrid, warp
 per cell), ragged cell counts, random stiffness ranges and time steps. The
 forward is checked against the oracle on sampled cells at 1e-13 of the velocity
@@ -11,6 +12,7 @@ import pytest
 
 import oracle
 from paper_2509_25347_gb300 import workloads as W
+from tests.dispatch_sizes import binned_threshold
 from tests.test_backward_gpu import assert_adjoint_parity
 
 pytestmark = pytest.mark.gpu
@@ -36,9 +38,9 @@ def t(a):
 def cases():
     rng = np.random.default_rng(2024)
     out = []
-    for k in range(10):
+    for k in range(16):
         N = int(rng.choice([1, 3, 5, 6, 7, 8, 11, 12, 16, 20]))
-        C = int(rng.choice([1, 31, 4097, 262143, 262145, 300007]))
+        C = str(rng.choice(["1", "31", "4097", "below", "at", "above", "adj_below", "adj_at", "300007"]))
         lo = float(rng.uniform(-6.0, 0.0))
         hi = float(rng.uniform(lo + 4.5, 9.0))
         dt = float(2.0 ** -int(rng.integers(0, 5)))
@@ -46,9 +48,21 @@ def cases():
     return out
 
 
+def resolve_size(dx, N, label):
+    """A size label of cases() as a cell count: a number, or one relative to
+    the forward's ("below", "at", "above") or the adjoint's ("adj_below",
+    "adj_at") binning size; 262,144 stands in for sizes that never bin."""
+    if label.isdigit():
+        return int(label)
+    adj = label.startswith("adj_")
+    thr = binned_threshold(dx, N, adjoint=adj) or 262144
+    return thr + {"below": -1, "at": 0, "above": 1}[label.split("_")[-1]]
+
+
 @pytest.mark.parametrize("k,N,C,lo,hi,dt", cases())
 def test_dispatch_fuzz(dx, k, N, C, lo, hi, dt):
     import torch
+    C = resolve_size(dx, N, C)
     cells = W.mrn(C, N, seed=5000 + k, stiff_lo=lo, stiff_hi=hi, dt=dt, t_ref=1.0)
     rg, rd, ts, v = t(cells.rho_g), t(cells.rho_d), t(cells.t_s), t(cells.v)
     out = dx.apply(rg, rd, ts, dt, v)
@@ -94,7 +108,7 @@ def test_targets_above_binning_threshold(dx, N, ubits):
 @pytest.mark.parametrize("N,C,chunk", [(4, 600011, 0), (8, 524300, 0), (16, 300001, 65536), (3, 270000, 100000)])
 def test_host_pipeline_large(dx, N, C, chunk):
     """drag_expm_apply_host over several chunks, binned ones included (default
-    chunk 262,144 for N <= 8): bit-identical to drag_expm_apply on the device."""
+    chunk 262,144 for N = 2..8): bit-identical to drag_expm_apply on the device."""
     import torch
     cells = W.mrn(C, N, seed=90 + N, stiff_lo=-4.0, stiff_hi=8.0)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()

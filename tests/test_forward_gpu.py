@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 from paper_2509_25347_gb300 import workloads as W
+from tests.dispatch_sizes import binned_threshold
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-13
@@ -173,7 +174,7 @@ def test_full_size_sampled(dx, name):
 @pytest.mark.parametrize("N", [1, 4, 7, 9])
 def test_sorted_tiles_parity(dx, N):
     """320,077 cells, every cell against the oracle, through both lane-per-cell
-    paths: the binned pipeline (the default at this size for N <= 8) and the
+    paths: the binned pipeline (the default at this size for N = 2..8) and the
     tile-sorted kernel (each tile of up to 512 cells sorted by a cost proxy,
     ragged last tile; forced here by the all-shared storage mode)."""
     cells = W.mrn(320077, N, seed=900 + N, stiff_lo=-4.0, stiff_hi=8.0)
@@ -193,17 +194,19 @@ def test_sorted_tiles_parity(dx, N):
 
 @pytest.mark.parametrize("N", [1, 4, 6, 8])
 def test_binned_forward(dx, N):
-    """From 262,144 cells the default lane-per-cell sizes run the batched
-    pipeline over one block (6 launches). The per-cell arithmetic is that of
-    the tile-sorted kernel, which drag_expm_apply_heat always uses: identical
-    v_out. In place, invalid cells (NaN and the status bit) and dt = 0 too."""
+    """From its binning size on (per N, as the library reports it) a default
+    lane-per-cell size runs the batched pipeline over one block (6 launches).
+    The per-cell arithmetic is that of the tile-sorted kernel, which
+    drag_expm_apply_heat always uses: identical v_out. In place, invalid cells
+    (NaN and the status bit) and dt = 0 too."""
     import torch
-    C = 300001
+    thr = binned_threshold(dx, N)
+    C = max(300001, thr + 17)
     cells = W.mrn(C, N, seed=40 + N, stiff_lo=-4.0, stiff_hi=8.0)
     cells.rho_d[0, 11] = np.nan
     cells.t_s[-1, 222222] = 0.0
     rg, rd, ts, v = dev(cells)
-    assert dx.apply_launches(C, N) == 6 and dx.apply_launches(262143, N) == 1
+    assert dx.apply_launches(C, N) == 6 and dx.apply_launches(thr - 1, N) == 1
     out = dx.apply(rg, rd, ts, cells.dt, v)
     assert dx.get_status() & dx.STATUS_BAD_CELL
     heat_out, _ = dx.apply_heat(rg, rd, ts, cells.dt, v)
@@ -224,21 +227,22 @@ def test_binned_forward(dx, N):
 
 @pytest.mark.parametrize("N", [1, 3, 5])
 def test_tile_sorted_forward_small_and_prefix(dx, N):
-    """Below 262,144 cells the register-storage sizes (n <= 6) run one tile-sorted
-    launch. Ragged sizes (part of a CTA, one cell) against the oracle; and, since
-    the per-cell routine is the binned pipeline's, the first 200,003 cells of a
-    300,001-cell input give the binned run's v_out bit for bit."""
+    """Below its binning size a register-storage size (n <= 6) runs one
+    tile-sorted (or balanced-block) launch. Ragged sizes (part of a CTA, one
+    cell) against the oracle; and, since the per-cell routine is the binned
+    pipeline's, the cells below the binning size of an input ~100,000 cells
+    above it give the binned run's v_out bit for bit."""
     import torch
     for C in (1, 100, 1025, 32785):
         cells = W.mrn(C, N, seed=70 + C % 97 + N, stiff_lo=-5.0, stiff_hi=8.0)
         ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v)
         assert dx.apply_launches(C, N) == 1
         assert_parity(gpu_apply(dx, cells), ref, cells.v)
-    C = 300001
+    thr = binned_threshold(dx, N)
+    C, head = thr + 99998, thr - 1
     cells = W.mrn(C, N, seed=80 + N, stiff_lo=-4.0, stiff_hi=8.0)
     rg, rd, ts, v = dev(cells)
     binned = dx.apply(rg, rd, ts, cells.dt, v)
-    head = 200003
     sub = cells.subset(np.arange(head))
     srg, srd, sts, sv = dev(sub)
     tiled = dx.apply(srg, srd, sts, cells.dt, sv)

@@ -319,7 +319,7 @@ def test_taped_finite_differences_64_cells(dx):
 
 @pytest.mark.parametrize("N", [4, 8])
 def test_binned_tape(dx, N):
-    """From 262,144 cells the lane-per-cell taped forward runs the binned
+    """Above its binning size the lane-per-cell taped forward runs the binned
     pipeline (6 launches), writing the same tape: v_out equals drag_expm_apply's
     bit for bit, and the taped gradients match the recomputing adjoint's to the
     adjoint tolerance on 1,500 sampled cells."""
