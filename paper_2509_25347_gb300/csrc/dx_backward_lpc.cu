@@ -272,6 +272,7 @@ __device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpc
                 dx_lpc_horner_step<NF>(Fr, Gm, xs, ds, bsh[jb]);
                 dx_lane_take(Fr, Gm);
             }
+            dx_lpc_taylor_finish<NF>(Fr, xs);
             dx_lpc_restore<NF>(Fr, sig, tau);
 #pragma unroll
             for (int e = 0; e < NT; e++) Fm[e] = Fr[e];
@@ -309,6 +310,7 @@ __device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpc
 #pragma unroll
             for (int e = 0; e < NT; e++) Fm[e] = tcell[e];
         } else {
+            dx_lpc_taylor_finish<NF>(Fm, xs);
             dx_lpc_restore<NF>(Fm, sig, tau);
         }
     }
@@ -351,7 +353,7 @@ __device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpc
 #pragma unroll
         for (int i = 0; i < N; i++) {
             eps[i] = __ddiv_rn(a.rho_d[i * C + c], rg);
-            alpha[i] = __ddiv_rn(1.0, a.t_s[i * C + c]);
+            alpha[i] = __drcp_rn(a.t_s[i * C + c]);
         }
     }
     if (a.g_vin) {

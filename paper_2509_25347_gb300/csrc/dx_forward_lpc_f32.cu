@@ -68,6 +68,7 @@ __device__ __forceinline__ void f32_cell(int lane, long long c, long long C, con
         dx_lpc_horner_step<NF>(Fm, Gm, xs, ds, K.b[j]);
         dx_lane_take(Fm, Gm);
     }
+    dx_lpc_taylor_finish<NF>(Fm, xs);
     dx_lpc_restore<NF>(Fm, sig, tau);
     for (int it = 0; it < s; it++) {
         dx_lpc_square_offdiag<NF>(Fm, Gm);

@@ -96,12 +96,30 @@ using DxElem = typename std::remove_reference<decltype(std::declval<A &>()[0])>:
 // exactly these operations, so a lane-per-cell adjoint that recomputes them
 // gets the values the forward's tape holds.
 
+// n = 2 (one dust species), FP64. The symmetric form X of a 2 x 2 generator
+// with zero row sums is singular (det X = 0), so Cayley-Hamilton gives
+// X^2 = tr(X) X and every polynomial in X is a I + b X. The Horner chain then
+// runs on the two coefficients, F X + b_j I = b_j I + (a + tr(X) b) X: one FMA
+// a step where the packed product takes six. While the chain runs, the packed
+// slots (0,0), (0,1), (1,1) hold a, b and tr(X); dx_lpc_taylor_finish turns
+// them into the matrix. The mixed-precision path keeps the matrix Horner.
+template <int NF, class FA>
+__host__ __device__ constexpr bool dx_lpc_coef_chain() {
+    return NF == 2 && std::is_same<DxElem<FA>, double>::value;
+}
+
 // F = b_m X + b_{m-1} I for the arrowhead X (xs: row 0, ds: diagonal).
 template <int NF, class FA, class VA>
 __device__ __forceinline__ void dx_lpc_taylor_init(FA &Fm, VA &xs, VA &ds, double bm_, double bm1_) {
     using P = DxPacked<NF>;
     using T = DxElem<FA>;
     const T bm = (T)bm_, bm1 = (T)bm1_;
+    if constexpr (dx_lpc_coef_chain<NF, FA>()) {
+        Fm[0] = bm1;
+        Fm[1] = bm;
+        Fm[2] = xs[0] + ds[1];
+        return;
+    }
 #pragma unroll
     for (int e = 0; e < P::NT; e++) Fm[e] = T(0);
     Fm[0] = fma(bm, xs[0], bm1);
@@ -119,6 +137,12 @@ __device__ __forceinline__ void dx_lpc_horner_step(FA &Fm, GA &Gm, VA &xs, VA &d
     using P = DxPacked<NF>;
     using T = DxElem<FA>;
     const T bj = (T)bj_;
+    if constexpr (dx_lpc_coef_chain<NF, FA>()) {
+        Gm[0] = bj;
+        Gm[1] = fma(Fm[2], Fm[1], Fm[0]);
+        Gm[2] = Fm[2];
+        return;
+    }
     T g00 = fma(Fm[0], xs[0], bj);
 #pragma unroll
     for (int k = 1; k < NF; k++) g00 = fma(Fm[P::at(0, k)], xs[k], g00);
@@ -133,11 +157,26 @@ __device__ __forceinline__ void dx_lpc_horner_step(FA &Fm, GA &Gm, VA &xs, VA &d
     Gm[0] = g00;
 }
 
-// Row-sum restoration E_ii = 1 - tau_i sum_{k != i} E_ik sigma_k.
+// Ends the Horner chain: nothing to do for the arrowhead chain; for the n = 2
+// coefficient chain, the off-diagonal entry b X_01 (the diagonal, which holds a
+// and tr(X) until then, is left to dx_lpc_restore, which every caller runs next).
+template <int NF, class FA, class VA>
+__device__ __forceinline__ void dx_lpc_taylor_finish(FA &Fm, VA &xs) {
+    if constexpr (dx_lpc_coef_chain<NF, FA>()) Fm[1] = Fm[1] * xs[1];
+}
+
+// Row-sum restoration E_ii = 1 - tau_i sum_{k != i} E_ik sigma_k (for n = 2
+// in FP64, with sigma_0 = tau_0 = 1, the two entries as single FMAs).
 template <int NF, class MA, class VA>
 __device__ __forceinline__ void dx_lpc_restore(MA &M, VA &sig, VA &tau) {
     using P = DxPacked<NF>;
     using T = DxElem<MA>;
+    if constexpr (dx_lpc_coef_chain<NF, MA>()) {
+        const T e01 = M[1];
+        M[0] = fma(-e01, sig[1], T(1));
+        M[2] = fma(-tau[1], e01, T(1));
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < NF; i++) {
         T acc = T(0);
@@ -253,7 +292,7 @@ __device__ __forceinline__ bool dx_lpc_setup(const double *rgp, const double *rd
 #pragma unroll
     for (int i = 0; i < N; i++) {
         eps[i] = __ddiv_rn(eps[i], rg);      // Eq. DragEqVar2
-        alpha[i] = __ddiv_rn(1.0, alpha[i]); // Eq. DragEqVar3
+        alpha[i] = __drcp_rn(alpha[i]);       // Eq. DragEqVar3
         s1 = __dadd_rn(s1, __dmul_rn(__dmul_rn(eps[i], alpha[i]), dt));
     }
     double col0 = s1;
@@ -277,7 +316,7 @@ __device__ __forceinline__ bool dx_lpc_setup(const double *rgp, const double *rd
         const double e = dx_bits(eps[i - 1]) < dx_bits(eps_floor) ? eps_floor : eps[i - 1];
         const double sg = __dsqrt_rn(e);
         sig[i] = sg;
-        tau[i] = __ddiv_rn(1.0, sg);
+        tau[i] = __drcp_rn(sg);
         xs[i] = __dmul_rn(__dmul_rn(sg, alpha[i - 1]), dx_scale2(dt, s));
         ds[i] = -dx_scale2(__dmul_rn(alpha[i - 1], dt), s);
     }
@@ -348,6 +387,7 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
         dx_lpc_horner_step<NF>(Fm, Gm, xs, ds, bsh[j]);
         dx_lane_take(Fm, Gm);
     }
+    dx_lpc_taylor_finish<NF>(Fm, xs);
 
     // ---------------- restore E_ii = 1 - tau_i sum_{k != i} E_ik sigma_k, then s squarings
     dx_lpc_restore<NF>(Fm, sig, tau);

@@ -52,7 +52,12 @@ def built_flops(N, k, s, warp_per_cell: bool) -> np.ndarray:
       3 (n (2n + 1) + n) = 6n^2 + 6n.
 
     Lane per cell: s* squarings and one application. Warp per cell: s* - q
-    squarings and 2^q applications, q = min(s*, 2)."""
+    squarings and 2^q applications, q = min(s*, 2).
+
+    Lane per cell at n = 2 (one dust species) the Taylor step runs on the two
+    coefficients of F = a I + b X (X^2 = tr(X) X): tr(X), one FMA per degree
+    and b X_01, 2 m - 1 in all; a restoration is two FMAs (4) and a squaring
+    one 2-term product and a restoration (8)."""
     n = N + 1
     k = np.asarray(k, dtype=np.int64)
     s = np.asarray(s, dtype=np.float64)
@@ -60,6 +65,8 @@ def built_flops(N, k, s, warp_per_cell: bool) -> np.ndarray:
     fixed = 13.0 * N + 3.0 * n + (m - 1.0) * (2.0 * n * n + 4.0 * n - 4.0) + 2.0 * n * n
     sq = n * n * (n + 1.0)
     app = 6.0 * n * n + 6.0 * n
+    if n == 2 and not warp_per_cell:
+        return 13.0 * N + (2.0 * m - 1.0) + 4.0 + s * 8.0 + app
     if warp_per_cell:
         q = np.minimum(s, APPLY_Q)
         return fixed + (s - q) * sq + np.exp2(q) * app
