@@ -169,6 +169,35 @@ __device__ __forceinline__ void bwd_lpc_ystep(WA &yv, VA &xs, VA &ds, WA &av, do
 template <int NF, bool TRIM, class FA, class LA, class NA>
 __device__ __forceinline__ void bwd_lpc_el_le(FA &Fm, LA &Lm, NA &Ln) {
     using P = DxPacked<NF>;
+    if constexpr (!TRIM && BwdLpcStore<NF>::kHybrid) {
+        // Hybrid storage (E in shared memory): a whole row of the new L at a
+        // time, its n sums side by side, so E_ik is loaded once for the row and
+        // row k of E once per k, and every step issues n independent FMAs.
+        // Each entry still sums E_ik L_kj, then L_ik E_kj, in ascending k: the
+        // same roundings as entry by entry (forward + adjoint on 262,144 cells of
+        // N = 8: 24.7 against 25.3 ms, 21.8 against 22.2 through the tape).
+#pragma unroll
+        for (int i = 0; i < NF; i++) {
+            double acc[NF];
+#pragma unroll
+            for (int j = 0; j < NF; j++) acc[j] = 0.0;
+#pragma unroll
+            for (int k = 0; k < NF; k++) {
+                const double e = dx_lane_ld(Fm, P::at(i, k));
+#pragma unroll
+                for (int j = 0; j < NF; j++) acc[j] = fma(e, Lm[k * NF + j], acc[j]);
+            }
+#pragma unroll
+            for (int k = 0; k < NF; k++) {
+                const double l = Lm[i * NF + k];
+#pragma unroll
+                for (int j = 0; j < NF; j++) acc[j] = fma(l, dx_lane_ld(Fm, P::at(k, j)), acc[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < NF; j++) Ln[i * NF + j] = acc[j];
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < NF; i++) {
 #pragma unroll

@@ -89,7 +89,9 @@ dx_forward_lpc(long long C, int rounds, const double *rho_g, const double *rho_d
 // slot, so one SM sub-partition (warp w runs on sub-partition w % 4) gets the
 // costliest group of every block. Instead: blocks of up to 16 warps, as many
 // as a multiple of the SM count, each on a contiguous share of C / gridDim.x
-// cells sorted by the cost proxy, with the sorted groups of 32 dealt to the
+// cells ordered by the cost proxy's half-octave (a counting sort, cheaper than
+// the rank sort: 15.7 against 17.1 us per launch at 32,768 cells of N = 1, the
+// same at N = 4), with the sorted groups of 32 dealt to the
 // warp slots in snake order over the four sub-partitions (costliest to 0, 1,
 // 2, 3, then 3, 2, 1, 0, ...), which pairs costly groups with cheap ones.
 // Groups are cut from the costly end, so the ragged one holds the cheapest
@@ -103,12 +105,12 @@ dx_forward_lpc_wave(long long C, const double *rho_g, const double *rho_d, const
                     double *v_out, double dt, uint32_t *status, double *heat, DxConsts K) {
     constexpr int kMax = 32 * lpc_wave_warps<NF>();
     __shared__ double bsh[32];
-    __shared__ unsigned long long key[kMax];
+    __shared__ unsigned int hist[128];
     __shared__ unsigned short order[kMax];
     const long long c0 = (long long)blockIdx.x * C / gridDim.x;
     const long long c1 = ((long long)blockIdx.x + 1) * C / gridDim.x;
     for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
-    dx_lpc_tile_order<NF - 1>(c0, 1, blockDim.x, c1, C, rho_g, rho_d, t_s, dt, key, order);
+    dx_lpc_bucket_order<NF - 1>(c0, c1, C, rho_g, rho_d, t_s, dt, hist, order);
     const int T = (int)(c1 - c0);
     const int q = threadIdx.x >> 5, row = q >> 2, sp = q & 3;
     const int k = 4 * row + ((row & 1) ? 3 - sp : sp);   // this slot's rank, costliest group first

@@ -250,6 +250,51 @@ __device__ __forceinline__ void dx_lpc_tile_order(long long base, int rounds, in
     __syncthreads();
 }
 
+// Orders the cells [c0, c1) of a block (c1 - c0 <= blockDim.x) by the
+// half-octave of the cost proxy: a counting sort over 128 buckets (norms from
+// 2^-31 to 2^32; the rest clamped to the end buckets), order[rank] = tile
+// index. One shared-memory atomic per cell instead of dx_lpc_tile_order's pass
+// over the whole tile; a warp's cells then share s* to within one. The order
+// within a bucket follows the atomics' timing, which changes no output (a
+// cell's arithmetic does not depend on its lane). hist: 128 words of shared
+// memory. Block-wide; ends with a barrier.
+template <int N>
+__device__ __forceinline__ void dx_lpc_bucket_order(long long c0, long long c1, long long C, const double *rho_g,
+                                                    const double *rho_d, const double *t_s, double dt,
+                                                    unsigned int *hist, unsigned short *order) {
+    constexpr int kBuckets = 128;
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const long long c = c0 + threadIdx.x;
+    int bucket = 0;
+    unsigned int slot = 0;
+    if (c < c1) {
+        const int h = (int)(dx_lpc_cost_proxy<N>(rho_g + c, rho_d + c, t_s + c, C, dt) >> 22) - 192;
+        bucket = h < 0 ? 0 : (h > kBuckets - 1 ? kBuckets - 1 : h);
+        slot = atomicAdd(&hist[bucket], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {   // exclusive scan of the counts, four buckets per lane
+        const int l = threadIdx.x;
+        const unsigned int v0 = hist[4 * l], v1 = hist[4 * l + 1], v2 = hist[4 * l + 2], v3 = hist[4 * l + 3];
+        const unsigned int tot = v0 + v1 + v2 + v3;
+        unsigned int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(DX_FULL, incl, o);
+            if (l >= o) incl += t;
+        }
+        const unsigned int ex = incl - tot;
+        hist[4 * l] = ex;
+        hist[4 * l + 1] = ex + v0;
+        hist[4 * l + 2] = ex + v0 + v1;
+        hist[4 * l + 3] = ex + v0 + v1 + v2;
+    }
+    __syncthreads();
+    if (c < c1) order[hist[bucket] + slot] = (unsigned short)threadIdx.x;
+    __syncthreads();
+}
+
 // Tile position of this thread's cell in round r of a multi-round tile. The
 // rounds' groups of 32 sorted cells are dealt to the block's warps in snake
 // order, warp w taking group w of even rounds and group nw - 1 - w of odd
@@ -260,21 +305,18 @@ __device__ __forceinline__ int dx_lpc_round_pos(int r, int threads) {
     return r * threads + 32 * ((r & 1) ? nw - 1 - w : w) + (threadIdx.x & 31);
 }
 
-// Per-lane set-up of one cell. Loads and validates rho_g, rho_d, t_s (integer
-// checks on bit patterns); forms eps_i = rho_d,i / rho_g and alpha_i = 1 / t_s,i
-// (Eqs. DragEqVar2, DragEqVar3) and the 1-norm of A = dt Omega_v summed in
-// ascending species order (as the oracle sums it, so (k*, s*) are reproducible);
-// runs Algorithm 2; and writes the scaled symmetric arrowhead X = 2^-s*
-// D_sigma A D_sigma^-1 (sig, tau: sigma and 1 / sigma; xs: row 0; ds: the
-// diagonal). With want_fp, fph is the XOR of the species' fingerprint terms over
-// the raw inputs. Dust-to-gas ratios below eps_floor are raised to it in the
-// symmetric form. Returns false for an invalid cell, before writing the vectors.
-template <int NF, class VA>
-__device__ __forceinline__ bool dx_lpc_setup(const double *rgp, const double *rdp, const double *tsp, long long stride,
-                                             double dt, const DxConsts &K, bool want_fp, double &rg,
-                                             double (&eps)[NF - 1], double (&alpha)[NF - 1], int &kk, int &s,
-                                             unsigned long long &fph, VA &sig, VA &tau, VA &xs, VA &ds,
-                                             double eps_floor = DX_EPS_FLOOR) {
+// Per-lane selection for one cell. Loads and validates rho_g, rho_d, t_s
+// (integer checks on bit patterns); forms eps_i = rho_d,i / rho_g and
+// alpha_i = 1 / t_s,i (Eqs. DragEqVar2, DragEqVar3) and the 1-norm of
+// A = dt Omega_v summed in ascending species order (as the oracle sums it, so
+// (k*, s*) are reproducible); runs Algorithm 2. s1 = -A_00 = sum_i eps_i
+// alpha_i dt. With want_fp, fph is the XOR of the species' fingerprint terms
+// over the raw inputs. Returns false for an invalid cell.
+template <int NF>
+__device__ __forceinline__ bool dx_lpc_select_cell(const double *rgp, const double *rdp, const double *tsp,
+                                                   long long stride, double dt, const DxConsts &K, bool want_fp,
+                                                   double &rg, double (&eps)[NF - 1], double (&alpha)[NF - 1],
+                                                   int &kk, int &s, unsigned long long &fph, double &s1) {
     constexpr int N = NF - 1;
     rg = *rgp;
     bool ok = dx_pos_finite(rg);
@@ -288,7 +330,7 @@ __device__ __forceinline__ bool dx_lpc_setup(const double *rgp, const double *rd
         alpha[i] = ts;
     }
     if (!ok) return false;
-    double s1 = 0.0;
+    s1 = 0.0;
 #pragma unroll
     for (int i = 0; i < N; i++) {
         eps[i] = __ddiv_rn(eps[i], rg);      // Eq. DragEqVar2
@@ -307,6 +349,16 @@ __device__ __forceinline__ bool dx_lpc_setup(const double *rgp, const double *rd
     const long long nb = dx_bits(col0) > cmax ? dx_bits(col0) : cmax;
     if (!dx_norm_ok(nb)) return false;
     dx_select(__longlong_as_double(nb), K, kk, s);
+    return true;
+}
+
+// The scaled symmetric arrowhead X = 2^-s* D_sigma A D_sigma^-1 of a selected
+// cell (sig, tau: sigma and 1 / sigma; xs: row 0; ds: the diagonal).
+// Dust-to-gas ratios below eps_floor are raised to it in the symmetric form.
+template <int NF, class VA>
+__device__ __forceinline__ void dx_lpc_arrowhead(const double (&eps)[NF - 1], const double (&alpha)[NF - 1],
+                                                 double dt, int s, double s1, VA &sig, VA &tau, VA &xs, VA &ds,
+                                                 double eps_floor) {
     sig[0] = 1.0;
     tau[0] = 1.0;
     xs[0] = dx_scale2(-s1, s);
@@ -320,6 +372,20 @@ __device__ __forceinline__ bool dx_lpc_setup(const double *rgp, const double *rd
         xs[i] = __dmul_rn(__dmul_rn(sg, alpha[i - 1]), dx_scale2(dt, s));
         ds[i] = -dx_scale2(__dmul_rn(alpha[i - 1], dt), s);
     }
+}
+
+// Per-lane set-up of one cell: dx_lpc_select_cell, then the symmetric
+// arrowhead X (dx_lpc_arrowhead). Returns false for an invalid cell, before
+// writing the vectors.
+template <int NF, class VA>
+__device__ __forceinline__ bool dx_lpc_setup(const double *rgp, const double *rdp, const double *tsp, long long stride,
+                                             double dt, const DxConsts &K, bool want_fp, double &rg,
+                                             double (&eps)[NF - 1], double (&alpha)[NF - 1], int &kk, int &s,
+                                             unsigned long long &fph, VA &sig, VA &tau, VA &xs, VA &ds,
+                                             double eps_floor = DX_EPS_FLOOR) {
+    double s1;
+    if (!dx_lpc_select_cell<NF>(rgp, rdp, tsp, stride, dt, K, want_fp, rg, eps, alpha, kk, s, fph, s1)) return false;
+    dx_lpc_arrowhead<NF>(eps, alpha, dt, s, s1, sig, tau, xs, ds, eps_floor);
     return true;
 }
 
@@ -330,18 +396,136 @@ __host__ __device__ constexpr int dx_lpc_warp_smem_doubles() {
                                : (ST == DX_LPC_HYBRID ? 32 * (DxPacked<NF>::NT + 4 * NF) : 0);
 }
 
+// Invalid cell: NaN outputs and the status bit.
+template <int NF>
+__device__ __forceinline__ void dx_lpc_fail_cell(double *vop, long long stride, double *heat, uint32_t *status) {
+#pragma unroll
+    for (int e = 0; e < 3 * NF; e++) vop[e * stride] = NAN;
+    if (heat) *heat = NAN;
+    atomicOr(status, DRAG_STATUS_BAD_CELL);
+}
+
+// Writes the cell's tape fingerprint (complemented when its s* - 1 levels do
+// not fit) and returns where its levels go, or null.
+template <int NF>
+__device__ __forceinline__ double *dx_lpc_tape_begin(const DxTapeCell &tp, unsigned long long fph, double rg,
+                                                     double dt, int s) {
+    if (!tp.hdr) return nullptr;
+    const long long h = dx_fingerprint_final(fph, rg, dt, dx_tape_salt(tp.levels, NF));
+    const bool fits = dx_tape_levels(s) <= tp.levels;
+    *tp.hdr = fits ? h : ~h;
+    return fits ? tp.m : nullptr;
+}
+
+// The restored iterates of one cell in the symmetric form: the Taylor step
+// F = b_m X + b_{m-1} I, F <- F X + b_j I (Horner in X), the restoration
+// E_ii = 1 - tau_i sum_{k != i} E_ik sigma_k, then s squarings, each restored.
+// Leaves E_s in Fm. tape (may be null): E_0 .. E_{tlev-1} stored at tape + t P.
+template <int NF, class FA, class GA, class VA>
+__device__ __forceinline__ void dx_lpc_chain(FA &Fm, GA &Gm, VA &sig, VA &tau, VA &xs, VA &ds, int m, int s,
+                                             const double *bsh, double *tape, int tlev, int P) {
+    constexpr int NT = DxPacked<NF>::NT;
+    dx_lpc_taylor_init<NF>(Fm, xs, ds, bsh[m], bsh[m - 1]);
+    for (int j = m - 2; j >= 0; j--) {
+        dx_lpc_horner_step<NF>(Fm, Gm, xs, ds, bsh[j]);
+        dx_lane_take(Fm, Gm);
+    }
+    dx_lpc_taylor_finish<NF>(Fm, xs);
+    dx_lpc_restore<NF>(Fm, sig, tau);
+    if (tape) {
+#pragma unroll
+        for (int e = 0; e < NT; e++) tape[e] = Fm[e];
+    }
+    for (int it = 0; it < s; it++) {
+        dx_lpc_square_offdiag<NF>(Fm, Gm);
+        dx_lpc_restore<NF>(Gm, sig, tau);
+        if (tape && it + 1 < tlev) {
+            double *lv = tape + (size_t)(it + 1) * P;
+#pragma unroll
+            for (int e = 0; e < NT; e++) lv[e] = Gm[e];
+        }
+        dx_lane_take(Fm, Gm);
+    }
+}
+
+// One cell of n = 2 (one dust species) in the velocity form. The propagator
+// of a 2 x 2 generator with zero row sums is P = I + W, W = [[-p, p], [q, -q]],
+// so the pair (p, q) carries the whole update. For X = 2^-s* A, with
+// x = X_01 and y = X_10, X^2 = -(x + y) X, so the Taylor polynomial is I + b X
+// with b = sum_{k=1..m} b_k (-(x + y))^(k-1) (Horner, one FMA a degree), and a
+// squaring maps W to 2 W + W^2 = (2 - p - q) W. Rows sum to one by
+// construction, and no square root is needed: the symmetric form is formed
+// only when the adjoint tape is written, by the symmetric steps the
+// lane-per-cell adjoint recomputes (dx_lpc_chain), so that taped and recomputed
+// gradients stay bit-identical. The outputs are v_0 + p (v_1 - v_0) and
+// v_1 - q (v_1 - v_0).
+__device__ __forceinline__ void dx_lpc2_forward_cell(const double *rgp, const double *rdp, const double *tsp,
+                                                     const double *vip, double *vop, long long stride, double dt,
+                                                     const DxConsts &K, const double *bsh, uint32_t *status,
+                                                     double *heat, const DxTapeCell &tp) {
+    double rg, eps[1], alpha[1], s1;
+    int kk, s;
+    unsigned long long fph;
+    if (!dx_lpc_select_cell<2>(rgp, rdp, tsp, stride, dt, K, tp.hdr != nullptr, rg, eps, alpha, kk, s, fph, s1)) {
+        dx_lpc_fail_cell<2>(vop, stride, heat, status);
+        return;
+    }
+    const int m = K.mk[kk];
+    double *tape = dx_lpc_tape_begin<2>(tp, fph, rg, dt, s);
+    if (tape) {
+        DxLaneArr<2, false> sig, tau, xs, ds;
+        DxLaneArr<3, false> Fm, Gm;
+        dx_lpc_arrowhead<2>(eps, alpha, dt, s, s1, sig, tau, xs, ds, DX_EPS_FLOOR);
+        dx_lpc_chain<2>(Fm, Gm, sig, tau, xs, ds, m, s, bsh, tape, dx_tape_levels(s), tp.P);
+    }
+    const double x = dx_scale2(s1, s), y = dx_scale2(__dmul_rn(alpha[0], dt), s);
+    const double tr = -(x + y);
+    double b = bsh[m];
+    for (int k = m - 1; k >= 1; k--) b = fma(tr, b, bsh[k]);
+    double p = b * x, q = b * y;
+    for (int it = 0; it < s; it++) {
+        const double u = 2.0 - (p + q);
+        p *= u;
+        q *= u;
+    }
+    double rd = 0.0, mass = 0.0, hsum = 0.0;
+    if (heat) {
+        rd = *rdp;
+        mass = rg + rd;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const double v0 = vip[(2 * d) * stride], v1 = vip[(2 * d + 1) * stride];
+        const double dv = v1 - v0;
+        const double o0 = fma(p, dv, v0), o1 = fma(-q, dv, v1);
+        vop[(2 * d) * stride] = o0;
+        vop[(2 * d + 1) * stride] = o1;
+        if (heat) {
+            const double vc = __ddiv_rn(fma(rd, v1, rg * v0), mass);
+            const double a0 = v0 - vc, b0 = o0 - vc, a1 = v1 - vc, b1 = o1 - vc;
+            hsum = fma(0.5 * rg, (a0 - b0) * (a0 + b0), hsum);
+            hsum = fma(0.5 * rd, (a1 - b1) * (a1 + b1), hsum);
+        }
+    }
+    if (heat) *heat = hsum;
+}
+
 // One cell per lane. Pointers address this cell; element (i) of a per-species
 // array is at p[i * stride]; velocity (d, f) at p[(d * NF + f) * stride].
 // smem_warp: this warp's slice (ST != DX_LPC_REGS); bsh: b_i = 1/i! in shared memory.
 // tp (tp.hdr null: none): the cell's adjoint tape, written as by the warp-per-cell
 // forward (the packed order here is the tape's): E_0 .. E_{s-2} when they fit,
-// the fingerprint word always.
+// the fingerprint word always. n = 2 takes the velocity form (dx_lpc2_forward_cell).
 template <int NF, int ST>
 __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp, const double *rdp, const double *tsp,
                                                     const double *vip, double *vop, long long stride, double dt,
                                                     const DxConsts &K, const double *bsh, double *smem_warp,
                                                     uint32_t *status, double *heat = nullptr,
                                                     DxTapeCell tp = DxTapeCell{nullptr, nullptr, 0, 0}) {
+    if constexpr (NF == 2) {
+        dx_lpc2_forward_cell(rgp, rdp, tsp, vip, vop, stride, dt, K, bsh, status, heat, tp);
+        return;
+    }
     constexpr int N = NF - 1;
     constexpr int NT = DxPacked<NF>::NT;
     using P = DxPacked<NF>;
@@ -365,46 +549,14 @@ __device__ __forceinline__ void dx_lpc_forward_cell(int lane, const double *rgp,
     unsigned long long fph;   // fingerprint of the raw inputs (tape)
     if (!dx_lpc_setup<NF>(rgp, rdp, tsp, stride, dt, K, tp.hdr != nullptr, rg, eps, alpha, kk, s, fph, sig, tau, xs,
                           ds)) {
-#pragma unroll
-        for (int e = 0; e < 3 * NF; e++) vop[e * stride] = NAN;
-        if (heat) *heat = NAN;
-        atomicOr(status, DRAG_STATUS_BAD_CELL);
+        dx_lpc_fail_cell<NF>(vop, stride, heat, status);
         return;
     }
     const int m = K.mk[kk];
-    double *tape = nullptr;
-    const int tlev = dx_tape_levels(s);
-    if (tp.hdr) {
-        const long long h = dx_fingerprint_final(fph, rg, dt, dx_tape_salt(tp.levels, NF));
-        const bool fits = tlev <= tp.levels;
-        *tp.hdr = fits ? h : ~h;
-        if (fits) tape = tp.m;
-    }
+    double *tape = dx_lpc_tape_begin<NF>(tp, fph, rg, dt, s);
 
-    // ---------------- Taylor: F = b_m X + b_{m-1} I, then F <- F X + b_j I (Horner in X)
-    dx_lpc_taylor_init<NF>(Fm, xs, ds, bsh[m], bsh[m - 1]);
-    for (int j = m - 2; j >= 0; j--) {
-        dx_lpc_horner_step<NF>(Fm, Gm, xs, ds, bsh[j]);
-        dx_lane_take(Fm, Gm);
-    }
-    dx_lpc_taylor_finish<NF>(Fm, xs);
-
-    // ---------------- restore E_ii = 1 - tau_i sum_{k != i} E_ik sigma_k, then s squarings
-    dx_lpc_restore<NF>(Fm, sig, tau);
-    if (tape) {
-#pragma unroll
-        for (int e = 0; e < NT; e++) tape[e] = Fm[e];
-    }
-    for (int it = 0; it < s; it++) {
-        dx_lpc_square_offdiag<NF>(Fm, Gm);
-        dx_lpc_restore<NF>(Gm, sig, tau);
-        if (tape && it + 1 < tlev) {
-            double *lv = tape + (size_t)(it + 1) * tp.P;
-#pragma unroll
-            for (int e = 0; e < NT; e++) lv[e] = Gm[e];
-        }
-        dx_lane_take(Fm, Gm);
-    }
+    // ---------------- Taylor, restoration and s squarings
+    dx_lpc_chain<NF>(Fm, Gm, sig, tau, xs, ds, m, s, bsh, tape, dx_tape_levels(s), tp.P);
 
     // ---------------- apply: v_out_i = E_ii v_i + tau_i sum_{k != i} E_ik sigma_k v_k
     double rho[NF];

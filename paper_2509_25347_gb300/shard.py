@@ -54,10 +54,11 @@ def built_flops(N, k, s, warp_per_cell: bool) -> np.ndarray:
     Lane per cell: s* squarings and one application. Warp per cell: s* - q
     squarings and 2^q applications, q = min(s*, 2).
 
-    Lane per cell at n = 2 (one dust species) the Taylor step runs on the two
-    coefficients of F = a I + b X (X^2 = tr(X) X): tr(X), one FMA per degree
-    and b X_01, 2 m - 1 in all; a restoration is two FMAs (4) and a squaring
-    one 2-term product and a restoration (8)."""
+    Lane per cell at n = 2 (one dust species) the update runs in the velocity
+    form on the off-diagonal pair (p, q) of P = I + W: set-up 10 (eps, alpha,
+    the norm's products and sums, x and y); Taylor -(x + y), one FMA per degree
+    and p = b x, q = b y, 2 (m - 1) + 3; a squaring (p, q) <- (2 - p - q)(p, q),
+    4; the application v_1 - v_0 and two FMAs per component, 15."""
     n = N + 1
     k = np.asarray(k, dtype=np.int64)
     s = np.asarray(s, dtype=np.float64)
@@ -66,7 +67,7 @@ def built_flops(N, k, s, warp_per_cell: bool) -> np.ndarray:
     sq = n * n * (n + 1.0)
     app = 6.0 * n * n + 6.0 * n
     if n == 2 and not warp_per_cell:
-        return 13.0 * N + (2.0 * m - 1.0) + 4.0 + s * 8.0 + app
+        return 10.0 + 2.0 * (m - 1.0) + 3.0 + s * 4.0 + 15.0
     if warp_per_cell:
         q = np.minimum(s, APPLY_Q)
         return fixed + (s - q) * sq + np.exp2(q) * app

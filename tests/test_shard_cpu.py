@@ -60,10 +60,10 @@ def test_built_flops_structure():
     # s* < 2: the warp-per-cell form squares nothing and applies 2^s* times
     assert shard.built_flops(4, np.array([1]), np.array([0]), True)[0] == shard.built_flops(4, np.array([1]),
                                                                                            np.array([0]), False)[0]
-    # n = 2 lane per cell: the coefficient chain, 2 FLOPs per degree and 8 per squaring
+    # n = 2 lane per cell: the velocity form, 2 FLOPs per degree and 4 per squaring
     one = shard.built_flops(1, np.array([6, 7]), np.array([3, 4]), False)
-    assert one[1] - one[0] == pytest.approx(2 * (20 - 16) + 8)
-    assert one[0] == pytest.approx(13 + 2 * 16 - 1 + 4 + 3 * 8 + 36)
+    assert one[1] - one[0] == pytest.approx(2 * (20 - 16) + 4)
+    assert one[0] == pytest.approx(10 + 2 * 15 + 3 + 3 * 4 + 15)
 
 
 def _free_port():
