@@ -66,10 +66,10 @@ KERNEL_SOURCES = {
 }
 MEASURED_TRAFFIC = {
     ("mrn_n16_128cube", "dx_forward_wpc"): {
-        "sources_sha256": "f950f6c493d2a33d0c91a98262307d52299e93c66fbed3697cfecb38b8e7fd88",
-        "bytes_per_cell": (188.071936e6 + 81.039104e6) / 262144,
-        # FP64 FLOPs the kernel executes: thread-level (2 DFMA + DADD + DMUL) per cycle x elapsed cycles
-        "executed_flop_per_cell": (2 * 231.801724 + 15.894142 + 3.616074) * 49135479.171 / 262144,
+        "sources_sha256": "572e7fe313d17009cb748ea49e0bc6c5a3b4bcd74181fb20ab96f30e08e1c737",
+        "bytes_per_cell": (186883328 + 79435776) / 262144,
+        # FP64 FLOPs the kernel executes: thread-level 2 DFMA + DADD + DMUL (sm__sass_thread_inst_executed_op_*)
+        "executed_flop_per_cell": (2 * 11389688778 + 780966306 + 177677552) / 262144,
         "capture": "profiles/dx_forward_wpc_mrn_n16.md",
     },
 }

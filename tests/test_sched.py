@@ -12,9 +12,10 @@ import pytest
 from paper_2509_25347_gb300 import sched
 
 
+@pytest.mark.parametrize("restore_first", [False, True])
 @pytest.mark.parametrize("n", list(range(2, 33)))
-def test_schedule_dependencies(n):
-    rounds, end = sched.schedule(n)
+def test_schedule_dependencies(n, restore_first):
+    rounds, end = sched.schedule(n, restore_first=restore_first)
     sched.check(n, rounds)
     assert len(end) == sched.H + 1
     assert all(end[h] <= end[h + 1] for h in range(sched.H))
@@ -28,12 +29,26 @@ def test_schedule_dependencies(n):
 
 def test_pipelining_saves_rounds():
     """Phase by phase a squaring costs ceil(n(n-1)/2/32) + ceil(n/32) rounds;
-    the pipelined schedule needs fewer on average."""
-    for n, expect in ((13, 3.5), (17, 5.05), (24, 9.6)):
-        rounds, end = sched.schedule(n)
+    the pipelined schedule the library uses needs fewer on average, at n = 17
+    within 1 % of the lane count's bound of (n(n-1)/2 + n) / 32."""
+    for n, expect in ((13, 3.5), (17, 4.8), (24, 9.6)):
+        rounds, end = sched.best_schedule(n)
+        sched.check(n, rounds)
         per = (end[32] - end[16]) / 16
         phased = -(-(n * (n - 1) // 2) // 32) + -(-n // 32)
         assert per <= expect < phased
+    rounds, end = sched.best_schedule(17)
+    assert len(rounds) <= 1.01 * (17 + 32 * (17 * 16 // 2 + 17)) / 32
+
+
+def test_best_schedule_is_the_shorter_order():
+    """Per n the library takes the order with fewer rounds summed over every
+    chunk length, never more than the products-first order."""
+    for n in range(2, 33):
+        a = sched.schedule(n)[1]
+        b = sched.schedule(n, restore_first=True)[1]
+        best = sched.best_schedule(n)[1]
+        assert sum(best) == min(sum(a), sum(b)) and sum(best) <= sum(a)
 
 
 def test_packing_and_header(tmp_path):
