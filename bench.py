@@ -66,10 +66,10 @@ KERNEL_SOURCES = {
 }
 MEASURED_TRAFFIC = {
     ("mrn_n16_128cube", "dx_forward_wpc"): {
-        "sources_sha256": "572e7fe313d17009cb748ea49e0bc6c5a3b4bcd74181fb20ab96f30e08e1c737",
-        "bytes_per_cell": (186883328 + 79435776) / 262144,
+        "sources_sha256": "a68f6f8cd8b67783a90a66af49e4631b7aa30ece23565c28767b8430b8713fc6",
+        "bytes_per_cell": (188609792 + 80553216) / 262144,
         # FP64 FLOPs the kernel executes: thread-level 2 DFMA + DADD + DMUL (sm__sass_thread_inst_executed_op_*)
-        "executed_flop_per_cell": (2 * 11389688778 + 780966306 + 177677552) / 262144,
+        "executed_flop_per_cell": (2 * 11389688778 + 642554274 + 164832496) / 262144,
         "capture": "profiles/dx_forward_wpc_mrn_n16.md",
     },
 }

@@ -196,19 +196,19 @@ __device__ __forceinline__ void bwd_lpc_el_le(FA &Fm, LA &Lm, NA &Ln) {
 #pragma unroll
             for (int j = 0; j < NF; j++) Ln[i * NF + j] = acc[j];
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int i = 0; i < NF; i++) {
+        for (int i = 0; i < NF; i++) {
 #pragma unroll
-        for (int j = 0; j < NF; j++) {
-            if (TRIM && i != 0 && j != 0 && i != j) continue;
-            double acc = 0.0;
+            for (int j = 0; j < NF; j++) {
+                if (TRIM && i != 0 && j != 0 && i != j) continue;
+                double acc = 0.0;
 #pragma unroll
-            for (int k = 0; k < NF; k++) acc = fma(dx_lane_ld(Fm, P::at(i, k)), Lm[k * NF + j], acc);
+                for (int k = 0; k < NF; k++) acc = fma(dx_lane_ld(Fm, P::at(i, k)), Lm[k * NF + j], acc);
 #pragma unroll
-            for (int k = 0; k < NF; k++) acc = fma(Lm[i * NF + k], dx_lane_ld(Fm, P::at(j, k)), acc);
-            Ln[i * NF + j] = acc;
+                for (int k = 0; k < NF; k++) acc = fma(Lm[i * NF + k], dx_lane_ld(Fm, P::at(j, k)), acc);
+                Ln[i * NF + j] = acc;
+            }
         }
     }
 }

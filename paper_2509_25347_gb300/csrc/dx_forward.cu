@@ -47,35 +47,94 @@ struct FwdTape {
     int levels, P;
 };
 
+// Cells of up to 16 species take their set-up two at a time
+// (dx_wpc_setup_pair): each warp then holds a second cell's vectors (4 n
+// doubles) while it runs the first.
+__host__ __device__ constexpr bool fwd_paired(int N) { return N <= 16; }
+
+// Per-warp shared memory of the FP64 forward (doubles), and the block's pair
+// tables: n(n-1)/2 + n(n+1)/2 - 1 shorts after the warps' slices.
+__host__ __device__ inline int fwd_warp_doubles(int n) {
+    return dx_wpc_fwd_warp_doubles(n) + (fwd_paired(n - 1) ? 4 * n : 0);
+}
+__host__ __device__ inline int fwd_pair_shorts(int n) { return n * (n - 1) / 2 + n * (n + 1) / 2 - 1; }
+
 template <bool TAPE>
 __device__ __forceinline__ void fwd_wpc_body(const FwdArgs &a, const DxConsts &K, const FwdTape &tp) {
     extern __shared__ double smem[];
-    const int n = a.N + 1;
+    const int n = a.N + 1, ns = dx_stride(n);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int wd = dx_wpc_fwd_warp_doubles(n);
+    const int wd = fwd_warp_doubles(n);
     unsigned short *od = reinterpret_cast<unsigned short *>(smem + kWarpsPerBlock * wd);
-    unsigned short *hp = od + kPairSlots;
+    unsigned short *hp = od + n * (n - 1) / 2;
     dx_build_pairs(n, od, hp);
     __syncthreads();
     double *wsm = smem + wib * wd;
-    // Each block owns kCellsPerBlock consecutive cells; its warps take them one
-    // at a time from a shared counter, so cells of different cost (s* varies
-    // per cell) balance inside the block, and the hardware block scheduler
-    // balances blocks across the SMs. At most kCellsPerBlock iterations.
+    // Each block owns kCellsPerBlock consecutive cells; its warps take them (one
+    // or two at a time) from a shared counter, so cells of different cost (s*
+    // varies per cell) balance inside the block, and the hardware block
+    // scheduler balances blocks across the SMs.
     __shared__ int next;
     if (threadIdx.x == 0) next = 0;
     __syncthreads();
     const long long base = (long long)blockIdx.x * kCellsPerBlock;
-    for (int it = 0; it < kCellsPerBlock; it++) {
+    if (!fwd_paired(a.N)) {
+        for (int it = 0; it < kCellsPerBlock; it++) {
+            int k = 0;
+            if (lane == 0) k = atomicAdd(&next, 1);
+            k = __shfl_sync(DX_FULL, k, 0);
+            const long long c = base + k;
+            if (k >= kCellsPerBlock || c >= a.C) break;
+            DxTapeCell tc{nullptr, nullptr, 0, 0};
+            if (TAPE) tc = DxTapeCell{tp.hdr + c, tp.m + (size_t)c * tp.levels * tp.P, tp.levels, tp.P};
+            dx_wpc_forward_cell(lane, a.N, a.rho_g + c, a.rho_d + c, a.t_s + c, a.v_in + c, a.v_out + c, a.C, a.dt,
+                                K, wsm, od, hp, a.status, a.heat ? a.heat + c : nullptr, (double *)nullptr, tc);
+        }
+        return;
+    }
+    double *E0 = wsm, *E1 = wsm + n * ns;
+    DxVecs V0;
+    DxFwdBufs B;
+    dx_wpc_fwd_layout(E1 + n * ns, n, V0, B);
+    double *v1 = wsm + dx_wpc_fwd_warp_doubles(n);
+    const DxVecs V1{v1, v1 + n, v1 + 2 * n, v1 + 3 * n};
+    const int h = lane >> 4, l = lane & 15;
+    for (int it = 0; it < kCellsPerBlock; it += 2) {
         int k = 0;
-        if (lane == 0) k = atomicAdd(&next, 1);
+        if (lane == 0) k = atomicAdd(&next, 2);
         k = __shfl_sync(DX_FULL, k, 0);
-        const long long c = base + k;
-        if (k >= kCellsPerBlock || c >= a.C) break;
-        DxTapeCell tc{nullptr, nullptr, 0, 0};
-        if (TAPE) tc = DxTapeCell{tp.hdr + c, tp.m + (size_t)c * tp.levels * tp.P, tp.levels, tp.P};
-        dx_wpc_forward_cell(lane, a.N, a.rho_g + c, a.rho_d + c, a.t_s + c, a.v_in + c, a.v_out + c, a.C, a.dt, K, wsm,
-                            od, hp, a.status, a.heat ? a.heat + c : nullptr, (double *)nullptr, tc);
+        const long long cA = base + k;
+        if (k >= kCellsPerBlock || cA >= a.C) break;
+        const int cells = (k + 1 < kCellsPerBlock && cA + 1 < a.C) ? 2 : 1;
+        // set-up inputs: half h takes cell cA + h (half 1 repeats cell cA when there is no
+        // second cell; its result is not used), lane 16 h + i - 1 its species i
+        const long long ch = cA + (h < cells ? h : 0);
+        const double rg = a.rho_g[ch];
+        double rd = 0.0, ts = INFINITY;
+        if (l < a.N) {
+            rd = a.rho_d[(long long)l * a.C + ch];
+            ts = a.t_s[(long long)l * a.C + ch];
+        }
+        int k0, s0, k1, s1;
+        const unsigned valid = dx_wpc_setup_pair(lane, a.N, rg, rd, ts, a.dt, K, V0, V1, k0, s0, k1, s1);
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            if (e >= cells) break;
+            const long long c = cA + e;
+            const DxVecs &V = e ? V1 : V0;
+            double *heat = a.heat ? a.heat + c : nullptr;
+            if (!((valid >> e) & 1u)) {
+                dx_wpc_fail_cell(lane, n, a.v_out + c, a.C, a.status, heat);
+                continue;
+            }
+            DxCellIn ci;
+            dx_wpc_load_cell(lane, a.N, a.rho_g + c, a.rho_d + c, a.t_s + c, a.v_in + c, a.C, ci);
+            DxTapeCell tc{nullptr, nullptr, 0, 0};
+            if (TAPE) tc = DxTapeCell{tp.hdr + c, tp.m + (size_t)c * tp.levels * tp.P, tp.levels, tp.P};
+            const double sg = lane < n ? V.sig[lane] : 1.0;
+            dx_wpc_forward_run(lane, a.N, V, E0, E1, B, e ? k1 : k0, e ? s1 : s0, sg, ci, a.v_out + c, a.C, a.dt, K,
+                               od, hp, heat, (double *)nullptr, tc);
+        }
     }
 }
 
@@ -173,7 +232,7 @@ int check_common(long long C, int N, const double *rho_g, const double *rho_d, c
 }  // namespace
 
 size_t dx_forward_smem_bytes(int n) {
-    return sizeof(double) * (size_t)kWarpsPerBlock * dx_wpc_fwd_warp_doubles(n) + 2 * kPairSlots * sizeof(unsigned short);
+    return sizeof(double) * (size_t)kWarpsPerBlock * fwd_warp_doubles(n) + fwd_pair_shorts(n) * sizeof(unsigned short);
 }
 
 size_t dx_forward_f32_smem_bytes(int n) {

@@ -118,15 +118,15 @@ __device__ __forceinline__ void dx_lpc_taylor_init(FA &Fm, VA &xs, VA &ds, doubl
         Fm[0] = bm1;
         Fm[1] = bm;
         Fm[2] = xs[0] + ds[1];
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int e = 0; e < P::NT; e++) Fm[e] = T(0);
-    Fm[0] = fma(bm, xs[0], bm1);
+        for (int e = 0; e < P::NT; e++) Fm[e] = T(0);
+        Fm[0] = fma(bm, xs[0], bm1);
 #pragma unroll
-    for (int i = 1; i < NF; i++) {
-        Fm[P::at(0, i)] = bm * xs[i];
-        Fm[P::at(i, i)] = fma(bm, ds[i], bm1);
+        for (int i = 1; i < NF; i++) {
+            Fm[P::at(0, i)] = bm * xs[i];
+            Fm[P::at(i, i)] = fma(bm, ds[i], bm1);
+        }
     }
 }
 
@@ -141,20 +141,20 @@ __device__ __forceinline__ void dx_lpc_horner_step(FA &Fm, GA &Gm, VA &xs, VA &d
         Gm[0] = bj;
         Gm[1] = fma(Fm[2], Fm[1], Fm[0]);
         Gm[2] = Fm[2];
-        return;
-    }
-    T g00 = fma(Fm[0], xs[0], bj);
+    } else {
+        T g00 = fma(Fm[0], xs[0], bj);
 #pragma unroll
-    for (int k = 1; k < NF; k++) g00 = fma(Fm[P::at(0, k)], xs[k], g00);
+        for (int k = 1; k < NF; k++) g00 = fma(Fm[P::at(0, k)], xs[k], g00);
 #pragma unroll
-    for (int jj = 1; jj < NF; jj++) {
+        for (int jj = 1; jj < NF; jj++) {
 #pragma unroll
-        for (int i = 0; i <= jj; i++) {
-            T acc = fma(Fm[P::at(i, 0)], xs[jj], i == jj ? bj : T(0));
-            Gm[P::at(i, jj)] = fma(Fm[P::at(i, jj)], ds[jj], acc);
+            for (int i = 0; i <= jj; i++) {
+                T acc = fma(Fm[P::at(i, 0)], xs[jj], i == jj ? bj : T(0));
+                Gm[P::at(i, jj)] = fma(Fm[P::at(i, jj)], ds[jj], acc);
+            }
         }
+        Gm[0] = g00;
     }
-    Gm[0] = g00;
 }
 
 // Ends the Horner chain: nothing to do for the arrowhead chain; for the n = 2
@@ -175,15 +175,15 @@ __device__ __forceinline__ void dx_lpc_restore(MA &M, VA &sig, VA &tau) {
         const T e01 = M[1];
         M[0] = fma(-e01, sig[1], T(1));
         M[2] = fma(-tau[1], e01, T(1));
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int i = 0; i < NF; i++) {
-        T acc = T(0);
+        for (int i = 0; i < NF; i++) {
+            T acc = T(0);
 #pragma unroll
-        for (int k = 0; k < NF; k++)
-            if (k != i) acc = fma(M[P::at(i, k)], sig[k], acc);
-        M[P::at(i, i)] = fma(-tau[i], acc, T(1));
+            for (int k = 0; k < NF; k++)
+                if (k != i) acc = fma(M[P::at(i, k)], sig[k], acc);
+            M[P::at(i, i)] = fma(-tau[i], acc, T(1));
+        }
     }
 }
 

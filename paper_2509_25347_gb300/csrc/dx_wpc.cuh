@@ -110,6 +110,69 @@ __device__ __forceinline__ bool dx_wpc_setup(int lane, int N, double rg, double 
     return true;
 }
 
+// Set-up of two cells at once, for N <= 16 in FP64: half-warp h (lanes
+// 16 h .. 16 h + 15) takes cell h, and its lane 16 h + i - 1 species i. The
+// species' divisions and square roots, and the norm's two ascending sums, then
+// run for both cells in the same instructions (a warp-wide FP64 instruction
+// costs the same with 16 or 32 lanes working). Every value is formed by the
+// operations dx_wpc_setup uses, in the same order, so the results are the same
+// bits. rg: this half's cell; rd, ts: this lane's species (anything past N).
+// Writes cell h's vectors (sigma, tau, X_0f, X_ff; fluid f at index f) to V0
+// or V1, and (k*, s*) of both cells to (k0, s0), (k1, s1c) on every lane.
+// Returns bit h set for a valid cell h.
+__device__ __forceinline__ unsigned dx_wpc_setup_pair(int lane, int N, double rg, double rd, double ts, double dt,
+                                                      const DxConsts &K, const DxVecs &V0, const DxVecs &V1, int &k0,
+                                                      int &s0, int &k1, int &s1c) {
+    const int h = lane >> 4, l = lane & 15, base = lane & 16;
+    const bool sp = l < N;
+    const bool okl = !sp || (dx_nonneg_finite(rd) && dx_pos_or_inf(ts));
+    const unsigned bad = __ballot_sync(DX_FULL, !okl);
+    bool ok = ((bad >> base) & 0xffffu) == 0 && dx_pos_finite(rg);
+    const double eps = sp ? __ddiv_rn(rd, rg) : 0.0;          // Eq. DragEqVar2
+    const double alpha = sp ? __ddiv_rn(1.0, ts) : 0.0;       // Eq. DragEqVar3
+    const double a0i = __dmul_rn(__dmul_rn(eps, alpha), dt);  // A_0i
+    const double ai0 = __dmul_rn(alpha, dt);                  // A_i0 = -A_ii
+    double s1 = 0.0;
+    for (int i = 0; i < N; i++) s1 = __dadd_rn(s1, dx_shfl(a0i, base + i));
+    double col0 = s1;
+    for (int i = 0; i < N; i++) col0 = __dadd_rn(col0, dx_shfl(ai0, base + i));
+    const double colj = sp ? __dadd_rn(a0i, ai0) : 0.0;
+    long long nb = dx_bits(colj);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+        const long long w = __shfl_xor_sync(DX_FULL, nb, o);
+        nb = w > nb ? w : nb;
+    }
+    nb = nb > dx_bits(col0) ? nb : dx_bits(col0);
+    ok = ok && dx_norm_ok(nb);
+    int k = 0, s = 0;
+    if (ok) dx_select(__longlong_as_double(nb), K, k, s);
+    k0 = __shfl_sync(DX_FULL, k, 0);
+    s0 = __shfl_sync(DX_FULL, s, 0);
+    k1 = __shfl_sync(DX_FULL, k, 16);
+    s1c = __shfl_sync(DX_FULL, s, 16);
+    const DxVecs V = h ? V1 : V0;
+    if (ok) {
+        if (sp) {
+            const double e = dx_bits(eps) < dx_bits(DX_EPS_FLOOR) ? DX_EPS_FLOOR : eps;
+            const double sg = __dsqrt_rn(e);
+            V.sig[l + 1] = sg;
+            V.tau[l + 1] = __ddiv_rn(1.0, sg);
+            V.xs[l + 1] = __dmul_rn(__dmul_rn(sg, alpha), dx_scale2(dt, s));
+            V.ds[l + 1] = -dx_scale2(ai0, s);
+        }
+        if (l == 0) {
+            V.sig[0] = 1.0;
+            V.tau[0] = 1.0;
+            V.xs[0] = dx_scale2(-s1, s);
+            V.ds[0] = -dx_scale2(0.0, s);
+        }
+    }
+    const unsigned valid = __ballot_sync(DX_FULL, ok);
+    __syncwarp();
+    return (valid & 1u) | ((valid >> 16) & 1u) << 1;
+}
+
 // F = b_m X + b_{m-1} I (arrowhead), written into a zeroed n x n buffer.
 template <typename T>
 __device__ __forceinline__ void dx_wpc_taylor_init(int lane, int n, int ns, int m, const DxConsts &K,
@@ -482,38 +545,24 @@ __device__ __forceinline__ void dx_wpc_apply_tail(int lane, int n, int ns, const
     __syncwarp();
 }
 
-// Forward update of one cell by one warp (warp-uniform arguments). Element i
-// of a per-species array is at p[i * stride]; velocity (d, f) at
-// p[(d * n + f) * stride]. od/hp: pair tables for this n. v_out may alias v_in.
-// heat: see dx_wpc_apply_tail. tp (FP64 only; tp.hdr null: none): the cell's
-// adjoint tape, written when its levels fit (the fingerprint word always).
+// The forward of one cell after its set-up (dx_wpc_setup or
+// dx_wpc_setup_pair): the Taylor step, s* - q squarings and 2^q applications.
+// V: the cell's vectors; E0, E1: the two matrix buffers; B: the apply buffers;
+// kk, s: (k*, s*); sg: sigma of this lane's fluid (1 past n); c: the cell's
+// inputs on the lanes. tp: see dx_wpc_forward_cell.
 template <typename T>
-__device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const double *rgp, const double *rdp,
-                                                    const double *tsp, const double *vip, double *vop,
-                                                    long long stride, double dt, const DxConsts &K, T *wsm,
-                                                    const unsigned short *od, const unsigned short *hp,
-                                                    uint32_t *status, double *heat = nullptr, T *wz = nullptr,
-                                                    DxTapeCell tp = DxTapeCell{nullptr, nullptr, 0, 0}) {
+__device__ __forceinline__ void dx_wpc_forward_run(int lane, int N, const DxVecsT<T> &V, T *E0, T *E1,
+                                                   const DxFwdBufsT<T> &B, int kk, int s, double sg,
+                                                   const DxCellIn &c, double *vop, long long stride, double dt,
+                                                   const DxConsts &K, const unsigned short *od,
+                                                   const unsigned short *hp, double *heat, T *wz, DxTapeCell tp) {
     const int n = N + 1, ns = dx_stride(n);
     const int n_hp = n * (n + 1) / 2 - 1;
-    T *E0 = wsm;
-    T *E1 = E0 + n * ns;
-    DxVecsT<T> V;
-    DxFwdBufsT<T> B;
-    dx_wpc_fwd_layout(E1 + n * ns, n, V, B);
-
-    DxCellIn c;
-    dx_wpc_load_cell(lane, N, rgp, rdp, tsp, vip, stride, c);
-    DxLane L;
-    if (!dx_wpc_setup(lane, N, c.rg, c.rd, c.ts, dt, K, V, L)) {
-        dx_wpc_fail_cell(lane, n, vop, stride, status, heat);
-        return;
-    }
-    const int m = K.mk[L.k];
+    const int m = K.mk[kk];
     double *tape = nullptr;
     if (sizeof(T) == sizeof(double) && tp.hdr) {
         const long long h = dx_cell_fingerprint(lane, N, c.rg, c.rd, c.ts, dt, dx_tape_salt(tp.levels, n));
-        const bool fits = dx_tape_levels(L.s) <= tp.levels;
+        const bool fits = dx_tape_levels(s) <= tp.levels;
         if (lane == 0) *tp.hdr = fits ? h : ~h;
         if (fits) tape = tp.m;
     }
@@ -537,7 +586,7 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
 
     // row-sum restoration, then s - q squarings (Eq. ExpEq1 with n = 2^s), each
     // restored; the remaining q squarings become 2^q applications
-    const int q = L.s < DX_APPLY_Q ? L.s : DX_APPLY_Q;
+    const int q = s < DX_APPLY_Q ? s : DX_APPLY_Q;
     if (wz) {
         // row i of wz: sigma with a zero at i (restorations as plain n-term loops)
         for (int t = lane; t < n * n; t += 32) {
@@ -546,6 +595,35 @@ __device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const doubl
         }
         __syncwarp();
     }
-    F = dx_wpc_square_chain(lane, n, ns, L.s - q, E0, E1, F == E1 ? 1 : 0, V, wz, tape, tp.P) ? E1 : E0;
-    dx_wpc_apply_tail(lane, n, ns, V, B, F, q, c, L.sg, vop, stride, heat);
+    F = dx_wpc_square_chain(lane, n, ns, s - q, E0, E1, F == E1 ? 1 : 0, V, wz, tape, tp.P) ? E1 : E0;
+    dx_wpc_apply_tail(lane, n, ns, V, B, F, q, c, sg, vop, stride, heat);
+}
+
+// Forward update of one cell by one warp (warp-uniform arguments). Element i
+// of a per-species array is at p[i * stride]; velocity (d, f) at
+// p[(d * n + f) * stride]. od/hp: pair tables for this n. v_out may alias v_in.
+// heat: see dx_wpc_apply_tail. tp (FP64 only; tp.hdr null: none): the cell's
+// adjoint tape, written when its levels fit (the fingerprint word always).
+template <typename T>
+__device__ __forceinline__ void dx_wpc_forward_cell(int lane, int N, const double *rgp, const double *rdp,
+                                                    const double *tsp, const double *vip, double *vop,
+                                                    long long stride, double dt, const DxConsts &K, T *wsm,
+                                                    const unsigned short *od, const unsigned short *hp,
+                                                    uint32_t *status, double *heat = nullptr, T *wz = nullptr,
+                                                    DxTapeCell tp = DxTapeCell{nullptr, nullptr, 0, 0}) {
+    const int n = N + 1, ns = dx_stride(n);
+    T *E0 = wsm;
+    T *E1 = E0 + n * ns;
+    DxVecsT<T> V;
+    DxFwdBufsT<T> B;
+    dx_wpc_fwd_layout(E1 + n * ns, n, V, B);
+
+    DxCellIn c;
+    dx_wpc_load_cell(lane, N, rgp, rdp, tsp, vip, stride, c);
+    DxLane L;
+    if (!dx_wpc_setup(lane, N, c.rg, c.rd, c.ts, dt, K, V, L)) {
+        dx_wpc_fail_cell(lane, n, vop, stride, status, heat);
+        return;
+    }
+    dx_wpc_forward_run(lane, N, V, E0, E1, B, L.k, L.s, L.sg, c, vop, stride, dt, K, od, hp, heat, wz, tp);
 }
