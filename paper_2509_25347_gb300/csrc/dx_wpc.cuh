@@ -516,12 +516,21 @@ __device__ __forceinline__ void dx_wpc_apply_tail(int lane, int n, int ns, const
 #pragma unroll 4
                 for (int k = 0; k < n; k++) acc = fma(F[i * ns + k], y[k], acc);
                 out = V.tau[i] * acc;
+            } else if (!last) {
+                // before the last application only sigma o v is carried: (sigma o P v)_i =
+                // sum_k E_ik (sigma o v)_k, one n-term sum (v itself is not formed)
+                for (int k = 0; k < n; k++) acc = fma(F[i * ns + k], y[k], acc);
+                ny[d * n + i] = acc;
+                continue;
             } else {
                 for (int qq = 0; qq < n - 1; qq++) {
                     const int k = qq + (qq >= i);
                     acc = fma(F[i * ns + k], y[k], acc);
                 }
-                out = fma(V.tau[i], acc, F[i * ns + i] * cv[d * n + i]);
+                // v_i: the input itself for a single application (dt = 0 returns v_in exactly),
+                // else tau_i (sigma o v)_i of the previous one
+                const T vi = ap == 0 ? cv[d * n + i] : V.tau[i] * y[i];
+                out = fma(V.tau[i], acc, F[i * ns + i] * vi);
             }
             if (!last) {
                 nv[d * n + i] = out;
