@@ -66,10 +66,10 @@ KERNEL_SOURCES = {
 }
 MEASURED_TRAFFIC = {
     ("mrn_n16_128cube", "dx_forward_wpc"): {
-        "sources_sha256": "a68f6f8cd8b67783a90a66af49e4631b7aa30ece23565c28767b8430b8713fc6",
-        "bytes_per_cell": (188609792 + 80553216) / 262144,
+        "sources_sha256": "f1c31650b1fa9d1b759dec060d36e87ce40ef1dc843da6a09808c6c11952e015",
+        "bytes_per_cell": (189389312 + 81047296) / 262144,
         # FP64 FLOPs the kernel executes: thread-level 2 DFMA + DADD + DMUL (sm__sass_thread_inst_executed_op_*)
-        "executed_flop_per_cell": (2 * 11389688778 + 642554274 + 164832496) / 262144,
+        "executed_flop_per_cell": (2 * 11389688778 + 642554274 + 99185602) / 262144,
         "capture": "profiles/dx_forward_wpc_mrn_n16.md",
     },
 }
