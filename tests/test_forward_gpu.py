@@ -368,3 +368,55 @@ def test_binned_forward_in_cuda_graph(dx):
     torch.cuda.synchronize()
     assert torch.equal(out, dx.apply(rg, rd, ts, cells.dt, v))
     assert dx.get_status() == 0
+
+
+@pytest.mark.parametrize("N", [12, 15, 16, 17])
+def test_paired_setup_matches_single_setup(dx, N):
+    """For N <= 16 the warp-per-cell forward sets up two cells at a time (one
+    half-warp each); the batched entry point's warp-per-cell items set up one
+    cell at a time, by the same operations. One block of 37 cells through both
+    (the last pair of a 16-cell block holds one cell), with invalid cells in
+    the first and the second slot of a pair: v_out equal bit for bit (NaN where
+    invalid), the valid cells against the oracle, the status bit set by both.
+    N = 17 (no pairing) checks the same against itself."""
+    import torch
+    C = 37
+    cells = W.mrn(C, N, seed=600 + N, stiff_lo=-4.0, stiff_hi=8.0)
+    cells.rho_d[N - 1, 5] = -1.0         # second cell of a pair
+    cells.t_s[0, 8] = 0.0                # first cell of a pair
+    cells.rho_g[36] = np.nan             # the lone cell of the last pair
+    bad = [5, 8, 36]
+    rg, rd, ts, v = dev(cells)
+    dx.get_status()
+    plain = dx.apply(rg, rd, ts, cells.dt, v)
+    assert dx.get_status() & dx.STATUS_BAD_CELL
+    desc, brg, brd, bts, bv = W.Batch([(N, cells.dt, cells)]).pack()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    batched = dx.apply_batched(desc, t(brg), t(brd), t(bts), t(bv)).reshape(plain.shape)
+    assert dx.get_status() & dx.STATUS_BAD_CELL
+    assert torch.equal(torch.nan_to_num(plain, nan=5.0), torch.nan_to_num(batched, nan=5.0))
+    assert bool(torch.isnan(plain[:, :, bad]).all())
+    ok = np.setdiff1d(np.arange(C), bad)
+    sub = cells.subset(ok)
+    ref = oracle.drag_apply(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v)
+    assert_parity(plain[:, :, ok].cpu().numpy(), ref, sub.v)
+
+
+@pytest.mark.parametrize("C", [1000, 40000])
+def test_velocity_form_n1_special_cells(dx, C):
+    """N = 1 runs in the velocity form (the pair (p, q) of P = I + W), through the
+    tile-sorted kernel (1,000 cells) or the balanced blocks with the counting
+    sort (40,000). Decoupled cells (t_s = inf) return v_in exactly; cells
+    without dust keep the gas velocity exactly; a dust-to-gas ratio of 1e-250
+    and the rest against the oracle; dt = 0 returns v_in exactly."""
+    cells = W.mrn(C, 1, seed=77 + C % 13, stiff_lo=-4.0, stiff_hi=8.0)
+    cells.t_s[0, ::7] = np.inf
+    cells.rho_d[0, 3::7] = 0.0
+    cells.rho_d[0, 5::7] = 1e-250 * cells.rho_g[5::7]
+    out = gpu_apply(dx, cells)
+    assert dx.get_status() == 0
+    ref = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v)
+    assert_parity(out, ref, cells.v)
+    assert np.array_equal(out[:, :, ::7], cells.v[:, :, ::7])
+    assert np.array_equal(out[:, 0, 3::7], cells.v[:, 0, 3::7])
+    assert np.array_equal(gpu_apply(dx, cells, dt=0.0), cells.v)
