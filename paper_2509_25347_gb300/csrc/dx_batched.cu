@@ -87,6 +87,12 @@ __device__ __forceinline__ unsigned int bin_of(const Work &W, long long g, int n
 // Matrix size of the cells in a bin.
 __device__ __forceinline__ int n_of_bin(const Work &W, int bin) { return W.n_fixed ? W.n_fixed : bin / kBinsPerN + 2; }
 
+// Warp-per-cell items of a bin of c cells of size n: pairs of cells where the
+// forward sets up two at a time (dx_wpc_pairs), single cells above.
+__host__ __device__ __forceinline__ unsigned int wpc_items(int n, unsigned int c) {
+    return dx_wpc_pairs(n - 1) ? (c + 1) / 2 : c;
+}
+
 // A block is run only if its record is in range. N above nspecies_max is
 // rejected too: the main kernels' per-warp shared-memory slices are sized for
 // matrices up to nspecies_max + 1.
@@ -211,7 +217,7 @@ __global__ void __launch_bounds__(kScanThreads) dx_batch_bins(Work W, Modes M) {
         const unsigned int c = W.hist[i];
         const bool wpc = M.m[n_of_bin(W, i)] == DX_MODE_WPC;
         cs += c;
-        ws += wpc ? c : 0;
+        ws += wpc ? wpc_items(n_of_bin(W, i), c) : 0;
         ls += wpc ? 0 : (c + 31) / 32;
     }
     long long ctot, wtot, ltot;
@@ -226,7 +232,7 @@ __global__ void __launch_bounds__(kScanThreads) dx_batch_bins(Work W, Modes M) {
         W.item_w[i] = (unsigned int)wrun;
         W.item_l[i] = (unsigned int)lrun;
         crun += c;
-        wrun += wpc ? c : 0;
+        wrun += wpc ? wpc_items(n_of_bin(W, i), c) : 0;
         lrun += wpc ? 0 : (c + 31) / 32;
     }
     if (t == 0) {
@@ -255,6 +261,7 @@ struct MainArgs {
     double *v_out;
     uint32_t *status;
     int warp_doubles;   // per-warp shared-memory slice (doubles)
+    int pair_od, pair_doubles;   // warp-per-cell kernel: the pair tables after each slice (od entries, doubles)
     // adjoint tape (taped lane-per-cell kernel only): the cell at cell_offset +
     // c of its block has its fingerprint at thdr[cell], its level t at
     // tm + (cell * tlevels + t) * tP
@@ -325,26 +332,74 @@ __device__ __forceinline__ void dx_batch_queue(unsigned int *counter, unsigned i
     }
 }
 
+// Warp-per-cell items: one cell, or for sizes set up two at a time
+// (dx_wpc_pairs) two consecutive cells of the bin, which may belong to
+// different blocks (their own slabs and dt).
 __global__ void __launch_bounds__(kWpcWarps * 32, kWpcMinBlocks)
 dx_batch_main_wpc(MainArgs a, Work W, DxConsts K) {
     extern __shared__ double smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    double *wsm = smem + wib * (a.warp_doubles + 2 * kPairSlots / 4);
+    double *wsm = smem + wib * (a.warp_doubles + a.pair_doubles);
     unsigned short *od = reinterpret_cast<unsigned short *>(wsm + a.warp_doubles);
-    unsigned short *hp = od + kPairSlots;
+    unsigned short *hp = od + a.pair_od;
     int table_n = 0;
     dx_batch_queue(&W.ctr[0], W.ctr[1], W.item_w, W.nbins, a.status, [&](int bin, unsigned int sub) {
-        const int n = n_of_bin(W, bin);
-        const unsigned long long p = W.perm[W.offs[bin] + sub];
-        const Desc d = a.blocks[p >> 32];
-        const long long c = (long long)(p & 0xffffffffull);
+        const int n = n_of_bin(W, bin), N = n - 1;
         if (table_n != n) {
             dx_build_pairs_warp(lane, n, od, hp);
             table_n = n;
         }
-        dx_wpc_forward_cell(lane, d.nspecies, a.rho_g + d.cell_offset + c, a.rho_d + d.dust_offset + c,
-                            a.t_s + d.dust_offset + c, a.v_in + d.vel_offset + c, a.v_out + d.vel_offset + c,
-                            d.ncells, d.dt, K, wsm, od, hp, a.status);
+        if (!dx_wpc_pairs(N)) {
+            const unsigned long long p = W.perm[W.offs[bin] + sub];
+            const Desc d = a.blocks[p >> 32];
+            const long long c = (long long)(p & 0xffffffffull);
+            dx_wpc_forward_cell(lane, d.nspecies, a.rho_g + d.cell_offset + c, a.rho_d + d.dust_offset + c,
+                                a.t_s + d.dust_offset + c, a.v_in + d.vel_offset + c, a.v_out + d.vel_offset + c,
+                                d.ncells, d.dt, K, wsm, od, hp, a.status);
+            return;
+        }
+        const int ns = dx_stride(n);
+        double *E0 = wsm, *E1 = wsm + n * ns;
+        DxVecs V0;
+        DxFwdBufs B;
+        dx_wpc_fwd_layout(E1 + n * ns, n, V0, B);
+        double *v1 = wsm + dx_wpc_fwd_warp_doubles(n);
+        const DxVecs V1{v1, v1 + n, v1 + 2 * n, v1 + 3 * n};
+        const unsigned int pos0 = W.offs[bin] + 2 * sub;
+        const int cells = pos0 + 1 < W.offs[bin + 1] ? 2 : 1;
+        // set-up inputs: half h takes the item's cell h (half 1 repeats cell 0 when the
+        // item holds one cell; its result is not used), lane 16 h + i - 1 its species i
+        const int h = lane >> 4, l = lane & 15;
+        const unsigned long long ph = W.perm[pos0 + (h < cells ? h : 0)];
+        const Desc dh = a.blocks[ph >> 32];
+        const long long ch = (long long)(ph & 0xffffffffull);
+        const double rg = a.rho_g[dh.cell_offset + ch];
+        double rd = 0.0, ts = INFINITY;
+        if (l < N) {
+            rd = a.rho_d[dh.dust_offset + ch + (long long)l * dh.ncells];
+            ts = a.t_s[dh.dust_offset + ch + (long long)l * dh.ncells];
+        }
+        int k0, s0, k1, s1;
+        const unsigned valid = dx_wpc_setup_pair(lane, N, rg, rd, ts, dh.dt, K, V0, V1, k0, s0, k1, s1);
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            if (e >= cells) break;
+            const unsigned long long p = W.perm[pos0 + e];
+            const Desc d = a.blocks[p >> 32];
+            const long long c = (long long)(p & 0xffffffffull);
+            double *vop = a.v_out + d.vel_offset + c;
+            if (!((valid >> e) & 1u)) {
+                dx_wpc_fail_cell(lane, n, vop, d.ncells, a.status, nullptr);
+                continue;
+            }
+            DxCellIn ci;
+            dx_wpc_load_cell(lane, N, a.rho_g + d.cell_offset + c, a.rho_d + d.dust_offset + c,
+                             a.t_s + d.dust_offset + c, a.v_in + d.vel_offset + c, d.ncells, ci);
+            const DxVecs &V = e ? V1 : V0;
+            const double sg = lane < n ? V.sig[lane] : 1.0;
+            dx_wpc_forward_run(lane, N, V, E0, E1, B, e ? k1 : k0, e ? s1 : s0, sg, ci, vop, d.ncells, d.dt, K,
+                               od, hp, (double *)nullptr, (double *)nullptr, DxTapeCell{nullptr, nullptr, 0, 0});
+        }
     });
 }
 
@@ -401,7 +456,7 @@ void warp_doubles_for(const Modes &M, int n_max, int *wpc, int *lpc, bool *has_w
         int need = 0;
         if (M.m[n] == DX_MODE_WPC) {
             *has_wpc = true;
-            need = dx_wpc_fwd_warp_doubles(n);
+            need = dx_wpc_fwd_warp_doubles(n) + (dx_wpc_pairs(n - 1) ? 4 * n : 0);   // + a second cell's vectors
             *wpc = need > *wpc ? need : *wpc;
             continue;
         }
@@ -504,7 +559,7 @@ static int batched_run(const DxConsts &K, long long nblocks, const Desc *D, long
     bool has_wpc = false, has_lpc = false;
     warp_doubles_for(M, nspecies_max + 1, &wd_wpc, &wd_lpc, &has_wpc, &has_lpc);
     if (has_lpc) {
-        MainArgs a{D, rho_g, rho_d, t_s, v_in, v_out, st, wd_lpc, thdr, tm, tlevels, tP};
+        MainArgs a{D, rho_g, rho_d, t_s, v_in, v_out, st, wd_lpc, 0, 0, thdr, tm, tlevels, tP};
         void (*kern)(MainArgs, Work, Modes, DxConsts) = thdr ? dx_batch_main_lpc<true> : dx_batch_main_lpc<false>;
         const size_t smem = sizeof(double) * (32 + (size_t)kLpcWarps * wd_lpc);
         if (smem > 48 * 1024 &&
@@ -518,8 +573,12 @@ static int batched_run(const DxConsts &K, long long nblocks, const Desc *D, long
         if (cudaGetLastError() != cudaSuccess) return DRAG_ECUDA;
     }
     if (has_wpc) {
-        MainArgs a{D, rho_g, rho_d, t_s, v_in, v_out, st, wd_wpc, nullptr, nullptr, 0, 0};
-        const size_t smem = sizeof(double) * (size_t)kWpcWarps * (wd_wpc + 2 * kPairSlots / 4);
+        // pair tables of the largest size (the warp rebuilds them when an item's n changes)
+        const int nm = nspecies_max + 1;
+        const int pod = nm * (nm - 1) / 2, phs = nm * (nm + 1) / 2 - 1;
+        const int pdbl = (pod + phs + 3) / 4;
+        MainArgs a{D, rho_g, rho_d, t_s, v_in, v_out, st, wd_wpc, pod, pdbl, nullptr, nullptr, 0, 0};
+        const size_t smem = sizeof(double) * (size_t)kWpcWarps * (wd_wpc + pdbl);
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(dx_batch_main_wpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return DRAG_ECUDA;

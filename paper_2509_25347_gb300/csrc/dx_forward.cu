@@ -50,7 +50,7 @@ struct FwdTape {
 // Cells of up to 16 species take their set-up two at a time
 // (dx_wpc_setup_pair): each warp then holds a second cell's vectors (4 n
 // doubles) while it runs the first.
-__host__ __device__ constexpr bool fwd_paired(int N) { return N <= 16; }
+__host__ __device__ constexpr bool fwd_paired(int N) { return dx_wpc_pairs(N); }
 
 // Per-warp shared memory of the FP64 forward (doubles), and the block's pair
 // tables: n(n-1)/2 + n(n+1)/2 - 1 shorts after the warps' slices.

@@ -110,13 +110,16 @@ __device__ __forceinline__ bool dx_wpc_setup(int lane, int N, double rg, double 
     return true;
 }
 
+// Sizes whose warp-per-cell forward sets up two cells at a time (two half-warps of species lanes).
+__host__ __device__ constexpr bool dx_wpc_pairs(int N) { return N <= 16; }
+
 // Set-up of two cells at once, for N <= 16 in FP64: half-warp h (lanes
 // 16 h .. 16 h + 15) takes cell h, and its lane 16 h + i - 1 species i. The
 // species' divisions and square roots, and the norm's two ascending sums, then
 // run for both cells in the same instructions (a warp-wide FP64 instruction
 // costs the same with 16 or 32 lanes working). Every value is formed by the
 // operations dx_wpc_setup uses, in the same order, so the results are the same
-// bits. rg: this half's cell; rd, ts: this lane's species (anything past N).
+// bits. rg, dt: this half's cell; rd, ts: this lane's species (anything past N).
 // Writes cell h's vectors (sigma, tau, X_0f, X_ff; fluid f at index f) to V0
 // or V1, and (k*, s*) of both cells to (k0, s0), (k1, s1c) on every lane.
 // Returns bit h set for a valid cell h.

@@ -371,14 +371,18 @@ def test_binned_forward_in_cuda_graph(dx):
 
 
 @pytest.mark.parametrize("N", [12, 15, 16, 17])
-def test_paired_setup_matches_single_setup(dx, N):
+def test_paired_setup_any_partner(dx, N):
     """For N <= 16 the warp-per-cell forward sets up two cells at a time (one
-    half-warp each); the batched entry point's warp-per-cell items set up one
-    cell at a time, by the same operations. One block of 37 cells through both
-    (the last pair of a 16-cell block holds one cell), with invalid cells in
-    the first and the second slot of a pair: v_out equal bit for bit (NaN where
-    invalid), the valid cells against the oracle, the status bit set by both.
-    N = 17 (no pairing) checks the same against itself."""
+    half-warp each): consecutive cells in drag_expm_apply, consecutive cells
+    of a (k*, s*) bin in the batched entry point, so a cell gets another
+    partner in each. One block of 37 cells through both (the last pair of a
+    16-cell block holds one cell), with invalid cells in the first and the
+    second slot of a pair: v_out equal bit for bit (NaN where invalid), the
+    valid cells against the oracle, the status bit set by both. N = 17 sets up
+    one cell at a time in both. (That the paired set-up gives the one-cell
+    set-up's bits is checked through the tape: the warp-per-cell adjoint
+    re-forms E_t after a one-cell set-up and must reproduce the taped
+    gradients bit for bit, tests/test_tape_gpu.py.)"""
     import torch
     C = 37
     cells = W.mrn(C, N, seed=600 + N, stiff_lo=-4.0, stiff_hi=8.0)
