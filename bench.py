@@ -518,7 +518,8 @@ def roofline_entry(built_flop, dense_flop, alg_bytes, mean_s, peak, hbm_peak, fa
         "flop_per_launch": built_flop,
         "flop_model": "the update as the kernels compute it, from each cell's (k*, s*): set-up 13N, Horner in the "
                       "arrowhead (m* - 1) (2n^2 + 4n - 4), restorations 2n^2, symmetric squarings n^2 (n+1), "
-                      "applications 6n^2 + 6n (%s); n = 2 lane per cell in the velocity form: set-up 10, "
+                      "applications 6n^2 + 6n (%s; warp per cell: 2^q applications 2^q 6n^2 + 9n, sigma o v carried "
+                      "between them); n = 2 lane per cell in the velocity form: set-up 10, "
                       "Taylor 2 (m* - 1) + 3, 4 per squaring, 15 for the application" % family,
         "dense_model": {"flop_per_launch": dense_flop, "achieved": dense_flop / mean_s / 1e12,
                         "frac": dense_flop / mean_s / 1e12 / peak,

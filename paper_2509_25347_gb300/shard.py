@@ -52,7 +52,9 @@ def built_flops(N, k, s, warp_per_cell: bool) -> np.ndarray:
       3 (n (2n + 1) + n) = 6n^2 + 6n.
 
     Lane per cell: s* squarings and one application. Warp per cell: s* - q
-    squarings and 2^q applications, q = min(s*, 2).
+    squarings and 2^q applications, q = min(s*, 2); before the last one an
+    application carries sigma o v alone, n FMAs per entry (6n^2), and the last
+    one then forms v = tau o (sigma o v) first (6n^2 + 9n).
 
     Lane per cell at n = 2 (one dust species) the update runs in the velocity
     form on the off-diagonal pair (p, q) of P = I + W: set-up 10 (eps, alpha,
@@ -70,7 +72,8 @@ def built_flops(N, k, s, warp_per_cell: bool) -> np.ndarray:
         return 10.0 + 2.0 * (m - 1.0) + 3.0 + s * 4.0 + 15.0
     if warp_per_cell:
         q = np.minimum(s, APPLY_Q)
-        return fixed + (s - q) * sq + np.exp2(q) * app
+        apps = np.where(q > 0, np.exp2(q) * 6.0 * n * n + 9.0 * n, app)
+        return fixed + (s - q) * sq + apps
     return fixed + s * sq + app
 
 

@@ -52,7 +52,7 @@ def test_built_flops_structure():
     wpc = shard.built_flops(16, k, s, True)[0]
     lpc = shard.built_flops(16, k, s, False)[0]
     n = 17
-    assert lpc - wpc == pytest.approx(2 * n * n * (n + 1) - 3 * (6 * n * n + 6 * n))
+    assert lpc - wpc == pytest.approx(2 * n * n * (n + 1) - (4 * 6 * n * n + 9 * n - (6 * n * n + 6 * n)))
     assert shard.built_flops(16, k, s + 1, True)[0] - wpc == pytest.approx(n * n * (n + 1))
     # k* picks m_k of Table B.1: one more Horner step per degree
     assert shard.built_flops(4, np.array([7]), s, False)[0] - shard.built_flops(4, np.array([6]), s, False)[0] == \
