@@ -85,9 +85,11 @@ extern "C" {
  * Lane-per-cell sizes (N <= 8 with the default modes) on enough cells run the
  * batched pipeline over one block: the cells are binned by (k*, s*) first, so
  * each warp runs 32 cells of equal cost. "Enough" is where that measured
- * faster than one tile-sorted launch on GB300: 655,360 cells at N = 1,
- * 163,840 at N = 2, 131,072 at N = 3, 98,304 at N = 4 and 5, 40,960 at N = 6
- * and 7, 28,672 at N = 8 (drag_expm_apply_launches reports the choice). Its scratch (12 bytes per
+ * faster than one tile-sorted launch on GB300: 196,608 cells at N = 2,
+ * 131,072 at N = 3, 98,304 at N = 4 and 5, 40,960 at N = 6 and 7, 28,672 at
+ * N = 8; never at N = 1, whose single launch (a few dozen FP64 operations a
+ * cell) was the faster at every size measured (drag_expm_apply_launches
+ * reports the choice). Its scratch (12 bytes per
  * cell) is taken stream-ordered from a memory pool private to the library,
  * which keeps what it once allocated; the launches stay capturable in a CUDA
  * graph. If no scratch can be had, the single tile-sorted kernel runs instead.

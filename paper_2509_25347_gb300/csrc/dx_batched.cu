@@ -732,15 +732,17 @@ __global__ void dx_batch_single_desc(Desc *d, long long C, int N, double dt) {
 // one tile-sorted launch: the crossovers measured on GB300 (CUDA events, cold
 // L2, the MRN-like workloads, n = 2..9). Binning pays earlier for larger n,
 // whose per-warp work varies more with (k*, s*), and much earlier for the
-// adjoint, whose squarings cost 5x the forward's; at n = 2 the forward's five
-// binning launches outweigh the gain up to ~600k cells. Building with
+// adjoint, whose squarings cost 5x the forward's. At n = 2 the forward runs in
+// the velocity form, a few dozen FP64 operations a cell: its single launch beat
+// the binned pipeline at every size measured (411.7 against 685.0 us at
+// 2,097,152 cells), so it never bins. Building with
 // -DDX_BINNED_MIN_CELLS=<cells> sets one threshold for every n (measurements).
 long long dx_binned_min_cells(int n, bool adjoint) {
 #ifdef DX_BINNED_MIN_CELLS
     (void)adjoint;
     return n >= 2 && n <= kBatchLpcNMax ? (long long)(DX_BINNED_MIN_CELLS) : LLONG_MAX;
 #else
-    static constexpr long long kForward[kBatchLpcNMax + 1] = {0, 0, 655360, 163840, 131072, 98304, 98304,
+    static constexpr long long kForward[kBatchLpcNMax + 1] = {0, 0, LLONG_MAX, 196608, 131072, 98304, 98304,
                                                               40960, 40960, 28672};
     static constexpr long long kAdjoint[kBatchLpcNMax + 1] = {0, 0, 32768, 24576, 4096, 4096, 4096,
                                                               4096, 4096, 4096};

@@ -192,7 +192,7 @@ def test_sorted_tiles_parity(dx, N):
     assert dx.get_status() == 0
 
 
-@pytest.mark.parametrize("N", [1, 4, 6, 8])
+@pytest.mark.parametrize("N", [2, 4, 6, 8])
 def test_binned_forward(dx, N):
     """From its binning size on (per N, as the library reports it) a default
     lane-per-cell size runs the batched pipeline over one block (6 launches).
@@ -239,6 +239,9 @@ def test_tile_sorted_forward_small_and_prefix(dx, N):
         assert dx.apply_launches(C, N) == 1
         assert_parity(gpu_apply(dx, cells), ref, cells.v)
     thr = binned_threshold(dx, N)
+    if thr is None:   # N = 1 never bins: one launch at any size
+        assert dx.apply_launches(2 * 10**6, N) == 1
+        return
     C, head = thr + 99998, thr - 1
     cells = W.mrn(C, N, seed=80 + N, stiff_lo=-4.0, stiff_hi=8.0)
     rg, rd, ts, v = dev(cells)
@@ -283,11 +286,12 @@ def test_balanced_blocks_forward_edges(dx, N):
 
 def test_binned_forward_wide_chunks(dx):
     """Above 64 chunks of 65,536 cells the binned forward widens its chunks
-    (here 4,500,001 cells of N = 1: 64 chunks of 70,313 cells, the last one
-    ragged). Sampled cells against the oracle, the first 200,003 cells bit for
-    bit against the tile-sorted kernel, and the status word clean."""
+    (here 4,500,001 cells of N = 2: 64 chunks of 70,313 cells, the last one
+    ragged). Sampled cells against the oracle, the first 196,607 cells (below
+    the binning size) bit for bit against the tile-sorted kernel, and the
+    status word clean."""
     import torch
-    C, N = 4500001, 1
+    C, N = 4500001, 2
     cells = W.mrn(C, N, seed=4242, stiff_lo=-4.0, stiff_hi=8.0)
     rg, rd, ts, v = dev(cells)
     assert dx.apply_launches(C, N) == 6
@@ -298,7 +302,7 @@ def test_binned_forward_wide_chunks(dx):
     sub = cells.subset(idx)
     ref = oracle.drag_apply(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v)
     assert_parity(out[:, :, idx].cpu().numpy(), ref, sub.v)
-    head = 200003
+    head = binned_threshold(dx, N) - 1
     hrg, hrd, hts, hv = dev(cells.subset(np.arange(head)))
     tiled = dx.apply(hrg, hrd, hts, cells.dt, hv)
     assert torch.equal(tiled, out[:, :, :head])
