@@ -366,9 +366,13 @@ __device__ __forceinline__ void dx_lpc_arrowhead(const double (&eps)[NF - 1], co
 #pragma unroll
     for (int i = 1; i < NF; i++) {
         const double e = dx_bits(eps[i - 1]) < dx_bits(eps_floor) ? eps_floor : eps[i - 1];
-        const double sg = __dsqrt_rn(e);
+        // 1/sigma to within an ulp and sigma = eps / sqrt(eps) from it: the
+        // similarity only needs sigma and 1/sigma used consistently, and the
+        // adjoint forms them by this same routine
+        const double tu = rsqrt(e);
+        const double sg = __dmul_rn(e, tu);
         sig[i] = sg;
-        tau[i] = __drcp_rn(sg);
+        tau[i] = tu;
         xs[i] = __dmul_rn(__dmul_rn(sg, alpha[i - 1]), dx_scale2(dt, s));
         ds[i] = -dx_scale2(__dmul_rn(alpha[i - 1], dt), s);
     }
