@@ -66,8 +66,8 @@ KERNEL_SOURCES = {
 }
 MEASURED_TRAFFIC = {
     ("mrn_n16_128cube", "dx_forward_wpc"): {
-        "sources_sha256": "f1c31650b1fa9d1b759dec060d36e87ce40ef1dc843da6a09808c6c11952e015",
-        "bytes_per_cell": (189389312 + 81047296) / 262144,
+        "sources_sha256": "d37f403c45f46a356c12b2910a0d3cde745a84644ff5ad8d67f2c99a52d7c0e3",
+        "bytes_per_cell": (188641024 + 81163264) / 262144,
         # FP64 FLOPs the kernel executes: thread-level 2 DFMA + DADD + DMUL (sm__sass_thread_inst_executed_op_*)
         "executed_flop_per_cell": (2 * 11389688778 + 642554274 + 99185602) / 262144,
         "capture": "profiles/dx_forward_wpc_mrn_n16.md",
