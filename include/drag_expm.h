@@ -82,12 +82,13 @@ extern "C" {
  *              place) is allowed; other overlaps are not.
  *   stream   : CUDA stream for the launches.
  * Returns DRAG_OK or a DRAG_E* code (nothing launched on error).
- * Lane-per-cell sizes (N <= 8 with the default modes) on enough cells run the
+ * Lane-per-cell sizes (N <= 11 with the default modes) on enough cells run the
  * batched pipeline over one block: the cells are binned by (k*, s*) first, so
  * each warp runs 32 cells of equal cost. "Enough" is where that measured
  * faster than one tile-sorted launch on GB300: 196,608 cells at N = 2,
  * 131,072 at N = 3, 98,304 at N = 4 and 5, 40,960 at N = 6 and 7, 28,672 at
- * N = 8; never at N = 1, whose single launch (a few dozen FP64 operations a
+ * N = 8, 26,624 at N = 9 and 10, 24,576 at N = 11; never at N = 1, whose
+ * single launch (a few dozen FP64 operations a
  * cell) was the faster at every size measured (drag_expm_apply_launches
  * reports the choice). Its scratch (12 bytes per
  * cell) is taken stream-ordered from a memory pool private to the library,
@@ -174,7 +175,7 @@ int drag_expm_apply_opts(int64_t ncells, int32_t nspecies, const double *rho_g, 
 /*
  * drag_expm_apply_host — drag_expm_apply on HOST arrays (same SoA layout,
  * stride ncells): the cells are processed in chunks of chunk_cells (0: 262,144
- * where drag_expm_apply bins that many cells, N = 2..8 with the default
+ * where drag_expm_apply bins that many cells, N = 2..11 with the default
  * modes, see there, else 131,072)
  * through a two-stream pipeline, so the host-to-device copies of one chunk
  * and the device-to-host copy of another overlap the update of a third. The
@@ -302,7 +303,7 @@ int32_t drag_expm_tape_levels(int32_t sstar);
  * drag_expm_apply_taped — drag_expm_apply that also writes the adjoint tape.
  * v_out is bit-identical to drag_expm_apply's under the same mode table: the
  * taped forward runs the same kernel family, lane per cell for N <= 11 with the
- * default modes (binned up to N = 8 from the sizes drag_expm_apply bins,
+ * default modes (binned from the sizes drag_expm_apply bins,
  * tile-sorted otherwise),
  * one warp per cell for other sizes.
  *   levels : tape capacity per cell, 1 .. DRAG_TAPE_MAX_LEVELS.

@@ -42,6 +42,10 @@ constexpr int kWpcWarps = 4;                         // warps per CTA, warp-per-
 constexpr int kWpcMinBlocks = 6;                     // resident CTAs per SM the latter is compiled for
 constexpr int kScanThreads = 1024;
 constexpr int kBatchLpcNMax = 9;                     // largest n run lane-per-cell in the batched kernel
+// Largest n the binned single-N forward runs lane per cell. Its n = 10..12
+// items (hybrid storage, registers near the limit) have a kernel instance of
+// their own, so that they do not set the register use of the n <= 9 items.
+constexpr int kBinnedLpcNMax = 12;
 // One n (the binned drag_expm_apply and adjoint): the bins are chunk-major,
 // (chunk of consecutive cells, k*, s*), so that the items run one chunk after
 // the other and a chunk's cells, scattered over its bins, are read from DRAM
@@ -284,21 +288,31 @@ __device__ __forceinline__ void lpc_item(int lane, const MainArgs &a, const Desc
                                   d.dt, K, bsh, wsm, a.status, nullptr, tc);
 }
 
-template <bool TAPE>
+template <bool TAPE, bool BIG>
 __device__ __forceinline__ void lpc_dispatch(int n, int lane, const MainArgs &a, const Desc &d, long long c,
                                              const DxConsts &K, const double *bsh, double *wsm) {
-    // the storage per n is compiled in: registers up to n = 6, hybrid above
+    // the storage per n is compiled in: registers up to n = 6, hybrid above;
+    // BIG: the n = 10..12 items of the binned single-N forward
     switch (n) {
 #define DX_ITEM(NF, ST) \
     case NF: lpc_item<NF, ST, TAPE>(lane, a, d, c, K, bsh, wsm); break;
-        DX_ITEM(2, DX_LPC_REGS)
-        DX_ITEM(3, DX_LPC_REGS)
-        DX_ITEM(4, DX_LPC_REGS)
-        DX_ITEM(5, DX_LPC_REGS)
-        DX_ITEM(6, DX_LPC_REGS)
-        DX_ITEM(7, DX_LPC_HYBRID)
-        DX_ITEM(8, DX_LPC_HYBRID)
-        DX_ITEM(9, DX_LPC_HYBRID)
+#define DX_ITEM_SMALL(NF, ST) \
+    case NF: if constexpr (!BIG) lpc_item<NF, ST, TAPE>(lane, a, d, c, K, bsh, wsm); break;
+#define DX_ITEM_BIG(NF, ST) \
+    case NF: if constexpr (BIG) lpc_item<NF, ST, TAPE>(lane, a, d, c, K, bsh, wsm); break;
+        DX_ITEM_SMALL(2, DX_LPC_REGS)
+        DX_ITEM_SMALL(3, DX_LPC_REGS)
+        DX_ITEM_SMALL(4, DX_LPC_REGS)
+        DX_ITEM_SMALL(5, DX_LPC_REGS)
+        DX_ITEM_SMALL(6, DX_LPC_REGS)
+        DX_ITEM_SMALL(7, DX_LPC_HYBRID)
+        DX_ITEM_SMALL(8, DX_LPC_HYBRID)
+        DX_ITEM_SMALL(9, DX_LPC_HYBRID)
+        DX_ITEM_BIG(10, DX_LPC_HYBRID)
+        DX_ITEM_BIG(11, DX_LPC_HYBRID)
+        DX_ITEM_BIG(12, DX_LPC_HYBRID)
+#undef DX_ITEM_BIG
+#undef DX_ITEM_SMALL
 #undef DX_ITEM
         default: break;
     }
@@ -403,7 +417,7 @@ dx_batch_main_wpc(MainArgs a, Work W, DxConsts K) {
     });
 }
 
-template <bool TAPE>
+template <bool TAPE, bool BIG>
 __global__ void __launch_bounds__(kLpcWarps * 32)
 dx_batch_main_lpc(MainArgs a, Work W, Modes M, DxConsts K) {
     (void)M;   // lane-per-cell items only (the bins already carry the mode)
@@ -419,7 +433,7 @@ dx_batch_main_lpc(MainArgs a, Work W, Modes M, DxConsts K) {
         if (pos < W.offs[bin + 1]) {
             const unsigned long long p = W.perm[pos];
             const Desc d = a.blocks[p >> 32];
-            lpc_dispatch<TAPE>(n, lane, a, d, (long long)(p & 0xffffffffull), K, bsh, wsm);
+            lpc_dispatch<TAPE, BIG>(n, lane, a, d, (long long)(p & 0xffffffffull), K, bsh, wsm);
         }
         __syncwarp();
     });
@@ -447,12 +461,12 @@ Layout layout(long long nblocks, long long total_cells, int nbins = kNBins) {
     return L;
 }
 
-// Per-warp shared memory (doubles) each main kernel needs for matrices up to
-// n_max; *has_wpc / *has_lpc tell whether any n <= n_max runs that way.
-void warp_doubles_for(const Modes &M, int n_max, int *wpc, int *lpc, bool *has_wpc, bool *has_lpc) {
+// Per-warp shared memory (doubles) each main kernel needs for matrices of
+// n_min..n_max; *has_wpc / *has_lpc tell whether any of them runs that way.
+void warp_doubles_for(const Modes &M, int n_min, int n_max, int *wpc, int *lpc, bool *has_wpc, bool *has_lpc) {
     *wpc = *lpc = 0;
     *has_wpc = *has_lpc = false;
-    for (int n = 2; n <= n_max; n++) {
+    for (int n = n_min; n <= n_max; n++) {
         int need = 0;
         if (M.m[n] == DX_MODE_WPC) {
             *has_wpc = true;
@@ -474,6 +488,9 @@ void warp_doubles_for(const Modes &M, int n_max, int *wpc, int *lpc, bool *has_w
                 DX_NEED(7)
                 DX_NEED(8)
                 DX_NEED(9)
+                DX_NEED(10)
+                DX_NEED(11)
+                DX_NEED(12)
 #undef DX_NEED
                 default: break;
             }
@@ -551,16 +568,23 @@ static int batched_run(const DxConsts &K, long long nblocks, const Desc *D, long
                        int tlevels = 0, int tP = 0, int n_fixed = 0) {
     const Work W = n_fixed ? work_at(ws, L, fixed_n_bins(total_cells), n_fixed, fixed_n_chunk(total_cells))
                            : work_at(ws, L);
-    const Modes M = dx_batch_modes();
+    Modes M = dx_batch_modes();
+    if (n_fixed > kBatchLpcNMax && n_fixed <= kBinnedLpcNMax && dx_mode_for(n_fixed) == DX_MODE_LPC_HYB)
+        M.m[n_fixed] = DX_MODE_LPC_HYB;   // the binned single-N forward's n = 10..12 items
     const int sms = dx_sm_count();
     launch_binning(K, nblocks, D, nspecies_max, total_cells, rho_d_len, v_len, rho_g, rho_d, t_s, W, M, st, stream);
 
     int wd_wpc = 0, wd_lpc = 0;
     bool has_wpc = false, has_lpc = false;
-    warp_doubles_for(M, nspecies_max + 1, &wd_wpc, &wd_lpc, &has_wpc, &has_lpc);
+    // one n (n_fixed): only its own kernel family runs
+    warp_doubles_for(M, n_fixed ? n_fixed : 2, n_fixed ? n_fixed : nspecies_max + 1, &wd_wpc, &wd_lpc, &has_wpc,
+                     &has_lpc);
     if (has_lpc) {
         MainArgs a{D, rho_g, rho_d, t_s, v_in, v_out, st, wd_lpc, 0, 0, thdr, tm, tlevels, tP};
-        void (*kern)(MainArgs, Work, Modes, DxConsts) = thdr ? dx_batch_main_lpc<true> : dx_batch_main_lpc<false>;
+        const bool big = n_fixed > kBatchLpcNMax;
+        void (*kern)(MainArgs, Work, Modes, DxConsts) =
+            big ? (thdr ? dx_batch_main_lpc<true, true> : dx_batch_main_lpc<false, true>)
+                : (thdr ? dx_batch_main_lpc<true, false> : dx_batch_main_lpc<false, false>);
         const size_t smem = sizeof(double) * (32 + (size_t)kLpcWarps * wd_lpc);
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -730,7 +754,7 @@ __global__ void dx_batch_single_desc(Desc *d, long long C, int N, double dt) {
 
 // Smallest input from which binning the whole input by (chunk, k*, s*) beats
 // one tile-sorted launch: the crossovers measured on GB300 (CUDA events, cold
-// L2, the MRN-like workloads, n = 2..9). Binning pays earlier for larger n,
+// L2, the MRN-like workloads, n = 2..12). Binning pays earlier for larger n,
 // whose per-warp work varies more with (k*, s*), and much earlier for the
 // adjoint, whose squarings cost 5x the forward's. At n = 2 the forward runs in
 // the velocity form, a few dozen FP64 operations a cell: its single launch beat
@@ -739,20 +763,21 @@ __global__ void dx_batch_single_desc(Desc *d, long long C, int N, double dt) {
 // -DDX_BINNED_MIN_CELLS=<cells> sets one threshold for every n (measurements).
 long long dx_binned_min_cells(int n, bool adjoint) {
 #ifdef DX_BINNED_MIN_CELLS
-    (void)adjoint;
-    return n >= 2 && n <= kBatchLpcNMax ? (long long)(DX_BINNED_MIN_CELLS) : LLONG_MAX;
+    return n >= 2 && n <= (adjoint ? kBatchLpcNMax : kBinnedLpcNMax) ? (long long)(DX_BINNED_MIN_CELLS) : LLONG_MAX;
 #else
-    static constexpr long long kForward[kBatchLpcNMax + 1] = {0, 0, LLONG_MAX, 196608, 131072, 98304, 98304,
-                                                              40960, 40960, 28672};
+    static constexpr long long kForward[kBinnedLpcNMax + 1] = {0, 0, LLONG_MAX, 196608, 131072, 98304, 98304,
+                                                               40960, 40960, 28672, 26624, 26624, 24576};
     static constexpr long long kAdjoint[kBatchLpcNMax + 1] = {0, 0, 32768, 24576, 4096, 4096, 4096,
                                                               4096, 4096, 4096};
-    if (n < 2 || n > kBatchLpcNMax) return LLONG_MAX;
+    if (n < 2 || n > (adjoint ? kBatchLpcNMax : kBinnedLpcNMax)) return LLONG_MAX;
     return adjoint ? kAdjoint[n] : kForward[n];
 #endif
 }
 
 bool dx_binned_eligible(int n, int mode, long long C) {
-    return n >= 2 && n <= kBatchLpcNMax && mode == dx_batch_modes().m[n] && C >= dx_binned_min_cells(n, false) &&
+    // the storage the binned kernel compiles for n: registers up to DX_LPC_REG_NMAX, hybrid above
+    const int binned_mode = n <= DX_LPC_REG_NMAX ? DX_MODE_LPC_REG : DX_MODE_LPC_HYB;
+    return n >= 2 && n <= kBinnedLpcNMax && mode == binned_mode && C >= dx_binned_min_cells(n, false) &&
            C <= 0x7fffffffLL;
 }
 

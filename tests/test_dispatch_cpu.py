@@ -15,16 +15,19 @@ def lib():
 
 
 def test_binned_thresholds_per_size(lib):
-    fwd = {N: binned_threshold(dx, N) for N in range(1, 9)}
-    bwd = {N: binned_threshold(dx, N, adjoint=True) for N in range(1, 9)}
+    fwd = {N: binned_threshold(dx, N) for N in range(1, 12)}
+    bwd = {N: binned_threshold(dx, N, adjoint=True) for N in range(1, 12)}
     # N = 1 runs the forward in the velocity form, a few dozen FP64 operations a
     # cell: one launch at every size (binning measured slower up to 2,097,152 cells)
     assert fwd[1] is None
     for C in (1, 10**5, 10**6, INT32_MAX, INT32_MAX + 1):
         assert dx.apply_launches(C, 1) == 1
-    for N in range(1, 9):
+    # the lane-per-cell adjoint stops at N = 8 (n = 9); the binned forward reaches N = 11 (n = 12)
+    for N in (9, 10, 11):
+        assert bwd[N] is None and fwd[N] is not None
+    for N in range(1, 12):
         for q, thr in ((dx.apply_launches, fwd[N]), (dx.backward_launches, bwd[N])):
-            if q is dx.apply_launches and N == 1:
+            if (q is dx.apply_launches and N == 1) or (q is dx.backward_launches and N >= 9):
                 continue
             assert thr is not None and thr > 1
             # one launch below the threshold, six from it on, up to the int32 cell limit
@@ -34,12 +37,12 @@ def test_binned_thresholds_per_size(lib):
                 assert q(C, N) == 6
             assert q(INT32_MAX + 1, N) == 1
         # the adjoint's squarings cost ~5x the forward's: binning pays no later there
-        assert N == 1 or bwd[N] <= fwd[N]
+        assert N == 1 or N >= 9 or bwd[N] <= fwd[N]
     # larger matrices vary more in per-warp work with (k*, s*): binning pays earlier
-    assert all(fwd[N + 1] <= fwd[N] for N in range(2, 8))
+    assert all(fwd[N + 1] <= fwd[N] for N in range(2, 11))
     assert all(bwd[N + 1] <= bwd[N] for N in range(1, 8))
     # warp-per-cell sizes never bin
-    for N in (9, 12, 16, 31):
+    for N in (12, 16, 31):
         assert binned_threshold(dx, N) is None and binned_threshold(dx, N, adjoint=True) is None
         assert dx.apply_launches(10**6, N) == 1 and dx.backward_launches(10**6, N) == 1
 

@@ -192,7 +192,7 @@ def test_sorted_tiles_parity(dx, N):
     assert dx.get_status() == 0
 
 
-@pytest.mark.parametrize("N", [2, 4, 6, 8])
+@pytest.mark.parametrize("N", [2, 4, 6, 8, 10])
 def test_binned_forward(dx, N):
     """From its binning size on (per N, as the library reports it) a default
     lane-per-cell size runs the batched pipeline over one block (6 launches).

@@ -317,7 +317,7 @@ def test_taped_finite_differences_64_cells(dx):
 
 
 
-@pytest.mark.parametrize("N", [4, 8])
+@pytest.mark.parametrize("N", [4, 8, 10])
 def test_binned_tape(dx, N):
     """Above its binning size the lane-per-cell taped forward runs the binned
     pipeline (6 launches), writing the same tape: v_out equals drag_expm_apply's
