@@ -22,13 +22,15 @@
 // n = 7..9 (the hybrid storage) the per-lane state no longer fits: L (n^2
 // doubles) stays in registers, E in shared memory, and the squaring's new L
 // goes to shared memory before it is copied back (it needs all of the old L).
-// E^2 forms in registers once the old L is dead, and the Horner chain of F
-// before the derivative chain starts (the latter carries y_d = F a_d by its
-// own recurrence). The Taylor derivative updates L in place (its row i needs
-// only the old row i), so the n^2 slice of the new L can share its shared
-// memory with the Taylor phase's vectors a_d, b_d, y_d (9n >= n^2 for n <= 9);
-// a_d is formed again for the outputs, and eps, alpha are divided again
-// there (the same roundings) instead of holding registers through the cell.
+// E^2 forms in registers once the old L is dead. The derivative chain runs
+// first (it carries y_d = F a_d by its own recurrence and never reads F); L
+// then waits in shared memory while the Horner chain of F runs in registers.
+// The Taylor derivative updates L in place (its row i needs only the old row
+// i), so the n^2 slice of the new L can share its shared memory with the
+// Taylor phase's vectors a_d, b_d, y_d (9n >= n^2 for n <= 9), and E with X
+// and a_3, dead once F is done; a_d is formed again for the outputs, and eps,
+// alpha are divided again there (the same roundings) instead of holding
+// registers through the cell.
 #include <cmath>
 
 #include "dx_lpc.cuh"
@@ -36,7 +38,7 @@
 
 namespace {
 
-// Threads per block: 2 warps, or one for the hybrid storage, whose 39-55 KB of
+// Threads per block: 2 warps, or one for the hybrid storage, whose 27-37 KB of
 // shared memory per warp would otherwise strand part of an SM; and the largest
 // tile of cells a block sorts.
 template <int NF>
@@ -58,18 +60,22 @@ struct BwdLpcArgs {
 // Storage per n: E (packed, double-buffered) and L (full, double-buffered) in
 // registers; the n-vectors (sigma, tau, X_0f, X_ff, a_d, -kappa sigma, b_d, y_d:
 // 14 n doubles) in registers up to n = 3 and in shared memory above. Hybrid
-// (n >= 7): L in registers, E and the squaring's new L in shared memory, the
-// latter over the slices of a_d, b_d, y_d; the Horner chain and E^2 form in
-// registers while L is not live (171 doubles of shared memory per lane at
-// n = 9: five warps per SM).
+// (n >= 7): L in registers, E and the squaring's new L in shared memory; the
+// Horner chain and E^2 form in registers while L is not live. Per lane the
+// hybrid slice is sigma, tau (2n), then X_0f, X_ff, a_3 (3n) under E (n(n+1)/2),
+// then a_d, b_d, y_d (9n) under the new L (n^2): 144 doubles at n = 9, six
+// one-warp CTAs per SM (seven at n = 8, eight at n = 7).
 template <int NF>
 struct BwdLpcStore {
     static constexpr bool kVecShared = NF >= 4;
     static constexpr bool kHybrid = NF >= 7;
     static constexpr int kVec = 14 * NF;
     static constexpr int kNT = NF * (NF + 1) / 2;
-    static constexpr int kWarpDoubles = (kVecShared ? 32 * kVec : 0) + (kHybrid ? 32 * kNT : 0);
+    static constexpr int kE = 2 * NF;                           // hybrid: E over X_0f, X_ff, a_3
+    static constexpr int kAv = kHybrid ? kE + kNT : 5 * NF;     // a_d, b_d, y_d (hybrid: under the new L)
+    static constexpr int kWarpDoubles = kHybrid ? 32 * (kAv + 9 * NF) : kVecShared ? 32 * kVec : 0;
     static_assert(!kHybrid || NF * NF <= 9 * NF, "the new L overlays a_d, b_d, y_d");
+    static_assert(!kHybrid || 3 * NF <= kNT, "E overlays X_0f, X_ff, a_3");
 };
 
 template <int NF>
@@ -233,9 +239,10 @@ __device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpc
         xs.bind(wsm + 64 * NF, lane);
         ds.bind(wsm + 96 * NF, lane);
         a3.bind(wsm + 128 * NF, lane);
-        av.bind(wsm + 160 * NF, lane);
-        bv.bind(wsm + 256 * NF, lane);
-        yv.bind(wsm + 352 * NF, lane);
+        constexpr int kAv = BwdLpcStore<NF>::kAv;
+        av.bind(wsm + 32 * kAv, lane);
+        bv.bind(wsm + 32 * (kAv + 3 * NF), lane);
+        yv.bind(wsm + 32 * (kAv + 6 * NF), lane);
     }
     double rg, eps[N], alpha[N];
     int kk, s;
@@ -282,15 +289,32 @@ __device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpc
     DxLaneArr<NF * NF, false> Lm, Lt;     // L, and the Taylor step's new L (in place for the compiler)
     DxLaneArr<NF * NF, HY> Ln;            // the squaring's new L
     if constexpr (HY) {
-        Fm.bind(wsm + 32 * BwdLpcStore<NF>::kVec, lane);
-        Ln.bind(wsm + 160 * NF, lane);   // over a_d, b_d, y_d, dead in the squarings
+        Fm.bind(wsm + 32 * BwdLpcStore<NF>::kE, lane);    // over X_0f, X_ff, a_3, dead once F is done
+        Ln.bind(wsm + 32 * BwdLpcStore<NF>::kAv, lane);   // over a_d, b_d, y_d, dead in the squarings
     }
     const double bm = bsh[m], bm1 = bsh[m - 1];
     if constexpr (HY) {
-        // The Horner chain of F shares only X with the derivative chain (which
-        // carries y_d = F a_d by its own recurrence): it runs first, in
-        // registers, and leaves E_0 in shared memory; then the derivative
-        // chain runs with L in registers.
+        // The derivative chain shares only X with the Horner chain of F (it
+        // carries y_d = F a_d by its own recurrence): it runs first, with L in
+        // registers; L then goes to the new L's slice (a_d, b_d, y_d are dead)
+        // while the Horner chain runs in registers and leaves E_0 over X and
+        // a_3, and comes back for the squarings.
+        bwd_lpc_dinit<NF>(Lm, av, bv, a3, sig, bm);
+        bwd_lpc_yinit<NF>(yv, xs, ds, av, bm, bm1);
+        for (int jb = m - 2; jb >= 0; jb--) {
+#pragma unroll
+            for (int i = 0; i < NF; i++) {
+                bwd_lpc_drow<NF>(Lm, Lt, i, yv, bv, a3, sig, xs, ds, bsh[jb + 1]);
+                // one row at a time: overlapped, the rows' vector loads would
+                // outgrow the registers L leaves free
+                asm volatile("" ::: "memory");
+            }
+            bwd_lpc_ystep<NF>(yv, xs, ds, av, bsh[jb]);
+            dx_lane_take(Lm, Lt);
+        }
+#pragma unroll
+        for (int e = 0; e < NF * NF; e++) Ln[e] = Lm[e];
+        asm volatile("" ::: "memory");   // L stored before the Horner chain takes its registers
         if (taped) {
 #pragma unroll
             for (int e = 0; e < NT; e++) Fm[e] = tcell[e];
@@ -306,19 +330,9 @@ __device__ __forceinline__ void bwd_lpc_cell(int lane, long long c, const BwdLpc
 #pragma unroll
             for (int e = 0; e < NT; e++) Fm[e] = Fr[e];
         }
-        bwd_lpc_dinit<NF>(Lm, av, bv, a3, sig, bm);
-        bwd_lpc_yinit<NF>(yv, xs, ds, av, bm, bm1);
-        for (int jb = m - 2; jb >= 0; jb--) {
+        asm volatile("" ::: "memory");   // E_0 stored before L takes the registers back
 #pragma unroll
-            for (int i = 0; i < NF; i++) {
-                bwd_lpc_drow<NF>(Lm, Lt, i, yv, bv, a3, sig, xs, ds, bsh[jb + 1]);
-                // one row at a time: overlapped, the rows' vector loads would
-                // outgrow the registers L leaves free
-                asm volatile("" ::: "memory");
-            }
-            bwd_lpc_ystep<NF>(yv, xs, ds, av, bsh[jb]);
-            dx_lane_take(Lm, Lt);
-        }
+        for (int e = 0; e < NF * NF; e++) Lm[e] = Ln[e];
     } else {
         if (!taped) dx_lpc_taylor_init<NF>(Fm, xs, ds, bm, bm1);
         bwd_lpc_dinit<NF>(Lm, av, bv, a3, sig, bm);
@@ -446,7 +460,7 @@ __global__ void __launch_bounds__(bwd_threads<NF>()) dx_backward_lpc(BwdLpcArgs 
     double *bsh = smem;
     for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
     double *wsm = smem + 32 + (threadIdx.x >> 5) * BwdLpcStore<NF>::kWarpDoubles;
-    unsigned long long *key = HY ? reinterpret_cast<unsigned long long *>(smem + 32 + 32 * BwdLpcStore<NF>::kVec)
+    unsigned long long *key = HY ? reinterpret_cast<unsigned long long *>(smem + 32 + 32 * BwdLpcStore<NF>::kE)
                                  : key_static;
     unsigned short *order = HY ? reinterpret_cast<unsigned short *>(key + kTile) : order_static;
     const long long C = a.C;
