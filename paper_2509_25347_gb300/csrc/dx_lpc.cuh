@@ -305,18 +305,18 @@ __device__ __forceinline__ int dx_lpc_round_pos(int r, int threads) {
     return r * threads + 32 * ((r & 1) ? nw - 1 - w : w) + (threadIdx.x & 31);
 }
 
-// Per-lane selection for one cell. Loads and validates rho_g, rho_d, t_s
-// (integer checks on bit patterns); forms eps_i = rho_d,i / rho_g and
-// alpha_i = 1 / t_s,i (Eqs. DragEqVar2, DragEqVar3) and the 1-norm of
-// A = dt Omega_v summed in ascending species order (as the oracle sums it, so
-// (k*, s*) are reproducible); runs Algorithm 2. s1 = -A_00 = sum_i eps_i
+// Per-lane norm of one cell. Loads and validates rho_g, rho_d, t_s (integer
+// checks on bit patterns); forms eps_i = rho_d,i / rho_g and alpha_i =
+// 1 / t_s,i (Eqs. DragEqVar2, DragEqVar3) and the 1-norm of A = dt Omega_v
+// summed in ascending species order (as the oracle sums it, so the selection
+// is reproducible), returned as its bit pattern nb. s1 = -A_00 = sum_i eps_i
 // alpha_i dt. With want_fp, fph is the XOR of the species' fingerprint terms
 // over the raw inputs. Returns false for an invalid cell.
 template <int NF>
-__device__ __forceinline__ bool dx_lpc_select_cell(const double *rgp, const double *rdp, const double *tsp,
-                                                   long long stride, double dt, const DxConsts &K, bool want_fp,
-                                                   double &rg, double (&eps)[NF - 1], double (&alpha)[NF - 1],
-                                                   int &kk, int &s, unsigned long long &fph, double &s1) {
+__device__ __forceinline__ bool dx_lpc_norm_cell(const double *rgp, const double *rdp, const double *tsp,
+                                                 long long stride, double dt, bool want_fp, double &rg,
+                                                 double (&eps)[NF - 1], double (&alpha)[NF - 1],
+                                                 unsigned long long &fph, double &s1, long long &nb) {
     constexpr int N = NF - 1;
     rg = *rgp;
     bool ok = dx_pos_finite(rg);
@@ -346,8 +346,18 @@ __device__ __forceinline__ bool dx_lpc_select_cell(const double *rgp, const doub
         const long long cb = dx_bits(__dadd_rn(__dmul_rn(__dmul_rn(eps[i], alpha[i]), dt), ai0));
         cmax = cb > cmax ? cb : cmax;
     }
-    const long long nb = dx_bits(col0) > cmax ? dx_bits(col0) : cmax;
-    if (!dx_norm_ok(nb)) return false;
+    nb = dx_bits(col0) > cmax ? dx_bits(col0) : cmax;
+    return dx_norm_ok(nb);
+}
+
+// dx_lpc_norm_cell, then Algorithm 2 on the norm: (k*, s*).
+template <int NF>
+__device__ __forceinline__ bool dx_lpc_select_cell(const double *rgp, const double *rdp, const double *tsp,
+                                                   long long stride, double dt, const DxConsts &K, bool want_fp,
+                                                   double &rg, double (&eps)[NF - 1], double (&alpha)[NF - 1],
+                                                   int &kk, int &s, unsigned long long &fph, double &s1) {
+    long long nb;
+    if (!dx_lpc_norm_cell<NF>(rgp, rdp, tsp, stride, dt, want_fp, rg, eps, alpha, fph, s1, nb)) return false;
     dx_select(__longlong_as_double(nb), K, kk, s);
     return true;
 }

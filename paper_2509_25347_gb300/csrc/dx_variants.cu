@@ -19,7 +19,10 @@
 //    without pivoting and two triangular solves.
 //
 // Both then take the row-sum restoration, the squaring chain and the apply of
-// the plain forward (dx_wpc.cuh).
+// the plain forward (dx_wpc.cuh). For n = 3..6 under a lane-per-cell mode
+// (the default there) the Pade variant runs one cell per lane instead
+// (dx_forward_lpc_pade): its matrices fit in registers, and a warp-per-cell
+// round at these sizes keeps few lanes busy.
 #include <cmath>
 
 #include "dx_modes.h"
@@ -268,6 +271,159 @@ dx_forward_wpc_var(VarArgs a, DxConsts K, DxPade P) {
     }
 }
 
+// ---- Pade, lane per cell (n = 3..6): the same steps as the warp-per-cell
+// variant, each on one lane's packed symmetric matrices in registers. The
+// 1-norm and the selection are the plain forward's (dx_lpc_norm_cell), so
+// (m, s) match the warp-per-cell kernel's and the oracle's bit for bit.
+constexpr int kPadeThreads = 128;
+constexpr int kPadeTile = 512;   // cells a block orders by the cost proxy and runs
+
+// R = D^-1 N for packed symmetric D (positive definite) and N: LDL^T of D in
+// place (L_ij, i > j, in the slot of (i, j); d_j on the diagonal), then the
+// two triangular solves for all n columns of N at once. R is symmetric (D and
+// N are polynomials in X); its upper triangle is taken from the solves.
+template <int NF, class MA>
+__device__ __forceinline__ void pade_lpc_solve(MA &D, MA &Nm) {
+    using Pk = DxPacked<NF>;
+    double rcp[NF];
+#pragma unroll
+    for (int j = 0; j < NF; j++) {
+        const double r = __ddiv_rn(1.0, D[Pk::at(j, j)]);
+        rcp[j] = r;
+#pragma unroll
+        for (int i = j + 1; i < NF; i++) {
+            const double lij = -D[Pk::at(i, j)] * r;
+#pragma unroll
+            for (int k = i; k < NF; k++) D[Pk::at(i, k)] = fma(lij, D[Pk::at(j, k)], D[Pk::at(i, k)]);
+        }
+#pragma unroll
+        for (int i = j + 1; i < NF; i++) D[Pk::at(i, j)] *= r;
+    }
+    double R[NF][NF];
+#pragma unroll
+    for (int i = 0; i < NF; i++) {
+#pragma unroll
+        for (int c = 0; c < NF; c++) R[i][c] = Nm[Pk::at(i, c)];
+    }
+    // L Y = N, then Z = Delta^-1 Y, then L^T R = Z
+#pragma unroll
+    for (int k = 0; k < NF - 1; k++) {
+#pragma unroll
+        for (int i = k + 1; i < NF; i++) {
+#pragma unroll
+            for (int c = 0; c < NF; c++) R[i][c] = fma(-D[Pk::at(i, k)], R[k][c], R[i][c]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NF; i++) {
+#pragma unroll
+        for (int c = 0; c < NF; c++) R[i][c] *= rcp[i];
+    }
+#pragma unroll
+    for (int k = NF - 1; k > 0; k--) {
+#pragma unroll
+        for (int i = 0; i < k; i++) {
+#pragma unroll
+            for (int c = 0; c < NF; c++) R[i][c] = fma(-D[Pk::at(k, i)], R[k][c], R[i][c]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NF; i++) {
+#pragma unroll
+        for (int c = i; c < NF; c++) Nm[Pk::at(i, c)] = R[i][c];
+    }
+}
+
+template <int NF>
+__device__ __forceinline__ void pade_lpc_cell(long long c, const VarArgs &a, const DxPade &P) {
+    constexpr int N = NF - 1;
+    constexpr int NT = DxPacked<NF>::NT;
+    using Pk = DxPacked<NF>;
+    const long long C = a.C;
+    const double dt = a.dt;
+    double *vop = a.v_out + c;
+    double rg, eps[N], alpha[N], s1;
+    unsigned long long fph;
+    long long nb;
+    if (!dx_lpc_norm_cell<NF>(a.rho_g + c, a.rho_d + c, a.t_s + c, C, dt, false, rg, eps, alpha, fph, s1, nb)) {
+        dx_lpc_fail_cell<NF>(vop, C, nullptr, a.status);
+        if (a.m_out) a.m_out[c] = 0;
+        if (a.s_out) a.s_out[c] = -1;
+        return;
+    }
+    int idx, s;
+    dx_select_pade(__longlong_as_double(nb), P, idx, s);
+    DxLaneArr<NF, false> sig, tau, xs, ds;
+    dx_lpc_arrowhead<NF>(eps, alpha, dt, s, s1, sig, tau, xs, ds, DX_EPS_FLOOR);
+    // N(X) and D(X) = N(-X) by Horner in the arrowhead X (coefficients c_j and (-1)^j c_j)
+    const int m = P.m[idx];
+    const double *cc = P.c[idx];
+    const double sm = (m & 1) ? -1.0 : 1.0;
+    DxLaneArr<NT, false> Fn, Gn, Fd, Gd;
+    dx_lpc_taylor_init<NF>(Fn, xs, ds, cc[m], cc[m - 1]);
+    dx_lpc_taylor_init<NF>(Fd, xs, ds, sm * cc[m], -sm * cc[m - 1]);
+    for (int j = m - 2; j >= 0; j--) {
+        dx_lpc_horner_step<NF>(Fn, Gn, xs, ds, cc[j]);
+        dx_lpc_horner_step<NF>(Fd, Gd, xs, ds, (j & 1) ? -cc[j] : cc[j]);
+        dx_lane_take(Fn, Gn);
+        dx_lane_take(Fd, Gd);
+    }
+    pade_lpc_solve<NF>(Fd, Fn);
+    // restoration, s squarings each restored, then the apply of the plain forward
+    dx_lpc_restore<NF>(Fn, sig, tau);
+    for (int it = 0; it < s; it++) {
+        dx_lpc_square_offdiag<NF>(Fn, Gn);
+        dx_lpc_restore<NF>(Gn, sig, tau);
+        dx_lane_take(Fn, Gn);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        double v[NF], y[NF];
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            v[f] = a.v_in[(d * NF + f) * C + c];
+            y[f] = sig[f] * v[f];
+        }
+#pragma unroll
+        for (int i = 0; i < NF; i++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < NF; k++)
+                if (k != i) acc = fma(Fn[Pk::at(i, k)], y[k], acc);
+            vop[(d * NF + i) * C] = fma(tau[i], acc, Fn[Pk::at(i, i)] * v[i]);
+        }
+    }
+    if (a.m_out) a.m_out[c] = (int8_t)m;
+    if (a.s_out) a.s_out[c] = (int16_t)s;
+}
+
+// Each block orders a tile of rounds x threads consecutive cells by the cost
+// proxy first, so that a warp's 32 cells share their degree and scaling.
+template <int NF>
+__global__ void __launch_bounds__(kPadeThreads) dx_forward_lpc_pade(VarArgs a, DxPade P, int rounds) {
+    __shared__ unsigned long long key[kPadeTile];
+    __shared__ unsigned short order[kPadeTile];
+    const long long base = (long long)blockIdx.x * rounds * kPadeThreads;
+    dx_lpc_tile_order<NF - 1>(base, rounds, kPadeThreads, a.C, a.C, a.rho_g, a.rho_d, a.t_s, a.dt, key, order);
+    for (int r = 0; r < rounds; r++) {
+        const long long c = base + order[dx_lpc_round_pos(r, kPadeThreads)];
+        if (c < a.C) pade_lpc_cell<NF>(c, a, P);
+    }
+}
+
+template <int NF>
+int launch_pade_lpc(const VarArgs &a, const DxPade &P, cudaStream_t stream) {
+    int rounds = kPadeTile / kPadeThreads;
+    while (rounds > 1 && (a.C + rounds * kPadeThreads - 1) / (rounds * kPadeThreads) < 4LL * dx_sm_count())
+        rounds >>= 1;
+    const long long blocks = (a.C + rounds * kPadeThreads - 1) / (rounds * kPadeThreads);
+    dx_forward_lpc_pade<NF><<<(unsigned)blocks, kPadeThreads, 0, stream>>>(a, P, rounds);
+    return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
+}
+
+// Matrix sizes the lane-per-cell Pade kernel takes.
+constexpr int kPadeLpcNMin = 3, kPadeLpcNMax = DX_LPC_REG_NMAX;
+
 bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
 
 }  // namespace
@@ -326,6 +482,15 @@ extern "C" int drag_expm_apply_opts(int64_t ncells, int32_t nspecies, const doub
     const int n = nspecies + 1;
     VarArgs a{ncells, nspecies, rho_g, rho_d, t_s, v_in, v_out, dt, st, m_out, s_out, opts->method,
               opts->bound_test ? 1 : 0};
+    if (opts->method == DRAG_METHOD_PADE && n >= kPadeLpcNMin && n <= kPadeLpcNMax && dx_mode_for(n) != DX_MODE_WPC) {
+        switch (n) {
+            case 3: return launch_pade_lpc<3>(a, *P, stream);
+            case 4: return launch_pade_lpc<4>(a, *P, stream);
+            case 5: return launch_pade_lpc<5>(a, *P, stream);
+            case 6: return launch_pade_lpc<6>(a, *P, stream);
+            default: break;
+        }
+    }
     const long long grid = (ncells + kCellsPerBlock - 1) / kCellsPerBlock;
     dx_forward_wpc_var<<<(unsigned)grid, kWarpsPerBlock * 32, var_smem_bytes(n), stream>>>(a, *K, *P);
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;

@@ -137,3 +137,37 @@ def test_variants_full_size_sampled(dx, kw):
     got = out[:, :, torch.from_numpy(idx).cuda()].cpu().numpy()
     assert_parity(got, ref, sub.v)
     assert dx.get_status() == 0
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+def test_pade_lane_per_cell(dx, N):
+    """N = 2..5 (n = 3..6) under their default lane-per-cell mode run the Pade
+    variant one cell per lane: (m, s) bit for bit against the warp-per-cell
+    variant and the oracle, v_out at the forward bar against both, over a few
+    tiles with a ragged tail; in place; an invalid cell."""
+    saved = dx.get_mode(N)
+    assert saved != dx.MODE_WARP_PER_CELL
+    cells = W.mrn(2 * 512 + 77, N, seed=660 + N, stiff_lo=-4.0, stiff_hi=8.0)
+    cells.t_s[0, 5] = np.nan
+    ok = np.ones(cells.ncells, dtype=bool)
+    ok[5] = False
+    out, m, s = run(dx, cells, method="pade")
+    assert dx.get_status() & dx.STATUS_BAD_CELL
+    assert np.all(np.isnan(out[:, :, 5])) and m[5] == 0 and s[5] == -1
+    dx.set_mode(N, dx.MODE_WARP_PER_CELL)
+    try:
+        outw, mw, sw = run(dx, cells, method="pade")
+    finally:
+        dx.set_mode(N, saved)
+    dx.get_status()
+    assert np.array_equal(m, mw) and np.array_equal(s, sw)
+    sub = cells.subset(np.flatnonzero(ok))
+    ref, _, mo, so, _, st = oracle.drag_apply_opts(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v, method="pade")
+    assert st == 0
+    assert np.array_equal(m[ok], mo) and np.array_equal(s[ok], so)
+    assert_parity(out[:, :, ok], ref, sub.v)
+    assert_parity(out[:, :, ok], outw[:, :, ok], sub.v)
+    rg, rd, ts, v = dev(cells)
+    dx.apply_opts(rg, rd, ts, cells.dt, v, v, method="pade")   # in place
+    dx.get_status()
+    assert np.array_equal(np.nan_to_num(v.cpu().numpy(), nan=2.0), np.nan_to_num(out, nan=2.0))
