@@ -161,10 +161,10 @@ typedef struct {
  *           evaluated per cell (Taylor: m_{k*} or fewer terms after the bound
  *           test; Pade: m); 0 for invalid cells.
  *   s_out : DEVICE int16[ncells] or NULL, receives s* (-1 for invalid cells).
- * The Pade variant runs one lane per cell for N = 2..5 under a lane-per-cell
- * mode (the default there; cells ordered by cost within tiles, 1 launch) and
- * one warp per cell otherwise; the bound test runs one warp per cell whatever
- * the mode table says; the mixed-precision path runs one lane per cell for N <= 11 under
+ * Both variants (and the plain Taylor method when m_out or s_out is asked
+ * for) run one lane per cell for N = 2..5 under a lane-per-cell mode (the
+ * default there; cells ordered by cost within tiles, 1 launch) and one warp
+ * per cell otherwise; the mixed-precision path runs one lane per cell for N <= 11 under
  * a lane-per-cell mode (the default there) and for N = 12..16 always, one warp
  * per cell otherwise.
  * Returns DRAG_ENULL (opts NULL), DRAG_EINVAL_OPTION, DRAG_EINVAL_TARGET, or as

@@ -271,12 +271,13 @@ dx_forward_wpc_var(VarArgs a, DxConsts K, DxPade P) {
     }
 }
 
-// ---- Pade, lane per cell (n = 3..6): the same steps as the warp-per-cell
-// variant, each on one lane's packed symmetric matrices in registers. The
-// 1-norm and the selection are the plain forward's (dx_lpc_norm_cell), so
-// (m, s) match the warp-per-cell kernel's and the oracle's bit for bit.
-constexpr int kPadeThreads = 128;
-constexpr int kPadeTile = 512;   // cells a block orders by the cost proxy and runs
+// ---- Both variants, lane per cell (n = 3..6): the same steps as the
+// warp-per-cell kernel, each on one lane's packed symmetric matrices in
+// registers. The 1-norm and the selection are the plain forward's
+// (dx_lpc_norm_cell), so (k*, s*) and the Pade (m, s) match the warp-per-cell
+// kernel's and the oracle's bit for bit.
+constexpr int kVarLpcThreads = 128;
+constexpr int kVarLpcTile = 512;   // cells a block orders by the cost proxy and runs
 
 // R = D^-1 N for packed symmetric D (positive definite) and N: LDL^T of D in
 // place (L_ij, i > j, in the slot of (i, j); d_j on the diagonal), then the
@@ -397,32 +398,148 @@ __device__ __forceinline__ void pade_lpc_cell(long long c, const VarArgs &a, con
     if (a.s_out) a.s_out[c] = (int16_t)s;
 }
 
+// Velocity-form 1-norm of a packed symmetric-form matrix, max_j sigma_j sum_i
+// |M_ij| tau_i (the lane-per-cell counterpart of var_norm1: the same sums in
+// the same order, the maximum taken on bit patterns).
+template <int NF, class MA, class VA>
+__device__ __forceinline__ double bound_lpc_norm1(MA &M, VA &sig, VA &tau) {
+    using Pk = DxPacked<NF>;
+    long long best = 0;
+#pragma unroll
+    for (int j = 0; j < NF; j++) {
+        double col = 0.0;
+#pragma unroll
+        for (int i = 0; i < NF; i++) col = fma(fabs(M[Pk::at(i, j)]), tau[i], col);
+        col *= sig[j];
+        const long long b = dx_bits(col);
+        best = b > best ? b : best;
+    }
+    return __longlong_as_double(best);
+}
+
+// B = c[0] I + sum_{j=1}^{q} c[j] X^j by Horner in the arrowhead X (the
+// warp-per-cell variant forms the powers first; the sums differ in rounding
+// only).
+template <int NF, class MA, class VA>
+__device__ __forceinline__ void bound_lpc_block(MA &F, MA &G, VA &xs, VA &ds, int q, const double *c) {
+    dx_lpc_taylor_init<NF>(F, xs, ds, c[q], c[q - 1]);
+    for (int j = q - 2; j >= 0; j--) {
+        dx_lpc_horner_step<NF>(F, G, xs, ds, c[j]);
+        dx_lane_take(F, G);
+    }
+}
+
+// The second modification (Algorithms 8 and 9) on one lane: blocks of the
+// Taylor sum to keep (>= 1), as var_bound_test decides it.
+template <int NF, class MA, class VA>
+__device__ __forceinline__ int bound_lpc_keep(MA &F, MA &G, VA &sig, VA &tau, VA &xs, VA &ds, const double *bsh,
+                                              double u, int q, int r) {
+    double c[6];
+    // |X^q|
+#pragma unroll
+    for (int j = 0; j < 6; j++) c[j] = 0.0;
+    c[q] = 1.0;
+    bound_lpc_block<NF>(F, G, xs, ds, q, c);
+    const double xq = bound_lpc_norm1<NF>(F, sig, tau);
+    double bexp = 0.0, xql = 1.0;
+    for (int l = 0; l < r; l++) {
+        c[0] = l == 0 ? bsh[0] : 0.0;
+        for (int j = 1; j <= q; j++) c[j] = ((q * l + j) & 1) ? -bsh[q * l + j] : bsh[q * l + j];
+        bound_lpc_block<NF>(F, G, xs, ds, q, c);
+        bexp = fma(bound_lpc_norm1<NF>(F, sig, tau), xql, bexp);
+        xql *= xq;
+    }
+    int keep = r;
+    while (keep > 1) {
+        const int l = keep - 1;
+        c[0] = 0.0;
+        for (int j = 1; j <= q; j++) c[j] = bsh[q * l + j];
+        bound_lpc_block<NF>(F, G, xs, ds, q, c);
+        double val = bexp * bound_lpc_norm1<NF>(F, sig, tau);
+        for (int t = 0; t < l; t++) val *= xq;
+        if (!(val <= u)) break;
+        keep--;
+    }
+    return keep;
+}
+
+template <int NF>
+__device__ __forceinline__ void bound_lpc_cell(long long c, const VarArgs &a, const DxConsts &K, const double *bsh) {
+    constexpr int N = NF - 1;
+    constexpr int NT = DxPacked<NF>::NT;
+    using Pk = DxPacked<NF>;
+    const long long C = a.C;
+    const double dt = a.dt;
+    double *vop = a.v_out + c;
+    DxLaneArr<NF, false> sig, tau, xs, ds;
+    double rg, eps[N], alpha[N];
+    int kk, s;
+    unsigned long long fph;
+    if (!dx_lpc_setup<NF>(a.rho_g + c, a.rho_d + c, a.t_s + c, C, dt, K, false, rg, eps, alpha, kk, s, fph, sig, tau,
+                          xs, ds)) {
+        dx_lpc_fail_cell<NF>(vop, C, nullptr, a.status);
+        if (a.m_out) a.m_out[c] = 0;
+        if (a.s_out) a.s_out[c] = -1;
+        return;
+    }
+    DxLaneArr<NT, false> Fm, Gm;
+    // Taylor of degree m_{k*}, or q_{k*} times the blocks the bound test keeps
+    const int q = K.qk[kk];
+    const int m = a.bound_test ? q * bound_lpc_keep<NF>(Fm, Gm, sig, tau, xs, ds, bsh, K.u, q, K.rk[kk]) : K.mk[kk];
+    dx_lpc_chain<NF>(Fm, Gm, sig, tau, xs, ds, m, s, bsh, nullptr, 0, 0);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        double v[NF], y[NF];
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            v[f] = a.v_in[(d * NF + f) * C + c];
+            y[f] = sig[f] * v[f];
+        }
+#pragma unroll
+        for (int i = 0; i < NF; i++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < NF; k++)
+                if (k != i) acc = fma(Fm[Pk::at(i, k)], y[k], acc);
+            vop[(d * NF + i) * C] = fma(tau[i], acc, Fm[Pk::at(i, i)] * v[i]);
+        }
+    }
+    if (a.m_out) a.m_out[c] = (int8_t)m;
+    if (a.s_out) a.s_out[c] = (int16_t)s;
+}
+
 // Each block orders a tile of rounds x threads consecutive cells by the cost
 // proxy first, so that a warp's 32 cells share their degree and scaling.
 template <int NF>
-__global__ void __launch_bounds__(kPadeThreads) dx_forward_lpc_pade(VarArgs a, DxPade P, int rounds) {
-    __shared__ unsigned long long key[kPadeTile];
-    __shared__ unsigned short order[kPadeTile];
-    const long long base = (long long)blockIdx.x * rounds * kPadeThreads;
-    dx_lpc_tile_order<NF - 1>(base, rounds, kPadeThreads, a.C, a.C, a.rho_g, a.rho_d, a.t_s, a.dt, key, order);
+__global__ void __launch_bounds__(kVarLpcThreads) dx_forward_lpc_var(VarArgs a, DxConsts K, DxPade P, int rounds) {
+    __shared__ unsigned long long key[kVarLpcTile];
+    __shared__ unsigned short order[kVarLpcTile];
+    __shared__ double bsh[32];
+    for (int t = threadIdx.x; t < 32; t += blockDim.x) bsh[t] = K.b[t];
+    const long long base = (long long)blockIdx.x * rounds * kVarLpcThreads;
+    dx_lpc_tile_order<NF - 1>(base, rounds, kVarLpcThreads, a.C, a.C, a.rho_g, a.rho_d, a.t_s, a.dt, key, order);
     for (int r = 0; r < rounds; r++) {
-        const long long c = base + order[dx_lpc_round_pos(r, kPadeThreads)];
-        if (c < a.C) pade_lpc_cell<NF>(c, a, P);
+        const long long c = base + order[dx_lpc_round_pos(r, kVarLpcThreads)];
+        if (c >= a.C) continue;
+        if (a.method == DRAG_METHOD_PADE)
+            pade_lpc_cell<NF>(c, a, P);
+        else
+            bound_lpc_cell<NF>(c, a, K, bsh);
     }
 }
 
 template <int NF>
-int launch_pade_lpc(const VarArgs &a, const DxPade &P, cudaStream_t stream) {
-    int rounds = kPadeTile / kPadeThreads;
-    while (rounds > 1 && (a.C + rounds * kPadeThreads - 1) / (rounds * kPadeThreads) < 4LL * dx_sm_count())
+int launch_var_lpc(const VarArgs &a, const DxConsts &K, const DxPade &P, cudaStream_t stream) {
+    int rounds = kVarLpcTile / kVarLpcThreads;
+    while (rounds > 1 && (a.C + rounds * kVarLpcThreads - 1) / (rounds * kVarLpcThreads) < 4LL * dx_sm_count())
         rounds >>= 1;
-    const long long blocks = (a.C + rounds * kPadeThreads - 1) / (rounds * kPadeThreads);
-    dx_forward_lpc_pade<NF><<<(unsigned)blocks, kPadeThreads, 0, stream>>>(a, P, rounds);
+    const long long blocks = (a.C + rounds * kVarLpcThreads - 1) / (rounds * kVarLpcThreads);
+    dx_forward_lpc_var<NF><<<(unsigned)blocks, kVarLpcThreads, 0, stream>>>(a, K, P, rounds);
     return cudaGetLastError() == cudaSuccess ? DRAG_OK : DRAG_ECUDA;
 }
 
-// Matrix sizes the lane-per-cell Pade kernel takes.
-constexpr int kPadeLpcNMin = 3, kPadeLpcNMax = DX_LPC_REG_NMAX;
+// Matrix sizes the lane-per-cell variant kernel takes.
+constexpr int kVarLpcNMin = 3, kVarLpcNMax = DX_LPC_REG_NMAX;
 
 bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
 
@@ -482,12 +599,12 @@ extern "C" int drag_expm_apply_opts(int64_t ncells, int32_t nspecies, const doub
     const int n = nspecies + 1;
     VarArgs a{ncells, nspecies, rho_g, rho_d, t_s, v_in, v_out, dt, st, m_out, s_out, opts->method,
               opts->bound_test ? 1 : 0};
-    if (opts->method == DRAG_METHOD_PADE && n >= kPadeLpcNMin && n <= kPadeLpcNMax && dx_mode_for(n) != DX_MODE_WPC) {
+    if (n >= kVarLpcNMin && n <= kVarLpcNMax && dx_mode_for(n) != DX_MODE_WPC) {
         switch (n) {
-            case 3: return launch_pade_lpc<3>(a, *P, stream);
-            case 4: return launch_pade_lpc<4>(a, *P, stream);
-            case 5: return launch_pade_lpc<5>(a, *P, stream);
-            case 6: return launch_pade_lpc<6>(a, *P, stream);
+            case 3: return launch_var_lpc<3>(a, *K, *P, stream);
+            case 4: return launch_var_lpc<4>(a, *K, *P, stream);
+            case 5: return launch_var_lpc<5>(a, *K, *P, stream);
+            case 6: return launch_var_lpc<6>(a, *K, *P, stream);
             default: break;
         }
     }

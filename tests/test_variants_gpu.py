@@ -139,35 +139,58 @@ def test_variants_full_size_sampled(dx, kw):
     assert dx.get_status() == 0
 
 
+@pytest.mark.parametrize("kw", [{"method": "pade"}, {"bound_test": True}, {"bound_test": True, "ubits": 24}])
 @pytest.mark.parametrize("N", [2, 3, 4, 5])
-def test_pade_lane_per_cell(dx, N):
-    """N = 2..5 (n = 3..6) under their default lane-per-cell mode run the Pade
-    variant one cell per lane: (m, s) bit for bit against the warp-per-cell
-    variant and the oracle, v_out at the forward bar against both, over a few
-    tiles with a ragged tail; in place; an invalid cell."""
+def test_variants_lane_per_cell(dx, N, kw):
+    """N = 2..5 (n = 3..6) under their default lane-per-cell mode run both
+    variants one cell per lane: the selection bit for bit against the
+    warp-per-cell variant and the oracle (the bound test's kept degree up to
+    its documented 1e-9 band around u), v_out at the forward bar against both,
+    over a few tiles with a ragged tail; in place; an invalid cell."""
     saved = dx.get_mode(N)
     assert saved != dx.MODE_WARP_PER_CELL
     cells = W.mrn(2 * 512 + 77, N, seed=660 + N, stiff_lo=-4.0, stiff_hi=8.0)
     cells.t_s[0, 5] = np.nan
     ok = np.ones(cells.ncells, dtype=bool)
     ok[5] = False
-    out, m, s = run(dx, cells, method="pade")
+    out, m, s = run(dx, cells, **kw)
     assert dx.get_status() & dx.STATUS_BAD_CELL
     assert np.all(np.isnan(out[:, :, 5])) and m[5] == 0 and s[5] == -1
     dx.set_mode(N, dx.MODE_WARP_PER_CELL)
     try:
-        outw, mw, sw = run(dx, cells, method="pade")
+        outw, mw, sw = run(dx, cells, **kw)
     finally:
         dx.set_mode(N, saved)
     dx.get_status()
-    assert np.array_equal(m, mw) and np.array_equal(s, sw)
     sub = cells.subset(np.flatnonzero(ok))
-    ref, _, mo, so, _, st = oracle.drag_apply_opts(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v, method="pade")
+    okw = {"u": 2.0 ** -kw.get("ubits", 53)}
+    okw.update({k: v for k, v in kw.items() if k != "ubits"})
+    ref, _, mo, so, ratio, st = oracle.drag_apply_opts(sub.rho_g, sub.rho_d, sub.t_s, sub.dt, sub.v, **okw)
     assert st == 0
-    assert np.array_equal(m[ok], mo) and np.array_equal(s[ok], so)
+    assert np.array_equal(s, sw) and np.array_equal(s[ok], so)
+    if kw.get("method") == "pade":
+        assert np.array_equal(m, mw) and np.array_equal(m[ok], mo)
+    else:
+        assert np.all((m[ok] == mo) | (np.abs(ratio - 1.0) < 1e-9))
+        assert np.all((m[ok] == mw[ok]) | (np.abs(ratio - 1.0) < 1e-9))
     assert_parity(out[:, :, ok], ref, sub.v)
     assert_parity(out[:, :, ok], outw[:, :, ok], sub.v)
     rg, rd, ts, v = dev(cells)
-    dx.apply_opts(rg, rd, ts, cells.dt, v, v, method="pade")   # in place
+    dx.apply_opts(rg, rd, ts, cells.dt, v, v, **kw)   # in place
     dx.get_status()
     assert np.array_equal(np.nan_to_num(v.cpu().numpy(), nan=2.0), np.nan_to_num(out, nan=2.0))
+
+
+def test_plain_taylor_through_opts_lane_per_cell(dx):
+    """Asking for the degrees at N = 4 runs the lane-per-cell variant kernel
+    with the bound test off: the plain forward's numbers bit for bit (the same
+    per-cell chain and apply)."""
+    cells = W.workload("mrn_n4_128cube", ncells=3001)
+    rg, rd, ts, v = dev(cells)
+    a = dx.apply(rg, rd, ts, cells.dt, v).cpu().numpy()
+    out, m, s = run(dx, cells)
+    assert np.array_equal(a, out)
+    _, ko, so, _ = oracle.drag_apply(cells.rho_g, cells.rho_d, cells.t_s, cells.dt, cells.v, return_ks=True)
+    assert np.array_equal(s, so)
+    assert np.array_equal(m, np.array([oracle.table_b1(int(k))[0] for k in ko]))
+    assert dx.get_status() == 0
