@@ -636,8 +636,19 @@ def leg_single(dx, args, name, rank, world, stream, peak, hbm_peak, local, steps
             holder[0] = None
             if dx.get_status():
                 raise RuntimeError(f"device status set after the {name} taped forward + adjoint")
+    # the paper's variants at N = 4 (lane per cell there, one launch each), outside the timed region
+    var_ms = {}
+    if name == "mrn_n4_128cube":
+        for vname, kw in (("pade", {"method": "pade"}), ("taylor_bound_test", {"bound_test": True})):
+            run_var = (lambda kw=kw: dx.apply_opts(rg, rd, ts, cells.dt, v, vout, stream=stream, **kw))
+            with torch.cuda.stream(stream):
+                run_var()
+                torch.cuda.synchronize()
+                var_ms[vname] = float(np.mean(time_steps(run_var, max(3, min(steps, 5)), stream, flush)))
+        if dx.get_status():
+            raise RuntimeError(f"device status set after the {name} variants")
     mean_ms = float(np.mean(per))
-    vals = [float(np.sum(per)), mean_ms] + ([fb_ms, ft_ms or 0.0] if adjoint else [])
+    vals = [float(np.sum(per)), mean_ms] + ([fb_ms, ft_ms or 0.0] if adjoint else []) + list(var_ms.values())
     red = max_over_ranks(vals, world, device="cuda")
     ms_step = red[0] / steps
     entry = {
@@ -662,6 +673,13 @@ def leg_single(dx, args, name, rank, world, stream, peak, hbm_peak, local, steps
                 "value": total / (red[3] * 1e-3), "unit": UNIT, "ms_per_step": red[3],
                 "adjoint_over_forward_time": red[3] / ms_step, "tape_levels": levels, "tape_bytes": tape_nbytes,
                 "note": "drag_expm_apply_taped + dL/dv_out (torch sub) + drag_expm_backward_taped, CUDA events"}
+    if var_ms:
+        red_var = red[2 + (2 if adjoint else 0):]
+        entry["variants"] = {
+            "note": "drag_expm_apply_opts: the Pade variant (Eq. PadeEqu) and the paper's second modification "
+                    "(bound test), one cell per lane at this N; outside the timed region",
+            **{vn: {"value": total / (t * 1e-3), "unit": UNIT, "ms_per_step": t}
+               for vn, t in zip(var_ms.keys(), red_var)}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         entry["cpu_baseline"] = cpu_baseline_entry(cells, name, cpu_seconds, adjoint=adjoint)
     return entry, (cells, rg, rd, ts, v, vout, k, s, per, total)
@@ -1014,7 +1032,7 @@ def run_ours(args, rank, world):
         line["config"]["partition"] = ("contiguous cell ranges / cost-balanced whole blocks over ranks"
                                        if scaling == "strong" else
                                        "each rank its own independent draw of the workload")
-        for k_ in ("fwd_adjoint", "fwd_adjoint_taped", "plain_per_block", "cpu_baseline"):
+        for k_ in ("fwd_adjoint", "fwd_adjoint_taped", "plain_per_block", "cpu_baseline", "variants"):
             if k_ in head and k_ not in line:
                 line[k_] = head[k_]
         if "e2e" not in line:
