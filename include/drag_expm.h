@@ -162,7 +162,7 @@ typedef struct {
  *           test; Pade: m); 0 for invalid cells.
  *   s_out : DEVICE int16[ncells] or NULL, receives s* (-1 for invalid cells).
  * Both variants (and the plain Taylor method when m_out or s_out is asked
- * for) run one lane per cell for N = 2..5 under a lane-per-cell mode (the
+ * for) run one lane per cell for N = 1..5 under a lane-per-cell mode (the
  * default there; cells ordered by cost within tiles, 1 launch) and one warp
  * per cell otherwise; the mixed-precision path runs one lane per cell for N <= 11 under
  * a lane-per-cell mode (the default there) and for N = 12..16 always, one warp

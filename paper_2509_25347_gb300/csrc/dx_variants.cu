@@ -19,9 +19,9 @@
 //    without pivoting and two triangular solves.
 //
 // Both then take the row-sum restoration, the squaring chain and the apply of
-// the plain forward (dx_wpc.cuh). For n = 3..6 under a lane-per-cell mode
-// (the default there) the Pade variant runs one cell per lane instead
-// (dx_forward_lpc_pade): its matrices fit in registers, and a warp-per-cell
+// the plain forward (dx_wpc.cuh). For n = 2..6 under a lane-per-cell mode
+// (the default there) both variants run one cell per lane instead
+// (dx_forward_lpc_var): their matrices fit in registers, and a warp-per-cell
 // round at these sizes keeps few lanes busy.
 #include <cmath>
 
@@ -271,7 +271,7 @@ dx_forward_wpc_var(VarArgs a, DxConsts K, DxPade P) {
     }
 }
 
-// ---- Both variants, lane per cell (n = 3..6): the same steps as the
+// ---- Both variants, lane per cell (n = 2..6): the same steps as the
 // warp-per-cell kernel, each on one lane's packed symmetric matrices in
 // registers. The 1-norm and the selection are the plain forward's
 // (dx_lpc_norm_cell), so (k*, s*) and the Pade (m, s) match the warp-per-cell
@@ -508,6 +508,104 @@ __device__ __forceinline__ void bound_lpc_cell(long long c, const VarArgs &a, co
     if (a.s_out) a.s_out[c] = (int16_t)s;
 }
 
+// n = 2 (one dust species) in the velocity form of the plain forward
+// (dx_lpc2_forward_cell): every polynomial in X is c_0 I + beta X, since
+// X^2 = tr(X) X with tr(X) = -(x + y). Pade: N(X) = c_0 I + b_N X and
+// D(X) = N(-X) = c_0 I + b_D X give R = D^-1 N = I + (b_N - b_D) / (c_0 + b_D tr) X
+// (c_0 + b_D tr = N(-tr) >= c_0 > 0). Bound test: a block c_0 I + beta X has the
+// velocity-form 1-norm max(|c_0 - beta x| + |beta y|, |beta x| + |c_0 - beta y|),
+// and |X^q| = |tr|^(q-1) (x + y).
+__device__ __forceinline__ double var2_block_norm(double c0, const double *c, int q, double tr, double x, double y) {
+    double beta = c[q];
+    for (int j = q - 1; j >= 1; j--) beta = fma(tr, beta, c[j]);
+    const double bx = beta * x, by = beta * y;
+    const double n0 = fabs(c0 - bx) + fabs(by), n1 = fabs(bx) + fabs(c0 - by);
+    const long long b0 = dx_bits(n0), b1 = dx_bits(n1);
+    return __longlong_as_double(b0 > b1 ? b0 : b1);
+}
+
+__device__ __forceinline__ int var2_bound_keep(double tr, double x, double y, const double *bsh, double u, int q,
+                                               int r) {
+    double xq = x + y;
+    for (int j = 1; j < q; j++) xq *= -tr;
+    double c[6];
+    double bexp = 0.0, xql = 1.0;
+    for (int l = 0; l < r; l++) {
+        for (int j = 1; j <= q; j++) c[j] = ((q * l + j) & 1) ? -bsh[q * l + j] : bsh[q * l + j];
+        bexp = fma(var2_block_norm(l == 0 ? bsh[0] : 0.0, c, q, tr, x, y), xql, bexp);
+        xql *= xq;
+    }
+    int keep = r;
+    while (keep > 1) {
+        const int l = keep - 1;
+        for (int j = 1; j <= q; j++) c[j] = bsh[q * l + j];
+        double val = bexp * var2_block_norm(0.0, c, q, tr, x, y);
+        for (int t = 0; t < l; t++) val *= xq;
+        if (!(val <= u)) break;
+        keep--;
+    }
+    return keep;
+}
+
+__device__ __forceinline__ void var2_lpc_cell(long long c, const VarArgs &a, const DxConsts &K, const DxPade &P,
+                                              const double *bsh) {
+    const long long C = a.C;
+    const double dt = a.dt;
+    double *vop = a.v_out + c;
+    double rg, eps[1], alpha[1], s1;
+    unsigned long long fph;
+    long long nb;
+    if (!dx_lpc_norm_cell<2>(a.rho_g + c, a.rho_d + c, a.t_s + c, C, dt, false, rg, eps, alpha, fph, s1, nb)) {
+        dx_lpc_fail_cell<2>(vop, C, nullptr, a.status);
+        if (a.m_out) a.m_out[c] = 0;
+        if (a.s_out) a.s_out[c] = -1;
+        return;
+    }
+    int s, deg;
+    double b;
+    double x, y;
+    if (a.method == DRAG_METHOD_PADE) {
+        int idx;
+        dx_select_pade(__longlong_as_double(nb), P, idx, s);
+        x = dx_scale2(s1, s);
+        y = dx_scale2(__dmul_rn(alpha[0], dt), s);
+        const double tr = -(x + y);
+        deg = P.m[idx];
+        const double *cc = P.c[idx];
+        double bn = cc[deg], bd = (deg & 1) ? -cc[deg] : cc[deg];
+        for (int j = deg - 1; j >= 1; j--) {
+            bn = fma(tr, bn, cc[j]);
+            bd = fma(tr, bd, (j & 1) ? -cc[j] : cc[j]);
+        }
+        b = __ddiv_rn(bn - bd, fma(bd, tr, cc[0]));
+    } else {
+        int kk;
+        dx_select(__longlong_as_double(nb), K, kk, s);
+        x = dx_scale2(s1, s);
+        y = dx_scale2(__dmul_rn(alpha[0], dt), s);
+        const double tr = -(x + y);
+        deg = a.bound_test ? K.qk[kk] * var2_bound_keep(tr, x, y, bsh, K.u, K.qk[kk], K.rk[kk]) : K.mk[kk];
+        b = bsh[deg];
+        for (int k = deg - 1; k >= 1; k--) b = fma(tr, b, bsh[k]);
+    }
+    // P = I + b X as the pair (p, q); squarings and the apply of the plain forward
+    double p = b * x, q = b * y;
+    for (int it = 0; it < s; it++) {
+        const double w = 2.0 - (p + q);
+        p *= w;
+        q *= w;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const double v0 = a.v_in[(2 * d) * C + c], v1 = a.v_in[(2 * d + 1) * C + c];
+        const double dv = v1 - v0;
+        vop[(2 * d) * C] = fma(p, dv, v0);
+        vop[(2 * d + 1) * C] = fma(-q, dv, v1);
+    }
+    if (a.m_out) a.m_out[c] = (int8_t)deg;
+    if (a.s_out) a.s_out[c] = (int16_t)s;
+}
+
 // Each block orders a tile of rounds x threads consecutive cells by the cost
 // proxy first, so that a warp's 32 cells share their degree and scaling.
 template <int NF>
@@ -521,7 +619,9 @@ __global__ void __launch_bounds__(kVarLpcThreads) dx_forward_lpc_var(VarArgs a, 
     for (int r = 0; r < rounds; r++) {
         const long long c = base + order[dx_lpc_round_pos(r, kVarLpcThreads)];
         if (c >= a.C) continue;
-        if (a.method == DRAG_METHOD_PADE)
+        if constexpr (NF == 2)
+            var2_lpc_cell(c, a, K, P, bsh);
+        else if (a.method == DRAG_METHOD_PADE)
             pade_lpc_cell<NF>(c, a, P);
         else
             bound_lpc_cell<NF>(c, a, K, bsh);
@@ -539,7 +639,7 @@ int launch_var_lpc(const VarArgs &a, const DxConsts &K, const DxPade &P, cudaStr
 }
 
 // Matrix sizes the lane-per-cell variant kernel takes.
-constexpr int kVarLpcNMin = 3, kVarLpcNMax = DX_LPC_REG_NMAX;
+constexpr int kVarLpcNMin = 2, kVarLpcNMax = DX_LPC_REG_NMAX;
 
 bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
 
@@ -601,6 +701,7 @@ extern "C" int drag_expm_apply_opts(int64_t ncells, int32_t nspecies, const doub
               opts->bound_test ? 1 : 0};
     if (n >= kVarLpcNMin && n <= kVarLpcNMax && dx_mode_for(n) != DX_MODE_WPC) {
         switch (n) {
+            case 2: return launch_var_lpc<2>(a, *K, *P, stream);
             case 3: return launch_var_lpc<3>(a, *K, *P, stream);
             case 4: return launch_var_lpc<4>(a, *K, *P, stream);
             case 5: return launch_var_lpc<5>(a, *K, *P, stream);

@@ -140,10 +140,11 @@ def test_variants_full_size_sampled(dx, kw):
 
 
 @pytest.mark.parametrize("kw", [{"method": "pade"}, {"bound_test": True}, {"bound_test": True, "ubits": 24}])
-@pytest.mark.parametrize("N", [2, 3, 4, 5])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
 def test_variants_lane_per_cell(dx, N, kw):
-    """N = 2..5 (n = 3..6) under their default lane-per-cell mode run both
-    variants one cell per lane: the selection bit for bit against the
+    """N = 1..5 (n = 2..6) under their default lane-per-cell mode run both
+    variants one cell per lane (N = 1 in the velocity form, as the plain
+    forward): the selection bit for bit against the
     warp-per-cell variant and the oracle (the bound test's kept degree up to
     its documented 1e-9 band around u), v_out at the forward bar against both,
     over a few tiles with a ragged tail; in place; an invalid cell."""
@@ -181,11 +182,12 @@ def test_variants_lane_per_cell(dx, N, kw):
     assert np.array_equal(np.nan_to_num(v.cpu().numpy(), nan=2.0), np.nan_to_num(out, nan=2.0))
 
 
-def test_plain_taylor_through_opts_lane_per_cell(dx):
-    """Asking for the degrees at N = 4 runs the lane-per-cell variant kernel
-    with the bound test off: the plain forward's numbers bit for bit (the same
-    per-cell chain and apply)."""
-    cells = W.workload("mrn_n4_128cube", ncells=3001)
+@pytest.mark.parametrize("name", ["dustybox_n1_32k", "mrn_n4_128cube"])
+def test_plain_taylor_through_opts_lane_per_cell(dx, name):
+    """Asking for the degrees at N = 1 or 4 runs the lane-per-cell variant
+    kernel with the bound test off: the plain forward's numbers bit for bit
+    (the same per-cell chain and apply)."""
+    cells = W.workload(name, ncells=3001)
     rg, rd, ts, v = dev(cells)
     a = dx.apply(rg, rd, ts, cells.dt, v).cpu().numpy()
     out, m, s = run(dx, cells)
